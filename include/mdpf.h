@@ -1,0 +1,265 @@
+/*
+ * mdpf.h -- C ABI of the B300 MD force provider.
+ *
+ * The contract is the force provider of arXiv 2412.18271 ("OpenMM-Python-
+ * Force"): the MD engine hands the provider the current positions, the
+ * provider returns the potential energy and the forces, and the engine then
+ * advances the state (Methods section: the callable registered with the force
+ * object returns an energy, and forces are obtained by differentiating it when
+ * they are not returned explicitly; Results section, "Example: Ethanol": NVE
+ * velocity-Verlet runs on the forces so obtained).  Here the provider and the
+ * integrator both run as CUDA kernels on one GPU behind this ABI:
+ *
+ *   mdpf_create(topology, params)            build a context (device buffers, exclusions)
+ *   mdpf_compute(ctx, positions, &E, forces) one energy/force evaluation   (host buffers)
+ *   mdpf_step(ctx, n_steps)                  n velocity-Verlet steps, entirely on the device
+ *
+ * Units: A, fs, amu, e, kcal/mol.  Forces are -dE/dx in kcal/mol/A.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: MDPF_OK (0) or a negative MDPF_ERR_* code.  Nothing aborts
+ *    or exits the process.  mdpf_last_error() gives a message for the last
+ *    failure on a context.
+ *  - A CUDA error is sticky: once a context reports MDPF_ERR_CUDA every later
+ *    call on it returns MDPF_ERR_CUDA; destroy it.
+ *  - Inputs are copied; the caller keeps ownership of every pointer it passes.
+ *    Host output buffers are caller-owned and must hold the stated sizes.
+ *  - A context is not thread-safe; calls on one context must be serialised.
+ *  - Array layouts are C row-major: "[N,3]" means x0 y0 z0 x1 y1 z1 ...
+ */
+#ifndef MDPF_H
+#define MDPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MDPF_API __attribute__((visibility("default")))
+#else
+#define MDPF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDPF_OK 0
+#define MDPF_ERR_INVALID_ARG (-1)       /* bad pointer, size or value; nothing was changed */
+#define MDPF_ERR_CUDA (-2)              /* CUDA runtime error; sticky */
+#define MDPF_ERR_OOM (-3)               /* device allocation failed */
+#define MDPF_ERR_NEIGHBOR_OVERFLOW (-4) /* a neighbour or exclusion list exceeded its capacity */
+#define MDPF_ERR_NONFINITE (-5)         /* energy or state became NaN/Inf */
+#define MDPF_ERR_TIMEOUT (-6)           /* a bounded device-side wait gave up */
+#define MDPF_ERR_OUT_OF_RANGE (-7)      /* learned features left the training range and fallback is off */
+#define MDPF_ERR_UNSUPPORTED (-8)       /* feature not available in this build or mode */
+
+/* device status-word bits (mdpf_counters.status), one per failure kind */
+#define MDPF_STATUS_NONFINITE 0x1u
+#define MDPF_STATUS_NEIGHBOR_OVERFLOW 0x2u
+#define MDPF_STATUS_TIMEOUT 0x4u
+#define MDPF_STATUS_OUT_OF_RANGE 0x8u
+
+#define MDPF_MODE_PLAIN 0   /* analytic bonded + all-pairs LJ + Coulomb */
+#define MDPF_MODE_LEARNED 1 /* symmetry-function features + per-element MLP */
+
+typedef struct mdpf_ctx mdpf_ctx;
+
+/*
+ * Topology and force-field parameters of a gas-phase system (no periodic
+ * images, no cutoff on the plain nonbonded sum).  Copied by mdpf_create.
+ *   element   [N]        0=H 1=C 2=N 3=O
+ *   mass      [N]        amu (> 0)
+ *   charge    [N]        e
+ *   bonds     [n_bonds,2] atom indices, each pair distinct and in [0,N)
+ *   bond_r0   [n_bonds]  A;   bond energy k/2 (r - r0)^2
+ *   bond_k    [n_bonds]  kcal/mol/A^2
+ *   angle_k, angle_theta0_deg: one harmonic angle k/2 (theta - theta0)^2 per
+ *             pair of bonds sharing an atom (derived from the bond graph)
+ *   lj_sigma, lj_eps [4] per element; pairs mix by Lorentz-Berthelot
+ *             (sigma_ij = (sigma_i + sigma_j)/2, eps_ij = sqrt(eps_i eps_j)).
+ * Pairs that are bonded (1-2) or share a bonded neighbour (1-3) are excluded
+ * from the LJ + Coulomb sum; 1-4 and farther pairs are included unscaled.
+ */
+typedef struct mdpf_topology {
+    int32_t n_atoms;
+    const int32_t *element;
+    const double *mass;
+    const double *charge;
+    int32_t n_bonds;
+    const int32_t *bonds;
+    const double *bond_r0;
+    const double *bond_k;
+    double angle_k;
+    double angle_theta0_deg;
+    double lj_sigma[4];
+    double lj_eps[4];
+} mdpf_topology;
+
+/*
+ * Run parameters.  Zero-initialise and set what you need; zeros select the
+ * documented defaults.
+ *   mode          MDPF_MODE_PLAIN or MDPF_MODE_LEARNED
+ *   dt_fs         velocity-Verlet time step in fs (> 0)
+ *   coulomb_k     Coulomb constant in kcal A/(mol e^2); 0 selects 332.06371
+ *   trace_capacity  energy trace ring length (0 selects 4096)
+ *   record_every  store a frame (positions, energy, forces) every this many
+ *                 steps into a device ring of max_frames entries (0 = off)
+ *   stepper       MDPF_STEPPER_PERSISTENT (0): mdpf_step runs as one resident
+ *                 cooperative kernel with bounded grid barriers;
+ *                 MDPF_STEPPER_KERNELS (1): one kernel sequence per step.
+ *                 Both give the same trajectory up to FP32 summation order.
+ *   energy_every  evaluate U and K every this many steps (0 selects 1); the
+ *                 trace holds one entry per such step; record_every must be a
+ *                 multiple of it.  Forces are evaluated every step regardless.
+ */
+#define MDPF_STEPPER_PERSISTENT 0
+#define MDPF_STEPPER_KERNELS 1
+typedef struct mdpf_params {
+    int32_t mode;
+    double dt_fs;
+    double coulomb_k;
+    int32_t trace_capacity;
+    int32_t record_every;
+    int32_t max_frames;
+    int32_t stepper;
+    int32_t energy_every;
+} mdpf_params;
+
+/* Counters and diagnostics of a context. */
+typedef struct mdpf_counters {
+    int64_t steps;          /* velocity-Verlet steps taken since create / set_state */
+    int64_t force_evals;    /* force evaluations by mdpf_step */
+    int64_t frames;         /* frames recorded so far (ring holds the last max_frames) */
+    uint32_t status;        /* MDPF_STATUS_* bits seen on the device */
+    uint32_t reserved;
+    double potential;       /* U at the last energy step, kcal/mol */
+    double kinetic;         /* K at the last energy step, kcal/mol */
+    double h_initial;       /* U + K right after the last set_state */
+} mdpf_counters;
+
+/*
+ * Build a context on the current CUDA device.  Copies the topology, derives
+ * angles and the 1-2/1-3 exclusion set on the device, allocates every buffer
+ * the path needs (the context owns them until mdpf_destroy).
+ * Errors: INVALID_ARG (N < 1, bad index, non-positive mass or dt, unknown
+ * mode or stepper), OOM, CUDA, NEIGHBOR_OVERFLOW (an atom with more than 255
+ * excluded partners), UNSUPPORTED (cooperative launch unavailable for the
+ * persistent stepper).  On error *out is NULL.
+ */
+MDPF_API int mdpf_create(const mdpf_topology *topology, const mdpf_params *params, mdpf_ctx **out);
+
+/* Free every device buffer and the context.  NULL is ignored. */
+MDPF_API void mdpf_destroy(mdpf_ctx *ctx);
+
+/* Message for the last failure on ctx (or of the last failed mdpf_create when ctx is NULL). */
+MDPF_API const char *mdpf_last_error(const mdpf_ctx *ctx);
+
+/* Number of atoms, and the number of angles derived from the bond graph. */
+MDPF_API int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles);
+
+/*
+ * One energy/force evaluation at host positions pos [N,3] (A, FP64).  Writes
+ * the potential energy (FP64, kcal/mol) to *energy and forces [N,3]
+ * (kcal/mol/A) to the host buffer forces; either output may be NULL.  Does
+ * not change the integrator state.  terms (may be NULL) receives the four
+ * components {bond, angle, LJ, Coulomb}.  Synchronous.
+ */
+MDPF_API int mdpf_compute(mdpf_ctx *ctx, const double *pos, double *energy, double *forces, double *terms);
+
+/*
+ * Device-pointer form of mdpf_compute: d_pos [N,3] FP64 device positions,
+ * d_energy one FP64 device scalar, d_forces [N,3] FP32 device forces, all
+ * enqueued on cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * Asynchronous: results are valid once the stream reaches this point.
+ */
+MDPF_API int mdpf_compute_device(mdpf_ctx *ctx, const double *d_pos, double *d_energy, float *d_forces,
+                                 void *cuda_stream);
+
+/*
+ * Set the integrator state from host buffers pos [N,3] (A) and vel [N,3]
+ * (A/fs), FP64.  Evaluates forces at pos, resets the step counter, the energy
+ * trace and the status word, and records h_initial.
+ */
+MDPF_API int mdpf_set_state(mdpf_ctx *ctx, const double *pos, const double *vel);
+
+/* Copy the current state to host buffers (any may be NULL): pos, vel [N,3] FP64. */
+MDPF_API int mdpf_get_state(mdpf_ctx *ctx, double *pos, double *vel);
+
+/*
+ * Advance n_steps velocity-Verlet steps of dt_fs on the device:
+ *   v += dt/2 a;  x += dt v;  F = F(x);  v += dt/2 a
+ * with FP32 forces and FP64 positions, velocities, energies.  The whole loop
+ * runs in one persistent kernel (or one kernel sequence per step); the host
+ * is not involved between steps.  Returns NONFINITE if U or K became
+ * non-finite, TIMEOUT if a device-side grid barrier gave up (the state is then
+ * undefined; call mdpf_set_state).  Synchronous.
+ */
+MDPF_API int mdpf_step(mdpf_ctx *ctx, int64_t n_steps);
+
+/* Asynchronous mdpf_step on cuda_stream; status is checked by the next synchronous call. */
+MDPF_API int mdpf_step_async(mdpf_ctx *ctx, int64_t n_steps, void *cuda_stream);
+
+/* Counters, energies of the current state and the device status word. */
+MDPF_API int mdpf_get_counters(mdpf_ctx *ctx, mdpf_counters *out);
+
+/*
+ * Energy trace, oldest first: one entry per energy step (every energy_every
+ * steps), the most recent min(count, trace_capacity) of them.  U[k], K[k] in
+ * kcal/mol after step step[k] (any output may be NULL).  *n_out receives the
+ * count written (at most max_n).
+ */
+MDPF_API int mdpf_get_trace(mdpf_ctx *ctx, double *U, double *K, int64_t *step, int64_t max_n, int64_t *n_out);
+
+/*
+ * Recorded frames, oldest first (at most max_frames of them): pos [n,N,3]
+ * FP64, energy [n] FP64, forces [n,N,3] FP32, step [n] int64 (any may be
+ * NULL).  A frame is taken after every record_every-th step.
+ */
+MDPF_API int mdpf_get_frames(mdpf_ctx *ctx, int64_t max_n, double *pos, double *energy, float *forces,
+                             int64_t *step, int64_t *n_out);
+
+/*
+ * The 1-2/1-3 exclusion set built on the device by mdpf_create, as CSR:
+ * offset [N+1] int32 and idx [capacity] int32, each row ascending.  *total
+ * receives the number of entries (idx may be NULL to query it).
+ */
+MDPF_API int mdpf_get_exclusions(mdpf_ctx *ctx, int32_t *offset, int32_t *idx, int64_t capacity, int64_t *total);
+
+/* Angles (a, vertex, b) derived on the device, [n_angles,3] int32, vertex-major order. */
+MDPF_API int mdpf_get_angles(mdpf_ctx *ctx, int32_t *angles, int64_t capacity, int64_t *n_out);
+
+/*
+ * Fault injection for tests (host side; no GPU fault is raised).  The given
+ * MDPF_STATUS_* bits are OR-ed into the device status word and reported by
+ * the next mdpf_step / mdpf_get_counters; bits == 0 clears the word.
+ */
+MDPF_API int mdpf_debug_set_status(mdpf_ctx *ctx, uint32_t bits);
+
+/*
+ * Bounded device-side wait on a flag that nothing sets: spins at most
+ * limit_us microseconds (1..2,000,000), then records MDPF_STATUS_TIMEOUT and
+ * returns MDPF_ERR_TIMEOUT.  Exercises the timeout path of the grid barrier
+ * without hanging the GPU.
+ */
+MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
+
+/*
+ * Per-kernel device timing with CUDA events recorded on the launching stream
+ * around every launch of the profiled kernels (off by default; costs two event
+ * records per launch).  Slots: MDPF_PROF_NONBONDED (all-pairs tile kernel of
+ * the kernel-sequence stepper), MDPF_PROF_STEPPER (persistent step-loop
+ * kernel), MDPF_PROF_STEP (one whole mdpf_step call on the device).
+ * mdpf_get_profile synchronises the recorded events and returns the summed
+ * duration in ms and the number of launches since mdpf_set_profiling(ctx, 1).
+ */
+#define MDPF_PROF_NONBONDED 0
+#define MDPF_PROF_STEPPER 1
+#define MDPF_PROF_STEP 2
+#define MDPF_PROF_SLOTS 8
+MDPF_API int mdpf_set_profiling(mdpf_ctx *ctx, int32_t enable);
+MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDPF_H */

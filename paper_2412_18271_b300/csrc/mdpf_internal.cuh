@@ -1,0 +1,173 @@
+// Internal declarations shared by the CUDA sources of libmdpf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mdpf.h"
+
+namespace mdpf {
+
+// (kcal/mol/A/amu) -> A/fs^2, i.e. 1 kcal/mol = 4.184e-4 amu A^2/fs^2.
+constexpr double kAcc = 4.184e-4;
+constexpr double kCoulombDefault = 332.06371;
+
+// Fixed-point accumulation of forces and energies: value * 2^32 in int64.
+// Integer addition is associative, so results do not depend on the order in
+// which threads add their contributions.
+constexpr double kFxScale = 4294967296.0;
+constexpr double kFxInv = 1.0 / 4294967296.0;
+
+constexpr int kTile = 32;          // atoms per tile (one per lane)
+constexpr int kPad = 64;           // atoms are padded to a multiple of 64 (two tiles)
+constexpr int kMaxExclPerAtom = 255;
+
+// Energy slot layout (int64 fixed point): bond, angle, LJ, Coulomb, kinetic.
+enum { E_BOND = 0, E_ANGLE = 1, E_LJ = 2, E_COUL = 3, E_KIN = 4, E_SLOTS = 8 };
+
+__host__ __device__ inline int64_t tile_pair_index(int I, int J, int T) {
+    // upper triangle (I <= J), row-major
+    return (int64_t)I * T - (int64_t)I * (I - 1) / 2 + (J - I);
+}
+
+// Per-system constant data on the device (plain path).
+struct PlainDev {
+    int n, n_pad, n_tiles;
+    int n_bonds, n_angles;
+    const float4 *pos4;      // x, y, z, q*sqrt(ke)   [n_pad]
+    const float2 *lj;        // sigma/2, sqrt(24 eps)  [n_pad]
+    const int2 *bonds;       // [n_bonds]
+    const float2 *bond_par;  // r0, k                  [n_bonds]
+    const int4 *angles;      // a, v, b, 0             [n_angles]
+    float angle_k, angle_theta0;
+    const uint32_t *tile_mask;  // [n_tile_pairs][32]: bit j of word i set = pair skipped
+    const uint32_t *tile_flag;  // [n_tile_pairs]: 1 if any bit set in the tile
+    const int4 *items;          // [n_items] work items of the all-pairs sum (forcefield.cuh)
+    int n_items;
+    uint32_t *status;           // device status word
+};
+
+struct Frames {
+    double *pos;      // [cap][n][3]
+    double *energy;   // [cap]
+    float *forces;    // [cap][n][3]
+    int64_t *step;    // [cap]
+    int cap;
+    int every;
+};
+
+}  // namespace mdpf
+
+struct mdpf_ctx {
+    int device = 0;
+    int mode = MDPF_MODE_PLAIN;
+    int n = 0, n_pad = 0, n_tiles = 0, n_bonds = 0, n_angles = 0;
+    int64_t n_tile_pairs = 0;
+    double dt = 0.5, coulomb_k = mdpf::kCoulombDefault;
+    int trace_cap = 4096;
+    int record_every = 0, max_frames = 0, energy_every = 1;
+    int stepper = 0;                       // 0 persistent, 1 per-step kernel sequence
+    int64_t excl_total = 0;
+
+    // topology on the device
+    int32_t *d_element = nullptr;
+    double *d_mass = nullptr;
+    double *d_hdt_m = nullptr;      // dt/2 * kAcc / m  [n]
+    float4 *d_pos4 = nullptr;       // state positions, FP32 copy for force kernels
+    float4 *d_pos4_b = nullptr;     // second position buffer of the persistent stepper
+    float4 *d_pos4_c = nullptr;     // compute() positions
+    float2 *d_lj = nullptr;
+    float *d_charge_s = nullptr;    // q * sqrt(ke) [n_pad]
+    int2 *d_bonds = nullptr;
+    float2 *d_bond_par = nullptr;
+    int4 *d_angles = nullptr;
+    int32_t *d_excl_off = nullptr;
+    int32_t *d_excl_idx = nullptr;
+    uint32_t *d_tile_mask = nullptr;
+    uint32_t *d_tile_flag = nullptr;
+    int4 *d_items = nullptr;
+    int n_items = 0;
+    float angle_k = 0, angle_theta0 = 0;
+
+    // integrator state
+    double *d_x = nullptr;          // [n][3]
+    double *d_v = nullptr;          // [n][3]
+    unsigned long long *d_fx_base = nullptr; // [2][n_pad][3] fixed-point force buffers
+    unsigned long long *d_fx = nullptr;      // = d_fx_base: forces at the current x (state)
+    unsigned long long *d_fx_c = nullptr;    // compute() forces
+    unsigned long long *d_efx = nullptr;     // [E_SLOTS] fixed-point energies (state)
+    unsigned long long *d_efx_c = nullptr;   // compute() energies
+    double *d_trace_u = nullptr, *d_trace_k = nullptr;
+    int64_t *d_trace_step = nullptr;
+    int64_t *d_step = nullptr;             // device step counter
+    uint32_t *d_status = nullptr;          // [0] state, [1] compute()
+    double *d_xc = nullptr;                // compute() FP64 position staging [n][3]
+    double *d_fc = nullptr;                // compute() FP64 forces out [n][3]
+    double *d_scalar = nullptr;            // [16]: [0] U, [1] K of the state; [2..7] compute outputs
+    unsigned int *d_barrier = nullptr;     // [8]: [0..1] grid-barrier counter (u64), [7] timeout flag
+    mdpf::Frames frames{};
+
+    // persistent stepper
+    double *d_part = nullptr;              // [2][step_grid][2] per-block pair energies
+    double *d_tile_e = nullptr;            // [2][n_tiles][4] per-tile bonded + kinetic energies
+    unsigned int *d_tile_cnt = nullptr;    // [n_tiles] contribution counters
+    int *d_tile_expect = nullptr;          // [n_tiles] contributions per step
+    int *d_inc_off = nullptr, *d_inc = nullptr;  // per-atom bonded incidence CSR
+    int step_grid = 0;                     // blocks of the persistent stepper
+
+    int64_t steps = 0, force_evals = 0;
+    double h_initial = 0;
+    bool state_set = false;
+
+    cudaStream_t stream = nullptr;
+    // profiling: event pairs recorded around launches of profiled kernels
+    bool profiling = false;
+    struct ProfRec {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    double prof_ms[MDPF_PROF_SLOTS] = {0};
+    int64_t prof_n[MDPF_PROF_SLOTS] = {0};
+    std::vector<double> h_mass;
+    std::string err;
+    bool sticky = false;
+};
+
+namespace mdpf {
+
+// status helpers (api.cu)
+int fail(mdpf_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(mdpf_ctx *ctx, cudaError_t e, const char *where);
+
+// profiling (api.cu): bracket a launch with events when profiling is on
+cudaEvent_t prof_begin(mdpf_ctx *ctx, cudaStream_t s);
+void prof_end(mdpf_ctx *ctx, int slot, cudaEvent_t a, cudaStream_t s);
+int prof_harvest(mdpf_ctx *ctx);
+
+// exclusions.cu
+int build_exclusions(mdpf_ctx *ctx);
+
+// plain.cu
+PlainDev plain_dev(const mdpf_ctx *ctx, const float4 *pos4);
+void launch_zero_fx(unsigned long long *fx, int n3, unsigned long long *efx, cudaStream_t s);
+void launch_pos4_from_x(const double *x, const float *charge_s, float4 *pos4, int n, int n_pad, cudaStream_t s);
+void launch_bonded(const PlainDev &p, unsigned long long *fx, unsigned long long *efx, cudaStream_t s);
+void launch_nonbonded(const PlainDev &p, unsigned long long *fx, unsigned long long *efx, bool energy,
+                      cudaStream_t s);
+void launch_fx_to_forces(const unsigned long long *fx, int n, double *f64, float *f32, cudaStream_t s);
+void launch_energy_out(const unsigned long long *efx, double *out6, cudaStream_t s);
+void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s);
+void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s);
+void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s);
+void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s);
+
+// stepper.cu
+int stepper_grid(const mdpf_ctx *ctx);
+cudaError_t launch_plain_persistent(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t s);
+
+}  // namespace mdpf

@@ -1,0 +1,289 @@
+// Plain analytic force field and velocity-Verlet kernels (kernel-sequence path
+// and the helpers that mdpf_compute / mdpf_set_state use).
+//
+// Energy terms (units kcal/mol, A):
+//   bonds    E = k/2 (r - r0)^2
+//   angles   E = k/2 (theta - theta0)^2, one per pair of bonds meeting at an atom
+//   pairs    E = 4 eps_ij [(sigma_ij/r)^12 - (sigma_ij/r)^6] + ke q_i q_j / r
+//            over every pair that is neither 1-2 nor 1-3, no cutoff
+// Forces are accumulated as int64 fixed point (value * 2^32), so the result
+// does not depend on the order in which warps finish.
+#include "forcefield.cuh"
+
+namespace mdpf {
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+__global__ void k_zero_fx(unsigned long long *fx, int n3, unsigned long long *efx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) fx[i] = 0ull;
+    if (efx != nullptr && i < E_SLOTS) efx[i] = 0ull;
+}
+
+__global__ void k_pos4_from_x(const double *x, const float *qs, float4 *pos4, int n, int n_pad) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n) {
+        pos4[a] = make_float4((float)x[3 * a], (float)x[3 * a + 1], (float)x[3 * a + 2], qs[a]);
+    } else if (a < n_pad) {
+        pos4[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void k_fx_to_forces(const unsigned long long *fx, int n3, double *f64, float *f32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) {
+        double v = fx_val(fx[i]);
+        if (f64) f64[i] = v;
+        if (f32) f32[i] = (float)v;
+    }
+}
+
+// out = {U, E_bond, E_angle, E_LJ, E_Coulomb, K}
+__global__ void k_energy_out(const unsigned long long *efx, double *out) {
+    int t = threadIdx.x;
+    if (t < 5) out[1 + t] = fx_val(efx[t]);
+    if (t == 0) out[0] = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]);
+}
+
+// ------------------------------------------------------------------ bonded
+
+__global__ void k_bonded(PlainDev p, unsigned long long *fx, unsigned long long *efx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    float eb = 0.f, ea = 0.f;
+    if (t < p.n_bonds + p.n_angles) bonded_term(p, t, fx, eb, ea);
+    if (!isfinite(eb + ea)) atomicOr(p.status, MDPF_STATUS_NONFINITE);
+    if (efx != nullptr) {
+        double sb = warp_sum_d((double)eb), sa = warp_sum_d((double)ea);
+        if ((threadIdx.x & 31) == 0) {
+            if (sb != 0.0) fx_add_d(&efx[E_BOND], sb);
+            if (sa != 0.0) fx_add_d(&efx[E_ANGLE], sa);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ all pairs
+
+constexpr int kNbThreads = 256;
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(kNbThreads, 2) k_nonbonded(PlainDev p, unsigned long long *fx,
+                                                             unsigned long long *efx, uint32_t *status) {
+    __shared__ JTile jt[kNbThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    float elj = 0.f, ec = 0.f;
+    bool bad = false;
+    for (int it = warp; it < p.n_items; it += nwarps)
+        nonbonded_item<ENERGY>(p, it, lane, jt[threadIdx.x >> 5], fx, elj, ec, bad);
+    if (bad) atomicOr(status, MDPF_STATUS_NONFINITE);
+    if (ENERGY) {
+        double e_lj = warp_sum_d((double)elj * (1.0 / 6.0));
+        double e_c = warp_sum_d((double)ec);
+        if (lane == 0) {
+            fx_add_d(&efx[E_LJ], e_lj);
+            fx_add_d(&efx[E_COUL], e_c);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ integrator
+
+// v += dt/2 a(F);  x += dt v;  refresh the FP32 copy; clear the force accumulators.
+__global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over_m, double *x, double *v,
+                             unsigned long long *fx, float4 *pos4, const float *qs, unsigned long long *efx) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < E_SLOTS && efx != nullptr) efx[a] = 0ull;
+    if (a >= n) {
+        if (a < n_pad) {
+            fx[3 * a] = fx[3 * a + 1] = fx[3 * a + 2] = 0ull;
+            pos4[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+    const double h = hdt_over_m[a];
+    double p[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double vc = v[3 * a + c] + h * fx_val(fx[3 * a + c]);
+        double xc = x[3 * a + c] + dt * vc;
+        v[3 * a + c] = vc;
+        x[3 * a + c] = xc;
+        p[c] = xc;
+        fx[3 * a + c] = 0ull;
+    }
+    pos4[a] = make_float4((float)p[0], (float)p[1], (float)p[2], qs[a]);
+}
+
+// v += dt/2 a(F_new) (when do_kick); kinetic energy into the fixed-point slot (when energy).
+__global__ void k_kick(int n, const double *hdt_over_m, const double *mass, double *v, const unsigned long long *fx,
+                       unsigned long long *efx, int do_kick, int energy) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (a < n) {
+        const double h = hdt_over_m[a];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double vc = v[3 * a + c];
+            if (do_kick) {
+                vc += h * fx_val(fx[3 * a + c]);
+                v[3 * a + c] = vc;
+            }
+            ke += vc * vc;
+        }
+        ke *= 0.5 * mass[a] / kAcc;
+    }
+    if (!energy) return;
+    ke = warp_sum_d(ke);
+    if ((threadIdx.x & 31) == 0 && ke != 0.0) fx_add_d(&efx[E_KIN], ke);
+}
+
+// After a step: counters; on energy steps the trace entry and the non-finite
+// check.  One thread.
+__global__ void k_finish_step(const unsigned long long *efx, double *trace_u, double *trace_k,
+                              int64_t *trace_step, int cap, int energy_every, int64_t *step, uint32_t *status,
+                              double *scalars, int energy) {
+    if (threadIdx.x != 0) return;
+    const int64_t s = *step + 1;
+    *step = s;
+    if (!energy) return;
+    double U = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]);
+    double K = fx_val(efx[E_KIN]);
+    const int64_t e = s / energy_every - 1;
+    trace_u[e % cap] = U;
+    trace_k[e % cap] = K;
+    trace_step[e % cap] = s;
+    scalars[0] = U;
+    scalars[1] = K;
+    // fixed-point slots saturate rather than turn NaN: treat huge values as non-finite too
+    bool bad = !isfinite(U) || !isfinite(K) || fabs(U) > 1e9 || fabs(K) > 1e9;
+    if (bad) atomicOr(status, MDPF_STATUS_NONFINITE);
+}
+
+__global__ void k_record(int n, int every, const int64_t *step, const double *x, const unsigned long long *fx,
+                         const double *scalars, Frames fr) {
+    const int64_t s = *step;  // steps completed
+    if (every <= 0 || s % every != 0) return;
+    const int64_t f = s / every - 1;
+    const int slot = (int)(f % fr.cap);
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n) {
+        for (int c = 0; c < 3; ++c) {
+            fr.pos[((size_t)slot * n + a) * 3 + c] = x[3 * a + c];
+            fr.forces[((size_t)slot * n + a) * 3 + c] = (float)fx_val(fx[3 * a + c]);
+        }
+    }
+    if (a == 0) {
+        fr.energy[slot] = scalars[0];
+        fr.step[slot] = s;
+    }
+}
+
+// Spin on a flag that nothing sets, for at most limit_ns of globaltimer.
+__global__ void k_wait_timeout(uint32_t *status, volatile unsigned int *flag, long long limit_ns) {
+    if (threadIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (*flag == 0u) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if ((long long)(t - t0) > limit_ns) {
+            atomicOr(status, MDPF_STATUS_TIMEOUT);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+PlainDev plain_dev(const mdpf_ctx *ctx, const float4 *pos4) {
+    PlainDev p;
+    p.n = ctx->n;
+    p.n_pad = ctx->n_pad;
+    p.n_tiles = ctx->n_tiles;
+    p.n_bonds = ctx->n_bonds;
+    p.n_angles = ctx->n_angles;
+    p.pos4 = pos4;
+    p.lj = ctx->d_lj;
+    p.bonds = ctx->d_bonds;
+    p.bond_par = ctx->d_bond_par;
+    p.angles = ctx->d_angles;
+    p.angle_k = ctx->angle_k;
+    p.angle_theta0 = ctx->angle_theta0;
+    p.tile_mask = ctx->d_tile_mask;
+    p.tile_flag = ctx->d_tile_flag;
+    p.items = ctx->d_items;
+    p.n_items = ctx->n_items;
+    p.status = ctx->d_status;
+    return p;
+}
+
+void launch_zero_fx(unsigned long long *fx, int n3, unsigned long long *efx, cudaStream_t s) {
+    int m = n3 > E_SLOTS ? n3 : E_SLOTS;
+    k_zero_fx<<<(m + 255) / 256, 256, 0, s>>>(fx, n3, efx);
+}
+
+void launch_pos4_from_x(const double *x, const float *qs, float4 *pos4, int n, int n_pad, cudaStream_t s) {
+    k_pos4_from_x<<<(n_pad + 255) / 256, 256, 0, s>>>(x, qs, pos4, n, n_pad);
+}
+
+void launch_bonded(const PlainDev &p, unsigned long long *fx, unsigned long long *efx, cudaStream_t s) {
+    int m = p.n_bonds + p.n_angles;
+    if (m > 0) k_bonded<<<(m + 255) / 256, 256, 0, s>>>(p, fx, efx);
+}
+
+void launch_nonbonded(const PlainDev &p, unsigned long long *fx, unsigned long long *efx, bool energy,
+                      cudaStream_t s) {
+    int blocks = (p.n_items * 32 + kNbThreads - 1) / kNbThreads;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks < 1) blocks = 1;
+    if (energy)
+        k_nonbonded<true><<<blocks, kNbThreads, 0, s>>>(p, fx, efx, p.status);
+    else
+        k_nonbonded<false><<<blocks, kNbThreads, 0, s>>>(p, fx, efx, p.status);
+}
+
+void launch_fx_to_forces(const unsigned long long *fx, int n, double *f64, float *f32, cudaStream_t s) {
+    k_fx_to_forces<<<(3 * n + 255) / 256, 256, 0, s>>>(fx, 3 * n, f64, f32);
+}
+
+void launch_energy_out(const unsigned long long *efx, double *out6, cudaStream_t s) {
+    k_energy_out<<<1, 32, 0, s>>>(efx, out6);
+}
+
+// FP64 integrator kernels use small blocks so that the (slow) FP64 work of a
+// few thousand atoms spreads over many SMs.
+constexpr int kIntThreads = 32;
+
+void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s) {
+    int m = ctx->n_pad > E_SLOTS ? ctx->n_pad : E_SLOTS;
+    k_kick_drift<<<(m + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(
+        ctx->n, ctx->n_pad, ctx->dt, ctx->d_hdt_m, ctx->d_x, ctx->d_v, ctx->d_fx, ctx->d_pos4, ctx->d_charge_s,
+        ctx->d_efx);
+}
+
+void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s) {
+    k_kick<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(ctx->n, ctx->d_hdt_m, ctx->d_mass,
+                                                                              ctx->d_v, ctx->d_fx, ctx->d_efx, 1,
+                                                                              energy ? 1 : 0);
+    k_finish_step<<<1, 32, 0, s>>>(ctx->d_efx, ctx->d_trace_u, ctx->d_trace_k, ctx->d_trace_step, ctx->trace_cap,
+                                   ctx->energy_every, ctx->d_step, ctx->d_status, ctx->d_scalar, energy ? 1 : 0);
+    if (ctx->record_every > 0 && ctx->frames.cap > 0)
+        k_record<<<(ctx->n + 255) / 256, 256, 0, s>>>(ctx->n, ctx->record_every, ctx->d_step, ctx->d_x, ctx->d_fx,
+                                                      ctx->d_scalar, ctx->frames);
+}
+
+// Kinetic energy of the current velocities into efx[E_KIN] (no kick).
+void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s) {
+    k_kick<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(ctx->n, ctx->d_hdt_m, ctx->d_mass,
+                                                                              ctx->d_v, ctx->d_fx, ctx->d_efx, 0, 1);
+}
+
+void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s) {
+    k_wait_timeout<<<1, 32, 0, s>>>(status, flag, limit_ns);
+}
+
+}  // namespace mdpf

@@ -1,0 +1,428 @@
+// Persistent velocity-Verlet stepper for the plain force field.
+//
+// One cooperative launch runs all n steps of mdpf_step; the kernel never
+// returns to the host between steps (the paper's timing table shows that for
+// small systems launch overhead, not arithmetic, decides the step time; CUDA
+// graphs were its remedy, a single resident kernel is the one used here).
+//
+// Each MD step costs one grid barrier:
+//   phase B(s)   every warp evaluates its all-pairs work items at x_{s+1}
+//                (FP32 copy P[s & 1]) and adds the forces into buffer
+//                buf(s) (int64 fixed point).  After each item the warp bumps
+//                the contribution counter of every 32-atom tile the item
+//                touched (release); the warp that brings a tile's counter to
+//                its expected value (acquire) owns the tile's completion:
+//                  F = F_pairs + bonded forces of the tile's atoms,
+//                  v_{s+1} = v_{s+1/2} + dt/2 a          (end of step s, K)
+//                  v_{s+3/2} = v_{s+1} + dt/2 a; x_{s+2} = x_{s+1} + dt v
+//                  FP32 copy of x_{s+2} into P[(s + 1) & 1]  (start of step s+1)
+//   grid barrier
+// A pre-phase performs the first half-kick and drift from the forces left in
+// the state buffer by mdpf_set_state or by the previous launch; the last step
+// writes F(x_n) back there instead.
+//
+// Forces are integer sums, and every energy is summed in a fixed order (pair
+// energies per block in block order, bonded and kinetic energies per tile in
+// tile order), so trajectories and energies are reproducible bit for bit.
+//
+// The grid barrier is a 64-bit arrival counter (release add, acquire poll)
+// that waits at most limit_ns; on time-out the block records
+// MDPF_STATUS_TIMEOUT and returns, and the others follow at their next
+// barrier.  Co-residency of all blocks is guaranteed by the cooperative launch.
+#include "forcefield.cuh"
+
+namespace mdpf {
+
+struct StepArgs {
+    PlainDev p;
+    int n, n_tiles;
+    double dt;
+    const double *hdt_m;          // dt/2 * kAcc / m
+    const double *mass;
+    const float *qs;
+    float4 *P0, *P1;              // FP32 position buffers (x, y, z, q sqrt(ke))
+    double *x, *v;
+    unsigned long long *fxA;      // state forces F(x) on entry and exit; accumulator of odd steps
+    unsigned long long *fxB;      // accumulator of even steps
+    unsigned int *tile_cnt;       // [T] contributions seen this step
+    const int *tile_expect;       // [T] contributions per step
+    const int *inc_off, *inc;     // per-atom bonded incidence: (term << 2) | role
+    double *part;                 // [2][grid][2] per-block pair energies (LJ, Coulomb)
+    double *tile_e;               // [2][T][4] per-tile bond, angle, kinetic energy
+    double *trace_u, *trace_k;
+    int64_t *trace_step;
+    int trace_cap;
+    int energy_every;
+    int64_t *step;
+    uint32_t *status;
+    double *scalars;
+    Frames frames;
+    int record_every;
+    unsigned long long *bar;      // arrival counter
+    int64_t n_steps;
+    long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier number `epoch` (1, 2, ...).  Returns false in every
+// thread of the block if this block gave up waiting.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned long long epoch, uint32_t *status,
+                                             long long limit_ns, int *s_fail) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        if (gridDim.x > 1) {
+            const unsigned long long target = epoch * gridDim.x;
+            atom_add_release(bar, 1ull);
+            const unsigned long long t0 = globaltimer();
+            unsigned int spins = 0;
+            while (ld_acquire(bar) < target) {
+                if ((++spins & 31u) == 0u && (long long)(globaltimer() - t0) > limit_ns) {
+                    atomicOr(status, MDPF_STATUS_TIMEOUT);
+                    fail = 1;
+                    break;
+                }
+            }
+        }
+        *s_fail = fail;
+    }
+    __syncthreads();
+    return *s_fail == 0;
+}
+
+// Force on atom a from the bonded terms it takes part in (FP32), and the
+// energies of the terms it is designated for (bonds: first atom; angles:
+// vertex).
+__device__ __forceinline__ float3 bonded_on_atom(const PlainDev &p, const float4 *pos, const int *inc_off,
+                                                 const int *inc, int a, float &eb, float &ea) {
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    for (int q = inc_off[a]; q < inc_off[a + 1]; ++q) {
+        const int code = inc[q], t = code >> 2, role = code & 3;
+        if (t < p.n_bonds) {
+            const int2 b = p.bonds[t];
+            const float4 xi = pos[b.x], xj = pos[b.y];
+            const float2 par = p.bond_par[t];
+            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float dr = r - par.x;
+            const float g = (role == 0 ? 1.f : -1.f) * par.y * dr / r;
+            f.x += g * dx;
+            f.y += g * dy;
+            f.z += g * dz;
+            if (role == 0) eb += 0.5f * par.y * dr * dr;
+        } else {
+            const int4 an = p.angles[t - p.n_bonds];
+            const float4 xa = pos[an.x], xv = pos[an.y], xb = pos[an.z];
+            const float ux = xa.x - xv.x, uy = xa.y - xv.y, uz = xa.z - xv.z;
+            const float wx = xb.x - xv.x, wy = xb.y - xv.y, wz = xb.z - xv.z;
+            const float ru = sqrtf(ux * ux + uy * uy + uz * uz), rw = sqrtf(wx * wx + wy * wy + wz * wz);
+            const float c = ux * wx + uy * wy + uz * wz;
+            const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+            const float cr = sqrtf(cx * cx + cy * cy + cz * cz);
+            const float th = atan2f(cr, c);
+            const float dth = th - p.angle_theta0;
+            const float cs = c / (ru * rw);
+            const float sn = cr / (ru * rw);
+            const float ga = p.angle_k * dth / (sn * ru);
+            const float gb = p.angle_k * dth / (sn * rw);
+            const float iu = 1.f / ru, iw = 1.f / rw;
+            const float fax = ga * (wx * iw - cs * ux * iu), fay = ga * (wy * iw - cs * uy * iu),
+                        faz = ga * (wz * iw - cs * uz * iu);
+            const float fbx = gb * (ux * iu - cs * wx * iw), fby = gb * (uy * iu - cs * wy * iw),
+                        fbz = gb * (uz * iu - cs * wz * iw);
+            if (role == 0) {
+                f.x += fax; f.y += fay; f.z += faz;
+            } else if (role == 2) {
+                f.x += fbx; f.y += fby; f.z += fbz;
+            } else {
+                f.x -= fax + fbx; f.y -= fay + fby; f.z -= faz + fbz;
+                ea += 0.5f * p.angle_k * dth * dth;
+            }
+        }
+    }
+    return f;
+}
+
+constexpr int kStepThreads = 256;
+constexpr int kStepWarps = kStepThreads / 32;
+
+// Completion of tile t by the warp that delivered its last contribution.
+__device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t s, const float4 *Pcur, float4 *Pnext,
+                                              unsigned long long *acc, bool energy, bool rec, int slot) {
+    const int lane = threadIdx.x & 31;
+    const int at = t * kTile + lane;
+    float eb = 0.f, ea = 0.f;
+    double kin = 0.0;
+    const bool last = s + 1 == a.n_steps;
+    if (at < a.n) {
+        float3 fb = bonded_on_atom(a.p, Pcur, a.inc_off, a.inc, at, eb, ea);
+        const double h = a.hdt_m[at];
+        double f[3], v[3], x[3];
+        const float fbv[3] = {fb.x, fb.y, fb.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            f[q] = fx_val(__ldcg(&acc[3 * at + q])) + (double)fbv[q];
+            v[q] = __ldcg(&a.v[3 * at + q]) + h * f[q];  // v_{s+1}
+            kin += v[q] * v[q];
+        }
+        kin *= 0.5 * a.mass[at] / kAcc;
+        if (rec) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                a.frames.pos[((size_t)slot * a.n + at) * 3 + q] = __ldcg(&a.x[3 * at + q]);
+                a.frames.forces[((size_t)slot * a.n + at) * 3 + q] = (float)f[q];
+            }
+        }
+        if (!last) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                v[q] += h * f[q];
+                x[q] = __ldcg(&a.x[3 * at + q]) + a.dt * v[q];
+                a.x[3 * at + q] = x[q];
+                acc[3 * at + q] = 0ull;
+            }
+            Pnext[at] = make_float4((float)x[0], (float)x[1], (float)x[2], a.qs[at]);
+        } else {
+            // leave F(x_n) in the state buffer for the next launch
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                acc[3 * at + q] = 0ull;
+                a.fxA[3 * at + q] = (unsigned long long)__double2ll_rn(f[q] * kFxScale);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a.v[3 * at + q] = v[q];
+        if (!isfinite(kin + eb + ea)) atomicOr(a.status, MDPF_STATUS_NONFINITE);
+    } else if (at < a.p.n_pad) {
+        acc[3 * at] = acc[3 * at + 1] = acc[3 * at + 2] = 0ull;
+    }
+    if (energy) {
+        const double sb = warp_sum_d((double)eb), sa = warp_sum_d((double)ea), sk = warp_sum_d(kin);
+        if (lane == 0) {
+            double *te = a.tile_e + ((size_t)(s & 1) * a.n_tiles + t) * 4;
+            te[0] = sb;
+            te[1] = sa;
+            te[2] = sk;
+        }
+    }
+}
+
+// Bump the counters of the tiles an item touched; complete every tile this
+// warp finished.
+__device__ __forceinline__ void item_done(const StepArgs &a, const int4 &item, int64_t s, const float4 *Pcur,
+                                          float4 *Pnext, unsigned long long *acc, bool energy, bool rec, int slot) {
+    const int lane = threadIdx.x & 31;
+    int tl[3], nt;
+    if (item.x == ITEM_OFF64) {
+        tl[0] = 2 * item.y; tl[1] = 2 * item.y + 1; tl[2] = item.z; nt = 3;
+    } else if (item.x == ITEM_OFF32) {
+        tl[0] = item.y; tl[1] = item.z; tl[2] = 0; nt = 2;
+    } else {
+        tl[0] = item.y; tl[1] = 0; tl[2] = 0; nt = 1;
+    }
+    unsigned int mine = 0;
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();  // release this warp's force additions
+        for (int k = 0; k < nt; ++k) {
+            const unsigned int old = atomicAdd(&a.tile_cnt[tl[k]], 1u);
+            if (old + 1 == (unsigned int)a.tile_expect[tl[k]]) mine |= 1u << k;
+        }
+    }
+    mine = __shfl_sync(0xffffffffu, mine, 0);
+    if (mine) __threadfence();  // acquire: every lane orders its reads of the tile after the counter
+    for (int k = 0; k < nt; ++k) {
+        if (!(mine & (1u << k))) continue;
+        complete_tile(a, tl[k], s, Pcur, Pnext, acc, energy, rec, slot);
+        __syncwarp();
+        if (lane == 0) a.tile_cnt[tl[k]] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a) {
+    __shared__ JTile jt[kStepWarps];
+    __shared__ double red[kStepWarps][2];
+    __shared__ int s_fail;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const int gwarp = gtid >> 5;
+    const int nwarps = nthreads >> 5;
+    const int64_t step0 = *a.step;
+    unsigned long long epoch = 0;
+
+    // ---- pre-phase: v_{1/2} = v_0 + dt/2 a(x_0); x_1 = x_0 + dt v_{1/2}; clear both accumulators
+    for (int at = gtid; at < a.p.n_pad; at += nthreads) {
+        if (at < a.n) {
+            const double h = a.hdt_m[at];
+            double x[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const double f = fx_val(a.fxA[3 * at + q]);
+                const double v = a.v[3 * at + q] + h * f;
+                x[q] = a.x[3 * at + q] + a.dt * v;
+                a.v[3 * at + q] = v;
+                a.x[3 * at + q] = x[q];
+            }
+            a.P0[at] = make_float4((float)x[0], (float)x[1], (float)x[2], a.qs[at]);
+        } else {
+            a.P0[at] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.P1[at] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            a.fxA[3 * at + q] = 0ull;
+            a.fxB[3 * at + q] = 0ull;
+        }
+    }
+    for (int t = gtid; t < a.n_tiles; t += nthreads) a.tile_cnt[t] = 0u;
+    if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
+
+    for (int64_t s = 0; s < a.n_steps; ++s) {
+        const float4 *Pcur = (s & 1) ? a.P1 : a.P0;
+        float4 *Pnext = (s & 1) ? a.P0 : a.P1;
+        unsigned long long *acc = (s & 1) ? a.fxA : a.fxB;
+        const int64_t done = step0 + s + 1;  // steps completed after this iteration
+        const bool energy = done % a.energy_every == 0;
+        const bool rec = a.record_every > 0 && done % a.record_every == 0;
+        const int slot = rec ? (int)((done / a.record_every - 1) % a.frames.cap) : 0;
+        PlainDev p = a.p;
+        p.pos4 = Pcur;
+        float elj = 0.f, ec = 0.f;
+        bool bad = false;
+        for (int it = gwarp; it < p.n_items; it += nwarps) {
+            if (energy)
+                nonbonded_item<true>(p, it, lane, jt[w], acc, elj, ec, bad);
+            else
+                nonbonded_item<false>(p, it, lane, jt[w], acc, elj, ec, bad);
+            item_done(a, p.items[it], s, Pcur, Pnext, acc, energy, rec, slot);
+        }
+        if (bad) atomicOr(a.status, MDPF_STATUS_NONFINITE);
+        if (energy) {
+            double vl = warp_sum_d((double)elj * (1.0 / 6.0)), vc = warp_sum_d((double)ec);
+            if (lane == 0) {
+                red[w][0] = vl;
+                red[w][1] = vc;
+            }
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                double sum = 0.0;
+                for (int q = 0; q < kStepWarps; ++q) sum += red[q][threadIdx.x];
+                a.part[((size_t)(s & 1) * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = sum;
+            }
+        }
+        if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
+        // ---- energies of step `done` (block 0, warp 0), read after the barrier
+        if (energy && blockIdx.x == 0 && w == 0) {
+            const double *pp = a.part + (size_t)(s & 1) * gridDim.x * 2;
+            const double *te = a.tile_e + (size_t)(s & 1) * a.n_tiles * 4;
+            double sl = 0, sc = 0, sb = 0, sa = 0, sk = 0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                sl += pp[2 * b];
+                sc += pp[2 * b + 1];
+            }
+            for (int t = lane; t < a.n_tiles; t += 32) {
+                sb += te[4 * t];
+                sa += te[4 * t + 1];
+                sk += te[4 * t + 2];
+            }
+            sl = warp_sum_d(sl);
+            sc = warp_sum_d(sc);
+            sb = warp_sum_d(sb);
+            sa = warp_sum_d(sa);
+            sk = warp_sum_d(sk);
+            if (lane == 0) {
+                const double U = sb + sa + sl + sc;
+                const int64_t e = done / a.energy_every - 1;
+                a.trace_u[e % a.trace_cap] = U;
+                a.trace_k[e % a.trace_cap] = sk;
+                a.trace_step[e % a.trace_cap] = done;
+                a.scalars[0] = U;
+                a.scalars[1] = sk;
+                if (!isfinite(U) || !isfinite(sk)) atomicOr(a.status, MDPF_STATUS_NONFINITE);
+                if (rec) {
+                    a.frames.energy[slot] = U;
+                    a.frames.step[slot] = done;
+                }
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0 && s + 1 == a.n_steps) *a.step = done;
+        // every block reads the status after the same barrier, so all stop together
+        if (energy && *(volatile uint32_t *)a.status != 0u) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *a.step = done;
+            return;
+        }
+    }
+}
+
+int stepper_grid(const mdpf_ctx *ctx) {
+    int dev = ctx->device, sms = 0, occ = 0, coop = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_plain_persistent, kStepThreads, 0) != cudaSuccess)
+        return 0;
+    if (occ < 1) return 0;
+    int want = (ctx->n_items + kStepWarps - 1) / kStepWarps;
+    if (want < 1) want = 1;
+    return want < sms ? want : sms;  // one block per SM keeps one barrier arrival per SM
+}
+
+cudaError_t launch_plain_persistent(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t s) {
+    StepArgs a;
+    a.p = plain_dev(ctx, ctx->d_pos4);
+    a.n = ctx->n;
+    a.n_tiles = ctx->n_tiles;
+    a.dt = ctx->dt;
+    a.hdt_m = ctx->d_hdt_m;
+    a.mass = ctx->d_mass;
+    a.qs = ctx->d_charge_s;
+    a.P0 = ctx->d_pos4;
+    a.P1 = ctx->d_pos4_b;
+    a.x = ctx->d_x;
+    a.v = ctx->d_v;
+    a.fxA = ctx->d_fx_base;
+    a.fxB = ctx->d_fx_base + 3 * (size_t)ctx->n_pad;
+    a.tile_cnt = ctx->d_tile_cnt;
+    a.tile_expect = ctx->d_tile_expect;
+    a.inc_off = ctx->d_inc_off;
+    a.inc = ctx->d_inc;
+    a.part = ctx->d_part;
+    a.tile_e = ctx->d_tile_e;
+    a.trace_u = ctx->d_trace_u;
+    a.trace_k = ctx->d_trace_k;
+    a.trace_step = ctx->d_trace_step;
+    a.trace_cap = ctx->trace_cap;
+    a.energy_every = ctx->energy_every;
+    a.step = ctx->d_step;
+    a.status = ctx->d_status;
+    a.scalars = ctx->d_scalar;
+    a.frames = ctx->frames;
+    a.record_every = ctx->frames.cap > 0 ? ctx->record_every : 0;
+    a.bar = reinterpret_cast<unsigned long long *>(ctx->d_barrier);
+    a.n_steps = n_steps;
+    a.limit_ns = 1000000000LL;  // 1 s per barrier wait
+    cudaError_t e = cudaMemsetAsync(ctx->d_barrier, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)k_plain_persistent, dim3(ctx->step_grid), dim3(kStepThreads),
+                                       args, 0, s);
+}
+
+}  // namespace mdpf

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of libmdpf (include/mdpf.h), same names as the C ABI.
+
+Only argument marshalling happens here; every step of the path runs in the
+CUDA kernels of the library.  There is no fallback: if ``libmdpf.so`` is
+missing or cannot be loaded, loading the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdpf.so")
+
+MDPF_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NEIGHBOR_OVERFLOW", -5: "NONFINITE", -6: "TIMEOUT",
+    -7: "OUT_OF_RANGE", -8: "UNSUPPORTED",
+}
+MDPF_STATUS_NONFINITE = 0x1
+MDPF_STATUS_NEIGHBOR_OVERFLOW = 0x2
+MDPF_STATUS_TIMEOUT = 0x4
+MDPF_STATUS_OUT_OF_RANGE = 0x8
+MDPF_MODE_PLAIN = 0
+MDPF_MODE_LEARNED = 1
+MDPF_PROF_NONBONDED = 0
+MDPF_PROF_STEPPER = 1
+MDPF_PROF_STEP = 2
+MDPF_STEPPER_PERSISTENT = 0
+MDPF_STEPPER_KERNELS = 1
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f64 = ctypes.c_double
+
+
+class MdpfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class mdpf_topology(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", _i32), ("element", _vp), ("mass", _vp), ("charge", _vp),
+        ("n_bonds", _i32), ("bonds", _vp), ("bond_r0", _vp), ("bond_k", _vp),
+        ("angle_k", _f64), ("angle_theta0_deg", _f64),
+        ("lj_sigma", _f64 * 4), ("lj_eps", _f64 * 4),
+    ]
+
+
+class mdpf_params(ctypes.Structure):
+    _fields_ = [
+        ("mode", _i32), ("dt_fs", _f64), ("coulomb_k", _f64), ("trace_capacity", _i32),
+        ("record_every", _i32), ("max_frames", _i32), ("stepper", _i32), ("energy_every", _i32),
+    ]
+
+
+class mdpf_counters(ctypes.Structure):
+    _fields_ = [
+        ("steps", _i64), ("force_evals", _i64), ("frames", _i64), ("status", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32), ("potential", _f64), ("kinetic", _f64), ("h_initial", _f64),
+    ]
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libmdpf.so not built at %s (run python -m paper_2412_18271_b300.build)" % path)
+    lib = ctypes.CDLL(path)
+    sig = {
+        "mdpf_create": (ctypes.c_int, [ctypes.POINTER(mdpf_topology), ctypes.POINTER(mdpf_params), ctypes.POINTER(_vp)]),
+        "mdpf_destroy": (None, [_vp]),
+        "mdpf_last_error": (ctypes.c_char_p, [_vp]),
+        "mdpf_sizes": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mdpf_compute": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "mdpf_compute_device": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "mdpf_set_state": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mdpf_get_state": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mdpf_step": (ctypes.c_int, [_vp, _i64]),
+        "mdpf_step_async": (ctypes.c_int, [_vp, _i64, _vp]),
+        "mdpf_get_counters": (ctypes.c_int, [_vp, ctypes.POINTER(mdpf_counters)]),
+        "mdpf_get_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
+        "mdpf_get_frames": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+        "mdpf_get_exclusions": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
+        "mdpf_get_angles": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+        "mdpf_debug_set_status": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+        "mdpf_debug_wait_timeout": (ctypes.c_int, [_vp, _i32]),
+        "mdpf_set_profiling": (ctypes.c_int, [_vp, _i32]),
+        "mdpf_get_profile": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Context:
+    """One mdpf context (a system on the current CUDA device)."""
+
+    def __init__(self, system, mode: int = MDPF_MODE_PLAIN, dt_fs: float = 0.5, coulomb_k: float = 0.0,
+                 trace_capacity: int = 0, record_every: int = 0, max_frames: int = 0,
+                 stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1):
+        L = lib()
+        s = system
+        self.n = int(s.element.shape[0])
+        self._keep = dict(
+            element=np.ascontiguousarray(s.element, dtype=np.int32),
+            mass=np.ascontiguousarray(s.mass, dtype=np.float64),
+            charge=np.ascontiguousarray(s.charge, dtype=np.float64),
+            bonds=np.ascontiguousarray(s.bonds, dtype=np.int32).reshape(-1, 2),
+            r0=np.ascontiguousarray(s.bond_r0, dtype=np.float64),
+            k=np.ascontiguousarray(s.bond_k, dtype=np.float64),
+        )
+        kp = self._keep
+        t = mdpf_topology()
+        t.n_atoms = self.n
+        t.element = kp["element"].ctypes.data
+        t.mass = kp["mass"].ctypes.data
+        t.charge = kp["charge"].ctypes.data
+        t.n_bonds = kp["bonds"].shape[0]
+        t.bonds = kp["bonds"].ctypes.data if kp["bonds"].size else None
+        t.bond_r0 = kp["r0"].ctypes.data if kp["r0"].size else None
+        t.bond_k = kp["k"].ctypes.data if kp["k"].size else None
+        t.angle_k = float(s.angle_k)
+        t.angle_theta0_deg = float(s.angle_theta0_deg)
+        for e in range(4):
+            t.lj_sigma[e] = float(s.lj_sigma[e])
+            t.lj_eps[e] = float(s.lj_eps[e])
+        p = mdpf_params()
+        p.mode = mode
+        p.dt_fs = dt_fs
+        p.coulomb_k = coulomb_k
+        p.trace_capacity = trace_capacity
+        p.record_every = record_every
+        p.max_frames = max_frames
+        p.stepper = stepper
+        p.energy_every = energy_every
+        h = _vp()
+        rc = L.mdpf_create(ctypes.byref(t), ctypes.byref(p), ctypes.byref(h))
+        if rc != MDPF_OK:
+            raise MdpfError(rc, L.mdpf_last_error(None).decode())
+        self._h = h
+        self.dt_fs = dt_fs
+        self.record_every = record_every
+        self.max_frames = max_frames
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mdpf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != MDPF_OK:
+            raise MdpfError(rc, lib().mdpf_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- the provider contract
+    def compute(self, pos):
+        """(E, F[N,3], terms) at host positions pos[N,3] (FP64)."""
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        e = ctypes.c_double()
+        f = np.zeros((self.n, 3))
+        terms = np.zeros(4)
+        self._check(lib().mdpf_compute(self._h, _ptr(x), ctypes.byref(e), _ptr(f), _ptr(terms)))
+        return e.value, f, dict(zip(("bond", "angle", "lj", "coulomb"), terms.tolist()))
+
+    def compute_device(self, d_pos: int, d_energy: int, d_forces: int, stream: int = 0):
+        """Device-pointer form (addresses as ints, e.g. tensor.data_ptr())."""
+        self._check(lib().mdpf_compute_device(self._h, _vp(d_pos), _vp(d_energy), _vp(d_forces), _vp(stream)))
+
+    def set_state(self, pos, vel):
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        v = np.ascontiguousarray(vel, dtype=np.float64).reshape(self.n, 3)
+        self._check(lib().mdpf_set_state(self._h, _ptr(x), _ptr(v)))
+
+    def get_state(self, pos=None, vel=None):
+        x = np.zeros((self.n, 3)) if pos is None else pos
+        v = np.zeros((self.n, 3)) if vel is None else vel
+        self._check(lib().mdpf_get_state(self._h, _ptr(x), _ptr(v)))
+        return x, v
+
+    def step(self, n_steps: int):
+        self._check(lib().mdpf_step(self._h, int(n_steps)))
+
+    def step_async(self, n_steps: int, stream: int = 0):
+        self._check(lib().mdpf_step_async(self._h, int(n_steps), _vp(stream)))
+
+    def counters(self) -> dict:
+        c = mdpf_counters()
+        self._check(lib().mdpf_get_counters(self._h, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in mdpf_counters._fields_ if k != "reserved"}
+
+    def trace(self, max_n: int = 1 << 20, with_steps: bool = False):
+        cap = max_n
+        U = np.zeros(cap)
+        K = np.zeros(cap)
+        st = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int64()
+        self._check(lib().mdpf_get_trace(self._h, _ptr(U), _ptr(K), _ptr(st), cap, ctypes.byref(n)))
+        if with_steps:
+            return U[:n.value], K[:n.value], st[:n.value]
+        return U[:n.value], K[:n.value]
+
+    def frames(self, max_n: int | None = None):
+        m = self.max_frames if max_n is None else max_n
+        pos = np.zeros((max(m, 1), self.n, 3))
+        en = np.zeros(max(m, 1))
+        frc = np.zeros((max(m, 1), self.n, 3), dtype=np.float32)
+        st = np.zeros(max(m, 1), dtype=np.int64)
+        n = ctypes.c_int64()
+        self._check(lib().mdpf_get_frames(self._h, m, _ptr(pos), _ptr(en), _ptr(frc), _ptr(st), ctypes.byref(n)))
+        k = n.value
+        return pos[:k], en[:k], frc[:k], st[:k]
+
+    def exclusions(self):
+        tot = ctypes.c_int64()
+        self._check(lib().mdpf_get_exclusions(self._h, None, None, 0, ctypes.byref(tot)))
+        off = np.zeros(self.n + 1, dtype=np.int32)
+        idx = np.zeros(max(tot.value, 1), dtype=np.int32)
+        self._check(lib().mdpf_get_exclusions(self._h, _ptr(off), _ptr(idx), idx.size, ctypes.byref(tot)))
+        return off, idx[:tot.value]
+
+    def angles(self):
+        na = ctypes.c_int64()
+        self._check(lib().mdpf_get_angles(self._h, None, 0, ctypes.byref(na)))
+        out = np.zeros((max(na.value, 1), 3), dtype=np.int32)
+        self._check(lib().mdpf_get_angles(self._h, _ptr(out), out.shape[0], ctypes.byref(na)))
+        return out[:na.value]
+
+    def debug_set_status(self, bits: int):
+        self._check(lib().mdpf_debug_set_status(self._h, bits))
+
+    def debug_wait_timeout(self, limit_us: int):
+        return lib().mdpf_debug_wait_timeout(self._h, int(limit_us))
+
+    def set_profiling(self, enable: bool):
+        self._check(lib().mdpf_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, slot: int):
+        """(total_ms, launches) of a profiled kernel slot since profiling was enabled."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(lib().mdpf_get_profile(self._h, slot, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
