@@ -248,3 +248,274 @@ void orc_vv_run(const orc_system *s, double dt, int32_t n_steps, double *x, doub
     if (f_out) memcpy(f_out, f, sizeof(double) * 3 * (size_t)n);
     free(f);
 }
+
+/* ====================================================================
+ * Learned potential: symmetry-function features + per-element MLP.
+ *
+ * The paper's force module is an ML force field called from the engine each
+ * step (Results, "Example: Ethanol"); its architecture is not given there.
+ * The stand-in evaluated here is an ANI-style potential (Smith et al. 2017):
+ *   radial    G[i, 16 Zj + k]           = sum_j  exp(-eta_R (r_ij - R_k)^2) fc_R(r_ij)
+ *   angular   G[i, 64 + 32 P + 8 m + p] = sum_{j<k} 2^(1-zeta) (1 + cos(theta - theta_p))^zeta
+ *                                         * exp(-eta_A ((r_ij + r_ik)/2 - R_m)^2) fc_A(r_ij) fc_A(r_ik)
+ *   with theta = acos(0.95 cos(theta_ijk)), P the unordered element pair of
+ *   (Zj, Zk) in the order HH HC HN HO CC CN CO NN NO OO, fc(r) = cos(pi r/rc)/2 + 1/2
+ *   for r < rc, 0 otherwise.
+ *   E = sum_i [ W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0 ]_{element of i}
+ * Forces are -dE/dx through the analytic feature derivatives.
+ * ==================================================================== */
+
+#define ORC_NFEAT 384
+#define ORC_NRAD 16
+#define ORC_RC_R 5.2
+#define ORC_RC_A 3.5
+#define ORC_ETA_R 16.0
+#define ORC_ETA_A 8.0
+#define ORC_ZETA 32.0
+#define ORC_ANG_SCALE 0.95
+#define ORC_PI 3.14159265358979323846
+
+static double orc_rk(int k) { return 0.9 + k * (ORC_RC_R - 0.9) / 16.0; }
+static double orc_rm(int m) { return 0.9 + m * (ORC_RC_A - 0.9) / 4.0; }
+static double orc_thp(int p) { return (2 * p + 1) * ORC_PI / 16.0; }
+
+static double orc_fc(double r, double rc) { return r < rc ? 0.5 * cos(ORC_PI * r / rc) + 0.5 : 0.0; }
+static double orc_dfc(double r, double rc) { return r < rc ? -0.5 * ORC_PI / rc * sin(ORC_PI * r / rc) : 0.0; }
+
+/* unordered element pair index for a <= b: HH HC HN HO CC CN CO NN NO OO */
+static int orc_pair(int a, int b) {
+    if (a > b) { int t = a; a = b; b = t; }
+    static const int base[4] = {0, 4, 7, 9};
+    return base[a] + (b - a);
+}
+
+/*
+ * Neighbour list by brute force with the single-precision predicate
+ *   dx = fl(x_j - x_i) (FP32 coordinates), d2 = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)),
+ *   neighbour iff d2 < rc2 (rc2 given in FP32), j != i.
+ * Rows ascending.  Returns the total count or -1 if a row exceeds max_per_atom.
+ */
+int orc_neighbors(int32_t n, const float *x, float rc2, int32_t max_per_atom, int32_t *count, int32_t *idx) {
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        int m = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            float dx = x[3 * j] - x[3 * i];
+            float dy = x[3 * j + 1] - x[3 * i + 1];
+            float dz = x[3 * j + 2] - x[3 * i + 2];
+            float sx = dx * dx;
+            float sy = dy * dy;
+            float sz = dz * dz;
+            float d2 = sx + sy;
+            d2 = d2 + sz;
+            if (d2 < rc2) {
+                if (m >= max_per_atom) return -1;
+                idx[(size_t)i * max_per_atom + m] = j;
+                m++;
+            }
+        }
+        count[i] = m;
+        total += m;
+    }
+    return total;
+}
+
+/*
+ * Per-term visitor.  For atom i, every term T of feature f that involves atoms
+ * (i, j[, k]) is visited with its value and its gradients with respect to the
+ * positions of the atoms involved.  mode 0: accumulate G; mode 1: forces
+ * F -= w[i,f] dT/dx; mode 2: JVP Gdot[i,f] += dT/dx . u.
+ */
+static void orc_feature_pass(int n, const int32_t *el, const double *x, int mode, const double *w, const double *u,
+                             double *out) {
+    for (int i = 0; i < n; ++i) {
+        const double *xi = x + 3 * i;
+        /* radial */
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3], r = 0;
+            for (int c = 0; c < 3; ++c) { d[c] = x[3 * j + c] - xi[c]; r += d[c] * d[c]; }
+            r = sqrt(r);
+            if (!(r < ORC_RC_R)) continue;
+            for (int k = 0; k < ORC_NRAD; ++k) {
+                int f = 16 * el[j] + k;
+                double e = exp(-ORC_ETA_R * (r - orc_rk(k)) * (r - orc_rk(k)));
+                double T = e * orc_fc(r, ORC_RC_R);
+                double dT = e * (-2.0 * ORC_ETA_R * (r - orc_rk(k)) * orc_fc(r, ORC_RC_R) + orc_dfc(r, ORC_RC_R));
+                /* dT/dx_j = dT * d/r, dT/dx_i = -dT * d/r */
+                if (mode == 0) out[(size_t)i * ORC_NFEAT + f] += T;
+                else if (mode == 1) {
+                    double wf = w[(size_t)i * ORC_NFEAT + f];
+                    for (int c = 0; c < 3; ++c) {
+                        out[3 * j + c] -= wf * dT * d[c] / r;
+                        out[3 * i + c] += wf * dT * d[c] / r;
+                    }
+                } else {
+                    double s = 0;
+                    for (int c = 0; c < 3; ++c) s += dT * d[c] / r * (u[3 * j + c] - u[3 * i + c]);
+                    out[(size_t)i * ORC_NFEAT + f] += s;
+                }
+            }
+        }
+        /* angular: unordered pairs j < k of neighbours within rc_A */
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dj[3], rj = 0;
+            for (int c = 0; c < 3; ++c) { dj[c] = x[3 * j + c] - xi[c]; rj += dj[c] * dj[c]; }
+            rj = sqrt(rj);
+            if (!(rj < ORC_RC_A)) continue;
+            for (int k = j + 1; k < n; ++k) {
+                if (k == i) continue;
+                double dk[3], rk = 0;
+                for (int c = 0; c < 3; ++c) { dk[c] = x[3 * k + c] - xi[c]; rk += dk[c] * dk[c]; }
+                rk = sqrt(rk);
+                if (!(rk < ORC_RC_A)) continue;
+                double uj[3], uk[3], ct = 0;
+                for (int c = 0; c < 3; ++c) { uj[c] = dj[c] / rj; uk[c] = dk[c] / rk; ct += uj[c] * uk[c]; }
+                /* d cos(theta_ijk) / d x_j, d x_k */
+                double dcj[3], dck[3];
+                for (int c = 0; c < 3; ++c) {
+                    dcj[c] = (uk[c] - ct * uj[c]) / rj;
+                    dck[c] = (uj[c] - ct * uk[c]) / rk;
+                }
+                double cs = ORC_ANG_SCALE * ct;
+                double sn = sqrt(1.0 - cs * cs);
+                double fj = orc_fc(rj, ORC_RC_A), fk = orc_fc(rk, ORC_RC_A);
+                double C = fj * fk;
+                double dCj = orc_dfc(rj, ORC_RC_A) * fk, dCk = fj * orc_dfc(rk, ORC_RC_A);
+                int P = orc_pair(el[j], el[k]);
+                double ravg = 0.5 * (rj + rk);
+                for (int m = 0; m < 4; ++m) {
+                    double B = exp(-ORC_ETA_A * (ravg - orc_rm(m)) * (ravg - orc_rm(m)));
+                    double dB = -ORC_ETA_A * (ravg - orc_rm(m)) * B;  /* dB/dr_ij = dB/dr_ik */
+                    for (int p = 0; p < 8; ++p) {
+                        int f = 64 + 32 * P + 8 * m + p;
+                        double cp = cos(orc_thp(p)), sp = sin(orc_thp(p));
+                        double base = 1.0 + cs * cp + sn * sp;      /* 1 + cos(theta - theta_p) */
+                        double A = pow(2.0, 1.0 - ORC_ZETA) * pow(base, ORC_ZETA);
+                        double dAdcs = pow(2.0, 1.0 - ORC_ZETA) * ORC_ZETA * pow(base, ORC_ZETA - 1.0) * (cp - cs / sn * sp);
+                        double T = A * B * C;
+                        if (mode == 0) { out[(size_t)i * ORC_NFEAT + f] += T; continue; }
+                        /* gradient of T with respect to x_j and x_k; x_i gets minus their sum */
+                        double gj[3], gk[3];
+                        for (int c = 0; c < 3; ++c) {
+                            gj[c] = dAdcs * ORC_ANG_SCALE * dcj[c] * B * C + A * dB * uj[c] * C + A * B * dCj * uj[c];
+                            gk[c] = dAdcs * ORC_ANG_SCALE * dck[c] * B * C + A * dB * uk[c] * C + A * B * dCk * uk[c];
+                        }
+                        if (mode == 1) {
+                            double wf = w[(size_t)i * ORC_NFEAT + f];
+                            for (int c = 0; c < 3; ++c) {
+                                out[3 * j + c] -= wf * gj[c];
+                                out[3 * k + c] -= wf * gk[c];
+                                out[3 * i + c] += wf * (gj[c] + gk[c]);
+                            }
+                        } else {
+                            double s = 0;
+                            for (int c = 0; c < 3; ++c)
+                                s += gj[c] * (u[3 * j + c] - u[3 * i + c]) + gk[c] * (u[3 * k + c] - u[3 * i + c]);
+                            out[(size_t)i * ORC_NFEAT + f] += s;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* G [n][384] */
+void orc_features(int32_t n, const int32_t *el, const double *x, double *G) {
+    memset(G, 0, sizeof(double) * (size_t)n * ORC_NFEAT);
+    orc_feature_pass(n, el, x, 0, NULL, NULL, G);
+}
+
+/* F [n][3] = -sum_{i,f} w[i,f] dG[i,f]/dx  (w = dE/dG) */
+void orc_feature_forces(int32_t n, const int32_t *el, const double *x, const double *w, double *F) {
+    memset(F, 0, sizeof(double) * 3 * (size_t)n);
+    orc_feature_pass(n, el, x, 1, w, NULL, F);
+}
+
+/* Gdot [n][384] = sum_a dG[i,f]/dx_a . u_a */
+void orc_feature_jvp(int32_t n, const int32_t *el, const double *x, const double *u, double *Gdot) {
+    memset(Gdot, 0, sizeof(double) * (size_t)n * ORC_NFEAT);
+    orc_feature_pass(n, el, x, 2, NULL, u, Gdot);
+}
+
+/* ---------------------------------------------------------------- MLP */
+
+typedef struct {
+    int32_t n_feat, h1, h2;
+    double alpha;          /* CELU alpha */
+    const double *W1[4];   /* [h1][n_feat] */
+    const double *b1[4];   /* [h1] */
+    const double *W2[4];   /* [h2][h1] */
+    const double *b2[4];   /* [h2] */
+    const double *W3[4];   /* [h2] */
+    double b3[4];
+    double e0[4];
+} orc_mlp;
+
+static double orc_celu(double z, double a) { return z > 0 ? z : a * (exp(z / a) - 1.0); }
+static double orc_dcelu(double z, double a) { return z >= 0 ? 1.0 : exp(z / a); }
+
+/*
+ * Per-atom energies E_i (optional) and input gradients dEdG [n][n_feat]
+ * (optional); returns sum_i E_i.
+ *   h1 = W1 G + b1, a1 = celu(h1); h2 = W2 a1 + b2, a2 = celu(h2); E = W3 . a2 + b3 + e0
+ *   dE/dG = W1^T [celu'(h1) * W2^T (celu'(h2) * W3)]
+ */
+double orc_mlp_energy(const orc_mlp *M, int32_t n, const int32_t *el, const double *G, double *Ei, double *dEdG) {
+    const int F = M->n_feat, H1 = M->h1, H2 = M->h2;
+    double *h1 = (double *)malloc(sizeof(double) * H1), *a1 = (double *)malloc(sizeof(double) * H1);
+    double *h2 = (double *)malloc(sizeof(double) * H2), *a2 = (double *)malloc(sizeof(double) * H2);
+    double *d2 = (double *)malloc(sizeof(double) * H2), *d1 = (double *)malloc(sizeof(double) * H1);
+    double total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int e = el[i];
+        const double *g = G + (size_t)i * F;
+        for (int a = 0; a < H1; ++a) {
+            double s = M->b1[e][a];
+            for (int f = 0; f < F; ++f) s += M->W1[e][(size_t)a * F + f] * g[f];
+            h1[a] = s;
+            a1[a] = orc_celu(s, M->alpha);
+        }
+        for (int b = 0; b < H2; ++b) {
+            double s = M->b2[e][b];
+            for (int a = 0; a < H1; ++a) s += M->W2[e][(size_t)b * H1 + a] * a1[a];
+            h2[b] = s;
+            a2[b] = orc_celu(s, M->alpha);
+        }
+        double E = M->b3[e] + M->e0[e];
+        for (int b = 0; b < H2; ++b) E += M->W3[e][b] * a2[b];
+        if (Ei) Ei[i] = E;
+        total += E;
+        if (dEdG) {
+            for (int b = 0; b < H2; ++b) d2[b] = M->W3[e][b] * orc_dcelu(h2[b], M->alpha);
+            for (int a = 0; a < H1; ++a) {
+                double s = 0;
+                for (int b = 0; b < H2; ++b) s += M->W2[e][(size_t)b * H1 + a] * d2[b];
+                d1[a] = s * orc_dcelu(h1[a], M->alpha);
+            }
+            for (int f = 0; f < F; ++f) {
+                double s = 0;
+                for (int a = 0; a < H1; ++a) s += M->W1[e][(size_t)a * F + f] * d1[a];
+                dEdG[(size_t)i * F + f] = s;
+            }
+        }
+    }
+    free(h1); free(a1); free(h2); free(a2); free(d2); free(d1);
+    return total;
+}
+
+/* Learned energy and forces at x: E returned, F [n][3] = -dE/dx. */
+double orc_learned_energy_forces(const orc_mlp *M, int32_t n, const int32_t *el, const double *x, double *F,
+                                 double *G_out) {
+    double *G = G_out ? G_out : (double *)malloc(sizeof(double) * (size_t)n * ORC_NFEAT);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n * ORC_NFEAT);
+    orc_features(n, el, x, G);
+    double E = orc_mlp_energy(M, n, el, G, NULL, w);
+    if (F) orc_feature_forces(n, el, x, w, F);
+    free(w);
+    if (!G_out) free(G);
+    return E;
+}

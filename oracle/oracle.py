@@ -158,3 +158,107 @@ class Plain:
         f = np.zeros((self.n, 3))
         lib().orc_vv_run(ctypes.byref(self._st), ctypes.c_double(dt), n_steps, _p(x), _p(v), _p(U), _p(K), _p(f))
         return x, v, U[:n_steps], K[:n_steps], f
+
+
+# ---------------------------------------------------------------- learned potential
+
+N_FEAT = 384
+RC_LIST = 6.2           # neighbour-list radius (5.2 A cutoff + 1 A skin)
+
+
+class OrcMLP(ctypes.Structure):
+    _fields_ = [
+        ("n_feat", ctypes.c_int32), ("h1", ctypes.c_int32), ("h2", ctypes.c_int32), ("alpha", ctypes.c_double),
+        ("W1", ctypes.c_void_p * 4), ("b1", ctypes.c_void_p * 4), ("W2", ctypes.c_void_p * 4),
+        ("b2", ctypes.c_void_p * 4), ("W3", ctypes.c_void_p * 4), ("b3", ctypes.c_double * 4),
+        ("e0", ctypes.c_double * 4),
+    ]
+
+
+def _learned_lib():
+    L = lib()
+    for name in ("orc_mlp_energy", "orc_learned_energy_forces"):
+        getattr(L, name).restype = ctypes.c_double
+    for name in ("orc_features", "orc_feature_forces", "orc_feature_jvp"):
+        getattr(L, name).restype = None
+    L.orc_neighbors.restype = ctypes.c_int
+    return L
+
+
+def neighbors(pos32, rc_list: float = RC_LIST, max_per_atom: int = 256):
+    """Brute-force neighbour rows (list of ascending int arrays) with the FP32 predicate
+    d2 = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) < fl32(rc^2)."""
+    x = np.ascontiguousarray(pos32, dtype=np.float32).reshape(-1, 3)
+    n = x.shape[0]
+    cnt = np.zeros(n, dtype=np.int32)
+    idx = np.zeros((n, max_per_atom), dtype=np.int32)
+    rc2 = np.float32(rc_list * rc_list)
+    tot = _learned_lib().orc_neighbors(n, _p(x), ctypes.c_float(rc2), max_per_atom, _p(cnt), _p(idx))
+    if tot < 0:
+        raise RuntimeError("orc_neighbors: row longer than max_per_atom")
+    return [idx[i, :cnt[i]].copy() for i in range(n)]
+
+
+def features(element, pos):
+    el = np.ascontiguousarray(element, dtype=np.int32)
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    G = np.zeros((x.shape[0], N_FEAT))
+    _learned_lib().orc_features(x.shape[0], _p(el), _p(x), _p(G))
+    return G
+
+
+def feature_forces(element, pos, w):
+    """F = -sum_{i,f} w[i,f] dG[i,f]/dx."""
+    el = np.ascontiguousarray(element, dtype=np.int32)
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros_like(x)
+    _learned_lib().orc_feature_forces(x.shape[0], _p(el), _p(x), _p(w), _p(F))
+    return F
+
+
+def feature_jvp(element, pos, u):
+    """Gdot[i,f] = sum_a dG[i,f]/dx_a . u_a."""
+    el = np.ascontiguousarray(element, dtype=np.int32)
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+    Gd = np.zeros((x.shape[0], N_FEAT))
+    _learned_lib().orc_feature_jvp(x.shape[0], _p(el), _p(x), _p(u), _p(Gd))
+    return Gd
+
+
+class Learned:
+    """The learned potential of a ``model.Model`` evaluated in FP64 (weights taken as stored)."""
+
+    def __init__(self, model):
+        self.m = model
+        self._arr = {}
+        st = OrcMLP()
+        st.n_feat, st.h1, st.h2, st.alpha = N_FEAT, model.W1.shape[1], model.W2.shape[1], float(model.alpha)
+        for e in range(4):
+            for name in ("W1", "b1", "W2", "b2", "W3"):
+                a = np.ascontiguousarray(getattr(model, name)[e], dtype=np.float64)
+                self._arr[(name, e)] = a
+                getattr(st, name)[e] = a.ctypes.data
+            st.b3[e] = float(model.b3[e])
+            st.e0[e] = float(model.e0[e])
+        self._st = st
+
+    def mlp(self, element, G):
+        """(E_total, E_i [N], dE/dG [N,384])."""
+        el = np.ascontiguousarray(element, dtype=np.int32)
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        n = el.shape[0]
+        Ei = np.zeros(n)
+        dG = np.zeros((n, N_FEAT))
+        E = _learned_lib().orc_mlp_energy(ctypes.byref(self._st), n, _p(el), _p(G), _p(Ei), _p(dG))
+        return E, Ei, dG
+
+    def energy_forces(self, element, pos):
+        """(E, F [N,3], G [N,384])."""
+        el = np.ascontiguousarray(element, dtype=np.int32)
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        F = np.zeros_like(x)
+        G = np.zeros((x.shape[0], N_FEAT))
+        E = _learned_lib().orc_learned_energy_forces(ctypes.byref(self._st), x.shape[0], _p(el), _p(x), _p(F), _p(G))
+        return E, F, G
