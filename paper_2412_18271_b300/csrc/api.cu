@@ -98,7 +98,7 @@ static void free_ctx(mdpf_ctx *c) {
                     c->d_tile_mask, c->d_tile_flag, c->d_items, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
                     c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_step, c->d_status,
                     c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e, c->d_tile_cnt,
-                    c->d_tile_expect, c->d_inc_off, c->d_inc, c->frames.pos, c->frames.energy, c->frames.forces,
+                    c->d_tile_expect, c->d_own_off, c->d_own, c->d_touch_off, c->d_touch, c->frames.pos, c->frames.energy, c->frames.forces,
                     c->frames.step};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -297,43 +297,54 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
                 expect[it.y]++;
             }
         }
-        // bonded incidence of every atom: (term << 2) | role; the angle list comes from the device
+        // bonded terms by owning tile (bond: first atom; angle: vertex) and the other tiles they touch;
+        // the angle list comes from the device
         std::vector<int4> angles(c->n_angles);
         if (c->n_angles > 0)
             CKC(cudaMemcpy(angles.data(), c->d_angles, sizeof(int4) * c->n_angles, cudaMemcpyDeviceToHost));
-        std::vector<int> inc_cnt(n + 1, 0);
+        std::vector<std::vector<int>> own(T), touch(T);
+        auto add_touch = [&](int t, int atom) {
+            const int u = atom / kTile;
+            if (u == t) return;
+            for (int v : touch[t])
+                if (v == u) return;
+            touch[t].push_back(u);
+        };
         for (int b = 0; b < t->n_bonds; ++b) {
-            inc_cnt[t->bonds[2 * b]]++;
-            inc_cnt[t->bonds[2 * b + 1]]++;
-        }
-        for (const int4 &an : angles) {
-            inc_cnt[an.x]++;
-            inc_cnt[an.y]++;
-            inc_cnt[an.z]++;
-        }
-        std::vector<int> inc_off(n + 1, 0);
-        for (int i = 0; i < n; ++i) inc_off[i + 1] = inc_off[i] + inc_cnt[i];
-        std::vector<int> inc(inc_off[n] + 1), fillp(inc_off.begin(), inc_off.end() - 1);
-        for (int b = 0; b < t->n_bonds; ++b) {
-            inc[fillp[t->bonds[2 * b]]++] = (b << 2) | 0;
-            inc[fillp[t->bonds[2 * b + 1]]++] = (b << 2) | 1;
+            const int owner = t->bonds[2 * b] / kTile;
+            own[owner].push_back(b);
+            add_touch(owner, t->bonds[2 * b + 1]);
         }
         for (int k = 0; k < c->n_angles; ++k) {
-            const int code = (t->n_bonds + k) << 2;
-            inc[fillp[angles[k].x]++] = code | 0;
-            inc[fillp[angles[k].y]++] = code | 1;
-            inc[fillp[angles[k].z]++] = code | 2;
+            const int owner = angles[k].y / kTile;
+            own[owner].push_back(t->n_bonds + k);
+            add_touch(owner, angles[k].x);
+            add_touch(owner, angles[k].z);
         }
-        CKC(dalloc(&c->d_part, 2 * (size_t)c->step_grid * 2));
+        std::vector<int> own_off(T + 1, 0), touch_off(T + 1, 0), own_flat, touch_flat;
+        for (int tt = 0; tt < T; ++tt) {
+            own_flat.insert(own_flat.end(), own[tt].begin(), own[tt].end());
+            touch_flat.insert(touch_flat.end(), touch[tt].begin(), touch[tt].end());
+            own_off[tt + 1] = (int)own_flat.size();
+            touch_off[tt + 1] = (int)touch_flat.size();
+            for (int u : touch[tt]) expect[u]++;  // the self item of tt also contributes to u
+        }
+        own_flat.push_back(0);
+        touch_flat.push_back(0);
+        CKC(dalloc(&c->d_part, 2 * (size_t)c->step_grid * 4));
         CKC(dalloc(&c->d_tile_e, 2 * (size_t)T * 4));
         CKC(dalloc(&c->d_tile_cnt, T));
         CKC(dalloc(&c->d_tile_expect, T));
-        CKC(dalloc(&c->d_inc_off, n + 1));
-        CKC(dalloc(&c->d_inc, inc.size()));
+        CKC(dalloc(&c->d_own_off, T + 1));
+        CKC(dalloc(&c->d_own, own_flat.size()));
+        CKC(dalloc(&c->d_touch_off, T + 1));
+        CKC(dalloc(&c->d_touch, touch_flat.size()));
         CKC(dalloc(&c->d_pos4_b, np));
         CKC(cudaMemcpy(c->d_tile_expect, expect.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_inc_off, inc_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_inc, inc.data(), sizeof(int) * inc.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_own_off, own_off.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_own, own_flat.data(), sizeof(int) * own_flat.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_touch_off, touch_off.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_touch, touch_flat.data(), sizeof(int) * touch_flat.size(), cudaMemcpyHostToDevice));
         CKC(cudaMemset(c->d_tile_cnt, 0, sizeof(unsigned int) * T));
         CKC(cudaMemset(c->d_tile_e, 0, sizeof(double) * 2 * T * 4));
     }

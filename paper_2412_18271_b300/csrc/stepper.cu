@@ -8,11 +8,12 @@
 // Each MD step costs one grid barrier:
 //   phase B(s)   every warp evaluates its all-pairs work items at x_{s+1}
 //                (FP32 copy P[s & 1]) and adds the forces into buffer
-//                buf(s) (int64 fixed point).  After each item the warp bumps
-//                the contribution counter of every 32-atom tile the item
-//                touched (release); the warp that brings a tile's counter to
-//                its expected value (acquire) owns the tile's completion:
-//                  F = F_pairs + bonded forces of the tile's atoms,
+//                buf(s) (int64 fixed point); the warp of a tile's self item
+//                also evaluates the bonded terms that tile owns (bond: first
+//                atom; angle: vertex).  After each item the warp bumps the
+//                contribution counter of every 32-atom tile the item touched
+//                (release); the warp that brings a tile's counter to its
+//                expected value (acquire) owns the tile's completion:
 //                  v_{s+1} = v_{s+1/2} + dt/2 a          (end of step s, K)
 //                  v_{s+3/2} = v_{s+1} + dt/2 a; x_{s+2} = x_{s+1} + dt v
 //                  FP32 copy of x_{s+2} into P[(s + 1) & 1]  (start of step s+1)
@@ -21,9 +22,10 @@
 // the state buffer by mdpf_set_state or by the previous launch; the last step
 // writes F(x_n) back there instead.
 //
-// Forces are integer sums, and every energy is summed in a fixed order (pair
-// energies per block in block order, bonded and kinetic energies per tile in
-// tile order), so trajectories and energies are reproducible bit for bit.
+// Forces are integer sums of the same FP32 terms the kernel-sequence stepper
+// adds, so both steppers produce the same trajectory bit for bit; energies are
+// summed in a fixed order (pair and bonded energies per block in block order,
+// kinetic energy per tile in tile order), so they are reproducible too.
 //
 // The grid barrier is a 64-bit arrival counter (release add, acquire poll)
 // that waits at most limit_ns; on time-out the block records
@@ -46,9 +48,10 @@ struct StepArgs {
     unsigned long long *fxB;      // accumulator of even steps
     unsigned int *tile_cnt;       // [T] contributions seen this step
     const int *tile_expect;       // [T] contributions per step
-    const int *inc_off, *inc;     // per-atom bonded incidence: (term << 2) | role
-    double *part;                 // [2][grid][2] per-block pair energies (LJ, Coulomb)
-    double *tile_e;               // [2][T][4] per-tile bond, angle, kinetic energy
+    const int *own_off, *own;     // bonded terms owned by each tile (CSR over tiles)
+    const int *touch_off, *touch; // other tiles those terms touch (CSR over tiles)
+    double *part;                 // [2][grid][4] per-block energies (bond, angle, LJ, Coulomb)
+    double *tile_e;               // [2][T][4] per-tile kinetic energy (slot 2)
     double *trace_u, *trace_k;
     int64_t *trace_step;
     int trace_cap;
@@ -107,86 +110,37 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
     return *s_fail == 0;
 }
 
-// Force on atom a from the bonded terms it takes part in (FP32), and the
-// energies of the terms it is designated for (bonds: first atom; angles:
-// vertex).
-__device__ __forceinline__ float3 bonded_on_atom(const PlainDev &p, const float4 *pos, const int *inc_off,
-                                                 const int *inc, int a, float &eb, float &ea) {
-    float3 f = make_float3(0.f, 0.f, 0.f);
-    for (int q = inc_off[a]; q < inc_off[a + 1]; ++q) {
-        const int code = inc[q], t = code >> 2, role = code & 3;
-        if (t < p.n_bonds) {
-            const int2 b = p.bonds[t];
-            const float4 xi = pos[b.x], xj = pos[b.y];
-            const float2 par = p.bond_par[t];
-            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float dr = r - par.x;
-            const float g = (role == 0 ? 1.f : -1.f) * par.y * dr / r;
-            f.x += g * dx;
-            f.y += g * dy;
-            f.z += g * dz;
-            if (role == 0) eb += 0.5f * par.y * dr * dr;
-        } else {
-            const int4 an = p.angles[t - p.n_bonds];
-            const float4 xa = pos[an.x], xv = pos[an.y], xb = pos[an.z];
-            const float ux = xa.x - xv.x, uy = xa.y - xv.y, uz = xa.z - xv.z;
-            const float wx = xb.x - xv.x, wy = xb.y - xv.y, wz = xb.z - xv.z;
-            const float ru = sqrtf(ux * ux + uy * uy + uz * uz), rw = sqrtf(wx * wx + wy * wy + wz * wz);
-            const float c = ux * wx + uy * wy + uz * wz;
-            const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-            const float cr = sqrtf(cx * cx + cy * cy + cz * cz);
-            const float th = atan2f(cr, c);
-            const float dth = th - p.angle_theta0;
-            const float cs = c / (ru * rw);
-            const float sn = cr / (ru * rw);
-            const float ga = p.angle_k * dth / (sn * ru);
-            const float gb = p.angle_k * dth / (sn * rw);
-            const float iu = 1.f / ru, iw = 1.f / rw;
-            const float fax = ga * (wx * iw - cs * ux * iu), fay = ga * (wy * iw - cs * uy * iu),
-                        faz = ga * (wz * iw - cs * uz * iu);
-            const float fbx = gb * (ux * iu - cs * wx * iw), fby = gb * (uy * iu - cs * wy * iw),
-                        fbz = gb * (uz * iu - cs * wz * iw);
-            if (role == 0) {
-                f.x += fax; f.y += fay; f.z += faz;
-            } else if (role == 2) {
-                f.x += fbx; f.y += fby; f.z += fbz;
-            } else {
-                f.x -= fax + fbx; f.y -= fay + fby; f.z -= faz + fbz;
-                ea += 0.5f * p.angle_k * dth * dth;
-            }
-        }
-    }
-    return f;
-}
-
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 
 // Completion of tile t by the warp that delivered its last contribution.
-__device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t s, const float4 *Pcur, float4 *Pnext,
+__device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t s, float4 *Pnext,
                                               unsigned long long *acc, bool energy, bool rec, int slot) {
     const int lane = threadIdx.x & 31;
     const int at = t * kTile + lane;
-    float eb = 0.f, ea = 0.f;
     double kin = 0.0;
     const bool last = s + 1 == a.n_steps;
     if (at < a.n) {
-        float3 fb = bonded_on_atom(a.p, Pcur, a.inc_off, a.inc, at, eb, ea);
         const double h = a.hdt_m[at];
+        unsigned long long fi[3];
         double f[3], v[3], x[3];
-        const float fbv[3] = {fb.x, fb.y, fb.z};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            f[q] = fx_val(__ldcg(&acc[3 * at + q])) + (double)fbv[q];
-            v[q] = __ldcg(&a.v[3 * at + q]) + h * f[q];  // v_{s+1}
+            fi[q] = __ldcg(&acc[3 * at + q]);
+            v[q] = __ldcg(&a.v[3 * at + q]);
+            x[q] = __ldcg(&a.x[3 * at + q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            f[q] = fx_val(fi[q]);
+            v[q] += h * f[q];  // v_{s+1}
             kin += v[q] * v[q];
         }
         kin *= 0.5 * a.mass[at] / kAcc;
         if (rec) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                a.frames.pos[((size_t)slot * a.n + at) * 3 + q] = __ldcg(&a.x[3 * at + q]);
+                a.frames.pos[((size_t)slot * a.n + at) * 3 + q] = x[q];
                 a.frames.forces[((size_t)slot * a.n + at) * 3 + q] = (float)f[q];
             }
         }
@@ -194,7 +148,7 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 v[q] += h * f[q];
-                x[q] = __ldcg(&a.x[3 * at + q]) + a.dt * v[q];
+                x[q] += a.dt * v[q];
                 a.x[3 * at + q] = x[q];
                 acc[3 * at + q] = 0ull;
             }
@@ -204,61 +158,64 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 acc[3 * at + q] = 0ull;
-                a.fxA[3 * at + q] = (unsigned long long)__double2ll_rn(f[q] * kFxScale);
+                a.fxA[3 * at + q] = fi[q];
             }
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) a.v[3 * at + q] = v[q];
-        if (!isfinite(kin + eb + ea)) atomicOr(a.status, MDPF_STATUS_NONFINITE);
+        if (!isfinite(kin)) atomicOr(a.status, MDPF_STATUS_NONFINITE);
     } else if (at < a.p.n_pad) {
         acc[3 * at] = acc[3 * at + 1] = acc[3 * at + 2] = 0ull;
     }
     if (energy) {
-        const double sb = warp_sum_d((double)eb), sa = warp_sum_d((double)ea), sk = warp_sum_d(kin);
-        if (lane == 0) {
-            double *te = a.tile_e + ((size_t)(s & 1) * a.n_tiles + t) * 4;
-            te[0] = sb;
-            te[1] = sa;
-            te[2] = sk;
-        }
+        const double sk = warp_sum_d(kin);
+        if (lane == 0) a.tile_e[((size_t)(s & 1) * a.n_tiles + t) * 4 + 2] = sk;
     }
 }
 
-// Bump the counters of the tiles an item touched; complete every tile this
-// warp finished.
-__device__ __forceinline__ void item_done(const StepArgs &a, const int4 &item, int64_t s, const float4 *Pcur,
-                                          float4 *Pnext, unsigned long long *acc, bool energy, bool rec, int slot) {
+// Bump the counters of the tiles an item touched (one lane per tile, in
+// parallel); complete every tile whose last contribution this warp delivered.
+__device__ __forceinline__ void item_done(const StepArgs &a, const int4 &item, int64_t s, float4 *Pnext,
+                                          unsigned long long *acc, bool energy, bool rec, int slot) {
     const int lane = threadIdx.x & 31;
-    int tl[3], nt;
+    int base = 0, cnt;
     if (item.x == ITEM_OFF64) {
-        tl[0] = 2 * item.y; tl[1] = 2 * item.y + 1; tl[2] = item.z; nt = 3;
+        cnt = 3;
     } else if (item.x == ITEM_OFF32) {
-        tl[0] = item.y; tl[1] = item.z; tl[2] = 0; nt = 2;
+        cnt = 2;
     } else {
-        tl[0] = item.y; tl[1] = 0; tl[2] = 0; nt = 1;
+        base = a.touch_off[item.y];
+        cnt = 1 + a.touch_off[item.y + 1] - base;
     }
-    unsigned int mine = 0;
     __syncwarp();
-    if (lane == 0) {
-        __threadfence();  // release this warp's force additions
-        for (int k = 0; k < nt; ++k) {
-            const unsigned int old = atomicAdd(&a.tile_cnt[tl[k]], 1u);
-            if (old + 1 == (unsigned int)a.tile_expect[tl[k]]) mine |= 1u << k;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        int t = -1;
+        bool mine = false;
+        const int k = c0 + lane;
+        if (k < cnt) {
+            if (item.x == ITEM_OFF64) t = k == 0 ? 2 * item.y : (k == 1 ? 2 * item.y + 1 : item.z);
+            else if (item.x == ITEM_OFF32) t = k == 0 ? item.y : item.z;
+            else t = k == 0 ? item.y : a.touch[base + k - 1];
+            __threadfence();  // release this warp's force additions (ordered before by __syncwarp)
+            const unsigned int old = atomicAdd(&a.tile_cnt[t], 1u);
+            mine = old + 1 == (unsigned int)a.tile_expect[t];
         }
-    }
-    mine = __shfl_sync(0xffffffffu, mine, 0);
-    if (mine) __threadfence();  // acquire: every lane orders its reads of the tile after the counter
-    for (int k = 0; k < nt; ++k) {
-        if (!(mine & (1u << k))) continue;
-        complete_tile(a, tl[k], s, Pcur, Pnext, acc, energy, rec, slot);
-        __syncwarp();
-        if (lane == 0) a.tile_cnt[tl[k]] = 0u;
+        unsigned int bal = __ballot_sync(0xffffffffu, mine);
+        if (bal) __threadfence();  // acquire: every lane orders its reads of the tile after the counter
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int tt = __shfl_sync(0xffffffffu, t, src);
+            complete_tile(a, tt, s, Pnext, acc, energy, rec, slot);
+            __syncwarp();
+            if (lane == 0) a.tile_cnt[tt] = 0u;
+        }
     }
 }
 
 __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a) {
     __shared__ JTile jt[kStepWarps];
-    __shared__ double red[kStepWarps][2];
+    __shared__ double red[kStepWarps][4];
     __shared__ int s_fail;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -305,44 +262,47 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
         const int slot = rec ? (int)((done / a.record_every - 1) % a.frames.cap) : 0;
         PlainDev p = a.p;
         p.pos4 = Pcur;
-        float elj = 0.f, ec = 0.f;
+        float elj = 0.f, ec = 0.f, eb = 0.f, ea = 0.f;
         bool bad = false;
         for (int it = gwarp; it < p.n_items; it += nwarps) {
             if (energy)
                 nonbonded_item<true>(p, it, lane, jt[w], acc, elj, ec, bad);
             else
                 nonbonded_item<false>(p, it, lane, jt[w], acc, elj, ec, bad);
-            item_done(a, p.items[it], s, Pcur, Pnext, acc, energy, rec, slot);
+            const int4 item = p.items[it];
+            if (item.x == ITEM_SELF)
+                for (int q = a.own_off[item.y] + lane; q < a.own_off[item.y + 1]; q += 32)
+                    bonded_term(p, a.own[q], acc, eb, ea);
+            item_done(a, item, s, Pnext, acc, energy, rec, slot);
         }
+        bad |= !isfinite(eb + ea);
         if (bad) atomicOr(a.status, MDPF_STATUS_NONFINITE);
         if (energy) {
-            double vl = warp_sum_d((double)elj * (1.0 / 6.0)), vc = warp_sum_d((double)ec);
-            if (lane == 0) {
-                red[w][0] = vl;
-                red[w][1] = vc;
-            }
+            double v4[4] = {warp_sum_d((double)eb), warp_sum_d((double)ea), warp_sum_d((double)elj * (1.0 / 6.0)),
+                            warp_sum_d((double)ec)};
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) red[w][k] = v4[k];
             __syncthreads();
-            if (threadIdx.x < 2) {
+            if (threadIdx.x < 4) {
                 double sum = 0.0;
                 for (int q = 0; q < kStepWarps; ++q) sum += red[q][threadIdx.x];
-                a.part[((size_t)(s & 1) * gridDim.x + blockIdx.x) * 2 + threadIdx.x] = sum;
+                a.part[((size_t)(s & 1) * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = sum;
             }
         }
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
         // ---- energies of step `done` (block 0, warp 0), read after the barrier
         if (energy && blockIdx.x == 0 && w == 0) {
-            const double *pp = a.part + (size_t)(s & 1) * gridDim.x * 2;
+            const double *pp = a.part + (size_t)(s & 1) * gridDim.x * 4;
             const double *te = a.tile_e + (size_t)(s & 1) * a.n_tiles * 4;
             double sl = 0, sc = 0, sb = 0, sa = 0, sk = 0;
             for (int b = lane; b < (int)gridDim.x; b += 32) {
-                sl += pp[2 * b];
-                sc += pp[2 * b + 1];
+                sb += pp[4 * b];
+                sa += pp[4 * b + 1];
+                sl += pp[4 * b + 2];
+                sc += pp[4 * b + 3];
             }
-            for (int t = lane; t < a.n_tiles; t += 32) {
-                sb += te[4 * t];
-                sa += te[4 * t + 1];
-                sk += te[4 * t + 2];
-            }
+            for (int t = lane; t < a.n_tiles; t += 32) sk += te[4 * t + 2];
             sl = warp_sum_d(sl);
             sc = warp_sum_d(sc);
             sb = warp_sum_d(sb);
@@ -401,8 +361,10 @@ cudaError_t launch_plain_persistent(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t
     a.fxB = ctx->d_fx_base + 3 * (size_t)ctx->n_pad;
     a.tile_cnt = ctx->d_tile_cnt;
     a.tile_expect = ctx->d_tile_expect;
-    a.inc_off = ctx->d_inc_off;
-    a.inc = ctx->d_inc;
+    a.own_off = ctx->d_own_off;
+    a.own = ctx->d_own;
+    a.touch_off = ctx->d_touch_off;
+    a.touch = ctx->d_touch;
     a.part = ctx->d_part;
     a.tile_e = ctx->d_tile_e;
     a.trace_u = ctx->d_trace_u;

@@ -216,16 +216,11 @@ def test_checkpoint_resume_is_bit_identical(stepper):
     c.set_state(xm, vm)
     c.step(80)
     xc, vc = c.get_state()
-    if stepper == mdpf.MDPF_STEPPER_KERNELS:
-        assert np.array_equal(xa, xc) and np.array_equal(va, vc)
-    else:
-        # the persistent stepper adds bonded forces in FP32 per atom, while set_state's
-        # evaluation sums them in fixed point: the restart differs by rounding only
-        assert np.abs(xa - xc).max() < 1e-6 and np.abs(va - vc).max() < 1e-6
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc)
 
 
 def test_steppers_agree_and_split_calls_agree():
-    # one persistent launch of 150 steps == 3 launches of 50 (same kernel), ~= the kernel-sequence stepper
+    # one persistent launch of 150 steps == 3 launches of 50 == the kernel-sequence stepper
     s = synth.workload("cluster2048")
     v0 = synth.velocities(s.mass, s.pos, 300.0, seed=100)
     a = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_PERSISTENT)
@@ -241,14 +236,13 @@ def test_steppers_agree_and_split_calls_agree():
     xa, va = a.get_state()
     xb, vb = b.get_state()
     xc, vc = c.get_state()
-    # a launch boundary rounds F(x_n) to fixed point (2^-32): equal up to that rounding
-    assert np.abs(xa - xb).max() < 1e-8 and np.abs(va - vb).max() < 1e-8
-    # the two steppers round the bonded sums differently; the hot cluster amplifies that
-    # chaotically, so they agree to the paper's trajectory criterion (1e-3 A), not bitwise
-    assert np.abs(xa - xc).max() < 1e-3
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    # both steppers add the same FP32 terms as integers and update the state with the same
+    # FP64 operations; any difference would come from instruction contraction only
+    assert np.abs(xa - xc).max() < 1e-9 and np.abs(va - vc).max() < 1e-9
     Ua, Ka = a.trace()
     Uc, Kc = c.trace()
-    assert np.abs(Ua - Uc).max() / s.n_atoms < 1e-4
+    assert np.abs(Ua - Uc).max() / s.n_atoms < 1e-7
 
 
 def test_persistent_is_reproducible():
