@@ -38,7 +38,7 @@ __device__ __forceinline__ void bonded_term(const PlainDev &p, int t, unsigned l
         float4 xi = p.pos4[b.x], xj = p.pos4[b.y];
         float2 par = p.bond_par[t];
         float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        float r = sqrtf(dx * dx + dy * dy + dz * dz);
+        float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         float dr = r - par.x;
         eb += 0.5f * par.y * dr * dr;
         float g = par.y * dr / r;
@@ -53,10 +53,10 @@ __device__ __forceinline__ void bonded_term(const PlainDev &p, int t, unsigned l
         float4 xa = p.pos4[an.x], xv = p.pos4[an.y], xb = p.pos4[an.z];
         float ux = xa.x - xv.x, uy = xa.y - xv.y, uz = xa.z - xv.z;
         float wx = xb.x - xv.x, wy = xb.y - xv.y, wz = xb.z - xv.z;
-        float ru = sqrtf(ux * ux + uy * uy + uz * uz), rw = sqrtf(wx * wx + wy * wy + wz * wz);
-        float c = ux * wx + uy * wy + uz * wz;
-        float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
-        float cr = sqrtf(cx * cx + cy * cy + cz * cz);
+        float ru = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), rw = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+        float c = fmaf(ux, wx, fmaf(uy, wy, uz * wz));
+        float cx = fmaf(uy, wz, -uz * wy), cy = fmaf(uz, wx, -ux * wz), cz = fmaf(ux, wy, -uy * wx);
+        float cr = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
         float th = atan2f(cr, c);
         float dth = th - p.angle_theta0;
         ea += 0.5f * p.angle_k * dth * dth;

@@ -106,8 +106,8 @@ __global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over
     double p[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double vc = v[3 * a + c] + h * fx_val(fx[3 * a + c]);
-        double xc = x[3 * a + c] + dt * vc;
+        double vc = fma(h, fx_val(fx[3 * a + c]), v[3 * a + c]);
+        double xc = fma(dt, vc, x[3 * a + c]);
         v[3 * a + c] = vc;
         x[3 * a + c] = xc;
         p[c] = xc;
@@ -127,7 +127,7 @@ __global__ void k_kick(int n, const double *hdt_over_m, const double *mass, doub
         for (int c = 0; c < 3; ++c) {
             double vc = v[3 * a + c];
             if (do_kick) {
-                vc += h * fx_val(fx[3 * a + c]);
+                vc = fma(h, fx_val(fx[3 * a + c]), vc);
                 v[3 * a + c] = vc;
             }
             ke += vc * vc;

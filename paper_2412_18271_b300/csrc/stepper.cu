@@ -23,7 +23,9 @@
 // writes F(x_n) back there instead.
 //
 // Forces are integer sums of the same FP32 terms the kernel-sequence stepper
-// adds, so both steppers produce the same trajectory bit for bit; energies are
+// adds, and every state update is an explicit FMA (v = fma(h, f, v),
+// x = fma(dt, v, x)) in both, so both steppers produce the same trajectory bit
+// for bit; energies are
 // summed in a fixed order (pair and bonded energies per block in block order,
 // kinetic energy per tile in tile order), so they are reproducible too.
 //
@@ -133,7 +135,7 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             f[q] = fx_val(fi[q]);
-            v[q] += h * f[q];  // v_{s+1}
+            v[q] = fma(h, f[q], v[q]);  // v_{s+1}
             kin += v[q] * v[q];
         }
         kin *= 0.5 * a.mass[at] / kAcc;
@@ -147,8 +149,8 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
         if (!last) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                v[q] += h * f[q];
-                x[q] += a.dt * v[q];
+                v[q] = fma(h, f[q], v[q]);
+                x[q] = fma(a.dt, v[q], x[q]);
                 a.x[3 * at + q] = x[q];
                 acc[3 * at + q] = 0ull;
             }
@@ -233,8 +235,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const double f = fx_val(a.fxA[3 * at + q]);
-                const double v = a.v[3 * at + q] + h * f;
-                x[q] = a.x[3 * at + q] + a.dt * v;
+                const double v = fma(h, f, a.v[3 * at + q]);
+                x[q] = fma(a.dt, v, a.x[3 * at + q]);
                 a.v[3 * at + q] = v;
                 a.x[3 * at + q] = x[q];
             }
