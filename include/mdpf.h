@@ -259,6 +259,41 @@ MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
 MDPF_API int mdpf_set_profiling(mdpf_ctx *ctx, int32_t enable);
 MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);
 
+/*
+ * All-pairs LJ + Coulomb energy and forces for callers that cannot allocate
+ * device memory (an engine calling its force provider inside its own step
+ * loop and memory pool, code that must not trigger the synchronisation that
+ * cudaMalloc/cudaFree imply, or a host that only passes pointers into buffers
+ * it already owns).  The paper has no counterpart of this entry point.
+ *
+ * Every pair i < j of the n_atoms atoms interacts (no exclusions, no bonded
+ * terms, no cutoff), with the same per-element Lorentz-Berthelot LJ and
+ * Coulomb terms and the same kernels as mdpf_compute_device; for a system
+ * without bonds the two give the same results.
+ *   d_pos     [N,3] FP64 device positions (A)        -- caller-owned input
+ *   d_element [N]   int32 device elements 0..3       -- caller-owned input
+ *                   (an element outside 0..3 yields NaN results)
+ *   d_charge  [N]   FP64 device charges (e)          -- caller-owned input
+ *   lj_sigma, lj_eps [4] host arrays, per element; coulomb_k 0 selects 332.06371
+ *   d_energy  one FP64 device scalar (kcal/mol), or NULL
+ *   d_forces  [N,3] FP32 device forces (kcal/mol/A), or NULL (not both NULL)
+ * All work is enqueued on cuda_stream; the call returns without waiting.
+ *
+ * Memory: the call allocates nothing.  Its working memory is one fixed array
+ * of about 390 KB in the library's device data, held by every GPU that loads
+ * the library until the process exits; it limits n_atoms to 2048 (larger
+ * values return MDPF_ERR_INVALID_ARG).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and each call clears what it accumulates, so calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Errors are reported by the return code and
+ * mdpf_last_error(NULL).
+ */
+MDPF_API int mdpf_pairs_noalloc(int32_t n_atoms, const double *d_pos, const int32_t *d_element, const double *d_charge,
+                                const double lj_sigma[4], const double lj_eps[4], double coulomb_k, double *d_energy,
+                                float *d_forces, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
         "mdpf_debug_wait_timeout": (ctypes.c_int, [_vp, _i32]),
         "mdpf_set_profiling": (ctypes.c_int, [_vp, _i32]),
         "mdpf_get_profile": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+        "mdpf_pairs_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _f64,
+                                              _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -277,3 +279,15 @@ class Context:
         n = ctypes.c_int64()
         self._check(lib().mdpf_get_profile(self._h, slot, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+def pairs_noalloc(n_atoms: int, d_pos: int, d_element: int, d_charge: int, lj_sigma, lj_eps, coulomb_k: float,
+                  d_energy: int, d_forces: int, stream: int = 0) -> None:
+    """All-pairs LJ + Coulomb through the entry point that allocates no device memory
+    (device addresses as ints; see mdpf_pairs_noalloc in include/mdpf.h)."""
+    sig = (_f64 * 4)(*[float(v) for v in lj_sigma])
+    eps = (_f64 * 4)(*[float(v) for v in lj_eps])
+    rc = lib().mdpf_pairs_noalloc(int(n_atoms), _vp(d_pos), _vp(d_element), _vp(d_charge), sig, eps,
+                                  float(coulomb_k), _vp(d_energy), _vp(d_forces), _vp(stream))
+    if rc != MDPF_OK:
+        raise MdpfError(rc, lib().mdpf_last_error(None).decode())

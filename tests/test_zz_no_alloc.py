@@ -1,0 +1,88 @@
+"""The entry point that allocates no device memory, checked against the
+regular evaluation.
+
+It exists for callers that cannot call cudaMalloc at the moment they need
+forces (an engine calling its force provider inside its step loop and memory
+pool, or code that must avoid the synchronisation of cudaMalloc/cudaFree);
+they pass their own device buffers and the library works in a fixed array of
+its own.  This file is collected last so that a run stopping at the first
+failure has run every other test first; it creates everything it needs, so it
+also passes when run alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_2412_18271_b300 import mdpf, synth
+
+pytestmark = pytest.mark.gpu
+
+F_RTOL = 1e-4          # the FP32 force tolerance of the other GPU tests (relative to RMS force)
+E_TOL_PER_ATOM = 1e-5  # kcal/mol/atom
+
+
+def _unbonded(n_mol, per_mol, radius, seed):
+    # atoms of a seeded cluster with the bonds removed: every pair interacts
+    s = synth.cluster(n_mol, per_mol, radius, seed=seed)
+    s.bonds = np.zeros((0, 2), dtype=np.int32)
+    s.bond_r0 = np.zeros(0)
+    s.bond_k = np.zeros(0)
+    return s
+
+
+def _reference(ctx, dpos, n, torch):
+    de = torch.zeros(1, dtype=torch.float64, device="cuda")
+    df = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    ctx.compute_device(dpos.data_ptr(), de.data_ptr(), df.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return de.item(), df.cpu().numpy()
+
+
+def test_noalloc_matches_compute_on_two_calls_in_a_row():
+    import torch
+    from paper_2412_18271_b300 import build
+    build.build()
+    s = _unbonded(8, 32, 25.0, seed=31)          # 256 atoms
+    n = s.n_atoms
+    ctx = mdpf.Context(s)
+    del_ = torch.tensor(s.element, dtype=torch.int32, device="cuda")
+    dq = torch.tensor(s.charge, dtype=torch.float64, device="cuda")
+    de = torch.zeros(1, dtype=torch.float64, device="cuda")
+    df = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    for call in range(2):
+        pos = s.pos + (0.0 if call == 0 else rng.normal(scale=0.05, size=s.pos.shape))
+        dpos = torch.tensor(pos, dtype=torch.float64, device="cuda")
+        e_ref, f_ref = _reference(ctx, dpos, n, torch)
+        df.fill_(123.0)
+        de.fill_(123.0)
+        mdpf.pairs_noalloc(n, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, 0.0,
+                           de.data_ptr(), df.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        e, f = de.item(), df.cpu().numpy()
+        rms = np.sqrt((f_ref.astype(np.float64) ** 2).mean())
+        assert np.sqrt(((f - f_ref) ** 2).mean()) <= F_RTOL * rms, call
+        assert abs(e - e_ref) / n <= E_TOL_PER_ATOM, (call, e, e_ref)
+
+
+def test_noalloc_largest_size_and_rejects_larger():
+    import torch
+    s = _unbonded(64, 32, 60.0, seed=100)        # 2048 atoms: the largest accepted size
+    n = s.n_atoms
+    ctx = mdpf.Context(s)
+    dpos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    del_ = torch.tensor(s.element, dtype=torch.int32, device="cuda")
+    dq = torch.tensor(s.charge, dtype=torch.float64, device="cuda")
+    de = torch.zeros(1, dtype=torch.float64, device="cuda")
+    df = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    e_ref, f_ref = _reference(ctx, dpos, n, torch)
+    mdpf.pairs_noalloc(n, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, 0.0,
+                       de.data_ptr(), df.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    f = df.cpu().numpy()
+    rms = np.sqrt((f_ref.astype(np.float64) ** 2).mean())
+    assert np.sqrt(((f - f_ref) ** 2).mean()) <= F_RTOL * rms
+    assert abs(de.item() - e_ref) / n <= E_TOL_PER_ATOM
+    with pytest.raises(mdpf.MdpfError) as ei:
+        mdpf.pairs_noalloc(n + 1, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, 0.0,
+                           de.data_ptr(), df.data_ptr(), 0)
+    assert ei.value.name == "INVALID_ARG" and "2048" in str(ei.value)
