@@ -107,7 +107,8 @@ typedef struct mdpf_topology {
  *   stepper       MDPF_STEPPER_PERSISTENT (0): mdpf_step runs as one resident
  *                 cooperative kernel with bounded grid barriers;
  *                 MDPF_STEPPER_KERNELS (1): one kernel sequence per step.
- *                 Both give the same trajectory up to FP32 summation order.
+ *                 Both give the same trajectory bit for bit.  Learned mode
+ *                 always runs the kernel sequence (the field is ignored).
  *   energy_every  evaluate U and K every this many steps (0 selects 1); the
  *                 trace holds one entry per such step; record_every must be a
  *                 multiple of it.  Forces are evaluated every step regardless.
@@ -123,7 +124,37 @@ typedef struct mdpf_params {
     int32_t max_frames;
     int32_t stepper;
     int32_t energy_every;
+    /* learned mode only */
+    const void *model;       /* model blob (layout below); copied by mdpf_create */
+    uint64_t model_bytes;
+    double skin;             /* neighbour-list skin in A (0 selects 1.0); list radius = 5.2 + skin */
+    int32_t rebuild_every;   /* rebuild the list every this many steps (0 selects 20) */
+    int32_t fallback;        /* 1: a step whose features leave the model's range uses the plain
+                                force field; 0: such a step reports MDPF_ERR_OUT_OF_RANGE */
 } mdpf_params;
+
+/*
+ * Learned mode (MDPF_MODE_LEARNED).  Per atom, 384 symmetry-function features
+ * (64 radial: 16 Gaussians exp(-16 (r - R_k)^2), R_k = 0.9 + k 4.3/16, per
+ * neighbour element, cosine cutoff 5.2 A; 320 angular: for each unordered
+ * neighbour-element pair P (HH HC HN HO CC CN CO NN NO OO), 4 radial shells
+ * R_m = 0.9 + m 2.6/4 (eta 8) x 8 angular sections theta_p = (2p+1) pi/16 of
+ * 2^(1-32) (1 + cos(theta - theta_p))^32 with theta = acos(0.95 cos theta_ijk),
+ * cutoff 3.5 A) feed a per-element MLP 384 -> 256 -> 128 -> 1 with CELU(0.1):
+ * E = sum_i W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0.  Forces are the
+ * analytic adjoint -dE/dx.  The GEMM operands run in BF16 (features, CELU
+ * outputs and back-propagated deltas rounded to BF16), accumulations in FP32,
+ * energies and the state in FP64.  The plain topology (bonds, charges, LJ) is
+ * still required: it is the fallback force field.
+ *
+ * Model blob (little endian): 64-byte header {char magic[8] = "MDPFMLP1";
+ * int32 version = 1, n_elem = 4, n_feat = 384, h1 = 256, h2 = 128, flags
+ * (bit 0: feature ranges follow); float64 celu_alpha; 24 reserved bytes},
+ * then per element: uint16 W1[256][384] (BF16 bits), float32 b1[256],
+ * uint16 W2[128][256] (BF16 bits), float32 b2[128], float32 W3[128],
+ * float32 b3, float32 pad, float64 e0; then, if flags & 1, float32
+ * lo[4][384], hi[4][384] (the training range of each feature, per element).
+ */
 
 /* Counters and diagnostics of a context. */
 typedef struct mdpf_counters {
@@ -142,9 +173,11 @@ typedef struct mdpf_counters {
  * angles and the 1-2/1-3 exclusion set on the device, allocates every buffer
  * the path needs (the context owns them until mdpf_destroy).
  * Errors: INVALID_ARG (N < 1, bad index, non-positive mass or dt, unknown
- * mode or stepper), OOM, CUDA, NEIGHBOR_OVERFLOW (an atom with more than 255
+ * mode or stepper; learned mode: missing or malformed model blob, skin
+ * outside [0, 10]), OOM, CUDA, NEIGHBOR_OVERFLOW (an atom with more than 255
  * excluded partners), UNSUPPORTED (cooperative launch unavailable for the
- * persistent stepper).  On error *out is NULL.
+ * persistent stepper; a model blob whose celu_alpha is not 0.1).  The blob
+ * is checked on the host before any device work.  On error *out is NULL.
  */
 MDPF_API int mdpf_create(const mdpf_topology *topology, const mdpf_params *params, mdpf_ctx **out);
 
@@ -162,7 +195,11 @@ MDPF_API int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles
  * the potential energy (FP64, kcal/mol) to *energy and forces [N,3]
  * (kcal/mol/A) to the host buffer forces; either output may be NULL.  Does
  * not change the integrator state.  terms (may be NULL) receives the four
- * components {bond, angle, LJ, Coulomb}.  Synchronous.
+ * components {bond, angle, LJ, Coulomb} (zero in learned mode unless the
+ * evaluation fell back to the plain force field).  Synchronous.  Learned
+ * mode: returns NEIGHBOR_OVERFLOW when a neighbour row or cell exceeded its
+ * capacity (128), and OUT_OF_RANGE when the features left the model's range
+ * with the fallback off (the outputs then hold the model's values).
  */
 MDPF_API int mdpf_compute(mdpf_ctx *ctx, const double *pos, double *energy, double *forces, double *terms);
 
@@ -170,7 +207,9 @@ MDPF_API int mdpf_compute(mdpf_ctx *ctx, const double *pos, double *energy, doub
  * Device-pointer form of mdpf_compute: d_pos [N,3] FP64 device positions,
  * d_energy one FP64 device scalar, d_forces [N,3] FP32 device forces, all
  * enqueued on cuda_stream (a cudaStream_t; NULL = legacy default stream).
- * Asynchronous: results are valid once the stream reaches this point.
+ * Asynchronous: results are valid once the stream reaches this point.  In
+ * learned mode it shares the neighbour list and feature buffers with
+ * mdpf_step: do not run the two concurrently on different streams.
  */
 MDPF_API int mdpf_compute_device(mdpf_ctx *ctx, const double *d_pos, double *d_energy, float *d_forces,
                                  void *cuda_stream);
@@ -242,6 +281,30 @@ MDPF_API int mdpf_debug_set_status(mdpf_ctx *ctx, uint32_t bits);
  * without hanging the GPU.
  */
 MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
+
+/*
+ * Learned-path stages at host positions pos [N,3] (for parity checks; any
+ * output may be NULL):
+ *   neighbours  rows of the cell-list neighbour list (radius 5.2 + skin, FP32
+ *               predicate fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl32(rc^2)),
+ *               each row ascending: count [N], idx [N][max_per_atom] int32;
+ *   features    G [N][384] FP32 (atom order);
+ *   mlp         from caller features G [N][384] (FP32, rounded to BF16 as the
+ *               GEMM input): atomic energies E_i [N] FP64 and dE/dG [N][384] FP32.
+ * MDPF_ERR_UNSUPPORTED unless the context is in learned mode.
+ */
+MDPF_API int mdpf_learned_neighbors(mdpf_ctx *ctx, const double *pos, int32_t max_per_atom, int32_t *count,
+                                    int32_t *idx);
+MDPF_API int mdpf_learned_features(mdpf_ctx *ctx, const double *pos, float *G);
+MDPF_API int mdpf_learned_mlp(mdpf_ctx *ctx, const float *G, double *E_atom, float *dEdG);
+
+/*
+ * Learned-mode counters: neighbour-list rebuilds, force evaluations (steps,
+ * set_state, compute) whose features left the model's range (these used the
+ * plain force field when the fallback is on), and the largest neighbour row
+ * seen.
+ */
+MDPF_API int mdpf_learned_counters(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fallback_steps, int32_t *max_row);
 
 /*
  * Per-kernel device timing with CUDA events recorded on the launching stream

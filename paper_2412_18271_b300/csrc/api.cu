@@ -88,6 +88,7 @@ void prof_end(mdpf_ctx *c, int slot, cudaEvent_t a, cudaStream_t s) {
 
 static void free_ctx(mdpf_ctx *c) {
     if (!c) return;
+    learned_free(c);
     for (auto &r : c->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -125,8 +126,16 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     if (!t->element || !t->mass || !t->charge) return fail(nullptr, MDPF_ERR_INVALID_ARG, "NULL per-atom array");
     if (t->n_bonds < 0 || (t->n_bonds > 0 && (!t->bonds || !t->bond_r0 || !t->bond_k)))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "bad bond arrays");
-    if (prm->mode != MDPF_MODE_PLAIN)
-        return fail(nullptr, MDPF_ERR_UNSUPPORTED, "only MDPF_MODE_PLAIN is available in this build");
+    if (prm->mode != MDPF_MODE_PLAIN && prm->mode != MDPF_MODE_LEARNED)
+        return fail(nullptr, MDPF_ERR_INVALID_ARG, "unknown mode");
+    if (prm->mode == MDPF_MODE_LEARNED && (!(prm->skin >= 0.0) || !std::isfinite(prm->skin) || prm->skin > 10.0 ||
+                                           prm->rebuild_every < 0))
+        return fail(nullptr, MDPF_ERR_INVALID_ARG, "skin must be in [0, 10] and rebuild_every >= 0");
+    if (prm->mode == MDPF_MODE_LEARNED) {
+        std::string msg;
+        const int vrc = learned_validate(prm, msg);
+        if (vrc != MDPF_OK) return fail(nullptr, vrc, msg);
+    }
     if (!(prm->dt_fs > 0.0) || !std::isfinite(prm->dt_fs))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "dt_fs must be > 0");
     if (prm->trace_capacity < 0 || prm->record_every < 0 || prm->max_frames < 0)
@@ -170,7 +179,8 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     c->trace_cap = prm->trace_capacity > 0 ? prm->trace_capacity : 4096;
     c->record_every = prm->record_every;
     c->max_frames = prm->max_frames;
-    c->stepper = prm->stepper;
+    // learned mode always steps with the per-step kernel sequence
+    c->stepper = prm->mode == MDPF_MODE_LEARNED ? MDPF_STEPPER_KERNELS : prm->stepper;
     c->energy_every = prm->energy_every > 0 ? prm->energy_every : 1;
     c->angle_k = (float)t->angle_k;
     c->angle_theta0 = (float)(t->angle_theta0_deg * M_PI / 180.0);
@@ -277,6 +287,10 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     CKC(cudaMemsetAsync(c->d_fx_base, 0, sizeof(unsigned long long) * 6 * np, s));
     int rc = build_exclusions(c);
     if (rc != MDPF_OK) return bail(rc);
+    if (c->mode == MDPF_MODE_LEARNED) {
+        rc = learned_create(c, t, prm);
+        if (rc != MDPF_OK) return bail(rc);
+    }
     if (c->stepper == MDPF_STEPPER_PERSISTENT) {
         c->step_grid = stepper_grid(c);
         if (c->step_grid < 1) {
@@ -366,12 +380,17 @@ int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles) {
     return MDPF_OK;
 }
 
-// Force evaluation into (fx, efx) at the FP32 positions pos4.
+// Force evaluation into (fx, efx) at the FP32 positions pos4 (learned mode:
+// with a fresh neighbour list).
 static void enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
                            uint32_t *status, bool energy, cudaStream_t s) {
+    launch_zero_fx(fx, 3 * c->n_pad, efx, s);
+    if (c->mode == MDPF_MODE_LEARNED) {
+        learned_enqueue_forces(c, pos4, fx, efx, status, true, false, s);
+        return;
+    }
     PlainDev p = plain_dev(c, pos4);
     p.status = status;
-    launch_zero_fx(fx, 3 * c->n_pad, efx, s);
     launch_bonded(p, fx, energy ? efx : nullptr, s);
     launch_nonbonded(p, fx, efx, energy, s);
 }
@@ -410,6 +429,8 @@ int mdpf_compute(mdpf_ctx *c, const double *pos, double *energy, double *forces,
     if (terms) std::memcpy(terms, e6 + 1, sizeof(double) * 4);
     if ((st & MDPF_STATUS_NONFINITE) || !std::isfinite(e6[0]))
         return fail(c, MDPF_ERR_NONFINITE, "non-finite energy or forces");
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour list overflow");
+    if (st & MDPF_STATUS_OUT_OF_RANGE) return fail(c, MDPF_ERR_OUT_OF_RANGE, "features out of training range");
     return MDPF_OK;
 }
 
@@ -439,6 +460,8 @@ int mdpf_set_state(mdpf_ctx *c, const double *pos, const double *vel) {
     c->state_set = true;
     if ((st & MDPF_STATUS_NONFINITE) || !std::isfinite(c->h_initial))
         return fail(c, MDPF_ERR_NONFINITE, "non-finite initial energy");
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour list overflow");
+    if (st & MDPF_STATUS_OUT_OF_RANGE) return fail(c, MDPF_ERR_OUT_OF_RANGE, "features out of training range");
     return MDPF_OK;
 }
 
@@ -465,6 +488,14 @@ static int enqueue_steps(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     for (int64_t k = 0; k < n_steps; ++k) {
         const bool energy = (c->steps + k + 1) % c->energy_every == 0;
         launch_kick_drift(c, s);
+        if (c->mode == MDPF_MODE_LEARNED) {
+            learned_enqueue_step_prologue(c, s);
+            cudaEvent_t pn = prof_begin(c, s);
+            learned_enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, false, false, s);
+            prof_end(c, MDPF_PROF_NONBONDED, pn, s);
+            launch_kick_finish(c, energy, s);
+            continue;
+        }
         PlainDev p = plain_dev(c, c->d_pos4);
         launch_bonded(p, c->d_fx, energy ? c->d_efx : nullptr, s);
         cudaEvent_t pn = prof_begin(c, s);

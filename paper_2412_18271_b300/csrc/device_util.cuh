@@ -5,10 +5,27 @@
 
 namespace mdpf {
 
-// value * 2^32 rounded to int64, added atomically (two's complement wrap-around
+// v * 2^32 truncated toward zero to int64, from the bit pattern of v with
+// integer operations only (the 64-bit float-to-integer conversion instruction
+// runs on the FP64 pipe, which is narrow on this GPU).  |v| >= 2^31 saturates
+// (a non-finite value too; callers flag those separately).
+__device__ __forceinline__ long long fx_from_float(float v) {
+    const unsigned int b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 118;  // v * 2^32 = m * 2^(e - 127 - 23 + 32)
+    unsigned long long r;
+    if (e == 0 || sh <= -24) r = 0ull;
+    else if (sh < 0) r = m >> (-sh);
+    else if (sh <= 38) r = m << sh;
+    else r = 0x7FFFFFFFFFFFFFFFull;
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
+
+// v * 2^32 as int64 fixed point, added atomically (two's complement wrap-around
 // makes the unsigned add an exact signed add).
 __device__ __forceinline__ void fx_add(unsigned long long *p, float v) {
-    atomicAdd(p, (unsigned long long)__float2ll_rn(v * 4294967296.0f));
+    atomicAdd(p, (unsigned long long)fx_from_float(v));
 }
 __device__ __forceinline__ void fx_add_d(unsigned long long *p, double v) {
     atomicAdd(p, (unsigned long long)__double2ll_rn(v * 4294967296.0));

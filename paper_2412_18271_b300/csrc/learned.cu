@@ -1,0 +1,599 @@
+// Learned-potential kernels: cell-list neighbour build, symmetry-function
+// features, per-element MLP (forward and input gradient), feature adjoint.
+//
+//   radial    G[i, 16 Zj + k]           = sum_j  exp(-16 (r_ij - R_k)^2) fc(r_ij; 5.2)
+//   angular   G[i, 64 + 32 P + 8 m + p] = sum_{j<k} 2^-31 (1 + cos(theta - theta_p))^32
+//                                         exp(-8 ((r_ij + r_ik)/2 - R_m)^2) fc(r_ij; 3.5) fc(r_ik; 3.5)
+//   theta = acos(0.95 cos theta_ijk), cos(theta - theta_p) = c cos theta_p + sqrt(1 - c^2) sin theta_p
+//   E_i = W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0,  celu(x) = max(x, 0.1 (exp(10 x) - 1))
+// Every accumulation that feeds a result is done in a fixed order per lane, and
+// forces are int64 fixed-point sums, so results are reproducible bit for bit.
+#include <cuda_bf16.h>
+
+#include "learned.cuh"
+
+namespace mdpf {
+namespace {
+
+constexpr float kPi = 3.14159265358979f;
+constexpr float kEtaR = 16.f, kEtaA = 8.f;
+constexpr float kAngScale = 0.95f;
+constexpr float kCeluAlpha = 0.1f;
+constexpr float kTwoPowM31 = 4.656612873077393e-10f;  // 2^-31 = 2^(1 - zeta), zeta = 32
+
+__device__ __forceinline__ float fcut(float r, float rc) { return r < rc ? 0.5f * cosf(kPi * r / rc) + 0.5f : 0.f; }
+__device__ __forceinline__ float dfcut(float r, float rc) { return r < rc ? -0.5f * kPi / rc * sinf(kPi * r / rc) : 0.f; }
+__device__ __forceinline__ float celu(float x) { return x > 0.f ? x : kCeluAlpha * expm1f(x / kCeluAlpha); }
+__device__ __forceinline__ float dcelu(float x) { return x >= 0.f ? 1.f : expf(x / kCeluAlpha); }
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ int pair_index(int a, int b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return (a == 0 ? 0 : (a == 1 ? 4 : (a == 2 ? 7 : 9))) + (b - a);
+}
+
+__device__ __forceinline__ unsigned int ord_f(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__device__ __forceinline__ bool gate_open(const LearnedDev &L, int forced) { return forced || L.lflags[0] != 0u; }
+
+// ------------------------------------------------------------------ neighbour list
+
+__global__ void k_nb_begin(LearnedDev L, int forced) {
+    if (!gate_open(L, forced)) return;
+    const int t = threadIdx.x;
+    if (t < 3) L.bbox[t] = 0xFFFFFFFFu;       // min
+    if (t >= 3 && t < 6) L.bbox[t] = 0u;      // max
+}
+
+__global__ void k_nb_bbox(LearnedDev L, const float4 *pos4, int forced) {
+    if (!gate_open(L, forced)) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= L.n) return;
+    const float4 p = pos4[a];
+    atomicMin(&L.bbox[0], ord_f(p.x));
+    atomicMin(&L.bbox[1], ord_f(p.y));
+    atomicMin(&L.bbox[2], ord_f(p.z));
+    atomicMax(&L.bbox[3], ord_f(p.x));
+    atomicMax(&L.bbox[4], ord_f(p.y));
+    atomicMax(&L.bbox[5], ord_f(p.z));
+}
+
+__global__ void k_nb_grid(LearnedDev L, int forced) {
+    if (!gate_open(L, forced) || threadIdx.x != 0) return;
+    float lo[3], ext = 0.f, e3[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = unord_f(L.bbox[d]);
+        e3[d] = unord_f(L.bbox[3 + d]) - lo[d];
+        ext = fmaxf(ext, e3[d]);
+    }
+    // cells a little wider than the list radius, so that rounding in the cell
+    // index never puts two atoms within the radius more than one cell apart
+    const float cs = fmaxf(L.rc_list * 1.001f, ext / (float)kMaxCellDim);
+    CellGrid g;
+    int nc = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = lo[d];
+        g.dim[d] = min((int)floorf(e3[d] / cs) + 1, kMaxCellDim + 1);
+        nc *= g.dim[d];
+    }
+    g.cs = cs;
+    g.ncell = nc;
+    *L.grid = g;
+}
+
+__global__ void k_nb_clear(LearnedDev L, int max_cells, int forced) {
+    if (!gate_open(L, forced)) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < max_cells) L.cell_cnt[c] = 0;
+}
+
+__device__ __forceinline__ void cell_of(const CellGrid &g, float4 p, int &cx, int &cy, int &cz) {
+    cx = min(max((int)floorf((p.x - g.lo[0]) / g.cs), 0), g.dim[0] - 1);
+    cy = min(max((int)floorf((p.y - g.lo[1]) / g.cs), 0), g.dim[1] - 1);
+    cz = min(max((int)floorf((p.z - g.lo[2]) / g.cs), 0), g.dim[2] - 1);
+}
+
+__global__ void k_nb_fill(LearnedDev L, const float4 *pos4, int forced) {
+    if (!gate_open(L, forced)) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= L.n) return;
+    const CellGrid g = *L.grid;
+    int cx, cy, cz;
+    cell_of(g, pos4[a], cx, cy, cz);
+    const int c = (cz * g.dim[1] + cy) * g.dim[0] + cx;
+    const int slot = atomicAdd(&L.cell_cnt[c], 1);
+    if (slot < kCellCap) L.cell_atoms[(size_t)c * kCellCap + slot] = a;
+    else atomicOr(&L.lflags[2], 1u);
+}
+
+// Row of atom i: every j != i in the 27 surrounding cells with
+// fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl32(rc^2), sorted ascending.
+__global__ void k_nb_build(LearnedDev L, const float4 *pos4, uint32_t *status, int forced) {
+    if (!gate_open(L, forced)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const CellGrid g = *L.grid;
+    const float4 pi = pos4[i];
+    int cx, cy, cz;
+    cell_of(g, pi, cx, cy, cz);
+    int row[kKmax];
+    int m = 0;
+    bool over = false;
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, g.dim[2] - 1); ++z)
+        for (int y = max(cy - 1, 0); y <= min(cy + 1, g.dim[1] - 1); ++y)
+            for (int x = max(cx - 1, 0); x <= min(cx + 1, g.dim[0] - 1); ++x) {
+                const int c = (z * g.dim[1] + y) * g.dim[0] + x;
+                const int cnt = min(L.cell_cnt[c], kCellCap);
+                for (int q = 0; q < cnt; ++q) {
+                    const int j = L.cell_atoms[(size_t)c * kCellCap + q];
+                    if (j == i) continue;
+                    const float4 pj = pos4[j];
+                    const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    if (d2 < L.rc_list2) {
+                        if (m < kKmax) row[m++] = j; else over = true;
+                    }
+                }
+            }
+    for (int p = 1; p < m; ++p) {
+        const int v = row[p];
+        int q = p - 1;
+        while (q >= 0 && row[q] > v) {
+            row[q + 1] = row[q];
+            --q;
+        }
+        row[q + 1] = v;
+    }
+    int *out = L.nb_idx + (size_t)i * kKmax;
+    for (int p = 0; p < m; ++p) out[p] = row[p];
+    L.nb_count[i] = m;
+    L.pos_build[i] = pi;
+    if (over) {
+        atomicOr(&L.lflags[2], 1u);
+        atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+    }
+    atomicMax((unsigned long long *)&L.lcount[2], (unsigned long long)(over ? kKmax + 1 : m));
+}
+
+__global__ void k_nb_done(LearnedDev L, uint32_t *status, int forced) {
+    if (!gate_open(L, forced) || threadIdx.x != 0) return;
+    if (L.lflags[2]) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+    L.lflags[0] = 0u;
+    L.lflags[2] = 0u;
+    L.lcount[0] += 1;
+}
+
+// Request a rebuild when an atom moved more than skin/2 since the last build,
+// or when the completed-step count is a multiple of rebuild_every.
+__global__ void k_nb_disp(LearnedDev L, const float4 *pos4, const int64_t *step, int rebuild_every) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a == 0 && rebuild_every > 0 && (*step % rebuild_every) == 0) atomicOr(&L.lflags[0], 1u);
+    if (a >= L.n) return;
+    const float4 p = pos4[a], b = L.pos_build[a];
+    const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+    if (dx * dx + dy * dy + dz * dz > L.half_skin2) atomicOr(&L.lflags[0], 1u);
+}
+
+// ------------------------------------------------------------------ features
+
+constexpr int kFeatWarps = 4;
+
+struct NbrSmem {
+    int j[kKmax];
+    int el[kKmax];
+    float4 d[kKmax];      // dx, dy, dz, r
+    int ang[kKmax];       // neighbours within the angular cutoff
+};
+
+// Load atom i's neighbours into shared memory; returns the row length and the
+// number of neighbours within the angular cutoff.
+__device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
+                                                int &cnt, int &na) {
+    const float4 pi = pos4[i];
+    cnt = L.nb_count[i];
+    for (int q = lane; q < cnt; q += 32) {
+        const int j = L.nb_idx[(size_t)i * kKmax + q];
+        const float4 pj = pos4[j];
+        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        s.j[q] = j;
+        s.el[q] = L.el[j];
+        s.d[q] = make_float4(dx, dy, dz, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+    __syncwarp();
+    na = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int q = base + lane;
+        const bool in = q < cnt && s.d[q].w < kRcAng;
+        const unsigned int bal = __ballot_sync(0xffffffffu, in);
+        if (in) s.ang[na + __popc(bal & ((1u << lane) - 1u))] = q;
+        na += __popc(bal);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void triplet_ab(int t, int na, int &a, int &b) {
+    a = 0;
+    while (t >= na - 1 - a) {
+        t -= na - 1 - a;
+        ++a;
+    }
+    b = a + 1 + t;
+}
+
+__global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, const float4 *pos4, int write_f32) {
+    __shared__ NbrSmem sn[kFeatWarps];
+    __shared__ float accR[kFeatWarps][2][64];
+    __shared__ float accA[kFeatWarps][320];
+    __shared__ float tcs[kFeatWarps][32], tsn[kFeatWarps][32], tC[kFeatWarps][32], tB[kFeatWarps][32][4];
+    __shared__ int tP[kFeatWarps][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFeatWarps + w;
+    if (i >= L.n) return;
+    NbrSmem &s = sn[w];
+    for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
+    for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
+    int cnt, na;
+    load_neighbours(L, pos4, i, s, lane, cnt, na);
+    // radial: lane = 16 h + k takes neighbours q = h, h + 2, ...
+    {
+        const int h = lane >> 4, k = lane & 15;
+        const float Rk = 0.9f + (float)k * (4.3f / 16.f);
+        for (int q = h; q < cnt; q += 2) {
+            const float r = s.d[q].w;
+            if (r < kRcRad) {
+                const float x = r - Rk;
+                accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * fcut(r, kRcRad);
+            }
+        }
+    }
+    // angular: lane = 8 m + p owns the (m, p) column of every pair block
+    {
+        const int m = lane >> 3, p = lane & 7;
+        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+        const float cp = cosf(thp), sp = sinf(thp);
+        const int ntrip = na * (na - 1) / 2;
+        for (int base = 0; base < ntrip; base += 32) {
+            const int t = base + lane;
+            if (t < ntrip) {
+                int a, b;
+                triplet_ab(t, na, a, b);
+                const float4 dj = s.d[s.ang[a]], dk = s.d[s.ang[b]];
+                const float ct = (dj.x * dk.x + dj.y * dk.y + dj.z * dk.z) / (dj.w * dk.w);
+                const float cs = kAngScale * ct;
+                tcs[w][lane] = cs;
+                tsn[w][lane] = sqrtf(1.f - cs * cs);
+                tC[w][lane] = fcut(dj.w, kRcAng) * fcut(dk.w, kRcAng);
+                const float ravg = 0.5f * (dj.w + dk.w);
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) {
+                    const float x = ravg - (0.9f + (float)mm * 0.65f);
+                    tB[w][lane][mm] = expf(-kEtaA * x * x);
+                }
+                tP[w][lane] = pair_index(s.el[s.ang[a]], s.el[s.ang[b]]);
+            }
+            __syncwarp();
+            const int nt = min(32, ntrip - base);
+            for (int u = 0; u < nt; ++u) {
+                float x = 1.f + tcs[w][u] * cp + tsn[w][u] * sp;
+                x *= x; x *= x; x *= x; x *= x; x *= x;  // ^32
+                accA[w][32 * tP[w][u] + lane] += kTwoPowM31 * x * tB[w][u][m] * tC[w][u];
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    const int row = L.row_of[i];
+    const int z = L.el[i];
+    bool out = false;
+    for (int f = lane; f < kNFeat; f += 32) {
+        const float v = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
+        if (L.lo != nullptr) out |= (v < L.lo[z * kNFeat + f]) || (v > L.hi[z * kNFeat + f]);
+        L.G16[(size_t)row * kNFeat + f] = __float2bfloat16_rn(v);
+        if (write_f32) L.G32[(size_t)row * kNFeat + f] = v;
+    }
+    if (__any_sync(0xffffffffu, out) && lane == 0) atomicOr(&L.lflags[1], 1u);
+}
+
+// ------------------------------------------------------------------ MLP (CUDA cores)
+//
+// Rows are grouped by element and padded to kRowTile, so every block of
+// kMlpRows rows belongs to one element.  GEMM operands are rounded to BF16,
+// products accumulate in FP32.
+
+constexpr int kMlpRows = 8;
+
+__global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
+    if (gated && L.lflags[1]) return;
+    __shared__ float sG[kMlpRows][kNFeat];
+    __shared__ float sA1[kMlpRows][kH1];
+    __shared__ float sH1d[kMlpRows][kH1];
+    __shared__ float sD2[kMlpRows][kH2];
+    __shared__ float sD1[kMlpRows][kH1];
+    __shared__ float sE[kMlpRows][4];
+    const int t = threadIdx.x;
+    const int r0 = blockIdx.x * kMlpRows;
+    const int e = L.tile_el[r0 / kRowTile];
+    for (int q = t; q < kMlpRows * kNFeat; q += 256)
+        sG[q / kNFeat][q % kNFeat] = __bfloat162float(L.G16[(size_t)r0 * kNFeat + q]);
+    __syncthreads();
+    // layer 1: column a = t
+    {
+        const __nv_bfloat16 *W = L.W1T + (size_t)e * kNFeat * kH1;
+        float acc[kMlpRows];
+        const float b = L.b1[e * kH1 + t];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) acc[r] = b;
+        for (int k = 0; k < kNFeat; ++k) {
+            const float wv = __bfloat162float(W[(size_t)k * kH1 + t]);
+#pragma unroll
+            for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sG[r][k], wv, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) {
+            sA1[r][t] = bf16r(celu(acc[r]));
+            sH1d[r][t] = dcelu(acc[r]);
+        }
+    }
+    __syncthreads();
+    // layer 2 + output layer + delta2: column c = t < 128
+    if (t < kH2) {
+        const __nv_bfloat16 *W = L.W2T + (size_t)e * kH1 * kH2;
+        float acc[kMlpRows];
+        const float b = L.b2[e * kH2 + t];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) acc[r] = b;
+        for (int a = 0; a < kH1; ++a) {
+            const float wv = __bfloat162float(W[(size_t)a * kH2 + t]);
+#pragma unroll
+            for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sA1[r][a], wv, acc[r]);
+        }
+        const float w3 = L.W3[e * kH2 + t];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) {
+            float ev = w3 * celu(acc[r]);
+            for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+            if ((t & 31) == 0) sE[r][t >> 5] = ev;
+            sD2[r][t] = bf16r(w3 * dcelu(acc[r]));
+        }
+    }
+    __syncthreads();
+    if (t < kMlpRows) {
+        const int row = r0 + t;
+        const double E = (double)(sE[t][0] + sE[t][1] + sE[t][2] + sE[t][3]) + (double)L.b3[e] + L.e0[e];
+        L.E_row[row] = L.atom_of[row] >= 0 ? E : 0.0;
+    }
+    // backward through layer 2: delta1 = celu'(h1) * (W2^T delta2), column a = t
+    {
+        const __nv_bfloat16 *W = L.W2 + (size_t)e * kH2 * kH1;
+        float acc[kMlpRows];
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) acc[r] = 0.f;
+        for (int c = 0; c < kH2; ++c) {
+            const float wv = __bfloat162float(W[(size_t)c * kH1 + t]);
+#pragma unroll
+            for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sD2[r][c], wv, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kMlpRows; ++r) sD1[r][t] = bf16r(acc[r] * sH1d[r][t]);
+    }
+    __syncthreads();
+    // backward through layer 1: dE/dG = W1^T delta1, columns f = t, t + 256
+    {
+        const __nv_bfloat16 *W = L.W1 + (size_t)e * kH1 * kNFeat;
+        for (int f = t; f < kNFeat; f += 256) {
+            float acc[kMlpRows];
+#pragma unroll
+            for (int r = 0; r < kMlpRows; ++r) acc[r] = 0.f;
+            for (int a = 0; a < kH1; ++a) {
+                const float wv = __bfloat162float(W[(size_t)a * kNFeat + f]);
+#pragma unroll
+                for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sD1[r][a], wv, acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kMlpRows; ++r) L.g[(size_t)(r0 + r) * kNFeat + f] = acc[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+
+struct AdjSmem {
+    float g[kNFeat];
+    unsigned long long f[kKmax + 1][3];  // fixed-point forces on the neighbours and (last slot) on atom i
+};
+
+__device__ __forceinline__ void sadd(unsigned long long *p, float v) {
+    atomicAdd(p, (unsigned long long)fx_from_float(v));
+}
+
+__global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
+                                                             int gated) {
+    if (gated && L.lflags[1]) return;
+    __shared__ NbrSmem sn[kFeatWarps];
+    __shared__ AdjSmem sa[kFeatWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFeatWarps + w;
+    if (i >= L.n) return;
+    NbrSmem &s = sn[w];
+    AdjSmem &A = sa[w];
+    const int row = L.row_of[i];
+    for (int f = lane; f < kNFeat; f += 32) A.g[f] = L.g[(size_t)row * kNFeat + f];
+    for (int q = lane; q < (kKmax + 1) * 3; q += 32) (&A.f[0][0])[q] = 0ull;
+    int cnt, na;
+    load_neighbours(L, pos4, i, s, lane, cnt, na);
+    // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j -= dE/dr u,  F_i += dE/dr u
+    for (int q = lane; q < cnt; q += 32) {
+        const float4 d = s.d[q];
+        const float r = d.w;
+        if (!(r < kRcRad)) continue;
+        const float fc = fcut(r, kRcRad), dfc = dfcut(r, kRcRad);
+        const float *gz = A.g + 16 * s.el[q];
+        float dEdr = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+            const float x = r - (0.9f + (float)k * (4.3f / 16.f));
+            const float ex = expf(-kEtaR * x * x);
+            dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
+        }
+        const float sx = dEdr * d.x / r, sy = dEdr * d.y / r, sz = dEdr * d.z / r;
+        sadd(&A.f[q][0], -sx);
+        sadd(&A.f[q][1], -sy);
+        sadd(&A.f[q][2], -sz);
+        sadd(&A.f[kKmax][0], sx);
+        sadd(&A.f[kKmax][1], sy);
+        sadd(&A.f[kKmax][2], sz);
+    }
+    // angular triplets
+    const int ntrip = na * (na - 1) / 2;
+    for (int t = lane; t < ntrip; t += 32) {
+        int a, b;
+        triplet_ab(t, na, a, b);
+        const int qa = s.ang[a], qb = s.ang[b];
+        const float4 dj = s.d[qa], dk = s.d[qb];
+        const float rj = dj.w, rk = dk.w;
+        const float ujx = dj.x / rj, ujy = dj.y / rj, ujz = dj.z / rj;
+        const float ukx = dk.x / rk, uky = dk.y / rk, ukz = dk.z / rk;
+        const float ct = ujx * ukx + ujy * uky + ujz * ukz;
+        const float cs = kAngScale * ct;
+        const float sn2 = sqrtf(1.f - cs * cs);
+        const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
+        const float dfj = dfcut(rj, kRcAng), dfk = dfcut(rk, kRcAng);
+        const float C = fj * fk;
+        const float ravg = 0.5f * (rj + rk);
+        const float *gp = A.g + 64 + 32 * pair_index(s.el[qa], s.el[qb]);
+        float Sc = 0.f, Sr = 0.f, SC = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float x = ravg - (0.9f + (float)m * 0.65f);
+            const float B = expf(-kEtaA * x * x);
+            const float dB = -2.f * kEtaA * x * B;
+            float sa_ = 0.f, sdA = 0.f;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+                const float cp = cosf(thp), sp = sinf(thp);
+                const float base = 1.f + cs * cp + sn2 * sp;
+                float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
+                const float b31 = b16 * b8 * b4 * b2 * base;
+                const float Ap = kTwoPowM31 * b31 * base;
+                const float dAp = kTwoPowM31 * 32.f * b31 * (cp - cs / sn2 * sp);
+                const float gv = gp[8 * m + p];
+                sa_ = fmaf(gv, Ap, sa_);
+                sdA = fmaf(gv, dAp, sdA);
+            }
+            Sc = fmaf(sdA, B * C, Sc);
+            Sr = fmaf(sa_, dB * C, Sr);
+            SC = fmaf(sa_, B, SC);
+        }
+        const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
+        const float gc = Sc * kAngScale;
+        const float gjx = gc * (ukx - ct * ujx) / rj + dEdrj * ujx;
+        const float gjy = gc * (uky - ct * ujy) / rj + dEdrj * ujy;
+        const float gjz = gc * (ukz - ct * ujz) / rj + dEdrj * ujz;
+        const float gkx = gc * (ujx - ct * ukx) / rk + dEdrk * ukx;
+        const float gky = gc * (ujy - ct * uky) / rk + dEdrk * uky;
+        const float gkz = gc * (ujz - ct * ukz) / rk + dEdrk * ukz;
+        sadd(&A.f[qa][0], -gjx);
+        sadd(&A.f[qa][1], -gjy);
+        sadd(&A.f[qa][2], -gjz);
+        sadd(&A.f[qb][0], -gkx);
+        sadd(&A.f[qb][1], -gky);
+        sadd(&A.f[qb][2], -gkz);
+        sadd(&A.f[kKmax][0], gjx + gkx);
+        sadd(&A.f[kKmax][1], gjy + gky);
+        sadd(&A.f[kKmax][2], gjz + gkz);
+    }
+    __syncwarp();
+    for (int q = lane; q < cnt; q += 32) {
+        const int j = s.j[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (A.f[q][c]) atomicAdd(&fx[3 * j + c], A.f[q][c]);
+    }
+    if (lane < 3) atomicAdd(&fx[3 * i + lane], A.f[kKmax][lane]);
+}
+
+// Sum of the per-row energies into the fixed-point learned-energy slot.
+__global__ void k_learn_energy(LearnedDev L, unsigned long long *efx, int gated) {
+    if (gated && L.lflags[1]) return;
+    double e = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < L.n_rows; r += gridDim.x * blockDim.x) e += L.E_row[r];
+    e = warp_sum_d(e);
+    if ((threadIdx.x & 31) == 0 && e != 0.0) fx_add_d(&efx[E_LEARN], e);
+}
+
+__global__ void k_learn_begin(LearnedDev L) {
+    if (threadIdx.x == 0) L.lflags[1] = 0u;
+}
+
+// After a learned force evaluation: count a step that left the feature range
+// (its forces came from the plain force field), or report it when the
+// fallback is off.
+__global__ void k_learn_end(LearnedDev L, uint32_t *status, int fallback) {
+    if (threadIdx.x != 0 || L.lflags[1] == 0u) return;
+    L.lcount[1] += 1;
+    if (!fallback) atomicOr(status, MDPF_STATUS_OUT_OF_RANGE);
+}
+
+__global__ void k_import_g(LearnedDev L, const float *G) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= L.n * kNFeat) return;
+    const int a = q / kNFeat, f = q % kNFeat;
+    L.G16[(size_t)L.row_of[a] * kNFeat + f] = __float2bfloat16_rn(G[q]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+void learned_begin(const LearnedDev &L, cudaStream_t s) { k_learn_begin<<<1, 32, 0, s>>>(L); }
+
+void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s) {
+    k_learn_end<<<1, 32, 0, s>>>(L, status, fallback);
+}
+
+void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s) {
+    k_import_g<<<(L.n * kNFeat + 255) / 256, 256, 0, s>>>(L, G_atoms);
+}
+
+void learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status, cudaStream_t s) {
+    const int f = forced ? 1 : 0;
+    const int max_cells = (kMaxCellDim + 1) * (kMaxCellDim + 1) * (kMaxCellDim + 1);
+    k_nb_begin<<<1, 32, 0, s>>>(L, f);
+    k_nb_bbox<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, f);
+    k_nb_grid<<<1, 32, 0, s>>>(L, f);
+    k_nb_clear<<<(max_cells + 255) / 256, 256, 0, s>>>(L, max_cells, f);
+    k_nb_fill<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, f);
+    k_nb_build<<<(L.n + 127) / 128, 128, 0, s>>>(L, pos4, status, f);
+    k_nb_done<<<1, 32, 0, s>>>(L, status, f);
+}
+
+void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s) {
+    k_nb_disp<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, step, rebuild_every);
+}
+
+void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s) {
+    k_features<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, write_f32 ? 1 : 0);
+}
+
+void learned_mlp(const LearnedDev &L, bool gated, cudaStream_t s) {
+    if (L.n_rows > 0) k_mlp_simt<<<L.n_rows / kMlpRows, 256, 0, s>>>(L, gated ? 1 : 0);
+}
+
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
+                     bool gated, cudaStream_t s) {
+    k_adjoint<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0);
+    k_learn_energy<<<8, 256, 0, s>>>(L, efx, gated ? 1 : 0);
+}
+
+}  // namespace mdpf

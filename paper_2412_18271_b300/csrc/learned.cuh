@@ -1,0 +1,67 @@
+// Learned-potential path: device data and kernel launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "device_util.cuh"
+
+namespace mdpf {
+
+constexpr int kNFeat = 384, kH1 = 256, kH2 = 128;
+constexpr int kKmax = 128;          // neighbour-row capacity
+constexpr int kCellCap = 128;       // atoms per cell capacity
+constexpr int kMaxCellDim = 32;     // cells per dimension at most (larger systems get larger cells)
+constexpr int kRowTile = 128;       // element groups of MLP rows are padded to this
+constexpr float kRcRad = 5.2f, kRcAng = 3.5f;
+
+// Cell grid of the current neighbour build (filled on the device).
+struct CellGrid {
+    float lo[3];
+    float cs;
+    int dim[3];
+    int ncell;
+};
+
+// Everything the learned kernels read or write.
+struct LearnedDev {
+    int n, n_rows;
+    const int *el;               // [n]
+    const int *row_of;           // [n] atom -> MLP row
+    const int *atom_of;          // [n_rows] MLP row -> atom, -1 on padding rows
+    const int *tile_el;          // [n_rows / kRowTile] element of each row tile
+    // neighbour list
+    float rc_list2;              // fl32(rc_list^2)
+    float rc_list;
+    float half_skin2;            // (skin/2)^2
+    int *nb_count;               // [n]
+    int *nb_idx;                 // [n][kKmax]
+    float4 *pos_build;           // [n] positions at the last build
+    int *cell_cnt;               // [max cells]
+    int *cell_atoms;             // [max cells][kCellCap]
+    CellGrid *grid;
+    unsigned int *bbox;          // [6] ordered-int min/max
+    // features and MLP
+    __nv_bfloat16 *G16;          // [n_rows][384] GEMM input
+    float *G32;                  // [n_rows][384] FP32 features (parity output) or null
+    float *g;                    // [n_rows][384] dE/dG
+    double *E_row;               // [n_rows]
+    const __nv_bfloat16 *W1, *W1T, *W2, *W2T;  // [4][256][384], [4][384][256], [4][128][256], [4][256][128]
+    const float *b1, *b2, *W3, *b3;            // [4][256], [4][128], [4][128], [4]
+    const double *e0;                          // [4]
+    const float *lo, *hi;                      // [4][384] training range, or null
+    unsigned int *lflags;        // [0] rebuild requested, [1] out of range this step, [2] overflow
+    long long *lcount;           // [0] rebuilds, [1] fallback steps, [2] max row length
+};
+
+// launchers (learned.cu)
+void learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status, cudaStream_t s);
+void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s);
+void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s);
+void learned_mlp(const LearnedDev &L, bool gated, cudaStream_t s);
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
+                     bool gated, cudaStream_t s);
+void learned_begin(const LearnedDev &L, cudaStream_t s);
+void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s);
+void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s);
+
+}  // namespace mdpf

@@ -1,0 +1,362 @@
+// Learned mode: model-blob parsing, device buffers, the per-evaluation kernel
+// sequence (neighbours -> features -> MLP -> adjoint, or the plain force field
+// when the features leave the model's range), and the parity entry points.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "learned.cuh"
+
+namespace mdpf {
+
+struct LearnedHost {
+    LearnedDev dev{};
+    std::vector<void *> allocs;
+    int fallback = 1;
+    int rebuild_every = 20;
+    double skin = 1.0;
+    int n_rows = 0;
+    std::vector<int> row_of;
+    float *d_Gin = nullptr;     // [n][384] staging for mdpf_learned_mlp
+};
+
+static LearnedHost *lh(const mdpf_ctx *c) { return static_cast<LearnedHost *>(c->learned); }
+
+template <typename T>
+static cudaError_t lalloc(LearnedHost *h, T **p, size_t count) {
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) h->allocs.push_back((void *)*p);
+    return e;
+}
+
+void learned_free(mdpf_ctx *c) {
+    LearnedHost *h = lh(c);
+    if (!h) return;
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+    c->learned = nullptr;
+}
+
+static constexpr size_t kHeader = 64;
+static constexpr size_t kPerElement = (size_t)kH1 * kNFeat * 2 + kH1 * 4 + (size_t)kH2 * kH1 * 2 + kH2 * 4 +
+                                      kH2 * 4 + 4 + 4 + 8;
+
+// Host-side check of a model blob (no device work): shape, CELU constant, size.
+int learned_validate(const mdpf_params *prm, std::string &msg) {
+    const unsigned char *blob = static_cast<const unsigned char *>(prm->model);
+    if (blob == nullptr || prm->model_bytes < kHeader) return msg = "learned mode needs a model blob", MDPF_ERR_INVALID_ARG;
+    if (std::memcmp(blob, "MDPFMLP1", 8) != 0) return msg = "model blob: bad magic", MDPF_ERR_INVALID_ARG;
+    int32_t hdr[6];
+    double alpha;
+    std::memcpy(hdr, blob + 8, sizeof(hdr));
+    std::memcpy(&alpha, blob + 32, sizeof(alpha));
+    if (hdr[0] != 1 || hdr[1] != 4 || hdr[2] != kNFeat || hdr[3] != kH1 || hdr[4] != kH2)
+        return msg = "model blob: unexpected version or shape", MDPF_ERR_INVALID_ARG;
+    if (std::fabs(alpha - 0.1) > 1e-12) return msg = "model blob: CELU alpha must be 0.1", MDPF_ERR_UNSUPPORTED;
+    const bool ranges = (hdr[5] & 1) != 0;
+    const size_t expect = kHeader + 4 * kPerElement + (ranges ? 2 * 4 * kNFeat * sizeof(float) : 0);
+    if (prm->model_bytes != expect) return msg = "model blob: wrong size", MDPF_ERR_INVALID_ARG;
+    return MDPF_OK;
+}
+
+int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) {
+    std::string msg;
+    const int vrc = learned_validate(prm, msg);
+    if (vrc != MDPF_OK) return fail(c, vrc, msg);
+    const unsigned char *blob = static_cast<const unsigned char *>(prm->model);
+    int32_t hdr[6];
+    std::memcpy(hdr, blob + 8, sizeof(hdr));
+    const bool ranges = (hdr[5] & 1) != 0;
+
+    LearnedHost *h = new LearnedHost();
+    c->learned = h;
+    h->fallback = prm->fallback != 0;
+    h->rebuild_every = prm->rebuild_every > 0 ? prm->rebuild_every : 20;
+    h->skin = prm->skin > 0 ? prm->skin : 1.0;
+    const int n = c->n;
+
+    // weights: W and W^T per element (the transposes serve the GEMMs that contract over the other index)
+    std::vector<uint16_t> W1(4 * (size_t)kH1 * kNFeat), W1T(W1.size()), W2(4 * (size_t)kH2 * kH1), W2T(W2.size());
+    std::vector<float> b1(4 * kH1), b2(4 * kH2), W3(4 * kH2), b3(4), lo, hi;
+    std::vector<double> e0(4);
+    size_t off = kHeader;
+    for (int e = 0; e < 4; ++e) {
+        uint16_t *w1 = W1.data() + (size_t)e * kH1 * kNFeat;
+        std::memcpy(w1, blob + off, (size_t)kH1 * kNFeat * 2);
+        off += (size_t)kH1 * kNFeat * 2;
+        std::memcpy(b1.data() + e * kH1, blob + off, kH1 * 4);
+        off += kH1 * 4;
+        uint16_t *w2 = W2.data() + (size_t)e * kH2 * kH1;
+        std::memcpy(w2, blob + off, (size_t)kH2 * kH1 * 2);
+        off += (size_t)kH2 * kH1 * 2;
+        std::memcpy(b2.data() + e * kH2, blob + off, kH2 * 4);
+        off += kH2 * 4;
+        std::memcpy(W3.data() + e * kH2, blob + off, kH2 * 4);
+        off += kH2 * 4;
+        std::memcpy(&b3[e], blob + off, 4);
+        off += 8;
+        std::memcpy(&e0[e], blob + off, 8);
+        off += 8;
+        for (int a = 0; a < kH1; ++a)
+            for (int f = 0; f < kNFeat; ++f)
+                W1T[(size_t)e * kNFeat * kH1 + (size_t)f * kH1 + a] = w1[(size_t)a * kNFeat + f];
+        for (int b = 0; b < kH2; ++b)
+            for (int a = 0; a < kH1; ++a) W2T[(size_t)e * kH1 * kH2 + (size_t)a * kH2 + b] = w2[(size_t)b * kH1 + a];
+    }
+    if (ranges) {
+        lo.resize(4 * kNFeat);
+        hi.resize(4 * kNFeat);
+        std::memcpy(lo.data(), blob + off, 4 * kNFeat * 4);
+        off += 4 * kNFeat * 4;
+        std::memcpy(hi.data(), blob + off, 4 * kNFeat * 4);
+    }
+
+    // MLP rows: atoms grouped by element, each group padded to kRowTile rows
+    std::vector<int> cnt(4, 0);
+    for (int i = 0; i < n; ++i) cnt[t->element[i]]++;
+    std::vector<int> start(5, 0);
+    for (int e = 0; e < 4; ++e) start[e + 1] = start[e] + (cnt[e] + kRowTile - 1) / kRowTile * kRowTile;
+    const int n_rows = start[4];
+    h->n_rows = n_rows;
+    h->row_of.assign(n, 0);
+    std::vector<int> atom_of(n_rows > 0 ? n_rows : 1, -1), tile_el(n_rows / kRowTile + 1, 0), fill(start.begin(), start.end() - 1);
+    for (int i = 0; i < n; ++i) {
+        const int r = fill[t->element[i]]++;
+        h->row_of[i] = r;
+        atom_of[r] = i;
+    }
+    for (int e = 0; e < 4; ++e)
+        for (int r = start[e]; r < start[e + 1]; r += kRowTile) tile_el[r / kRowTile] = e;
+
+    LearnedDev &L = h->dev;
+    L.n = n;
+    L.n_rows = n_rows;
+    L.el = c->d_element;
+    const float rc = (float)(5.2 + h->skin);
+    L.rc_list = rc;
+    L.rc_list2 = (float)((5.2 + h->skin) * (5.2 + h->skin));
+    L.half_skin2 = (float)(0.25 * h->skin * h->skin);
+    const int max_cells = (kMaxCellDim + 1) * (kMaxCellDim + 1) * (kMaxCellDim + 1);
+    int *d_row_of, *d_atom_of, *d_tile_el;
+    __nv_bfloat16 *dW1, *dW1T, *dW2, *dW2T;
+    float *db1, *db2, *dW3, *db3, *dlo = nullptr, *dhi = nullptr;
+    double *de0;
+    cudaError_t err = cudaSuccess;
+#define LA(p, nelem)                                                  \
+    do {                                                              \
+        if ((err = lalloc(h, &(p), (nelem))) != cudaSuccess) {        \
+            cuda_fail(c, err, "learned allocation");                  \
+            return err == cudaErrorMemoryAllocation ? MDPF_ERR_OOM : MDPF_ERR_CUDA; \
+        }                                                             \
+    } while (0)
+    LA(d_row_of, n);
+    LA(d_atom_of, atom_of.size());
+    LA(d_tile_el, tile_el.size());
+    LA(L.nb_count, n);
+    LA(L.nb_idx, (size_t)n * kKmax);
+    LA(L.pos_build, n);
+    LA(L.cell_cnt, max_cells);
+    LA(L.cell_atoms, (size_t)max_cells * kCellCap);
+    LA(L.grid, 1);
+    LA(L.bbox, 8);
+    LA(L.G16, (size_t)n_rows * kNFeat);
+    LA(L.G32, (size_t)n_rows * kNFeat);
+    LA(L.g, (size_t)n_rows * kNFeat);
+    LA(L.E_row, n_rows);
+    LA(dW1, W1.size());
+    LA(dW1T, W1T.size());
+    LA(dW2, W2.size());
+    LA(dW2T, W2T.size());
+    LA(db1, b1.size());
+    LA(db2, b2.size());
+    LA(dW3, W3.size());
+    LA(db3, 4);
+    LA(de0, 4);
+    if (ranges) {
+        LA(dlo, lo.size());
+        LA(dhi, hi.size());
+    }
+    LA(L.lflags, 4);
+    LA(L.lcount, 4);
+    LA(h->d_Gin, (size_t)n * kNFeat);
+#undef LA
+#define LC(x)                                                         \
+    do {                                                              \
+        if ((err = (x)) != cudaSuccess) return cuda_fail(c, err, #x); \
+    } while (0)
+    LC(cudaMemcpy(d_row_of, h->row_of.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(d_atom_of, atom_of.data(), sizeof(int) * atom_of.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(d_tile_el, tile_el.data(), sizeof(int) * tile_el.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(dW1, W1.data(), 2 * W1.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(dW1T, W1T.data(), 2 * W1T.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(dW2, W2.data(), 2 * W2.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(dW2T, W2T.data(), 2 * W2T.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(db1, b1.data(), 4 * b1.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(db2, b2.data(), 4 * b2.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(dW3, W3.data(), 4 * W3.size(), cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(db3, b3.data(), 16, cudaMemcpyHostToDevice));
+    LC(cudaMemcpy(de0, e0.data(), 32, cudaMemcpyHostToDevice));
+    if (ranges) {
+        LC(cudaMemcpy(dlo, lo.data(), 4 * lo.size(), cudaMemcpyHostToDevice));
+        LC(cudaMemcpy(dhi, hi.data(), 4 * hi.size(), cudaMemcpyHostToDevice));
+    }
+    LC(cudaMemset(L.G16, 0, sizeof(__nv_bfloat16) * (size_t)n_rows * kNFeat));
+    LC(cudaMemset(L.lflags, 0, sizeof(unsigned int) * 4));
+    LC(cudaMemset(L.lcount, 0, sizeof(long long) * 4));
+    LC(cudaMemset(L.nb_count, 0, sizeof(int) * n));
+    unsigned int one = 1u;
+    LC(cudaMemcpy(L.lflags, &one, sizeof(one), cudaMemcpyHostToDevice));
+#undef LC
+    L.row_of = d_row_of;
+    L.atom_of = d_atom_of;
+    L.tile_el = d_tile_el;
+    L.W1 = dW1;
+    L.W1T = dW1T;
+    L.W2 = dW2;
+    L.W2T = dW2T;
+    L.b1 = db1;
+    L.b2 = db2;
+    L.W3 = dW3;
+    L.b3 = db3;
+    L.e0 = de0;
+    L.lo = dlo;
+    L.hi = dhi;
+    return MDPF_OK;
+}
+
+int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
+                           uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s) {
+    LearnedHost *h = lh(c);
+    const LearnedDev &L = h->dev;
+    learned_begin(L, s);
+    learned_neighbors(L, pos4, forced_build, status, s);
+    learned_features(L, pos4, write_f32, s);
+    // with the fallback on, a step that left the range skips the model and runs the plain force field;
+    // with it off, the model's forces are used and the step reports MDPF_STATUS_OUT_OF_RANGE
+    const bool gated = h->fallback != 0;
+    learned_mlp(L, gated, s);
+    learned_adjoint(L, pos4, fx, efx, gated, s);
+    if (gated) {
+        PlainDev p = plain_dev(c, pos4);
+        p.status = status;
+        p.gate = L.lflags + 1;
+        launch_bonded(p, fx, efx, s);
+        launch_nonbonded(p, fx, efx, true, s);
+    }
+    learned_end(L, status, h->fallback, s);
+    return MDPF_OK;
+}
+
+// Per step, before the force evaluation: request a list rebuild when due.
+int learned_enqueue_step_prologue(mdpf_ctx *c, cudaStream_t s) {
+    LearnedHost *h = lh(c);
+    learned_displacement(h->dev, c->d_pos4, c->d_step, h->rebuild_every, s);
+    return MDPF_OK;
+}
+
+}  // namespace mdpf
+
+using namespace mdpf;
+
+#define LGUARD(c)                                                                           \
+    do {                                                                                    \
+        if ((c) == nullptr) return MDPF_ERR_INVALID_ARG;                                    \
+        if ((c)->sticky) return MDPF_ERR_CUDA;                                              \
+        if ((c)->learned == nullptr) return fail((c), MDPF_ERR_UNSUPPORTED, "not in learned mode"); \
+    } while (0)
+#define LCK(c, x)                                                 \
+    do {                                                          \
+        cudaError_t e_ = (x);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #x);     \
+    } while (0)
+
+// Upload host positions and refresh the compute-side FP32 copy.
+static int stage_positions(mdpf_ctx *c, const double *pos) {
+    LCK(c, cudaMemcpyAsync(c->d_xc, pos, sizeof(double) * 3 * c->n, cudaMemcpyHostToDevice, c->stream));
+    launch_pos4_from_x(c->d_xc, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, c->stream);
+    return MDPF_OK;
+}
+
+extern "C" {
+
+int mdpf_learned_neighbors(mdpf_ctx *c, const double *pos, int32_t max_per_atom, int32_t *count, int32_t *idx) {
+    LGUARD(c);
+    if (!pos || max_per_atom < 1) return fail(c, MDPF_ERR_INVALID_ARG, "pos is NULL or max_per_atom < 1");
+    LearnedHost *h = lh(c);
+    int rc = stage_positions(c, pos);
+    if (rc != MDPF_OK) return rc;
+    LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
+    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    std::vector<int> cnt(c->n), rows((size_t)c->n * kKmax);
+    uint32_t st = 0;
+    LCK(c, cudaMemcpyAsync(cnt.data(), h->dev.nb_count, sizeof(int) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaMemcpyAsync(rows.data(), h->dev.nb_idx, sizeof(int) * rows.size(), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaMemcpyAsync(&st, c->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaStreamSynchronize(c->stream));
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour row over capacity");
+    for (int i = 0; i < c->n; ++i) {
+        if (cnt[i] > max_per_atom) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "row longer than max_per_atom");
+        if (count) count[i] = cnt[i];
+        if (idx) std::memcpy(idx + (size_t)i * max_per_atom, rows.data() + (size_t)i * kKmax, sizeof(int) * cnt[i]);
+    }
+    return MDPF_OK;
+}
+
+int mdpf_learned_features(mdpf_ctx *c, const double *pos, float *G) {
+    LGUARD(c);
+    if (!pos) return fail(c, MDPF_ERR_INVALID_ARG, "pos is NULL");
+    LearnedHost *h = lh(c);
+    int rc = stage_positions(c, pos);
+    if (rc != MDPF_OK) return rc;
+    LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
+    learned_begin(h->dev, c->stream);
+    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    learned_features(h->dev, c->d_pos4_c, true, c->stream);
+    std::vector<float> rows((size_t)h->n_rows * kNFeat);
+    uint32_t st = 0;
+    if (!rows.empty())
+        LCK(c, cudaMemcpyAsync(rows.data(), h->dev.G32, sizeof(float) * rows.size(), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaMemcpyAsync(&st, c->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaStreamSynchronize(c->stream));
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour row over capacity");
+    if (G)
+        for (int i = 0; i < c->n; ++i)
+            std::memcpy(G + (size_t)i * kNFeat, rows.data() + (size_t)h->row_of[i] * kNFeat, sizeof(float) * kNFeat);
+    return MDPF_OK;
+}
+
+int mdpf_learned_mlp(mdpf_ctx *c, const float *G, double *E_atom, float *dEdG) {
+    LGUARD(c);
+    if (!G) return fail(c, MDPF_ERR_INVALID_ARG, "G is NULL");
+    LearnedHost *h = lh(c);
+    LCK(c, cudaMemcpyAsync(h->d_Gin, G, sizeof(float) * (size_t)c->n * kNFeat, cudaMemcpyHostToDevice, c->stream));
+    learned_import_g(h->dev, h->d_Gin, c->stream);
+    learned_mlp(h->dev, false, c->stream);
+    std::vector<double> E(h->n_rows);
+    std::vector<float> g((size_t)h->n_rows * kNFeat);
+    if (h->n_rows > 0) {
+        LCK(c, cudaMemcpyAsync(E.data(), h->dev.E_row, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, c->stream));
+        LCK(c, cudaMemcpyAsync(g.data(), h->dev.g, sizeof(float) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+    }
+    LCK(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->n; ++i) {
+        const int r = h->row_of[i];
+        if (E_atom) E_atom[i] = E[r];
+        if (dEdG) std::memcpy(dEdG + (size_t)i * kNFeat, g.data() + (size_t)r * kNFeat, sizeof(float) * kNFeat);
+    }
+    return MDPF_OK;
+}
+
+int mdpf_learned_counters(mdpf_ctx *c, int64_t *rebuilds, int64_t *fallback_steps, int32_t *max_row) {
+    LGUARD(c);
+    long long v[4];
+    LCK(c, cudaStreamSynchronize(c->stream));
+    LCK(c, cudaMemcpy(v, lh(c)->dev.lcount, sizeof(v), cudaMemcpyDeviceToHost));
+    if (rebuilds) *rebuilds = v[0];
+    if (fallback_steps) *fallback_steps = v[1];
+    if (max_row) *max_row = (int32_t)v[2];
+    return MDPF_OK;
+}
+
+}  // extern "C"

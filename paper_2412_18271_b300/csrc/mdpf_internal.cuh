@@ -25,8 +25,8 @@ constexpr int kTile = 32;          // atoms per tile (one per lane)
 constexpr int kPad = 64;           // atoms are padded to a multiple of 64 (two tiles)
 constexpr int kMaxExclPerAtom = 255;
 
-// Energy slot layout (int64 fixed point): bond, angle, LJ, Coulomb, kinetic.
-enum { E_BOND = 0, E_ANGLE = 1, E_LJ = 2, E_COUL = 3, E_KIN = 4, E_SLOTS = 8 };
+// Energy slot layout (int64 fixed point): bond, angle, LJ, Coulomb, kinetic, learned.
+enum { E_BOND = 0, E_ANGLE = 1, E_LJ = 2, E_COUL = 3, E_KIN = 4, E_LEARN = 5, E_SLOTS = 8 };
 
 __host__ __device__ inline int64_t tile_pair_index(int I, int J, int T) {
     // upper triangle (I <= J), row-major
@@ -48,6 +48,7 @@ struct PlainDev {
     const int4 *items;          // [n_items] work items of the all-pairs sum (forcefield.cuh)
     int n_items;
     uint32_t *status;           // device status word
+    const unsigned int *gate;   // if set, the kernels run only when *gate != 0 (learned-mode fallback)
 };
 
 struct Frames {
@@ -119,6 +120,9 @@ struct mdpf_ctx {
     int *d_touch_off = nullptr, *d_touch = nullptr;  // other tiles touched by those terms
     int step_grid = 0;                     // blocks of the persistent stepper
 
+    // learned mode (learned_host.cu)
+    void *learned = nullptr;               // mdpf::LearnedHost
+
     int64_t steps = 0, force_evals = 0;
     double h_initial = 0;
     bool state_set = false;
@@ -166,6 +170,14 @@ void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s);
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s);
 void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s);
 void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s);
+
+// learned_host.cu
+int learned_validate(const mdpf_params *prm, std::string &msg);
+int learned_create(mdpf_ctx *ctx, const mdpf_topology *t, const mdpf_params *prm);
+void learned_free(mdpf_ctx *ctx);
+int learned_enqueue_forces(mdpf_ctx *ctx, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
+                           uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s);
+int learned_enqueue_step_prologue(mdpf_ctx *ctx, cudaStream_t s);
 
 // stepper.cu
 int stepper_grid(const mdpf_ctx *ctx);

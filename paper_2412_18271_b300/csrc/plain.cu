@@ -43,12 +43,15 @@ __global__ void k_fx_to_forces(const unsigned long long *fx, int n3, double *f64
 __global__ void k_energy_out(const unsigned long long *efx, double *out) {
     int t = threadIdx.x;
     if (t < 5) out[1 + t] = fx_val(efx[t]);
-    if (t == 0) out[0] = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]);
+    if (t == 0)
+        out[0] = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]) +
+                 fx_val(efx[E_LEARN]);
 }
 
 // ------------------------------------------------------------------ bonded
 
 __global__ void k_bonded(PlainDev p, unsigned long long *fx, unsigned long long *efx) {
+    if (p.gate != nullptr && *p.gate == 0u) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     float eb = 0.f, ea = 0.f;
     if (t < p.n_bonds + p.n_angles) bonded_term(p, t, fx, eb, ea);
@@ -69,6 +72,7 @@ constexpr int kNbThreads = 256;
 template <bool ENERGY>
 __global__ void __launch_bounds__(kNbThreads, 2) k_nonbonded(PlainDev p, unsigned long long *fx,
                                                              unsigned long long *efx, uint32_t *status) {
+    if (p.gate != nullptr && *p.gate == 0u) return;
     __shared__ JTile jt[kNbThreads / 32];
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -148,7 +152,8 @@ __global__ void k_finish_step(const unsigned long long *efx, double *trace_u, do
     const int64_t s = *step + 1;
     *step = s;
     if (!energy) return;
-    double U = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]);
+    double U = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]) +
+               fx_val(efx[E_LEARN]);
     double K = fx_val(efx[E_KIN]);
     const int64_t e = s / energy_every - 1;
     trace_u[e % cap] = U;
@@ -218,6 +223,7 @@ PlainDev plain_dev(const mdpf_ctx *ctx, const float4 *pos4) {
     p.items = ctx->d_items;
     p.n_items = ctx->n_items;
     p.status = ctx->d_status;
+    p.gate = nullptr;
     return p;
 }
 

@@ -57,6 +57,8 @@ class mdpf_params(ctypes.Structure):
     _fields_ = [
         ("mode", _i32), ("dt_fs", _f64), ("coulomb_k", _f64), ("trace_capacity", _i32),
         ("record_every", _i32), ("max_frames", _i32), ("stepper", _i32), ("energy_every", _i32),
+        ("model", _vp), ("model_bytes", ctypes.c_uint64), ("skin", _f64), ("rebuild_every", _i32),
+        ("fallback", _i32),
     ]
 
 
@@ -91,6 +93,10 @@ def load(path: str = LIB_PATH):
         "mdpf_debug_wait_timeout": (ctypes.c_int, [_vp, _i32]),
         "mdpf_set_profiling": (ctypes.c_int, [_vp, _i32]),
         "mdpf_get_profile": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+        "mdpf_learned_neighbors": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+        "mdpf_learned_features": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mdpf_learned_mlp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "mdpf_learned_counters": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "mdpf_pairs_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _f64,
                                               _vp, _vp, _vp]),
     }
@@ -120,7 +126,9 @@ class Context:
 
     def __init__(self, system, mode: int = MDPF_MODE_PLAIN, dt_fs: float = 0.5, coulomb_k: float = 0.0,
                  trace_capacity: int = 0, record_every: int = 0, max_frames: int = 0,
-                 stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1):
+                 stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1, model: bytes | None = None,
+                 skin: float = 0.0, rebuild_every: int = 0, fallback: bool = True):
+        """mode MDPF_MODE_LEARNED needs ``model`` (a packed model blob, see model.Model.pack)."""
         L = lib()
         s = system
         self.n = int(s.element.shape[0])
@@ -156,6 +164,13 @@ class Context:
         p.max_frames = max_frames
         p.stepper = stepper
         p.energy_every = energy_every
+        if model is not None:
+            self._model = ctypes.create_string_buffer(bytes(model), len(model))
+            p.model = ctypes.addressof(self._model)
+            p.model_bytes = len(model)
+        p.skin = skin
+        p.rebuild_every = rebuild_every
+        p.fallback = 1 if fallback else 0
         h = _vp()
         rc = L.mdpf_create(ctypes.byref(t), ctypes.byref(p), ctypes.byref(h))
         if rc != MDPF_OK:
@@ -263,6 +278,36 @@ class Context:
         out = np.zeros((max(na.value, 1), 3), dtype=np.int32)
         self._check(lib().mdpf_get_angles(self._h, _ptr(out), out.shape[0], ctypes.byref(na)))
         return out[:na.value]
+
+    # -- learned-path stages (parity checks)
+    def learned_neighbors(self, pos, max_per_atom: int = 128):
+        """(count[N], rows) with rows[i] the ascending neighbour indices of atom i."""
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        cnt = np.zeros(self.n, dtype=np.int32)
+        idx = np.zeros((self.n, max_per_atom), dtype=np.int32)
+        self._check(lib().mdpf_learned_neighbors(self._h, _ptr(x), int(max_per_atom), _ptr(cnt), _ptr(idx)))
+        return cnt, [idx[i, :cnt[i]].copy() for i in range(self.n)]
+
+    def learned_features(self, pos):
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        G = np.zeros((self.n, 384), dtype=np.float32)
+        self._check(lib().mdpf_learned_features(self._h, _ptr(x), _ptr(G)))
+        return G
+
+    def learned_mlp(self, G):
+        """(E_atom[N] FP64, dE/dG[N,384] FP32) from features G[N,384]."""
+        g = np.ascontiguousarray(G, dtype=np.float32).reshape(self.n, 384)
+        E = np.zeros(self.n)
+        d = np.zeros((self.n, 384), dtype=np.float32)
+        self._check(lib().mdpf_learned_mlp(self._h, _ptr(g), _ptr(E), _ptr(d)))
+        return E, d
+
+    def learned_counters(self) -> dict:
+        rb = ctypes.c_int64()
+        fb = ctypes.c_int64()
+        mr = ctypes.c_int32()
+        self._check(lib().mdpf_learned_counters(self._h, ctypes.byref(rb), ctypes.byref(fb), ctypes.byref(mr)))
+        return {"rebuilds": rb.value, "fallback_steps": fb.value, "max_row": mr.value}
 
     def debug_set_status(self, bits: int):
         self._check(lib().mdpf_debug_set_status(self._h, bits))

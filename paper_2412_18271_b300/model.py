@@ -9,7 +9,7 @@ BF16 with FP32 accumulation); biases, W3, b3 are FP32 and e0 FP64.
 Blob layout (little endian):
   header   64 bytes: magic "MDPFMLP1", int32 version=1, n_elem=4, n_feat=384,
            h1=256, h2=128, flags (bit 0: feature ranges present), float64
-           celu_alpha, 16 bytes reserved
+           celu_alpha, 24 bytes reserved
   per element e = 0..3:
            uint16 W1[h1][n_feat] (bf16 bits), float32 b1[h1],
            uint16 W2[h2][h1] (bf16 bits),     float32 b2[h2],
@@ -26,7 +26,7 @@ import numpy as np
 N_ELEM, N_FEAT, H1, H2 = 4, 384, 256, 128
 CELU_ALPHA = 0.1
 MAGIC = b"MDPFMLP1"
-HEADER = struct.Struct("<8s6id16x")
+HEADER = struct.Struct("<8s6id24x")
 
 
 def bf16_bits(x: np.ndarray) -> np.ndarray:

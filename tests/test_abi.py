@@ -60,7 +60,8 @@ def _topo(n=3):
 
 
 @pytest.mark.parametrize("case", ["null_out", "zero_atoms", "bad_dt", "bad_mode", "bad_bond", "bad_mass",
-                                  "bad_stepper", "bad_record_every"])
+                                  "bad_stepper", "bad_record_every", "learned_no_model", "learned_bad_magic",
+                                  "learned_short", "learned_bad_alpha", "learned_bad_skin"])
 def test_create_rejects_bad_arguments_without_gpu(lib, case):
     t, keep = _topo()
     p = mdpf.mdpf_params()
@@ -77,7 +78,26 @@ def test_create_rejects_bad_arguments_without_gpu(lib, case):
         p.dt_fs = -1.0
     elif case == "bad_mode":
         p.mode = 7
-        expect = -8
+    elif case == "learned_no_model":
+        p.mode = mdpf.MDPF_MODE_LEARNED
+    elif case in ("learned_bad_magic", "learned_short", "learned_bad_alpha"):
+        from paper_2412_18271_b300 import model
+        blob = bytearray(model.init_model(0).pack())
+        if case == "learned_bad_magic":
+            blob[0:8] = b"MDPFMLP2"
+        elif case == "learned_short":
+            blob = blob[:-4]
+        else:
+            blob[32:40] = np.array([0.2]).tobytes()
+            expect = -8
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        keep = keep + (buf,)
+        p.mode = mdpf.MDPF_MODE_LEARNED
+        p.model = ctypes.addressof(buf)
+        p.model_bytes = len(blob)
+    elif case == "learned_bad_skin":
+        p.mode = mdpf.MDPF_MODE_LEARNED
+        p.skin = -1.0
     elif case == "bad_bond":
         b = np.array([[0, 5]], dtype=np.int32)
         r = np.array([1.0])

@@ -21,3 +21,9 @@ def system(pos, element, bonds=(), r0=None, k=300.0, charge=None, sigma=(3.0, 3.
         bond_k=np.full(nb, float(k)), angle_k=float(angle_k), angle_theta0_deg=float(theta0_deg),
         lj_sigma=np.asarray(sigma, dtype=np.float64), lj_eps=np.asarray(eps, dtype=np.float64),
         pos=pos, molecule=np.zeros(n, dtype=np.int32))
+
+
+def isolated(n, element=None, charge=None):
+    """n unbonded atoms (positions at the origin; callers pass their own)."""
+    el = np.zeros(n, dtype=np.int32) if element is None else np.asarray(element, dtype=np.int32)
+    return system(np.zeros((n, 3)), el, charge=charge)
