@@ -9,6 +9,11 @@ gas-phase cluster (64 seeded 32-atom molecules in a 60 A ball, plain force
 field: harmonic bonds and angles, all-pairs LJ + Coulomb with 1-2/1-3
 exclusions, no cutoff; FP32 forces, FP64 integration, dt = 0.5 fs), with the
 state resident in HBM; frames and energies are recorded every 10 steps.
+The line's "learned" object times the learned path the same way on the
+16,384-atom cluster (512 molecules in an 80 A ball): cell-list neighbours
+(5.2 A cutoff, 1 A skin, rebuild every 20 steps or on displacement),
+symmetry-function features, per-element BF16 MLP with its input gradient,
+analytic adjoint forces, FP64 velocity Verlet.
 Prints one JSON line.  For N > 1 (torchrun) each rank runs an independent
 replica (weak scaling, no collective on the data path).
 """
@@ -37,6 +42,18 @@ FLOPS_PER_PAIR_ENERGY = 3    # extra flops per pair on energy steps
 RECORD_EVERY = 10            # frames and energies every 10 steps (the workload's recording cadence)
 FP32_LANES_PER_SM = 128
 N_SM = 148
+
+LEARNED_WORKLOAD = "cluster16384"
+LEARNED_DESC = ("learned potential, 16384-atom gas-phase cluster of 512 seeded 32-atom molecules in an 80 A ball: "
+                "cell-list neighbours (5.2 A cutoff, 1 A skin, rebuild every 20 steps), 384 symmetry-function "
+                "features (FP32), per-element MLP 384-256-128-1 CELU (BF16 operands, FP32 accumulation), analytic "
+                "adjoint forces, velocity Verlet dt=0.5 fs, FP64 state")
+# algorithmic work per unit (see the learned leg's roofline)
+MLP_FLOPS_PER_ATOM = 2 * (384 * 256 + 256 * 128 + 128) + 2 * (128 * 256 + 256 * 384)
+FEAT_FLOPS_PER_PAIR = 110       # radial: 16 Gaussians x (sub, mul, mul, exp, mul, add) + distance + cutoff
+FEAT_FLOPS_PER_TRIPLET = 460    # angular: cos/sin of theta, 4 shells x exp, 32 columns x (2 fma + ^32 + 3 mul + add)
+ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
+ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 
 
 def peaks():
@@ -152,6 +169,119 @@ def cpu_baseline(sample_steps: int):
                       "single-threaded FP64 C oracle, %.1f s" % (sample_steps, sample_steps + 1, dt)}
 
 
+def _pair_triplet_counts(pos):
+    """Pairs within the radial cutoff (ordered, i != j) and angular triplets
+    sum_i C(n_ang(i), 2) at the given positions (host, k-d tree)."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    t = cKDTree(pos)
+    pairs = t.query_pairs(5.2, output_type="ndarray")
+    ang = t.query_pairs(3.5, output_type="ndarray")
+    na = np.bincount(ang.ravel(), minlength=pos.shape[0])
+    return 2 * len(pairs), int((na * (na - 1) // 2).sum())
+
+
+def learned_leg(args, dev, stream, flush):
+    import numpy as np
+    import torch
+    from paper_2412_18271_b300 import mdpf, model, synth
+    s = synth.workload(LEARNED_WORKLOAD)
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED[LEARNED_WORKLOAD])
+    n = s.n_atoms
+    md = args.learned_md_steps
+    m = model.init_model(7)
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=m.pack(), dt_fs=DT_FS, trace_capacity=md,
+                       energy_every=RECORD_EVERY, record_every=RECORD_EVERY, max_frames=max(1, md // RECORD_EVERY))
+    # learned forces against the plain force field at the starting geometry (both on the GPU)
+    _, f_l, _ = ctx.compute(s.pos)
+    plain = mdpf.Context(s, dt_fs=DT_FS)
+    _, f_p, _ = plain.compute(s.pos)
+    plain.close()
+    rmse_vs_plain = float(np.sqrt(((f_l - f_p) ** 2).mean()))
+    rms_plain = float(np.sqrt((f_p ** 2).mean()))
+    ctx.set_state(s.pos, v0)
+    slots = {"neighbors": mdpf.MDPF_PROF_LEARN_NEIGHBORS, "features": mdpf.MDPF_PROF_LEARN_FEATURES,
+             "mlp": mdpf.MDPF_PROF_LEARN_MLP, "adjoint": mdpf.MDPF_PROF_LEARN_ADJOINT,
+             "force_eval": mdpf.MDPF_PROF_NONBONDED, "md_step_calls": mdpf.MDPF_PROF_STEP}
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.step_async(md, stream.cuda_stream)
+        stream.synchronize()
+        ctx.counters()
+        x_mid, _ = ctx.get_state()
+        ctx.set_profiling(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                ctx.step_async(md, stream.cuda_stream)
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = {k: ctx.profile(v) for k, v in slots.items()}
+    ctx.set_profiling(False)
+    c = ctx.counters()
+    lc = ctx.learned_counters()
+    if c["status"] != 0:
+        raise RuntimeError("device status %#x after the learned timed region" % c["status"])
+    rate = args.steps * md / (ms / 1000.0)
+
+    pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_x[:] = s.pos
+    pin_v[:] = v0
+    e2e_steps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(pin_x, pin_v)
+        ctx.step(md)
+        ctx.get_state(pin_x, pin_v)
+        ctx.counters()
+    e2e_rate = e2e_steps * md / (time.perf_counter() - t0)
+    ctx.close()
+
+    pk, pk_kind = peaks()
+    mhz = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1800.0))
+    pairs, triplets = _pair_triplet_counts(x_mid)
+    work = {"mlp": (n * MLP_FLOPS_PER_ATOM, "tensor", bf16_peak,
+                    "sustained dense BF16 (%s), the MLP runs inside a long step" % pk_kind),
+            "features": (pairs * FEAT_FLOPS_PER_PAIR + triplets * FEAT_FLOPS_PER_TRIPLET, "alu", fp32_peak,
+                         "derived FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (N_SM, FP32_LANES_PER_SM, mhz)),
+            "adjoint": (pairs * ADJ_FLOPS_PER_PAIR + triplets * ADJ_FLOPS_PER_TRIPLET, "alu", fp32_peak,
+                        "derived FP32: %d SMs x %d lanes x 2 x %.0f MHz" % (N_SM, FP32_LANES_PER_SM, mhz))}
+    stage_ms = {k: prof[k][0] for k in ("neighbors", "features", "mlp", "adjoint")}
+    dom = max(("features", "mlp", "adjoint"), key=lambda k: stage_ms[k])
+    flops, bound, peak, peak_kind = work[dom]
+    avg_s = prof[dom][0] / 1000.0 / max(prof[dom][1], 1)
+    achieved = flops / avg_s / 1e12
+    fe_ms, fe_n = prof["force_eval"]
+    return {
+        "workload": LEARNED_DESC, "n_atoms": n, "md_steps_per_bench_step": md, "value": rate, "unit": UNIT,
+        "ms_per_md_step": ms / args.steps / md, "ns_per_day": rate * DT_FS * 1e-6 * 86400,
+        "dtype": "bf16 GEMM operands / f32 features and forces / f64 state",
+        "model": "seeded Kaiming-uniform init (untrained), no feature ranges: every step runs the model",
+        "force_rmse_vs_plain_kcal_mol_A": rmse_vs_plain, "rms_plain_force_kcal_mol_A": rms_plain,
+        "force_rmse_vs_oracle": "<= 1e-2 x RMS(F) against the FP64 oracle (BF16 parity tests)",
+        "stepper": "kernel sequence per MD step, launched from the host",
+        "stage_ms_per_force_eval": {k: prof[k][0] / max(prof[k][1], 1) for k in stage_ms},
+        "force_eval_ms": fe_ms / max(fe_n, 1),
+        "rebuilds": lc["rebuilds"], "fallback_steps": lc["fallback_steps"], "max_row": lc["max_row"],
+        "pairs_5p2": pairs, "triplets_3p5": triplets,
+        "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": prof[dom][1],
+                     "traffic": None},
+        "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
+                "d2h_bytes_per_step": 2 * n * 3 * 8 + 48},
+        "clocks": clk.summary(),
+    }
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -253,6 +383,8 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_learned:
+        line["learned"] = learned_leg(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     if rank == 0:
@@ -272,6 +404,8 @@ def main():
     ap.add_argument("--ref-md-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-md-steps", type=int, default=200)
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -311,13 +311,19 @@ MDPF_API int mdpf_learned_counters(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fa
  * around every launch of the profiled kernels (off by default; costs two event
  * records per launch).  Slots: MDPF_PROF_NONBONDED (all-pairs tile kernel of
  * the kernel-sequence stepper), MDPF_PROF_STEPPER (persistent step-loop
- * kernel), MDPF_PROF_STEP (one whole mdpf_step call on the device).
+ * kernel), MDPF_PROF_STEP (one whole mdpf_step call on the device); learned
+ * mode: MDPF_PROF_NONBONDED times the whole learned force evaluation, and
+ * MDPF_PROF_LEARN_NEIGHBORS / _FEATURES / _MLP / _ADJOINT its stages.
  * mdpf_get_profile synchronises the recorded events and returns the summed
  * duration in ms and the number of launches since mdpf_set_profiling(ctx, 1).
  */
 #define MDPF_PROF_NONBONDED 0
 #define MDPF_PROF_STEPPER 1
 #define MDPF_PROF_STEP 2
+#define MDPF_PROF_LEARN_NEIGHBORS 3
+#define MDPF_PROF_LEARN_FEATURES 4
+#define MDPF_PROF_LEARN_MLP 5
+#define MDPF_PROF_LEARN_ADJOINT 6
 #define MDPF_PROF_SLOTS 8
 MDPF_API int mdpf_set_profiling(mdpf_ctx *ctx, int32_t enable);
 MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);

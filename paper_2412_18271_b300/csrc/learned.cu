@@ -83,7 +83,7 @@ __global__ void k_nb_grid(LearnedDev L, int forced) {
     int nc = 1;
     for (int d = 0; d < 3; ++d) {
         g.lo[d] = lo[d];
-        g.dim[d] = min((int)floorf(e3[d] / cs) + 1, kMaxCellDim + 1);
+        g.dim[d] = max(1, min((int)floorf(e3[d] / cs) + 1, kMaxCellDim + 1));  // non-finite input stays in bounds
         nc *= g.dim[d];
     }
     g.cs = cs;

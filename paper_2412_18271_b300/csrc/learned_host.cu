@@ -230,13 +230,21 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     LearnedHost *h = lh(c);
     const LearnedDev &L = h->dev;
     learned_begin(L, s);
+    cudaEvent_t ev = prof_begin(c, s);
     learned_neighbors(L, pos4, forced_build, status, s);
+    prof_end(c, MDPF_PROF_LEARN_NEIGHBORS, ev, s);
+    ev = prof_begin(c, s);
     learned_features(L, pos4, write_f32, s);
+    prof_end(c, MDPF_PROF_LEARN_FEATURES, ev, s);
     // with the fallback on, a step that left the range skips the model and runs the plain force field;
     // with it off, the model's forces are used and the step reports MDPF_STATUS_OUT_OF_RANGE
     const bool gated = h->fallback != 0;
+    ev = prof_begin(c, s);
     learned_mlp(L, gated, s);
+    prof_end(c, MDPF_PROF_LEARN_MLP, ev, s);
+    ev = prof_begin(c, s);
     learned_adjoint(L, pos4, fx, efx, gated, s);
+    prof_end(c, MDPF_PROF_LEARN_ADJOINT, ev, s);
     if (gated) {
         PlainDev p = plain_dev(c, pos4);
         p.status = status;

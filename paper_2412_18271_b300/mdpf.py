@@ -28,6 +28,10 @@ MDPF_MODE_LEARNED = 1
 MDPF_PROF_NONBONDED = 0
 MDPF_PROF_STEPPER = 1
 MDPF_PROF_STEP = 2
+MDPF_PROF_LEARN_NEIGHBORS = 3
+MDPF_PROF_LEARN_FEATURES = 4
+MDPF_PROF_LEARN_MLP = 5
+MDPF_PROF_LEARN_ADJOINT = 6
 MDPF_STEPPER_PERSISTENT = 0
 MDPF_STEPPER_KERNELS = 1
 

@@ -257,6 +257,17 @@ def _ranged(m, s, widen=0.02):
     return r
 
 
+def _expanded(s, factor=1.02):
+    """The molecule stretched 2% about its centroid; some features then leave the
+    range of the unstretched geometry (checked on the oracle's features)."""
+    c = s.pos.mean(0)
+    pos = c + (s.pos - c) * factor
+    mr = _ranged(model.init_model(0), s)
+    G = O.features(s.element, pos)
+    assert np.any((G < mr.lo[s.element]) | (G > mr.hi[s.element]))
+    return pos
+
+
 def test_in_range_uses_the_model(mdl):
     s = synth.workload("mol256")
     mr = _ranged(mdl, s)
@@ -270,8 +281,7 @@ def test_in_range_uses_the_model(mdl):
 def test_out_of_range_falls_back_to_the_plain_force_field(mdl):
     s = synth.workload("mol256")
     mr = _ranged(mdl, s)
-    pos = s.pos.copy()
-    pos[17] += np.array([0.0, 0.0, 25.0])   # one atom pulled away: its features leave the range
+    pos = _expanded(s)
     ctx = _ctx(s, mr)
     e, f, terms = ctx.compute(pos)
     ep, fp, tp = O.Plain(s).energy_forces(pos)
@@ -290,8 +300,7 @@ def test_out_of_range_falls_back_to_the_plain_force_field(mdl):
 def test_out_of_range_without_fallback_is_an_error(mdl):
     s = synth.workload("mol256")
     mr = _ranged(mdl, s)
-    pos = s.pos.copy()
-    pos[17] += np.array([0.0, 0.0, 25.0])
+    pos = _expanded(s)
     ctx = _ctx(s, mr, fallback=False)
     with pytest.raises(mdpf.MdpfError) as ei:
         ctx.compute(pos)
