@@ -131,7 +131,12 @@ typedef struct mdpf_params {
     int32_t rebuild_every;   /* rebuild the list every this many steps (0 selects 20) */
     int32_t fallback;        /* 1: a step whose features leave the model's range uses the plain
                                 force field; 0: such a step reports MDPF_ERR_OUT_OF_RANGE */
+    int32_t mlp_kernel;      /* MDPF_MLP_TENSOR (0): tcgen05 tensor cores, TMA-fed;
+                                MDPF_MLP_SIMT (1): CUDA cores.  Same rounding points (BF16
+                                GEMM inputs, FP32 accumulation); sums differ in order only. */
 } mdpf_params;
+#define MDPF_MLP_TENSOR 0
+#define MDPF_MLP_SIMT 1
 
 /*
  * Learned mode (MDPF_MODE_LEARNED).  Per atom, 384 symmetry-function features

@@ -1,6 +1,7 @@
 // Learned-potential path: device data and kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "device_util.cuh"
@@ -49,8 +50,14 @@ struct LearnedDev {
     const float *b1, *b2, *W3, *b3;            // [4][256], [4][128], [4][128], [4]
     const double *e0;                          // [4]
     const float *lo, *hi;                      // [4][384] training range, or null
-    unsigned int *lflags;        // [0] rebuild requested, [1] out of range this step, [2] overflow
+    unsigned int *lflags;        // [0] rebuild requested, [1] out of range this step, [2] overflow, [3] MLP timeout
     long long *lcount;           // [0] rebuilds, [1] fallback steps, [2] max row length
+};
+
+// TMA descriptors of the MLP operands (BF16, 2-D, 64 x 128 boxes, 128-byte swizzle):
+// features G16 [n_rows][384], W1 [4*256][384], W2 [4*128][256], W2T [4*256][128], W1T [4*384][256].
+struct MlpMaps {
+    CUtensorMap g, w1, w2, w2t, w1t;
 };
 
 // launchers (learned.cu)
@@ -63,5 +70,9 @@ void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long
 void learned_begin(const LearnedDev &L, cudaStream_t s);
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s);
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s);
+
+// tensor-core MLP (mlp_tc.cu): forward energy and dE/dG, one 128-row tile per CTA
+cudaError_t learned_mlp_tc_prepare();
+cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated, cudaStream_t s);
 
 }  // namespace mdpf

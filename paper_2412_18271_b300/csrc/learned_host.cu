@@ -1,6 +1,8 @@
 // Learned mode: model-blob parsing, device buffers, the per-evaluation kernel
 // sequence (neighbours -> features -> MLP -> adjoint, or the plain force field
 // when the features leave the model's range), and the parity entry points.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -19,7 +21,42 @@ struct LearnedHost {
     int n_rows = 0;
     std::vector<int> row_of;
     float *d_Gin = nullptr;     // [n][384] staging for mdpf_learned_mlp
+    int mlp_kernel = MDPF_MLP_TENSOR;
+    MlpMaps maps{};
 };
+
+// 2-D BF16 tensor maps with 64 x 128 boxes and 128-byte swizzle for the MLP operands.
+static int make_maps(mdpf_ctx *c, LearnedHost *h) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr)
+        return fail(c, MDPF_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const LearnedDev &L = h->dev;
+    auto one = [&](CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows) {
+        cuuint64_t dims[2] = {inner, rows};
+        cuuint64_t strides[1] = {inner * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t estr[2] = {1, 1};
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!one(&h->maps.g, L.G16, kNFeat, (uint64_t)L.n_rows) || !one(&h->maps.w1, L.W1, kNFeat, 4 * kH1) ||
+        !one(&h->maps.w2, L.W2, kH1, 4 * kH2) || !one(&h->maps.w2t, L.W2T, kH2, 4 * kH1) ||
+        !one(&h->maps.w1t, L.W1T, kH1, 4 * kNFeat))
+        return fail(c, MDPF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    e = learned_mlp_tc_prepare();
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned_mlp_tc_prepare");
+    return MDPF_OK;
+}
+
+// The MLP (energy per row and dE/dG) on the selected units.
+static void enqueue_mlp(LearnedHost *h, uint32_t *status, bool gated, cudaStream_t s) {
+    if (h->mlp_kernel == MDPF_MLP_TENSOR) learned_mlp_tc(h->dev, h->maps, status, gated, s);
+    else learned_mlp(h->dev, gated, s);
+}
 
 static LearnedHost *lh(const mdpf_ctx *c) { return static_cast<LearnedHost *>(c->learned); }
 
@@ -74,6 +111,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     h->fallback = prm->fallback != 0;
     h->rebuild_every = prm->rebuild_every > 0 ? prm->rebuild_every : 20;
     h->skin = prm->skin > 0 ? prm->skin : 1.0;
+    h->mlp_kernel = prm->mlp_kernel;
     const int n = c->n;
 
     // weights: W and W^T per element (the transposes serve the GEMMs that contract over the other index)
@@ -222,7 +260,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     L.e0 = de0;
     L.lo = dlo;
     L.hi = dhi;
-    return MDPF_OK;
+    return make_maps(c, h);
 }
 
 int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
@@ -240,7 +278,7 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     // with it off, the model's forces are used and the step reports MDPF_STATUS_OUT_OF_RANGE
     const bool gated = h->fallback != 0;
     ev = prof_begin(c, s);
-    learned_mlp(L, gated, s);
+    enqueue_mlp(h, status, gated, s);
     prof_end(c, MDPF_PROF_LEARN_MLP, ev, s);
     ev = prof_begin(c, s);
     learned_adjoint(L, pos4, fx, efx, gated, s);
@@ -339,15 +377,19 @@ int mdpf_learned_mlp(mdpf_ctx *c, const float *G, double *E_atom, float *dEdG) {
     if (!G) return fail(c, MDPF_ERR_INVALID_ARG, "G is NULL");
     LearnedHost *h = lh(c);
     LCK(c, cudaMemcpyAsync(h->d_Gin, G, sizeof(float) * (size_t)c->n * kNFeat, cudaMemcpyHostToDevice, c->stream));
+    LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
     learned_import_g(h->dev, h->d_Gin, c->stream);
-    learned_mlp(h->dev, false, c->stream);
+    enqueue_mlp(h, c->d_status + 1, false, c->stream);
     std::vector<double> E(h->n_rows);
     std::vector<float> g((size_t)h->n_rows * kNFeat);
     if (h->n_rows > 0) {
         LCK(c, cudaMemcpyAsync(E.data(), h->dev.E_row, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, c->stream));
         LCK(c, cudaMemcpyAsync(g.data(), h->dev.g, sizeof(float) * g.size(), cudaMemcpyDeviceToHost, c->stream));
     }
+    uint32_t st = 0;
+    LCK(c, cudaMemcpyAsync(&st, c->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     LCK(c, cudaStreamSynchronize(c->stream));
+    if (st & MDPF_STATUS_TIMEOUT) return fail(c, MDPF_ERR_TIMEOUT, "tensor-core MLP wait timed out");
     for (int i = 0; i < c->n; ++i) {
         const int r = h->row_of[i];
         if (E_atom) E_atom[i] = E[r];

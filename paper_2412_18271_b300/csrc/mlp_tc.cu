@@ -1,0 +1,404 @@
+// Per-element MLP on the 5th-generation tensor cores: forward energy and the
+// input gradient dE/dG for one 128-row tile of same-element atoms per CTA.
+//
+//   GEMM1  H1 = G  W1^T      [128 x 256], K = 384   (TMEM columns   0..255)
+//   epi1   a1 = bf16(celu(H1 + b1))                  -> shared A operand
+//   GEMM2  H2 = a1 W2^T      [128 x 128], K = 256   (TMEM columns 256..383)
+//   epi2   E  = W3 . celu(H2 + b2) + b3 + e0;  d2 = bf16(W3 * celu'(H2 + b2))
+//   GEMM3  P1 = d2 W2        [128 x 256], K = 128   (TMEM columns 256..511)
+//   epi3   d1 = bf16(P1 * celu'(H1 + b1))
+//   GEMM4  g  = d1 W1        [128 x 384], K = 256   (TMEM columns 0..255, 256..383)
+//   epi4   g -> global FP32
+//
+// Operands are BF16 in shared memory in the 128-byte-swizzled K-major layout
+// (8-row x 128-byte atoms, the 16-byte unit index XOR-ed with the row index
+// mod 8); weight and feature K-chunks of 64 arrive by TMA through a two-stage
+// ring, the intermediate operands (a1, d2, d1) are written by the epilogue
+// warps straight into that layout.  Accumulation is FP32 in tensor memory.
+// Warps 0-3: epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows);
+// warp 4: TMA producer; warp 5: TMEM allocation and MMA issue.
+// Every wait is bounded (kWaitNs): on expiry the CTA records
+// MDPF_STATUS_TIMEOUT, drains its copies and MMAs in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "learned.cuh"
+
+namespace mdpf {
+namespace {
+
+constexpr int kTcThreads = 192;
+constexpr int kStageBytes = 64 * 1024;     // [A 16 KB][B 48 KB]
+constexpr int kStages = 2;
+constexpr int kResBytes = 64 * 1024;       // resident A operand: a1 / d2 / d1
+constexpr int kOffRes = kStages * kStageBytes;
+constexpr int kOffPar = kOffRes + kResBytes;   // b1[256] b2[128] w3[128] FP32
+constexpr int kOffBar = kOffPar + 2048;
+constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
+constexpr int kChunks = 16;                    // 6 + 4 + 2 + 4 K-chunks of 64
+constexpr long long kWaitNs = 200000000LL;     // 200 ms; a tile takes microseconds
+constexpr float kCeluAlphaTc = 0.1f;
+
+// barrier block: full[2] empty[2] acc epi drain, then tmem address, abort flag, issued, consumed
+enum { B_FULL = 0, B_EMPTY = 2, B_ACC = 4, B_EPI = 5, B_DRAIN = 6 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ long long gtimer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false when the CTA aborted (here or elsewhere).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort) {
+    if (mbar_try(a, parity)) return true;
+    const long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try(a, parity)) return true;
+        if (*abort) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+// Bounded wait used during teardown (ignores the abort flag).
+__device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity) {
+    const long long t0 = gtimer();
+    while (!mbar_try(a, parity) && gtimer() - t0 < kWaitNs) {
+    }
+}
+
+// Bounded wait by every lane of a warp, with a warp-uniform result (the
+// tensor-memory loads that follow are warp-collective).
+__device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, volatile int *abort) {
+    const bool ok = mbar_wait(a, parity, abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (load and wait in one statement).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float celu_tc(float x) { return x > 0.f ? x : kCeluAlphaTc * expm1f(x / kCeluAlphaTc); }
+__device__ __forceinline__ float dcelu_tc(float x) { return x >= 0.f ? 1.f : expf(x / kCeluAlphaTc); }
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+// Store 32 BF16 values (columns c0..c0+31 of row r, c0 a multiple of 32) into a
+// swizzled K-major operand whose 64-column chunks are 16 KB apart.
+__device__ __forceinline__ void st_operand32(unsigned char *res, int r, int c0, const float (&v)[32]) {
+    unsigned char *blk = res + (c0 >> 6) * 16384 + r * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int unit = ((c0 & 63) >> 3) + q;
+        uint4 w;
+        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+        *reinterpret_cast<uint4 *>(blk + ((unit ^ (r & 7)) << 4)) = w;
+    }
+}
+
+__device__ __forceinline__ void chunk_of(int c, int &g, int &kc) {
+    if (c < 6) { g = 0; kc = c; }
+    else if (c < 10) { g = 1; kc = c - 6; }
+    else if (c < 12) { g = 2; kc = c - 10; }
+    else { g = 3; kc = c - 12; }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, int gated) {
+    if (gated && L.lflags[1]) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(sm);
+    float *sb1 = (float *)(sm + kOffPar), *sb2 = sb1 + 256, *sw3 = sb2 + 128;
+    const uint32_t bar0 = sbase + kOffBar;
+    auto bar = [&](int k) { return bar0 + 8u * (uint32_t)k; };
+    volatile uint32_t *s_tmem = (volatile uint32_t *)(sm + kOffBar + 64);
+    volatile int *s_abort = (volatile int *)(sm + kOffBar + 68);
+    volatile int *s_issued = (volatile int *)(sm + kOffBar + 72);
+    volatile int *s_consumed = (volatile int *)(sm + kOffBar + 76);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int row0 = tile * kRowTile;
+    const int e = L.tile_el[tile];
+
+    if (tid == 0) {
+        mbar_init(bar(B_FULL), 1);
+        mbar_init(bar(B_FULL + 1), 1);
+        mbar_init(bar(B_EMPTY), 1);
+        mbar_init(bar(B_EMPTY + 1), 1);
+        mbar_init(bar(B_ACC), 1);
+        mbar_init(bar(B_EPI), 128);
+        mbar_init(bar(B_DRAIN), 1);
+        *s_abort = 0;
+        *s_issued = 0;
+        *s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32((const void *)s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int q = tid; q < 256; q += kTcThreads) sb1[q] = L.b1[e * kH1 + q];
+    for (int q = tid; q < 128; q += kTcThreads) {
+        sb2[q] = L.b2[e * kH2 + q];
+        sw3[q] = L.W3[e * kH2 + q];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 4) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int c = 0; c < kChunks; ++c) {
+                const int s = c & 1;
+                if (c >= 2 && !mbar_wait(bar(B_EMPTY + s), ((c >> 1) - 1) & 1, s_abort)) break;
+                int g, kc;
+                chunk_of(c, g, kc);
+                const uint32_t A = sbase + s * kStageBytes, B = A + 16384;
+                const int x = kc * 64;
+                const uint32_t fb = bar(B_FULL + s);
+                if (g == 0) {
+                    mbar_expect_tx(fb, 48 * 1024);
+                    tma_2d(A, &maps.g, x, row0, fb);
+                    tma_2d(B, &maps.w1, x, e * kH1, fb);
+                    tma_2d(B + 16384, &maps.w1, x, e * kH1 + 128, fb);
+                } else if (g == 1) {
+                    mbar_expect_tx(fb, 16 * 1024);
+                    tma_2d(B, &maps.w2, x, e * kH2, fb);
+                } else if (g == 2) {
+                    mbar_expect_tx(fb, 32 * 1024);
+                    tma_2d(B, &maps.w2t, x, e * kH1, fb);
+                    tma_2d(B + 16384, &maps.w2t, x, e * kH1 + 128, fb);
+                } else {
+                    mbar_expect_tx(fb, 48 * 1024);
+                    tma_2d(B, &maps.w1t, x, e * kNFeat, fb);
+                    tma_2d(B + 16384, &maps.w1t, x, e * kNFeat + 128, fb);
+                    tma_2d(B + 32768, &maps.w1t, x, e * kNFeat + 256, fb);
+                }
+                *s_issued = c + 1;
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issue
+        if (lane == 0) {
+            const uint32_t i256 = idesc_bf16(256), i128 = idesc_bf16(128);
+            const uint32_t res = sbase + kOffRes;
+            int c = 0;
+            bool ok = true;
+            for (int g = 0; g < 4 && ok; ++g) {
+                if (g > 0) {
+                    if (!mbar_wait(bar(B_EPI), (g - 1) & 1, s_abort)) break;
+                    tc_fence_after();
+                }
+                const int nk = g == 0 ? 6 : (g == 2 ? 2 : 4);
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = c & 1;
+                    if (!mbar_wait(bar(B_FULL + s), (c >> 1) & 1, s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    *s_consumed = c + 1;
+                    tc_fence_after();
+                    const uint32_t A = sbase + s * kStageBytes, B = A + 16384;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t acc = (kc | k) != 0;
+                        const uint32_t ko = 32u * k;
+                        if (g == 0) {
+                            mma_bf16(tmem, sdesc(A + ko), sdesc(B + ko), i256, acc);
+                        } else if (g == 1) {
+                            mma_bf16(tmem + 256, sdesc(res + kc * 16384 + ko), sdesc(B + ko), i128, acc);
+                        } else if (g == 2) {
+                            mma_bf16(tmem + 256, sdesc(res + kc * 16384 + ko), sdesc(B + ko), i256, acc);
+                        } else {
+                            const uint64_t a = sdesc(res + kc * 16384 + ko);
+                            mma_bf16(tmem, a, sdesc(B + ko), i256, acc);
+                            mma_bf16(tmem + 256, a, sdesc(B + 32768 + ko), i128, acc);
+                        }
+                    }
+                    mma_commit(bar(B_EMPTY + s));
+                }
+                if (ok) mma_commit(bar(B_ACC));
+            }
+        }
+    } else {
+        // ---------------- epilogue: thread = tile row (TMEM lane)
+        const int r = tid;
+        const int row = row0 + r;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        unsigned char *res = sm + kOffRes;
+        float v[32], h[32];
+        bool ok = true;
+        // epi1: a1 = bf16(celu(H1 + b1))
+        if ((ok = warp_wait(bar(B_ACC), 0, s_abort))) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int cc = 0; cc < 8; ++cc) {
+                tmem_ld32(tl + cc * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = celu_tc(v[j] + sb1[cc * 32 + j]);
+                st_operand32(res, r, cc * 32, v);
+            }
+            proxy_fence();
+            tc_fence_before();
+            mbar_arrive(bar(B_EPI));
+        }
+        // epi2: energy and d2 = bf16(W3 * celu'(H2 + b2))
+        if (ok && (ok = warp_wait(bar(B_ACC), 1, s_abort))) {
+            tc_fence_after();
+            float E = 0.f;
+#pragma unroll 1
+            for (int cc = 0; cc < 4; ++cc) {
+                tmem_ld32(tl + 256 + cc * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int c = cc * 32 + j;
+                    const float hv = v[j] + sb2[c];
+                    E = fmaf(sw3[c], celu_tc(hv), E);
+                    v[j] = sw3[c] * dcelu_tc(hv);
+                }
+                st_operand32(res, r, cc * 32, v);
+            }
+            L.E_row[row] = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
+            proxy_fence();
+            tc_fence_before();
+            mbar_arrive(bar(B_EPI));
+        }
+        // epi3: d1 = bf16(P1 * celu'(H1 + b1))
+        if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int cc = 0; cc < 8; ++cc) {
+                tmem_ld32(tl + 256 + cc * 32, v);
+                tmem_ld32(tl + cc * 32, h);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * dcelu_tc(h[j] + sb1[cc * 32 + j]);
+                st_operand32(res, r, cc * 32, v);
+            }
+            proxy_fence();
+            tc_fence_before();
+            mbar_arrive(bar(B_EPI));
+        }
+        // epi4: g = dE/dG
+        if (ok && warp_wait(bar(B_ACC), 1, s_abort)) {
+            tc_fence_after();
+            float *gr = L.g + (size_t)row * kNFeat;
+#pragma unroll 1
+            for (int cc = 0; cc < 12; ++cc) {
+                tmem_ld32(tl + cc * 32, v);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *reinterpret_cast<float4 *>(gr + cc * 32 + 4 * q) =
+                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (*s_abort) {
+        // teardown after a timeout: let copies and MMAs in flight finish before freeing tensor memory
+        if (tid == 0) {
+            for (int c = *s_consumed; c < *s_issued; ++c) mbar_drain(bar(B_FULL + (c & 1)), (c >> 1) & 1);
+            atomicOr(status, MDPF_STATUS_TIMEOUT);
+            atomicOr(&L.lflags[3], 1u);
+        }
+        if (tid == 32 * 5) {
+            mma_commit(bar(B_DRAIN));
+            mbar_drain(bar(B_DRAIN), 0);
+        }
+        __syncthreads();
+    }
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t learned_mlp_tc_prepare() {
+    return cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated, cudaStream_t s) {
+    if (L.n_rows > 0) k_mlp_tc<<<L.n_rows / kRowTile, kTcThreads, kSmemBytes, s>>>(L, maps, status, gated ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace mdpf

@@ -34,6 +34,8 @@ MDPF_PROF_LEARN_MLP = 5
 MDPF_PROF_LEARN_ADJOINT = 6
 MDPF_STEPPER_PERSISTENT = 0
 MDPF_STEPPER_KERNELS = 1
+MDPF_MLP_TENSOR = 0
+MDPF_MLP_SIMT = 1
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -62,7 +64,7 @@ class mdpf_params(ctypes.Structure):
         ("mode", _i32), ("dt_fs", _f64), ("coulomb_k", _f64), ("trace_capacity", _i32),
         ("record_every", _i32), ("max_frames", _i32), ("stepper", _i32), ("energy_every", _i32),
         ("model", _vp), ("model_bytes", ctypes.c_uint64), ("skin", _f64), ("rebuild_every", _i32),
-        ("fallback", _i32),
+        ("fallback", _i32), ("mlp_kernel", _i32),
     ]
 
 
@@ -131,7 +133,8 @@ class Context:
     def __init__(self, system, mode: int = MDPF_MODE_PLAIN, dt_fs: float = 0.5, coulomb_k: float = 0.0,
                  trace_capacity: int = 0, record_every: int = 0, max_frames: int = 0,
                  stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1, model: bytes | None = None,
-                 skin: float = 0.0, rebuild_every: int = 0, fallback: bool = True):
+                 skin: float = 0.0, rebuild_every: int = 0, fallback: bool = True,
+                 mlp_kernel: int = MDPF_MLP_TENSOR):
         """mode MDPF_MODE_LEARNED needs ``model`` (a packed model blob, see model.Model.pack)."""
         L = lib()
         s = system
@@ -175,6 +178,7 @@ class Context:
         p.skin = skin
         p.rebuild_every = rebuild_every
         p.fallback = 1 if fallback else 0
+        p.mlp_kernel = mlp_kernel
         h = _vp()
         rc = L.mdpf_create(ctypes.byref(t), ctypes.byref(p), ctypes.byref(h))
         if rc != MDPF_OK:

@@ -171,10 +171,14 @@ def _mlp_emulated(m, element, G):
     return E, g
 
 
+MLP_KERNELS = [mdpf.MDPF_MLP_TENSOR, mdpf.MDPF_MLP_SIMT]
+
+
+@pytest.mark.parametrize("kernel", MLP_KERNELS)
 @pytest.mark.parametrize("name", ["mol64", "mol256"])
-def test_mlp_matches_oracle_and_emulation(name, mdl):
+def test_mlp_matches_oracle_and_emulation(name, kernel, mdl):
     s = synth.workload(name)
-    ctx = _ctx(s, mdl)
+    ctx = _ctx(s, mdl, mlp_kernel=kernel)
     Go = O.features(s.element, s.pos)
     G32 = Go.astype(np.float32)
     E, dG = ctx.learned_mlp(G32)
@@ -188,11 +192,12 @@ def test_mlp_matches_oracle_and_emulation(name, mdl):
     assert np.sqrt(((dG - ge) ** 2).mean()) <= 1e-3 * np.sqrt((ge ** 2).mean())
 
 
-def test_mlp_rows_of_every_element_and_padding(mdl):
+@pytest.mark.parametrize("kernel", MLP_KERNELS)
+def test_mlp_rows_of_every_element_and_padding(kernel, mdl):
     # 1..3 atoms per element exercise the per-element row padding
     el = np.array([0, 1, 1, 2, 3, 3, 3, 0], dtype=np.int32)
     s = tiny.isolated(el.size, element=el)
-    ctx = _ctx(s, mdl)
+    ctx = _ctx(s, mdl, mlp_kernel=kernel)
     rng = np.random.default_rng(5)
     G = rng.uniform(0.0, 2.0, size=(el.size, 384)).astype(np.float32)
     E, dG = ctx.learned_mlp(G)
@@ -201,12 +206,41 @@ def test_mlp_rows_of_every_element_and_padding(mdl):
     assert np.sqrt(((dG - ge) ** 2).mean()) <= 1e-3 * np.sqrt((ge ** 2).mean())
 
 
+def test_tensor_and_simt_mlp_agree_over_many_tiles(mdl):
+    # 2048 atoms -> 17 row tiles of 128 over four elements; random features in the
+    # range the workloads produce, so every GEMM sees dense nonzero operands
+    s = synth.workload("cluster2048")
+    rng = np.random.default_rng(9)
+    G = (rng.gamma(0.5, 1.0, size=(s.n_atoms, 384)) * (rng.random((s.n_atoms, 384)) < 0.6)).astype(np.float32)
+    out = []
+    for kernel in MLP_KERNELS:
+        ctx = _ctx(s, mdl, mlp_kernel=kernel)
+        out.append(ctx.learned_mlp(G))
+    (Et, gt), (Es, gs) = out
+    Ee, ge = _mlp_emulated(mdl, s.element, G.astype(np.float64))
+    assert np.max(np.abs(Et - Ee)) <= 1e-4 * max(1.0, np.max(np.abs(Ee)))
+    assert np.max(np.abs(Et - Es)) <= 1e-4 * max(1.0, np.max(np.abs(Ee)))
+    assert np.sqrt(((gt - gs) ** 2).mean()) <= 1e-3 * np.sqrt((gs ** 2).mean())
+    assert np.sqrt(((gt - ge) ** 2).mean()) <= 1e-3 * np.sqrt((ge ** 2).mean())
+
+
+@pytest.mark.parametrize("kernel", MLP_KERNELS)
+def test_mlp_kernels_are_deterministic(kernel, mdl):
+    s = synth.workload("mol256")
+    ctx = _ctx(s, mdl, mlp_kernel=kernel)
+    G = O.features(s.element, s.pos).astype(np.float32)
+    E1, g1 = ctx.learned_mlp(G)
+    E2, g2 = ctx.learned_mlp(G)
+    assert np.array_equal(E1, E2) and np.array_equal(g1, g2)
+
+
 # ------------------------------------------------------------ energy and forces
 
+@pytest.mark.parametrize("kernel", MLP_KERNELS)
 @pytest.mark.parametrize("name", ["mol64", "mol256", "cluster2048"])
-def test_energy_forces_match_oracle(name, mdl):
+def test_energy_forces_match_oracle(name, kernel, mdl):
     s = synth.workload(name)
-    ctx = _ctx(s, mdl)
+    ctx = _ctx(s, mdl, mlp_kernel=kernel)
     e, f, terms = ctx.compute(s.pos)
     eo, fo, _ = O.Learned(mdl).energy_forces(s.element, s.pos)
     n = s.n_atoms
