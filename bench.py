@@ -282,6 +282,17 @@ def learned_leg(args, dev, stream, flush):
     }
 
 
+def run_learned_only(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2412_18271_b300 import build
+    build.build()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    print(json.dumps({"learned": learned_leg(args, dev, stream, flush)}), flush=True)
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -406,9 +417,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-md-steps", type=int, default=200)
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--only-learned", action="store_true",
+                    help="run and print the learned leg alone (profiling runs; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_learned:
+        run_learned_only(args)
     else:
         run_ours(args)
 

@@ -23,8 +23,9 @@ constexpr float kTwoPowM31 = 4.656612873077393e-10f;  // 2^-31 = 2^(1 - zeta), z
 
 __device__ __forceinline__ float fcut(float r, float rc) { return r < rc ? 0.5f * cosf(kPi * r / rc) + 0.5f : 0.f; }
 __device__ __forceinline__ float dfcut(float r, float rc) { return r < rc ? -0.5f * kPi / rc * sinf(kPi * r / rc) : 0.f; }
-__device__ __forceinline__ float celu(float x) { return x > 0.f ? x : kCeluAlpha * expm1f(x / kCeluAlpha); }
-__device__ __forceinline__ float dcelu(float x) { return x >= 0.f ? 1.f : expf(x / kCeluAlpha); }
+// CELU(0.1) and its derivative, exp(10 x) from the fast exponential (as in the tensor-core MLP)
+__device__ __forceinline__ float celu(float x) { return x > 0.f ? x : kCeluAlpha * (__expf(10.f * x) - 1.f); }
+__device__ __forceinline__ float dcelu(float x) { return x >= 0.f ? 1.f : __expf(10.f * x); }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ int pair_index(int a, int b) {
@@ -192,13 +193,16 @@ struct NbrSmem {
     int j[kKmax];
     int el[kKmax];
     float4 d[kKmax];      // dx, dy, dz, r
-    int ang[kKmax];       // neighbours within the angular cutoff
+    int rad[kKmax];       // neighbours within the radial cutoff, in row order
+    int ang[kKmax];       // neighbours within the angular cutoff, in row order
 };
 
 // Load atom i's neighbours into shared memory; returns the row length and the
-// number of neighbours within the angular cutoff.
+// numbers of neighbours within the radial and angular cutoffs.  The compacted
+// in-cutoff lists do not depend on how far the list radius reaches beyond the
+// cutoffs, so neither does any summation order below.
 __device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
-                                                int &cnt, int &na) {
+                                                int &cnt, int &nr, int &na) {
     const float4 pi = pos4[i];
     cnt = L.nb_count[i];
     for (int q = lane; q < cnt; q += 32) {
@@ -210,13 +214,18 @@ __device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float
         s.d[q] = make_float4(dx, dy, dz, sqrtf(dx * dx + dy * dy + dz * dz));
     }
     __syncwarp();
+    nr = 0;
     na = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int q = base + lane;
-        const bool in = q < cnt && s.d[q].w < kRcAng;
-        const unsigned int bal = __ballot_sync(0xffffffffu, in);
-        if (in) s.ang[na + __popc(bal & ((1u << lane) - 1u))] = q;
-        na += __popc(bal);
+        const float r = q < cnt ? s.d[q].w : 1e30f;
+        const unsigned int below = (1u << lane) - 1u;
+        const unsigned int br = __ballot_sync(0xffffffffu, r < kRcRad);
+        if (r < kRcRad) s.rad[nr + __popc(br & below)] = q;
+        nr += __popc(br);
+        const unsigned int ba = __ballot_sync(0xffffffffu, r < kRcAng);
+        if (r < kRcAng) s.ang[na + __popc(ba & below)] = q;
+        na += __popc(ba);
     }
     __syncwarp();
 }
@@ -242,18 +251,17 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
     NbrSmem &s = sn[w];
     for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
     for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
-    int cnt, na;
-    load_neighbours(L, pos4, i, s, lane, cnt, na);
-    // radial: lane = 16 h + k takes neighbours q = h, h + 2, ...
+    int cnt, nr, na;
+    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
+    // radial: lane = 16 h + k takes the in-cutoff neighbours u = h, h + 2, ...
     {
         const int h = lane >> 4, k = lane & 15;
         const float Rk = 0.9f + (float)k * (4.3f / 16.f);
-        for (int q = h; q < cnt; q += 2) {
+        for (int u = h; u < nr; u += 2) {
+            const int q = s.rad[u];
             const float r = s.d[q].w;
-            if (r < kRcRad) {
-                const float x = r - Rk;
-                accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * fcut(r, kRcRad);
-            }
+            const float x = r - Rk;
+            accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * fcut(r, kRcRad);
         }
     }
     // angular: lane = 8 m + p owns the (m, p) column of every pair block
@@ -407,15 +415,25 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
 
 // ------------------------------------------------------------------ adjoint
 
+// Angular blocks of g are stored 33 floats apart so that lanes working on
+// different element pairs read different banks.
+constexpr int kAngStride = 33;
+
 struct AdjSmem {
-    float g[kNFeat];
-    unsigned long long f[kKmax + 1][3];  // fixed-point forces on the neighbours and (last slot) on atom i
+    float g[64 + 10 * kAngStride];
+    unsigned long long f[kKmax][3];  // fixed-point forces on the neighbours
 };
 
 __device__ __forceinline__ void sadd(unsigned long long *p, float v) {
     atomicAdd(p, (unsigned long long)fx_from_float(v));
 }
 
+// F = -dE/dx by the chain rule through the features: for every radial pair and
+// angular triplet around atom i, the contraction of g = dE/dG_i with the
+// derivative of the feature terms.  Forces on the neighbours accumulate in
+// shared int64 fixed point (order-free); the force on atom i accumulates in
+// registers per lane in a fixed triplet order and is reduced over the warp in a
+// fixed shuffle order, so the result is reproducible bit for bit.
 __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
                                                              int gated) {
     if (gated && L.lflags[1]) return;
@@ -427,15 +445,19 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
     NbrSmem &s = sn[w];
     AdjSmem &A = sa[w];
     const int row = L.row_of[i];
-    for (int f = lane; f < kNFeat; f += 32) A.g[f] = L.g[(size_t)row * kNFeat + f];
-    for (int q = lane; q < (kKmax + 1) * 3; q += 32) (&A.f[0][0])[q] = 0ull;
-    int cnt, na;
-    load_neighbours(L, pos4, i, s, lane, cnt, na);
+    const float *grow = L.g + (size_t)row * kNFeat;
+    for (int f = lane; f < 64; f += 32) A.g[f] = grow[f];
+    for (int f = lane; f < 320; f += 32) A.g[64 + (f >> 5) * kAngStride + (f & 31)] = grow[64 + f];
+    int cnt, nr, na;
+    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
+    for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0ull;
+    __syncwarp();
+    float fix = 0.f, fiy = 0.f, fiz = 0.f;
     // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j -= dE/dr u,  F_i += dE/dr u
-    for (int q = lane; q < cnt; q += 32) {
+    for (int u = lane; u < nr; u += 32) {
+        const int q = s.rad[u];
         const float4 d = s.d[q];
         const float r = d.w;
-        if (!(r < kRcRad)) continue;
         const float fc = fcut(r, kRcRad), dfc = dfcut(r, kRcRad);
         const float *gz = A.g + 16 * s.el[q];
         float dEdr = 0.f;
@@ -445,15 +467,23 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
             const float ex = expf(-kEtaR * x * x);
             dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
         }
-        const float sx = dEdr * d.x / r, sy = dEdr * d.y / r, sz = dEdr * d.z / r;
+        const float ir = 1.f / r;
+        const float sx = dEdr * d.x * ir, sy = dEdr * d.y * ir, sz = dEdr * d.z * ir;
         sadd(&A.f[q][0], -sx);
         sadd(&A.f[q][1], -sy);
         sadd(&A.f[q][2], -sz);
-        sadd(&A.f[kKmax][0], sx);
-        sadd(&A.f[kKmax][1], sy);
-        sadd(&A.f[kKmax][2], sz);
+        fix += sx;
+        fiy += sy;
+        fiz += sz;
     }
     // angular triplets
+    float cpv[8], spv[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+        cpv[p] = cosf(thp);
+        spv[p] = sinf(thp);
+    }
     const int ntrip = na * (na - 1) / 2;
     for (int t = lane; t < ntrip; t += 32) {
         int a, b;
@@ -461,16 +491,28 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         const int qa = s.ang[a], qb = s.ang[b];
         const float4 dj = s.d[qa], dk = s.d[qb];
         const float rj = dj.w, rk = dk.w;
-        const float ujx = dj.x / rj, ujy = dj.y / rj, ujz = dj.z / rj;
-        const float ukx = dk.x / rk, uky = dk.y / rk, ukz = dk.z / rk;
+        const float irj = 1.f / rj, irk = 1.f / rk;
+        const float ujx = dj.x * irj, ujy = dj.y * irj, ujz = dj.z * irj;
+        const float ukx = dk.x * irk, uky = dk.y * irk, ukz = dk.z * irk;
         const float ct = ujx * ukx + ujy * uky + ujz * ukz;
         const float cs = kAngScale * ct;
         const float sn2 = sqrtf(1.f - cs * cs);
+        const float cot = cs / sn2;
         const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
         const float dfj = dfcut(rj, kRcAng), dfk = dfcut(rk, kRcAng);
         const float C = fj * fk;
         const float ravg = 0.5f * (rj + rk);
-        const float *gp = A.g + 64 + 32 * pair_index(s.el[qa], s.el[qb]);
+        const float *gp = A.g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
+        // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
+        float Ap[8], dAp[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
+            const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
+            const float b31 = b16 * b8 * b4 * b2 * base;
+            Ap[p] = kTwoPowM31 * b31 * base;
+            dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
+        }
         float Sc = 0.f, Sr = 0.f, SC = 0.f;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -480,16 +522,9 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
             float sa_ = 0.f, sdA = 0.f;
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
-                const float thp = (float)(2 * p + 1) * (kPi / 16.f);
-                const float cp = cosf(thp), sp = sinf(thp);
-                const float base = 1.f + cs * cp + sn2 * sp;
-                float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
-                const float b31 = b16 * b8 * b4 * b2 * base;
-                const float Ap = kTwoPowM31 * b31 * base;
-                const float dAp = kTwoPowM31 * 32.f * b31 * (cp - cs / sn2 * sp);
                 const float gv = gp[8 * m + p];
-                sa_ = fmaf(gv, Ap, sa_);
-                sdA = fmaf(gv, dAp, sdA);
+                sa_ = fmaf(gv, Ap[p], sa_);
+                sdA = fmaf(gv, dAp[p], sdA);
             }
             Sc = fmaf(sdA, B * C, Sc);
             Sr = fmaf(sa_, dB * C, Sr);
@@ -497,21 +532,21 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         }
         const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
         const float gc = Sc * kAngScale;
-        const float gjx = gc * (ukx - ct * ujx) / rj + dEdrj * ujx;
-        const float gjy = gc * (uky - ct * ujy) / rj + dEdrj * ujy;
-        const float gjz = gc * (ukz - ct * ujz) / rj + dEdrj * ujz;
-        const float gkx = gc * (ujx - ct * ukx) / rk + dEdrk * ukx;
-        const float gky = gc * (ujy - ct * uky) / rk + dEdrk * uky;
-        const float gkz = gc * (ujz - ct * ukz) / rk + dEdrk * ukz;
+        const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;
+        const float gjy = gc * (uky - ct * ujy) * irj + dEdrj * ujy;
+        const float gjz = gc * (ukz - ct * ujz) * irj + dEdrj * ujz;
+        const float gkx = gc * (ujx - ct * ukx) * irk + dEdrk * ukx;
+        const float gky = gc * (ujy - ct * uky) * irk + dEdrk * uky;
+        const float gkz = gc * (ujz - ct * ukz) * irk + dEdrk * ukz;
         sadd(&A.f[qa][0], -gjx);
         sadd(&A.f[qa][1], -gjy);
         sadd(&A.f[qa][2], -gjz);
         sadd(&A.f[qb][0], -gkx);
         sadd(&A.f[qb][1], -gky);
         sadd(&A.f[qb][2], -gkz);
-        sadd(&A.f[kKmax][0], gjx + gkx);
-        sadd(&A.f[kKmax][1], gjy + gky);
-        sadd(&A.f[kKmax][2], gjz + gkz);
+        fix += gjx + gkx;
+        fiy += gjy + gky;
+        fiz += gjz + gkz;
     }
     __syncwarp();
     for (int q = lane; q < cnt; q += 32) {
@@ -520,7 +555,17 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         for (int c = 0; c < 3; ++c)
             if (A.f[q][c]) atomicAdd(&fx[3 * j + c], A.f[q][c]);
     }
-    if (lane < 3) atomicAdd(&fx[3 * i + lane], A.f[kKmax][lane]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fix += __shfl_xor_sync(0xffffffffu, fix, o);
+        fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
+        fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&fx[3 * i + 0], (unsigned long long)fx_from_float(fix));
+        atomicAdd(&fx[3 * i + 1], (unsigned long long)fx_from_float(fiy));
+        atomicAdd(&fx[3 * i + 2], (unsigned long long)fx_from_float(fiz));
+    }
 }
 
 // Sum of the per-row energies into the fixed-point learned-energy slot.

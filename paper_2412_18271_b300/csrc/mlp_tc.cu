@@ -15,8 +15,9 @@
 // mod 8); weight and feature K-chunks of 64 arrive by TMA through a two-stage
 // ring, the intermediate operands (a1, d2, d1) are written by the epilogue
 // warps straight into that layout.  Accumulation is FP32 in tensor memory.
-// Warps 0-3: epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows);
-// warp 4: TMA producer; warp 5: TMEM allocation and MMA issue.
+// Warps 0-15: epilogue (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. those
+// tile rows, and column group w / 4); warp 16: TMA producer; warp 17: TMEM
+// allocation and MMA issue.
 // Every wait is bounded (kWaitNs): on expiry the CTA records
 // MDPF_STATUS_TIMEOUT, drains its copies and MMAs in flight, frees its tensor
 // memory and returns.
@@ -28,13 +29,17 @@
 namespace mdpf {
 namespace {
 
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kTcThreads = kEpiThreads + 64;
+constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
 constexpr int kStageBytes = 64 * 1024;     // [A 16 KB][B 48 KB]
 constexpr int kStages = 2;
 constexpr int kResBytes = 64 * 1024;       // resident A operand: a1 / d2 / d1
 constexpr int kOffRes = kStages * kStageBytes;
-constexpr int kOffPar = kOffRes + kResBytes;   // b1[256] b2[128] w3[128] FP32
-constexpr int kOffBar = kOffPar + 2048;
+constexpr int kOffPar = kOffRes + kResBytes;   // b1[256] b2[128] w3[128] E partials[4][128], FP32
+constexpr int kOffBar = kOffPar + 4096;
+constexpr int kGStride = 36;                   // padded row of a 32 x 32 FP32 staging block of g
 constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
 constexpr int kChunks = 16;                    // 6 + 4 + 2 + 4 K-chunks of 64
 constexpr long long kWaitNs = 200000000LL;     // 200 ms; a tile takes microseconds
@@ -144,8 +149,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float celu_tc(float x) { return x > 0.f ? x : kCeluAlphaTc * expm1f(x / kCeluAlphaTc); }
-__device__ __forceinline__ float dcelu_tc(float x) { return x >= 0.f ? 1.f : expf(x / kCeluAlphaTc); }
+// CELU(0.1) and its derivative; exp(10 x) from the fast exponential (its error
+// is far below the BF16 rounding that follows on every operand path)
+__device__ __forceinline__ float celu_tc(float x) { return x > 0.f ? x : kCeluAlphaTc * (__expf(10.f * x) - 1.f); }
+__device__ __forceinline__ float dcelu_tc(float x) { return x >= 0.f ? 1.f : __expf(10.f * x); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
@@ -180,7 +188,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
-    float *sb1 = (float *)(sm + kOffPar), *sb2 = sb1 + 256, *sw3 = sb2 + 128;
+    float *sb1 = (float *)(sm + kOffPar), *sb2 = sb1 + 256, *sw3 = sb2 + 128, *sEp = sw3 + 128;
     const uint32_t bar0 = sbase + kOffBar;
     auto bar = [&](int k) { return bar0 + 8u * (uint32_t)k; };
     volatile uint32_t *s_tmem = (volatile uint32_t *)(sm + kOffBar + 64);
@@ -199,14 +207,14 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         mbar_init(bar(B_EMPTY), 1);
         mbar_init(bar(B_EMPTY + 1), 1);
         mbar_init(bar(B_ACC), 1);
-        mbar_init(bar(B_EPI), 128);
+        mbar_init(bar(B_EPI), kEpiThreads);
         mbar_init(bar(B_DRAIN), 1);
         *s_abort = 0;
         *s_issued = 0;
         *s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          smem_u32((const void *)s_tmem))
                      : "memory");
@@ -222,7 +230,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    if (warp == 4) {
+    if (warp == kProducerWarp) {
         // ---------------- TMA producer
         if (lane == 0) {
             for (int c = 0; c < kChunks; ++c) {
@@ -254,7 +262,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
                 *s_issued = c + 1;
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == kMmaWarp) {
         // ---------------- MMA issue
         if (lane == 0) {
             const uint32_t i256 = idesc_bf16(256), i128 = idesc_bf16(128);
@@ -298,18 +306,19 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             }
         }
     } else {
-        // ---------------- epilogue: thread = tile row (TMEM lane)
-        const int r = tid;
+        // ---------------- epilogue: lane = tile row (TMEM lane), warp group cg = column range
+        const int q4 = warp & 3, cg = warp >> 2;
+        const int r = 32 * q4 + lane;
         const int row = row0 + r;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
         unsigned char *res = sm + kOffRes;
         float v[32], h[32];
         bool ok = true;
-        // epi1: a1 = bf16(celu(H1 + b1))
+        // epi1: a1 = bf16(celu(H1 + b1)), columns 64 cg .. 64 cg + 63
         if ((ok = warp_wait(bar(B_ACC), 0, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
-            for (int cc = 0; cc < 8; ++cc) {
+            for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = celu_tc(v[j] + sb1[cc * 32 + j]);
@@ -319,32 +328,34 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             tc_fence_before();
             mbar_arrive(bar(B_EPI));
         }
-        // epi2: energy and d2 = bf16(W3 * celu'(H2 + b2))
+        // epi2: energy partial and d2 = bf16(W3 * celu'(H2 + b2)), columns 32 cg .. 32 cg + 31
         if (ok && (ok = warp_wait(bar(B_ACC), 1, s_abort))) {
             tc_fence_after();
             float E = 0.f;
-#pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                tmem_ld32(tl + 256 + cc * 32, v);
+            tmem_ld32(tl + 256 + cg * 32, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int c = cc * 32 + j;
-                    const float hv = v[j] + sb2[c];
-                    E = fmaf(sw3[c], celu_tc(hv), E);
-                    v[j] = sw3[c] * dcelu_tc(hv);
-                }
-                st_operand32(res, r, cc * 32, v);
+            for (int j = 0; j < 32; ++j) {
+                const int c = cg * 32 + j;
+                const float hv = v[j] + sb2[c];
+                E = fmaf(sw3[c], celu_tc(hv), E);
+                v[j] = sw3[c] * dcelu_tc(hv);
             }
-            L.E_row[row] = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
+            st_operand32(res, r, cg * 32, v);
+            sEp[cg * 128 + r] = E;
             proxy_fence();
             tc_fence_before();
             mbar_arrive(bar(B_EPI));
         }
-        // epi3: d1 = bf16(P1 * celu'(H1 + b1))
+        epi_sync();   // energy partials of the four column groups are in shared memory
+        if (ok && cg == 0) {
+            const float E = ((sEp[r] + sEp[128 + r]) + sEp[256 + r]) + sEp[384 + r];
+            L.E_row[row] = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
+        }
+        // epi3: d1 = bf16(P1 * celu'(H1 + b1)), columns 64 cg .. 64 cg + 63
         if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
-            for (int cc = 0; cc < 8; ++cc) {
+            for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + 256 + cc * 32, v);
                 tmem_ld32(tl + cc * 32, h);
 #pragma unroll
@@ -355,17 +366,27 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             tc_fence_before();
             mbar_arrive(bar(B_EPI));
         }
-        // epi4: g = dE/dG
+        // epi4: g = dE/dG, columns 96 cg .. 96 cg + 95, through a per-warp 32 x 32 staging
+        // block (in the operand ring, idle once the last GEMM completed) for coalesced stores
         if (ok && warp_wait(bar(B_ACC), 1, s_abort)) {
             tc_fence_after();
-            float *gr = L.g + (size_t)row * kNFeat;
+            float *stg = (float *)sm + warp * 32 * kGStride;
+            float *gtile = L.g + (size_t)(row0 + 32 * q4) * kNFeat;
 #pragma unroll 1
-            for (int cc = 0; cc < 12; ++cc) {
+            for (int cc = 3 * cg; cc < 3 * cg + 3; ++cc) {
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    *reinterpret_cast<float4 *>(gr + cc * 32 + 4 * q) =
+                    *reinterpret_cast<float4 *>(stg + lane * kGStride + 4 * q) =
                         make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int f = it * 32 + lane, rr = f >> 3, c4 = f & 7;
+                    *reinterpret_cast<float4 *>(gtile + (size_t)rr * kNFeat + cc * 32 + 4 * c4) =
+                        *reinterpret_cast<const float4 *>(stg + rr * kGStride + 4 * c4);
+                }
+                __syncwarp();
             }
         }
         tc_fence_before();
@@ -378,13 +399,13 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             atomicOr(status, MDPF_STATUS_TIMEOUT);
             atomicOr(&L.lflags[3], 1u);
         }
-        if (tid == 32 * 5) {
+        if (tid == 32 * kMmaWarp) {
             mma_commit(bar(B_DRAIN));
             mbar_drain(bar(B_DRAIN), 0);
         }
         __syncthreads();
     }
-    if (warp == 5) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
