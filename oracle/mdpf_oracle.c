@@ -519,3 +519,89 @@ double orc_learned_energy_forces(const orc_mlp *M, int32_t n, const int32_t *el,
     if (!G_out) free(G);
     return E;
 }
+
+/* ---------------------------------------------------------------- training gradient */
+
+static double orc_d2celu(double z, double a) { return z >= 0 ? 0.0 : exp(z / a) / a; }
+
+/*
+ * Parameter gradient of  J = sum_i [ c_i E_i - D_i ],  D_i = u_i . dE_i/dG_i,
+ * accumulated into gW1 [4][h1][F], gb1 [4][h1], gW2 [4][h2][h1], gb2 [4][h2],
+ * gW3 [4][h2], gb3 [4].  With c_i the energy-loss weight of atom i's frame and
+ * u_i the feature JVP of the force-loss gradient, J's parameter gradient is
+ * the force-matching loss gradient (the force term reaches the parameters
+ * through the input gradient, so it is reverse mode over the tangent pass):
+ *   primal   h1 = W1 G + b1, a1 = s(h1); h2 = W2 a1 + b2, a2 = s(h2); E = W3 . a2 + b3 + e0
+ *   tangent  t1 = W1 u, ta1 = s'(h1) t1; t2 = W2 ta1, ta2 = s'(h2) t2; D = W3 . ta2
+ * then one reverse sweep over both, last operation first.  s'' is taken as 0
+ * for z >= 0 and exp(z/alpha)/alpha below.
+ */
+void orc_mlp_param_grad(const orc_mlp *M, int32_t n, const int32_t *el, const double *G, const double *U,
+                        const double *c, double *gW1, double *gb1, double *gW2, double *gb2, double *gW3,
+                        double *gb3) {
+    const int F = M->n_feat, H1 = M->h1, H2 = M->h2;
+    const double al = M->alpha;
+    double *h1 = (double *)malloc(sizeof(double) * H1), *a1 = (double *)malloc(sizeof(double) * H1);
+    double *t1 = (double *)malloc(sizeof(double) * H1), *ta1 = (double *)malloc(sizeof(double) * H1);
+    double *h2 = (double *)malloc(sizeof(double) * H2), *a2 = (double *)malloc(sizeof(double) * H2);
+    double *t2 = (double *)malloc(sizeof(double) * H2), *ta2 = (double *)malloc(sizeof(double) * H2);
+    double *bt2 = (double *)malloc(sizeof(double) * H2), *bh2 = (double *)malloc(sizeof(double) * H2);
+    double *bt1 = (double *)malloc(sizeof(double) * H1), *bh1 = (double *)malloc(sizeof(double) * H1);
+    double *bta1 = (double *)malloc(sizeof(double) * H1), *ba1 = (double *)malloc(sizeof(double) * H1);
+    for (int i = 0; i < n; ++i) {
+        const int e = el[i];
+        const double *g = G + (size_t)i * F, *u = U + (size_t)i * F;
+        const double *W1 = M->W1[e], *W2 = M->W2[e], *W3 = M->W3[e];
+        /* primal and tangent */
+        for (int a = 0; a < H1; ++a) {
+            double s = M->b1[e][a], t = 0;
+            for (int f = 0; f < F; ++f) {
+                s += W1[(size_t)a * F + f] * g[f];
+                t += W1[(size_t)a * F + f] * u[f];
+            }
+            h1[a] = s;
+            a1[a] = orc_celu(s, al);
+            t1[a] = t;
+            ta1[a] = orc_dcelu(s, al) * t;
+        }
+        for (int b = 0; b < H2; ++b) {
+            double s = M->b2[e][b], t = 0;
+            for (int a = 0; a < H1; ++a) {
+                s += W2[(size_t)b * H1 + a] * a1[a];
+                t += W2[(size_t)b * H1 + a] * ta1[a];
+            }
+            h2[b] = s;
+            a2[b] = orc_celu(s, al);
+            t2[b] = t;
+            ta2[b] = orc_dcelu(s, al) * t;
+        }
+        /* reverse: J = c E - W3 . ta2 */
+        const double ci = c[i];
+        gb3[e] += ci;
+        for (int b = 0; b < H2; ++b) {
+            gW3[e * H2 + b] += ci * a2[b] - ta2[b];
+            const double bta2 = -W3[b], ba2 = ci * W3[b];
+            bt2[b] = orc_dcelu(h2[b], al) * bta2;
+            bh2[b] = orc_d2celu(h2[b], al) * t2[b] * bta2 + orc_dcelu(h2[b], al) * ba2;
+            gb2[e * H2 + b] += bh2[b];
+            for (int a = 0; a < H1; ++a)
+                gW2[((size_t)e * H2 + b) * H1 + a] += bt2[b] * ta1[a] + bh2[b] * a1[a];
+        }
+        for (int a = 0; a < H1; ++a) {
+            double s_t = 0, s_h = 0;
+            for (int b = 0; b < H2; ++b) {
+                s_t += W2[(size_t)b * H1 + a] * bt2[b];
+                s_h += W2[(size_t)b * H1 + a] * bh2[b];
+            }
+            bta1[a] = s_t;
+            ba1[a] = s_h;
+            bt1[a] = orc_dcelu(h1[a], al) * bta1[a];
+            bh1[a] = orc_d2celu(h1[a], al) * t1[a] * bta1[a] + orc_dcelu(h1[a], al) * ba1[a];
+            gb1[e * H1 + a] += bh1[a];
+            for (int f = 0; f < F; ++f)
+                gW1[((size_t)e * H1 + a) * F + f] += bt1[a] * u[f] + bh1[a] * g[f];
+        }
+    }
+    free(h1); free(a1); free(t1); free(ta1); free(h2); free(a2); free(t2); free(ta2);
+    free(bt2); free(bh2); free(bt1); free(bh1); free(bta1); free(ba1);
+}

@@ -262,3 +262,80 @@ class Learned:
         G = np.zeros((x.shape[0], N_FEAT))
         E = _learned_lib().orc_learned_energy_forces(ctypes.byref(self._st), x.shape[0], _p(el), _p(x), _p(F), _p(G))
         return E, F, G
+
+
+# ---------------------------------------------------------------- training loss and gradient
+
+def _grad_arrays(model):
+    return {"W1": np.zeros((4,) + model.W1.shape[1:]), "b1": np.zeros((4, model.W1.shape[1])),
+            "W2": np.zeros((4,) + model.W2.shape[1:]), "b2": np.zeros((4, model.W2.shape[1])),
+            "W3": np.zeros((4, model.W2.shape[1])), "b3": np.zeros(4)}
+
+
+def mlp_param_grad(model, element, G, U, c, out=None):
+    """Parameter gradient of sum_i [c_i E_i - U_i . dE_i/dG_i] (accumulated into ``out``)."""
+    L = _learned_lib()
+    L.orc_mlp_param_grad.restype = None
+    lrn = Learned(model)
+    el = np.ascontiguousarray(element, dtype=np.int32)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    g = _grad_arrays(model) if out is None else out
+    L.orc_mlp_param_grad(ctypes.byref(lrn._st), el.shape[0], _p(el), _p(G), _p(U), _p(c),
+                         _p(g["W1"]), _p(g["b1"]), _p(g["W2"]), _p(g["b2"]), _p(g["W3"]), _p(g["b3"]))
+    return g
+
+
+def train_loss_grad(model, frames, w_force: float = 10.0):
+    """Force-matching loss over a batch of frames and its parameter gradient (FP64).
+
+    frames: list of (element [N], pos [N,3], E_ref, F_ref [N,3]).
+      L = (1/B) sum_f ((E_f - E_ref,f) / N_f)^2  +  w_force * mean over all force components (F - F_ref)^2
+    Steps per frame: features G; energies and dE/dG; forces F = -J^T dE/dG; the
+    loss terms; v = dL/dF; U = J v (feature JVP); then the MLP parameter
+    gradient of sum_i [c E_i - U_i . dE_i/dG_i] with c = dL/dE_f.
+    Returns (L, grads dict, per-frame (E, F)).
+    """
+    B = len(frames)
+    n_comp = sum(3 * f[0].shape[0] for f in frames)
+    lrn = Learned(model)
+    loss = 0.0
+    grads = _grad_arrays(model)
+    outs = []
+    for el, pos, e_ref, f_ref in frames:
+        n = el.shape[0]
+        G = features(el, pos)
+        E, _, dG = lrn.mlp(el, G)
+        F = feature_forces(el, pos, dG)
+        loss += ((E - e_ref) / n) ** 2 / B + w_force * float(((F - f_ref) ** 2).sum()) / n_comp
+        c = np.full(n, 2.0 * (E - e_ref) / (n * n) / B)
+        v = 2.0 * w_force * (F - f_ref) / n_comp
+        U = feature_jvp(el, pos, v)
+        mlp_param_grad(model, el, G, U, c, out=grads)
+        outs.append((E, F))
+    return loss, grads, outs
+
+
+# ---------------------------------------------------------------- AdamW with cosine decay
+
+def cosine_lr(t: int, lr_max: float, T: int) -> float:
+    """lr_t = lr_max * (1 + cos(pi t / T)) / 2, t = 0 .. T (0 afterwards)."""
+    if t >= T:
+        return 0.0
+    return lr_max * 0.5 * (1.0 + np.cos(np.pi * t / T))
+
+
+def adamw_step(theta, grad, m, v, t: int, lr: float, betas=(0.9, 0.999), eps=1e-8, wd=0.01):
+    """One AdamW update (decoupled weight decay) at step t (1-based), in place:
+    m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;  mh = m / (1 - b1^t);  vh = v / (1 - b2^t)
+    theta = theta - lr (mh / (sqrt(vh) + eps) + wd theta)."""
+    b1, b2 = betas
+    m *= b1
+    m += (1.0 - b1) * grad
+    v *= b2
+    v += (1.0 - b2) * grad * grad
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    theta -= lr * (mh / (np.sqrt(vh) + eps) + wd * theta)
+    return theta
