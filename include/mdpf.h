@@ -312,6 +312,55 @@ MDPF_API int mdpf_learned_mlp(mdpf_ctx *ctx, const float *G, double *E_atom, flo
 MDPF_API int mdpf_learned_counters(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fallback_steps, int32_t *max_row);
 
 /*
+ * Force-matching training of the learned potential on the device.  The caller
+ * owns every tensor (device pointers; e.g. torch tensors' data_ptr()):
+ *   parameters  flat FP32, per element e = 0..3 (H, C, N, O), 131,585 each
+ *               (526,340 in total): W1 [256][384], b1 [256], W2 [128][256],
+ *               b2 [128], W3 [128], b3 (the forward rounds W1, W2 to BF16);
+ *   batch       n_frames frames of atoms_per_frame atoms: positions
+ *               [n][3] FP64 (A), elements [n] int32, reference energies
+ *               [n_frames] FP64 (kcal/mol), reference forces [n][3] FP32.
+ * mdpf_trainer_loss_grad enqueues on cuda_stream:
+ *   L = (1/B) sum_f ((E_f - E_ref,f)/N)^2 + w_force (1/(3 N B)) sum (F - F_ref)^2
+ * into d_loss3 = {L, energy part, force part} (FP64) and dL/dparams into
+ * d_grad (same layout).  The force term's gradient is reverse mode over the
+ * MLP's tangent pass along U = J dL/dF (feature JVP); every reduction runs in
+ * a fixed order, so the gradient is reproducible bit for bit.  Neighbours: all
+ * pairs within 5.2 A of the same frame.  The trainer also tracks the min/max
+ * of every feature per element over all batches it has seen
+ * (mdpf_trainer_feature_range, host [4][384] each).  mdpf_trainer_status
+ * synchronises and reports NEIGHBOR_OVERFLOW (a row over 128) or TIMEOUT.
+ * mdpf_adamw_step: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr (m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps) + weight_decay p), step t >= 1.
+ */
+typedef struct mdpf_trainer mdpf_trainer;
+typedef struct mdpf_train_params {
+    int32_t max_frames;        /* frames per batch, at most */
+    int32_t atoms_per_frame;   /* N, the same for every frame */
+    double w_force;            /* force-loss weight (10) */
+    double e0[4];              /* per-element self energies (not trained) */
+} mdpf_train_params;
+#define MDPF_TRAIN_PARAMS_PER_ELEMENT 131585
+MDPF_API int mdpf_trainer_create(const mdpf_train_params *params, mdpf_trainer **out);
+MDPF_API void mdpf_trainer_destroy(mdpf_trainer *trainer);
+MDPF_API const char *mdpf_trainer_last_error(const mdpf_trainer *trainer);
+MDPF_API int mdpf_trainer_loss_grad(mdpf_trainer *trainer, const float *d_params, float *d_grad, int32_t n_frames,
+                                    const double *d_pos, const int32_t *d_element, const double *d_E_ref,
+                                    const float *d_F_ref, double *d_loss3, void *cuda_stream);
+MDPF_API int mdpf_trainer_status(mdpf_trainer *trainer, uint32_t *status);
+MDPF_API int mdpf_trainer_feature_range(mdpf_trainer *trainer, float *lo, float *hi);
+MDPF_API int mdpf_adamw_step(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t n, int64_t step,
+                             double lr, double beta1, double beta2, double eps, double weight_decay,
+                             void *cuda_stream);
+
+/*
+ * Feature JVP at host positions pos [N,3] along host vectors v [N,3]:
+ * U [N][384] FP32 = sum_a dG/dx_a . v_a (the tangent the training gradient
+ * uses; for parity checks).  Learned mode only.
+ */
+MDPF_API int mdpf_learned_jvp(mdpf_ctx *ctx, const double *pos, const float *v, float *U);
+
+/*
  * Per-kernel device timing with CUDA events recorded on the launching stream
  * around every launch of the profiled kernels (off by default; costs two event
  * records per launch).  Slots: MDPF_PROF_NONBONDED (all-pairs tile kernel of

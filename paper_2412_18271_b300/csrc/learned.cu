@@ -322,6 +322,7 @@ constexpr int kMlpRows = 8;
 
 __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
     if (gated && L.lflags[1]) return;
+    if (L.n_tiles_live != nullptr && (int)(blockIdx.x * kMlpRows / kRowTile) >= *L.n_tiles_live) return;
     __shared__ float sG[kMlpRows][kNFeat];
     __shared__ float sA1[kMlpRows][kH1];
     __shared__ float sH1d[kMlpRows][kH1];
@@ -568,6 +569,102 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
     }
 }
 
+// ------------------------------------------------------------------ feature JVP
+
+// Tangent of the features along per-atom vectors v: U_i = sum_a dG_i/dx_a . v_a.
+// Same lane layout and summation order as k_features; per pair the tangent of
+// r_ij is u_ij . (v_j - v_i), per triplet that of cos(theta) is
+// ((u_k - c u_j)/r_j) . (v_j - v_i) + ((u_j - c u_k)/r_k) . (v_k - v_i).
+__global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const float4 *pos4, const float *v, float *U) {
+    __shared__ NbrSmem sn[kFeatWarps];
+    __shared__ float accR[kFeatWarps][2][64];
+    __shared__ float accA[kFeatWarps][320];
+    __shared__ float tcs[kFeatWarps][32], tsn[kFeatWarps][32], tcot[kFeatWarps][32], tcsd[kFeatWarps][32];
+    __shared__ float tC[kFeatWarps][32], tCd[kFeatWarps][32], tB[kFeatWarps][32][4], tBd[kFeatWarps][32][4];
+    __shared__ int tP[kFeatWarps][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFeatWarps + w;
+    if (i >= L.n) return;
+    NbrSmem &s = sn[w];
+    for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
+    for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
+    int cnt, nr, na;
+    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
+    const float vix = v[3 * i], viy = v[3 * i + 1], viz = v[3 * i + 2];
+    {
+        const int h = lane >> 4, k = lane & 15;
+        const float Rk = 0.9f + (float)k * (4.3f / 16.f);
+        for (int u = h; u < nr; u += 2) {
+            const int q = s.rad[u];
+            const float4 d = s.d[q];
+            const int j = s.j[q];
+            const float r = d.w;
+            const float rdot = (d.x * (v[3 * j] - vix) + d.y * (v[3 * j + 1] - viy) + d.z * (v[3 * j + 2] - viz)) / r;
+            const float x = r - Rk;
+            const float ex = expf(-kEtaR * x * x);
+            accR[w][h][16 * s.el[q] + k] += ex * (-2.f * kEtaR * x * fcut(r, kRcRad) + dfcut(r, kRcRad)) * rdot;
+        }
+    }
+    {
+        const int m = lane >> 3, p = lane & 7;
+        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+        const float cp = cosf(thp), sp = sinf(thp);
+        const int ntrip = na * (na - 1) / 2;
+        for (int base = 0; base < ntrip; base += 32) {
+            const int t = base + lane;
+            if (t < ntrip) {
+                int a, b;
+                triplet_ab(t, na, a, b);
+                const int qa = s.ang[a], qb = s.ang[b];
+                const float4 dj = s.d[qa], dk = s.d[qb];
+                const int ja = s.j[qa], jb = s.j[qb];
+                const float rj = dj.w, rk = dk.w;
+                const float ujx = dj.x / rj, ujy = dj.y / rj, ujz = dj.z / rj;
+                const float ukx = dk.x / rk, uky = dk.y / rk, ukz = dk.z / rk;
+                const float wjx = v[3 * ja] - vix, wjy = v[3 * ja + 1] - viy, wjz = v[3 * ja + 2] - viz;
+                const float wkx = v[3 * jb] - vix, wky = v[3 * jb + 1] - viy, wkz = v[3 * jb + 2] - viz;
+                const float ct = (dj.x * dk.x + dj.y * dk.y + dj.z * dk.z) / (rj * rk);
+                const float rjd = ujx * wjx + ujy * wjy + ujz * wjz, rkd = ukx * wkx + uky * wky + ukz * wkz;
+                const float ctd = ((ukx - ct * ujx) * wjx + (uky - ct * ujy) * wjy + (ukz - ct * ujz) * wjz) / rj +
+                                  ((ujx - ct * ukx) * wkx + (ujy - ct * uky) * wky + (ujz - ct * ukz) * wkz) / rk;
+                const float cs = kAngScale * ct;
+                const float sn2 = sqrtf(1.f - cs * cs);
+                tcs[w][lane] = cs;
+                tsn[w][lane] = sn2;
+                tcot[w][lane] = cs / sn2;
+                tcsd[w][lane] = kAngScale * ctd;
+                const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
+                tC[w][lane] = fj * fk;
+                tCd[w][lane] = dfcut(rj, kRcAng) * fk * rjd + fj * dfcut(rk, kRcAng) * rkd;
+                const float ravg = 0.5f * (rj + rk), ravgd = 0.5f * (rjd + rkd);
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) {
+                    const float x = ravg - (0.9f + (float)mm * 0.65f);
+                    const float B = expf(-kEtaA * x * x);
+                    tB[w][lane][mm] = B;
+                    tBd[w][lane][mm] = -2.f * kEtaA * x * B * ravgd;
+                }
+                tP[w][lane] = pair_index(s.el[qa], s.el[qb]);
+            }
+            __syncwarp();
+            const int nt = min(32, ntrip - base);
+            for (int u = 0; u < nt; ++u) {
+                const float x = 1.f + tcs[w][u] * cp + tsn[w][u] * sp;
+                const float x2 = x * x, x4 = x2 * x2, x8 = x4 * x4, x16 = x8 * x8;
+                const float x31 = x16 * x8 * x4 * x2 * x;
+                const float A = kTwoPowM31 * x31 * x;
+                const float dA = kTwoPowM31 * 32.f * x31 * (cp - tcot[w][u] * sp);
+                const float B = tB[w][u][m], C = tC[w][u];
+                accA[w][32 * tP[w][u] + lane] += dA * tcsd[w][u] * B * C + A * (tBd[w][u][m] * C + B * tCd[w][u]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    float *out = U + (size_t)L.row_of[i] * kNFeat;
+    for (int f = lane; f < kNFeat; f += 32) out[f] = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
+}
+
 // Sum of the per-row energies into the fixed-point learned-energy slot.
 __global__ void k_learn_energy(LearnedDev L, unsigned long long *efx, int gated) {
     if (gated && L.lflags[1]) return;
@@ -605,6 +702,10 @@ void learned_begin(const LearnedDev &L, cudaStream_t s) { k_learn_begin<<<1, 32,
 
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s) {
     k_learn_end<<<1, 32, 0, s>>>(L, status, fallback);
+}
+
+void learned_jvp(const LearnedDev &L, const float4 *pos4, const float *v, float *U, cudaStream_t s) {
+    k_jvp<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, v, U);
 }
 
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s) {

@@ -26,6 +26,7 @@ struct CellGrid {
 // Everything the learned kernels read or write.
 struct LearnedDev {
     int n, n_rows;
+    const int *n_tiles_live;     // device count of row tiles in use (training batches), or null: all n_rows / 128
     const int *el;               // [n]
     const int *row_of;           // [n] atom -> MLP row
     const int *atom_of;          // [n_rows] MLP row -> atom, -1 on padding rows
@@ -70,6 +71,8 @@ void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long
 void learned_begin(const LearnedDev &L, cudaStream_t s);
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s);
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s);
+// feature JVP: U [n_rows][384] (rows of the atoms) = sum_a dG/dx_a . v_a, v [n][3]
+void learned_jvp(const LearnedDev &L, const float4 *pos4, const float *v, float *U, cudaStream_t s);
 
 // tensor-core MLP (mlp_tc.cu): forward energy and dE/dG, one 128-row tile per CTA
 cudaError_t learned_mlp_tc_prepare();

@@ -21,6 +21,8 @@ struct LearnedHost {
     int n_rows = 0;
     std::vector<int> row_of;
     float *d_Gin = nullptr;     // [n][384] staging for mdpf_learned_mlp
+    float *d_vin = nullptr;     // [n][3] tangent staging for mdpf_learned_jvp (allocated on first use)
+    float *d_U = nullptr;       // [n_rows][384] JVP output (allocated on first use)
     int mlp_kernel = MDPF_MLP_TENSOR;
     MlpMaps maps{};
 };
@@ -395,6 +397,33 @@ int mdpf_learned_mlp(mdpf_ctx *c, const float *G, double *E_atom, float *dEdG) {
         if (E_atom) E_atom[i] = E[r];
         if (dEdG) std::memcpy(dEdG + (size_t)i * kNFeat, g.data() + (size_t)r * kNFeat, sizeof(float) * kNFeat);
     }
+    return MDPF_OK;
+}
+
+int mdpf_learned_jvp(mdpf_ctx *c, const double *pos, const float *v, float *U) {
+    LGUARD(c);
+    if (!pos || !v) return fail(c, MDPF_ERR_INVALID_ARG, "pos or v is NULL");
+    LearnedHost *h = lh(c);
+    if (h->d_vin == nullptr) {
+        cudaError_t e = lalloc(h, &h->d_vin, 3 * (size_t)c->n);
+        if (e == cudaSuccess) e = lalloc(h, &h->d_U, (size_t)h->n_rows * kNFeat);
+        if (e != cudaSuccess) return cuda_fail(c, e, "learned JVP scratch");
+    }
+    int rc = stage_positions(c, pos);
+    if (rc != MDPF_OK) return rc;
+    LCK(c, cudaMemcpyAsync(h->d_vin, v, sizeof(float) * 3 * c->n, cudaMemcpyHostToDevice, c->stream));
+    LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
+    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    learned_jvp(h->dev, c->d_pos4_c, h->d_vin, h->d_U, c->stream);
+    std::vector<float> rows((size_t)h->n_rows * kNFeat);
+    uint32_t st = 0;
+    LCK(c, cudaMemcpyAsync(rows.data(), h->d_U, sizeof(float) * rows.size(), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaMemcpyAsync(&st, c->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    LCK(c, cudaStreamSynchronize(c->stream));
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return fail(c, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour row over capacity");
+    if (U)
+        for (int i = 0; i < c->n; ++i)
+            std::memcpy(U + (size_t)i * kNFeat, rows.data() + (size_t)h->row_of[i] * kNFeat, sizeof(float) * kNFeat);
     return MDPF_OK;
 }
 

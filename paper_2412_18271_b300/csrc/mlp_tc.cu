@@ -185,6 +185,7 @@ __device__ __forceinline__ void chunk_of(int c, int &g, int &kc) {
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, int gated) {
     if (gated && L.lflags[1]) return;
+    if (L.n_tiles_live != nullptr && (int)blockIdx.x >= *L.n_tiles_live) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);

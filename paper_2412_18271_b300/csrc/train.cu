@@ -1,0 +1,788 @@
+// Force-matching training of the learned potential on the device.
+//
+// One call evaluates, for a batch of B frames of N atoms each,
+//   L = (1/B) sum_f ((E_f - E_ref,f) / N)^2  +  w * (1/(3 N B)) sum_{f,a,c} (F - F_ref)^2
+// and its gradient in the FP32 master parameters:
+//   1. rows: per frame, atoms grouped by element into 128-row tiles;
+//   2. neighbours per frame (all pairs within 5.2 A, FP32 predicate, ascending);
+//   3. features (FP32 and the BF16 GEMM copy), MLP energies and dE/dG on the
+//      tensor cores, forces by the feature adjoint;
+//   4. per frame: c = dL/dE_f, v = dL/dF;  U = J v by the feature JVP;
+//   5. per row: primal and tangent passes of the MLP along U, then one reverse
+//      sweep over both for sum_i [c E_i - U_i . dE_i/dG_i]; the row adjoints
+//      are stored;
+//   6. weight gradients as fixed-order reductions over the rows of each
+//      element (split over the row range, splits summed in order), so the
+//      gradient is reproducible bit for bit.
+// Parameters (flat FP32, per element e = 0..3, kParamsPerElement each):
+//   W1 [256][384], b1 [256], W2 [128][256], b2 [128], W3 [128], b3.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "learned.cuh"
+
+namespace mdpf {
+namespace {
+
+constexpr int kOW1 = 0, kOb1 = kH1 * kNFeat, kOW2 = kOb1 + kH1, kOb2 = kOW2 + kH2 * kH1, kOW3 = kOb2 + kH2,
+              kOb3 = kOW3 + kH2, kPPE = kOb3 + 1;
+constexpr int kSplits = 8;
+constexpr int kTrRows = 8;   // rows per block of the training MLP kernel
+
+// ------------------------------------------------------------ batch layout
+
+// Per frame: atoms of each element and the frame's row tiles.
+__global__ void k_tr_count(const int *el, int N, int *cnt, int *ntile) {
+    __shared__ int c[4];
+    const int f = blockIdx.x;
+    if (threadIdx.x < 4) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int a = threadIdx.x; a < N; a += blockDim.x) atomicAdd(&c[el[(size_t)f * N + a]], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int e = 0; e < 4; ++e) {
+            cnt[4 * f + e] = c[e];
+            t += (c[e] + kRowTile - 1) / kRowTile;
+        }
+        ntile[f] = t;
+    }
+}
+
+__global__ void k_tr_scan(int B, const int *ntile, int *tile_off, int *n_tiles_live) {
+    if (threadIdx.x != 0) return;
+    int t = 0;
+    for (int f = 0; f < B; ++f) {
+        tile_off[f] = t;
+        t += ntile[f];
+    }
+    tile_off[B] = t;
+    *n_tiles_live = t;
+}
+
+// Rows: within a frame, element groups in order H, C, N, O, each padded to
+// 128 rows; within a group, atoms in index order (block-wide scans).
+__global__ void __launch_bounds__(1024) k_tr_rows(const int *el, int N, const int *cnt, const int *tile_off,
+                                                  int *row_of, int *atom_of, int *tile_el) {
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ int base[4];
+    const int f = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int start[4];
+    {
+        int tt = tile_off[f];
+        for (int e = 0; e < 4; ++e) {
+            start[e] = tt;
+            const int nt = (cnt[4 * f + e] + kRowTile - 1) / kRowTile;
+            for (int q = t; q < nt; q += blockDim.x) tile_el[tt + q] = e;
+            tt += nt;
+        }
+    }
+    if (t < 4) base[t] = 0;
+    __syncthreads();
+    for (int a0 = 0; a0 < N; a0 += blockDim.x) {
+        const int a = a0 + t;
+        const int e = a < N ? el[(size_t)f * N + a] : -1;
+        // packed per-element counters (16 bits each), inclusive scan over the block
+        unsigned long long x = e >= 0 ? (1ull << (16 * e)) : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long y = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            warp_tot[lane] = y;
+        }
+        __syncthreads();
+        const unsigned long long incl = x + (wid > 0 ? warp_tot[wid - 1] : 0ull);
+        if (e >= 0) {
+            const int rank = (int)((incl >> (16 * e)) & 0xFFFFull) - 1 + base[e];
+            const int row = start[e] * kRowTile + rank;
+            row_of[(size_t)f * N + a] = row;
+            atom_of[row] = f * N + a;
+        }
+        __syncthreads();
+        if (t < 4) base[t] += (int)((warp_tot[(blockDim.x >> 5) - 1] >> (16 * t)) & 0xFFFFull);
+        __syncthreads();
+    }
+}
+
+__global__ void k_tr_pos(const double *pos, int n, float4 *pos4) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n) pos4[a] = make_float4((float)pos[3 * a], (float)pos[3 * a + 1], (float)pos[3 * a + 2], 0.f);
+}
+
+// Neighbours within the atom's own frame, brute force, ascending; warp per atom.
+__global__ void k_tr_nb(LearnedDev L, const float4 *pos4, int N, uint32_t *status) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= L.n) return;
+    const int i = w, f0 = (i / N) * N;
+    const float4 pi = pos4[i];
+    int m = 0;
+    for (int j0 = f0; j0 < f0 + N; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        if (j < f0 + N && j != i) {
+            const float4 pj = pos4[j];
+            const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+            in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < L.rc_list2;
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, in);
+        const int q = m + __popc(bal & ((1u << lane) - 1u));
+        if (in && q < kKmax) L.nb_idx[(size_t)i * kKmax + q] = j;
+        m += __popc(bal);
+    }
+    if (lane == 0) {
+        L.nb_count[i] = min(m, kKmax);
+        if (m > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+    }
+}
+
+// BF16 weights (and their transposes) and contiguous FP32 bias / output vectors from the master parameters.
+__global__ void k_tr_weights(const float *P, __nv_bfloat16 *W1, __nv_bfloat16 *W1T, __nv_bfloat16 *W2,
+                             __nv_bfloat16 *W2T, float *b1, float *b2, float *W3, float *b3) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.y;
+    const float *p = P + (size_t)e * kPPE;
+    if (q < kH1 * kNFeat) {
+        const int a = q / kNFeat, f = q % kNFeat;
+        const __nv_bfloat16 v = __float2bfloat16_rn(p[kOW1 + q]);
+        W1[(size_t)e * kH1 * kNFeat + q] = v;
+        W1T[(size_t)e * kNFeat * kH1 + (size_t)f * kH1 + a] = v;
+    }
+    if (q < kH2 * kH1) {
+        const int b = q / kH1, a = q % kH1;
+        const __nv_bfloat16 v = __float2bfloat16_rn(p[kOW2 + q]);
+        W2[(size_t)e * kH2 * kH1 + q] = v;
+        W2T[(size_t)e * kH1 * kH2 + (size_t)a * kH2 + b] = v;
+    }
+    if (q < kH1) b1[e * kH1 + q] = p[kOb1 + q];
+    if (q < kH2) {
+        b2[e * kH2 + q] = p[kOb2 + q];
+        W3[e * kH2 + q] = p[kOW3 + q];
+    }
+    if (q == 0) b3[e] = p[kOb3];
+}
+
+// Feature range of the training data (per element and feature), order-free min/max.
+__device__ __forceinline__ unsigned int ord_u(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+// One block per row tile, one thread per feature.
+__global__ void k_tr_range(LearnedDev L, unsigned int *rmin, unsigned int *rmax) {
+    const int tile = blockIdx.x, f = threadIdx.x;
+    if (tile >= *L.n_tiles_live || f >= kNFeat) return;
+    const int e = L.tile_el[tile];
+    unsigned int lo = 0xFFFFFFFFu, hi = 0u;
+    for (int row = tile * kRowTile; row < (tile + 1) * kRowTile; ++row) {
+        if (L.atom_of[row] < 0) continue;
+        const unsigned int u = ord_u(L.G32[(size_t)row * kNFeat + f]);
+        lo = min(lo, u);
+        hi = max(hi, u);
+    }
+    if (hi != 0u) {
+        atomicMin(&rmin[e * kNFeat + f], lo);
+        atomicMax(&rmax[e * kNFeat + f], hi);
+    }
+}
+
+// ------------------------------------------------------------ loss
+
+__device__ double block_sum_d(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    return t;   // valid in thread 0
+}
+
+// Per frame: energy, energy-loss weight c (per row), force residual -> v, loss parts.
+__global__ void k_tr_loss(LearnedDev L, int N, int B, double w_force, const int *tile_off, const double *E_ref,
+                          const float *F_ref, const unsigned long long *fx, float *c_row, float *v,
+                          double *loss_parts) {
+    __shared__ double sh[32];
+    __shared__ double s_c;
+    const int f = blockIdx.x;
+    const int r0 = tile_off[f] * kRowTile, r1 = tile_off[f + 1] * kRowTile;
+    double e = 0.0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) e += L.E_row[r];
+    const double Ef = block_sum_d(e, sh);
+    if (threadIdx.x == 0) {
+        const double d = (Ef - E_ref[f]) / N;
+        loss_parts[2 * f] = d * d / B;
+        s_c = 2.0 * d / N / B;
+    }
+    __syncthreads();
+    const float cf = (float)s_c;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) c_row[r] = L.atom_of[r] >= 0 ? cf : 0.f;
+    const double scale = 2.0 * w_force / (3.0 * N * B);
+    double sse = 0.0;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        const size_t k = (size_t)f * 3 * N + q;
+        const double d = fx_val(fx[k]) - (double)F_ref[k];
+        v[k] = (float)(scale * d);
+        sse += d * d;
+    }
+    const double S = block_sum_d(sse, sh);
+    if (threadIdx.x == 0) loss_parts[2 * f + 1] = w_force * S / (3.0 * N * B);
+}
+
+__global__ void k_tr_loss_total(int B, const double *parts, double *loss3) {
+    if (threadIdx.x != 0) return;
+    double le = 0.0, lf = 0.0;
+    for (int f = 0; f < B; ++f) {
+        le += parts[2 * f];
+        lf += parts[2 * f + 1];
+    }
+    loss3[0] = le + lf;
+    loss3[1] = le;
+    loss3[2] = lf;
+}
+
+// ------------------------------------------------------------ per-row reverse over the tangent pass
+
+__device__ __forceinline__ float tr_s(float z) { return z > 0.f ? z : 0.1f * (__expf(10.f * z) - 1.f); }
+__device__ __forceinline__ float tr_ds(float z) { return z >= 0.f ? 1.f : __expf(10.f * z); }
+__device__ __forceinline__ float tr_dds(float z) { return z >= 0.f ? 0.f : 10.f * __expf(10.f * z); }
+
+struct RowOut {
+    float *bh1, *bt1, *a1, *ta1;   // [rows][256]
+    float *bh2, *bt2, *w3g;        // [rows][128]
+};
+
+// kTrRows rows of one element per block, thread t = hidden unit.  FP32
+// arithmetic on the BF16-valued weights; FP32 features G and tangents U.
+__global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U, const float *c_row, RowOut o) {
+    const int r0 = blockIdx.x * kTrRows;
+    if (r0 >= *L.n_tiles_live * kRowTile) return;
+    __shared__ float sX[2][kTrRows][kNFeat];    // G, U; later the layer-2 adjoints
+    __shared__ float sA1[kTrRows][kH1], sTA1[kTrRows][kH1];
+    __shared__ float sc[kTrRows];
+    __shared__ int sreal[kTrRows];
+    const int t = threadIdx.x;
+    const int e = L.tile_el[r0 / kRowTile];
+    if (t < kTrRows) {
+        sreal[t] = L.atom_of[r0 + t] >= 0;
+        sc[t] = c_row[r0 + t];
+    }
+    __syncthreads();
+    for (int q = t; q < kTrRows * kNFeat; q += 256) {
+        const int r = q / kNFeat, f = q % kNFeat;
+        const bool re = sreal[r];
+        sX[0][r][f] = re ? L.G32[(size_t)(r0 + r) * kNFeat + f] : 0.f;
+        sX[1][r][f] = re ? U[(size_t)(r0 + r) * kNFeat + f] : 0.f;
+    }
+    __syncthreads();
+    // layer 1 (thread = unit a): h1 = W1 G + b1, t1 = W1 U
+    float h1[kTrRows], t1[kTrRows];
+    {
+        const __nv_bfloat16 *W = L.W1T + (size_t)e * kNFeat * kH1;
+        const float b = L.b1[e * kH1 + t];
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) {
+            h1[r] = b;
+            t1[r] = 0.f;
+        }
+        for (int f = 0; f < kNFeat; ++f) {
+            const float wv = __bfloat162float(W[(size_t)f * kH1 + t]);
+#pragma unroll
+            for (int r = 0; r < kTrRows; ++r) {
+                h1[r] = fmaf(sX[0][r][f], wv, h1[r]);
+                t1[r] = fmaf(sX[1][r][f], wv, t1[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) {
+            const float a1 = tr_s(h1[r]), ta1 = tr_ds(h1[r]) * t1[r];
+            sA1[r][t] = a1;
+            sTA1[r][t] = ta1;
+            o.a1[(size_t)(r0 + r) * kH1 + t] = a1;
+            o.ta1[(size_t)(r0 + r) * kH1 + t] = ta1;
+        }
+    }
+    __syncthreads();
+    float (*sBT2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sX[0][0][0]);
+    float (*sBH2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sX[1][0][0]);
+    // layer 2 and its reverse (thread = unit b < 128): J = c E - W3 . ta2
+    if (t < kH2) {
+        const __nv_bfloat16 *W = L.W2T + (size_t)e * kH1 * kH2;
+        const float b = L.b2[e * kH2 + t], w3 = L.W3[e * kH2 + t];
+        float h2[kTrRows], t2[kTrRows];
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) {
+            h2[r] = b;
+            t2[r] = 0.f;
+        }
+        for (int a = 0; a < kH1; ++a) {
+            const float wv = __bfloat162float(W[(size_t)a * kH2 + t]);
+#pragma unroll
+            for (int r = 0; r < kTrRows; ++r) {
+                h2[r] = fmaf(sA1[r][a], wv, h2[r]);
+                t2[r] = fmaf(sTA1[r][a], wv, t2[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) {
+            const float cr = sc[r];
+            const float d1 = tr_ds(h2[r]);
+            const float bt2 = -w3 * d1;
+            const float bh2 = -w3 * tr_dds(h2[r]) * t2[r] + cr * w3 * d1;
+            sBT2[r][t] = bt2;
+            sBH2[r][t] = bh2;
+            o.bt2[(size_t)(r0 + r) * kH2 + t] = bt2;
+            o.bh2[(size_t)(r0 + r) * kH2 + t] = bh2;
+            o.w3g[(size_t)(r0 + r) * kH2 + t] = cr * tr_s(h2[r]) - d1 * t2[r];
+        }
+    }
+    __syncthreads();
+    // reverse through layer 2 into layer 1 (thread = unit a)
+    {
+        const __nv_bfloat16 *W = L.W2 + (size_t)e * kH2 * kH1;
+        float bta1[kTrRows], ba1[kTrRows];
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) bta1[r] = ba1[r] = 0.f;
+        for (int b = 0; b < kH2; ++b) {
+            const float wv = __bfloat162float(W[(size_t)b * kH1 + t]);
+#pragma unroll
+            for (int r = 0; r < kTrRows; ++r) {
+                bta1[r] = fmaf(sBT2[r][b], wv, bta1[r]);
+                ba1[r] = fmaf(sBH2[r][b], wv, ba1[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kTrRows; ++r) {
+            const float d1 = tr_ds(h1[r]);
+            o.bt1[(size_t)(r0 + r) * kH1 + t] = d1 * bta1[r];
+            o.bh1[(size_t)(r0 + r) * kH1 + t] = tr_dds(h1[r]) * t1[r] * bta1[r] + d1 * ba1[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------ weight gradients
+
+// out[split][e][m][n] = sum over the split's rows of element e of
+//   A0[r][m] B0[r][n] + A1[r][m] B1[r][n]
+// (rows of padding atoms skipped), 64 x 64 output tile per block, FP32, fixed order.
+template <int M, int N>
+__global__ void __launch_bounds__(256) k_wgrad(LearnedDev L, const float *A0, const float *A1, const float *B0,
+                                               const float *B1, int tiles_max, float *out) {
+    __shared__ float As[32][64 + 4];
+    __shared__ float Bs[32][64 + 4];
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    const int e = blockIdx.z / kSplits, sp = blockIdx.z % kSplits;
+    const int live = *L.n_tiles_live;
+    const int t0 = (int)((long long)tiles_max * sp / kSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kSplits);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int tile = t0; tile < t1 && tile < live; ++tile) {
+        if (L.tile_el[tile] != e) continue;
+        for (int k0 = tile * kRowTile; k0 < (tile + 1) * kRowTile; k0 += 16) {
+            // 16 rows x (A0 | A1) and (B0 | B1) -> 32 K-slices
+            for (int q = threadIdx.x; q < 32 * 64; q += 256) {
+                const int kk = q >> 6, c = q & 63;
+                const int r = k0 + (kk & 15);
+                const bool re = L.atom_of[r] >= 0;
+                const float *A = kk < 16 ? A0 : A1;
+                const float *Bp = kk < 16 ? B0 : B1;
+                As[kk][c] = re ? A[(size_t)r * M + mt * 64 + c] : 0.f;
+                Bs[kk][c] = re ? Bp[(size_t)r * N + nt * 64 + c] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < 32; ++kk) {
+                float a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = As[kk][ty * 4 + u];
+                    b[u] = Bs[kk][tx * 4 + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(a[u], b[w], acc[u][w]);
+            }
+            __syncthreads();
+        }
+    }
+    float *o = out + ((size_t)(sp * 4 + e) * M) * N;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) o[(size_t)(mt * 64 + ty * 4 + u) * N + nt * 64 + tx * 4 + w] = acc[u][w];
+}
+
+// out[split][e][j] = sum over the split's rows of element e of X[r][j] (X = null: c_row), fixed order.
+__global__ void k_vgrad(LearnedDev L, const float *X, const float *c_row, int len, int tiles_max, float *out) {
+    const int e = blockIdx.y / kSplits, sp = blockIdx.y % kSplits;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    const int live = *L.n_tiles_live;
+    const int t0 = (int)((long long)tiles_max * sp / kSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kSplits);
+    float s = 0.f;
+    for (int tile = t0; tile < t1 && tile < live; ++tile) {
+        if (L.tile_el[tile] != e) continue;
+        for (int r = tile * kRowTile; r < (tile + 1) * kRowTile; ++r)
+            if (L.atom_of[r] >= 0) s += X ? X[(size_t)r * len + j] : c_row[r];
+    }
+    out[((size_t)sp * 4 + e) * len + j] = s;
+}
+
+// grad[e][off + j] = sum_s part[s][e][j] (in split order)
+__global__ void k_reduce_splits(const float *part, int len, int off, float *grad) {
+    const int e = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    float s = 0.f;
+    for (int sp = 0; sp < kSplits; ++sp) s += part[((size_t)sp * 4 + e) * len + j];
+    grad[(size_t)e * kPPE + off + j] = s;
+}
+
+// ------------------------------------------------------------ AdamW
+
+__global__ void k_adamw(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                        float eps, float wd, float bc1, float bc2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / bc1, vh = vi / bc2;
+    p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+}
+
+}  // namespace
+}  // namespace mdpf
+
+using namespace mdpf;
+
+struct mdpf_trainer {
+    int device = 0;
+    int max_frames = 0, N = 0, n_max = 0, tiles_max = 0, rows_max = 0;
+    double w_force = 10.0;
+    double e0[4] = {0, 0, 0, 0};
+    LearnedDev L{};
+    MlpMaps maps{};
+    std::vector<void *> allocs;
+    int *d_cnt = nullptr, *d_ntile = nullptr, *d_tile_off = nullptr, *d_live = nullptr;
+    float4 *d_pos4 = nullptr;
+    unsigned long long *d_fx = nullptr, *d_efx = nullptr;
+    uint32_t *d_status = nullptr;
+    float *d_c = nullptr, *d_v = nullptr, *d_U = nullptr;
+    RowOut ro{};
+    float *d_part = nullptr;
+    double *d_lparts = nullptr;
+    unsigned int *d_rmin = nullptr, *d_rmax = nullptr;
+    std::string err;
+    bool sticky = false;
+};
+
+namespace {
+thread_local std::string g_tr_error;
+
+template <typename T>
+cudaError_t talloc(mdpf_trainer *t, T **p, size_t count) {
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) t->allocs.push_back((void *)*p);
+    return e;
+}
+
+void tr_free(mdpf_trainer *t) {
+    if (!t) return;
+    for (void *p : t->allocs) cudaFree(p);
+    delete t;
+}
+
+int tr_fail(mdpf_trainer *t, int code, const std::string &m) {
+    if (t) t->err = m; else g_tr_error = m;
+    return code;
+}
+int tr_cuda(mdpf_trainer *t, cudaError_t e, const char *where) {
+    std::string m = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+    if (t) {
+        t->sticky = true;
+        t->err = m;
+    } else {
+        g_tr_error = m;
+    }
+    return MDPF_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" {
+
+const char *mdpf_trainer_last_error(const mdpf_trainer *t) { return t ? t->err.c_str() : g_tr_error.c_str(); }
+
+int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
+    if (!out) return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "params is NULL");
+    if (p->max_frames < 1 || p->atoms_per_frame < 1 || (int64_t)p->max_frames * p->atoms_per_frame > (1 << 22))
+        return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "max_frames, atoms_per_frame out of range");
+    if (!(p->w_force >= 0.0)) return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "w_force must be >= 0");
+    mdpf_trainer *t = new mdpf_trainer();
+    t->max_frames = p->max_frames;
+    t->N = p->atoms_per_frame;
+    t->n_max = p->max_frames * p->atoms_per_frame;
+    t->tiles_max = p->max_frames * ((p->atoms_per_frame + kRowTile - 1) / kRowTile + 4);
+    t->rows_max = t->tiles_max * kRowTile;
+    t->w_force = p->w_force;
+    for (int e = 0; e < 4; ++e) t->e0[e] = p->e0[e];
+    LearnedDev &L = t->L;
+    cudaError_t ce = cudaSuccess;
+#define TA(ptr, count)                                                                   \
+    do {                                                                                 \
+        if ((ce = talloc(t, &(ptr), (count))) != cudaSuccess) {                          \
+            tr_cuda(nullptr, ce, "trainer allocation");                                  \
+            tr_free(t);                                                                  \
+            return ce == cudaErrorMemoryAllocation ? MDPF_ERR_OOM : MDPF_ERR_CUDA;       \
+        }                                                                                \
+    } while (0)
+    const size_t R = t->rows_max, n = t->n_max;
+    int *row_of, *atom_of, *tile_el, *live;
+    __nv_bfloat16 *W1, *W1T, *W2, *W2T;
+    float *b1, *b2, *W3, *b3;
+    double *e0;
+    CellGrid *grid;
+    cudaGetDevice(&t->device);
+    TA(t->d_cnt, 4 * (size_t)t->max_frames);
+    TA(t->d_ntile, t->max_frames);
+    TA(t->d_tile_off, t->max_frames + 1);
+    TA(live, 1);
+    t->d_live = live;
+    TA(row_of, n);
+    TA(atom_of, R);
+    TA(tile_el, t->tiles_max);
+    TA(L.nb_count, n);
+    TA(L.nb_idx, n * kKmax);
+    TA(L.pos_build, n);
+    TA(grid, 1);
+    TA(L.bbox, 8);
+    TA(L.G16, R * kNFeat);
+    TA(L.G32, R * kNFeat);
+    TA(L.g, R * kNFeat);
+    TA(L.E_row, R);
+    TA(W1, 4 * (size_t)kH1 * kNFeat);
+    TA(W1T, 4 * (size_t)kH1 * kNFeat);
+    TA(W2, 4 * (size_t)kH2 * kH1);
+    TA(W2T, 4 * (size_t)kH2 * kH1);
+    TA(b1, 4 * kH1);
+    TA(b2, 4 * kH2);
+    TA(W3, 4 * kH2);
+    TA(b3, 4);
+    TA(e0, 4);
+    TA(L.lflags, 4);
+    TA(L.lcount, 4);
+    TA(t->d_pos4, n);
+    TA(t->d_fx, 3 * n);
+    TA(t->d_efx, E_SLOTS);
+    TA(t->d_status, 4);
+    TA(t->d_c, R);
+    TA(t->d_v, 3 * n);
+    TA(t->d_U, R * kNFeat);
+    TA(t->ro.bh1, R * kH1);
+    TA(t->ro.bt1, R * kH1);
+    TA(t->ro.a1, R * kH1);
+    TA(t->ro.ta1, R * kH1);
+    TA(t->ro.bh2, R * kH2);
+    TA(t->ro.bt2, R * kH2);
+    TA(t->ro.w3g, R * kH2);
+    TA(t->d_part, (size_t)kSplits * 4 * kH1 * kNFeat);
+    TA(t->d_lparts, 2 * (size_t)t->max_frames);
+    TA(t->d_rmin, 4 * kNFeat);
+    TA(t->d_rmax, 4 * kNFeat);
+#undef TA
+    L.n = t->n_max;
+    L.n_rows = (int)R;
+    L.n_tiles_live = live;
+    L.row_of = row_of;
+    L.atom_of = atom_of;
+    L.tile_el = tile_el;
+    L.rc_list = 5.2f;
+    L.rc_list2 = (float)(5.2 * 5.2);
+    L.half_skin2 = 0.f;
+    L.grid = grid;
+    L.W1 = W1;
+    L.W1T = W1T;
+    L.W2 = W2;
+    L.W2T = W2T;
+    L.b1 = b1;
+    L.b2 = b2;
+    L.W3 = W3;
+    L.b3 = b3;
+    L.e0 = e0;
+    L.lo = L.hi = nullptr;
+    cudaError_t e1 = cudaMemcpy(e0, t->e0, sizeof(double) * 4, cudaMemcpyHostToDevice);
+    if (e1 == cudaSuccess) e1 = cudaMemset(atom_of, 0xFF, sizeof(int) * R);
+    if (e1 == cudaSuccess) e1 = cudaMemset(L.G16, 0, sizeof(__nv_bfloat16) * R * kNFeat);
+    if (e1 == cudaSuccess) e1 = cudaMemset(L.lflags, 0, sizeof(unsigned int) * 4);
+    if (e1 == cudaSuccess) e1 = cudaMemset(t->d_rmin, 0xFF, sizeof(unsigned int) * 4 * kNFeat);
+    if (e1 == cudaSuccess) e1 = cudaMemset(t->d_rmax, 0, sizeof(unsigned int) * 4 * kNFeat);
+    if (e1 != cudaSuccess) {
+        tr_cuda(nullptr, e1, "trainer initialisation");
+        tr_free(t);
+        return MDPF_ERR_CUDA;
+    }
+    // TMA descriptors of the tensor-core MLP operands
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    e1 = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e1 != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        tr_free(t);
+        return tr_fail(nullptr, MDPF_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    auto one = [&](CUtensorMap *m, const void *ptr, uint64_t inner, uint64_t rows) {
+        cuuint64_t dims[2] = {inner, rows};
+        cuuint64_t strides[1] = {inner * 2};
+        cuuint32_t box[2] = {64, 128};
+        cuuint32_t estr[2] = {1, 1};
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!one(&t->maps.g, L.G16, kNFeat, R) || !one(&t->maps.w1, W1, kNFeat, 4 * kH1) ||
+        !one(&t->maps.w2, W2, kH1, 4 * kH2) || !one(&t->maps.w2t, W2T, kH2, 4 * kH1) ||
+        !one(&t->maps.w1t, W1T, kH1, 4 * kNFeat)) {
+        tr_free(t);
+        return tr_fail(nullptr, MDPF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+    e1 = learned_mlp_tc_prepare();
+    if (e1 != cudaSuccess) {
+        tr_free(t);
+        return tr_cuda(nullptr, e1, "learned_mlp_tc_prepare");
+    }
+    *out = t;
+    return MDPF_OK;
+}
+
+void mdpf_trainer_destroy(mdpf_trainer *t) {
+    if (!t) return;
+    cudaDeviceSynchronize();
+    tr_free(t);
+}
+
+int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad, int32_t n_frames,
+                           const double *d_pos, const int32_t *d_element, const double *d_E_ref,
+                           const float *d_F_ref, double *d_loss3, void *stream) {
+    if (!t) return MDPF_ERR_INVALID_ARG;
+    if (t->sticky) return MDPF_ERR_CUDA;
+    if (n_frames < 1 || n_frames > t->max_frames) return tr_fail(t, MDPF_ERR_INVALID_ARG, "n_frames out of range");
+    if (!d_params || !d_grad || !d_pos || !d_element || !d_E_ref || !d_F_ref || !d_loss3)
+        return tr_fail(t, MDPF_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = t->N, B = n_frames, n = B * N;
+    LearnedDev L = t->L;
+    L.n = n;
+    L.el = d_element;
+    // 1. rows
+    k_tr_count<<<B, 256, 0, s>>>(d_element, N, t->d_cnt, t->d_ntile);
+    k_tr_scan<<<1, 32, 0, s>>>(B, t->d_ntile, t->d_tile_off, t->d_live);
+    cudaMemsetAsync(const_cast<int *>(L.atom_of), 0xFF, sizeof(int) * t->rows_max, s);
+    k_tr_rows<<<B, 1024, 0, s>>>(d_element, N, t->d_cnt, t->d_tile_off, const_cast<int *>(L.row_of),
+                                  const_cast<int *>(L.atom_of), const_cast<int *>(L.tile_el));
+    // 2. positions, neighbours, weights
+    k_tr_pos<<<(n + 255) / 256, 256, 0, s>>>(d_pos, n, t->d_pos4);
+    cudaMemsetAsync(t->d_status, 0, sizeof(uint32_t), s);
+    k_tr_nb<<<(n * 32 + 255) / 256, 256, 0, s>>>(L, t->d_pos4, N, t->d_status);
+    k_tr_weights<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(
+        d_params, const_cast<__nv_bfloat16 *>(L.W1), const_cast<__nv_bfloat16 *>(L.W1T),
+        const_cast<__nv_bfloat16 *>(L.W2), const_cast<__nv_bfloat16 *>(L.W2T), const_cast<float *>(L.b1),
+        const_cast<float *>(L.b2), const_cast<float *>(L.W3), const_cast<float *>(L.b3));
+    // 3. features, MLP (energies, dE/dG), forces
+    cudaMemsetAsync(L.G16, 0, sizeof(__nv_bfloat16) * (size_t)t->rows_max * kNFeat, s);
+    learned_features(L, t->d_pos4, true, s);
+    k_tr_range<<<t->tiles_max, kNFeat, 0, s>>>(L, t->d_rmin, t->d_rmax);
+    cudaError_t ce = learned_mlp_tc(L, t->maps, t->d_status, false, s);
+    if (ce != cudaSuccess) return tr_cuda(t, ce, "learned_mlp_tc");
+    cudaMemsetAsync(t->d_fx, 0, sizeof(unsigned long long) * 3 * (size_t)n, s);
+    learned_adjoint(L, t->d_pos4, t->d_fx, t->d_efx, false, s);
+    // 4. loss, c, v; U = J v
+    k_tr_loss<<<B, 256, 0, s>>>(L, N, B, t->w_force, t->d_tile_off, d_E_ref, d_F_ref, t->d_fx, t->d_c, t->d_v,
+                                 t->d_lparts);
+    k_tr_loss_total<<<1, 32, 0, s>>>(B, t->d_lparts, d_loss3);
+    learned_jvp(L, t->d_pos4, t->d_v, t->d_U, s);
+    // 5. per-row reverse over the tangent pass
+    k_mlp_train<<<t->rows_max / kTrRows, 256, 0, s>>>(L, t->d_U, t->d_c, t->ro);
+    // 6. weight gradients (split over the row range, splits summed in order)
+    k_wgrad<kH1, kNFeat><<<dim3(kH1 / 64, kNFeat / 64, 4 * kSplits), 256, 0, s>>>(
+        L, t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH1 * kNFeat, kOW1, d_grad);
+    k_wgrad<kH2, kH1><<<dim3(kH2 / 64, kH1 / 64, 4 * kSplits), 256, 0, s>>>(
+        L, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3((kH2 * kH1 + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH2 * kH1, kOW2, d_grad);
+    k_vgrad<<<dim3(1, 4 * kSplits), 256, 0, s>>>(L, t->ro.bh1, nullptr, kH1, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 256, 0, s>>>(t->d_part, kH1, kOb1, d_grad);
+    k_vgrad<<<dim3(1, 4 * kSplits), 128, 0, s>>>(L, t->ro.bh2, nullptr, kH2, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOb2, d_grad);
+    k_vgrad<<<dim3(1, 4 * kSplits), 128, 0, s>>>(L, t->ro.w3g, nullptr, kH2, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOW3, d_grad);
+    k_vgrad<<<dim3(1, 4 * kSplits), 32, 0, s>>>(L, nullptr, t->d_c, 1, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 32, 0, s>>>(t->d_part, 1, kOb3, d_grad);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) return tr_cuda(t, ce, "training launches");
+    return MDPF_OK;
+}
+
+int mdpf_trainer_status(mdpf_trainer *t, uint32_t *status) {
+    if (!t) return MDPF_ERR_INVALID_ARG;
+    if (t->sticky) return MDPF_ERR_CUDA;
+    uint32_t st = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&st, t->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return tr_cuda(t, e, "trainer status");
+    if (status) *status = st;
+    if (st & MDPF_STATUS_TIMEOUT) return tr_fail(t, MDPF_ERR_TIMEOUT, "tensor-core MLP wait timed out");
+    if (st & MDPF_STATUS_NEIGHBOR_OVERFLOW) return tr_fail(t, MDPF_ERR_NEIGHBOR_OVERFLOW, "neighbour row over 128");
+    return MDPF_OK;
+}
+
+int mdpf_trainer_feature_range(mdpf_trainer *t, float *lo, float *hi) {
+    if (!t) return MDPF_ERR_INVALID_ARG;
+    if (t->sticky) return MDPF_ERR_CUDA;
+    std::vector<unsigned int> a(4 * kNFeat), b(4 * kNFeat);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(a.data(), t->d_rmin, sizeof(unsigned int) * a.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(b.data(), t->d_rmax, sizeof(unsigned int) * b.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return tr_cuda(t, e, "feature range");
+    auto un = [](unsigned int u) {
+        const unsigned int bits = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+        float f;
+        std::memcpy(&f, &bits, 4);
+        return f;
+    };
+    for (int k = 0; k < 4 * kNFeat; ++k) {
+        const bool seen = a[k] != 0xFFFFFFFFu;
+        if (lo) lo[k] = seen ? un(a[k]) : 0.f;
+        if (hi) hi[k] = seen ? un(b[k]) : 0.f;
+    }
+    return MDPF_OK;
+}
+
+int mdpf_adamw_step(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t n, int64_t step, double lr,
+                    double beta1, double beta2, double eps, double weight_decay, void *stream) {
+    if (!d_params || !d_grad || !d_m || !d_v || n < 0 || step < 1) return MDPF_ERR_INVALID_ARG;
+    if (n == 0) return MDPF_OK;
+    const float bc1 = (float)(1.0 - std::pow(beta1, (double)step)), bc2 = (float)(1.0 - std::pow(beta2, (double)step));
+    k_adamw<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_params, d_grad, d_m, d_v, n, (float)lr,
+                                                                        (float)beta1, (float)beta2, (float)eps,
+                                                                        (float)weight_decay, bc1, bc2);
+    return cudaGetLastError() == cudaSuccess ? MDPF_OK : MDPF_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -68,6 +68,13 @@ class mdpf_params(ctypes.Structure):
     ]
 
 
+class mdpf_train_params(ctypes.Structure):
+    _fields_ = [("max_frames", _i32), ("atoms_per_frame", _i32), ("w_force", _f64), ("e0", _f64 * 4)]
+
+
+TRAIN_PARAMS_PER_ELEMENT = 131585
+
+
 class mdpf_counters(ctypes.Structure):
     _fields_ = [
         ("steps", _i64), ("force_evals", _i64), ("frames", _i64), ("status", ctypes.c_uint32),
@@ -103,6 +110,14 @@ def load(path: str = LIB_PATH):
         "mdpf_learned_features": (ctypes.c_int, [_vp, _vp, _vp]),
         "mdpf_learned_mlp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "mdpf_learned_counters": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "mdpf_learned_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "mdpf_trainer_create": (ctypes.c_int, [ctypes.POINTER(mdpf_train_params), ctypes.POINTER(_vp)]),
+        "mdpf_trainer_destroy": (None, [_vp]),
+        "mdpf_trainer_last_error": (ctypes.c_char_p, [_vp]),
+        "mdpf_trainer_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "mdpf_trainer_status": (ctypes.c_int, [_vp, _vp]),
+        "mdpf_trainer_feature_range": (ctypes.c_int, [_vp, _vp, _vp]),
+        "mdpf_adamw_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _f64, _f64, _f64, _f64, _f64, _vp]),
         "mdpf_pairs_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, ctypes.POINTER(_f64), ctypes.POINTER(_f64), _f64,
                                               _vp, _vp, _vp]),
     }
@@ -310,6 +325,14 @@ class Context:
         self._check(lib().mdpf_learned_mlp(self._h, _ptr(g), _ptr(E), _ptr(d)))
         return E, d
 
+    def learned_jvp(self, pos, v):
+        """U[N,384] = sum_a dG/dx_a . v_a (FP32) at host positions pos along host vectors v."""
+        x = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        vv = np.ascontiguousarray(v, dtype=np.float32).reshape(self.n, 3)
+        U = np.zeros((self.n, 384), dtype=np.float32)
+        self._check(lib().mdpf_learned_jvp(self._h, _ptr(x), _ptr(vv), _ptr(U)))
+        return U
+
     def learned_counters(self) -> dict:
         rb = ctypes.c_int64()
         fb = ctypes.c_int64()
@@ -344,3 +367,63 @@ def pairs_noalloc(n_atoms: int, d_pos: int, d_element: int, d_charge: int, lj_si
                                   float(coulomb_k), _vp(d_energy), _vp(d_forces), _vp(stream))
     if rc != MDPF_OK:
         raise MdpfError(rc, lib().mdpf_last_error(None).decode())
+
+
+class Trainer:
+    """Device-side force-matching loss and gradient (mdpf_trainer_*); all tensors
+    are caller-owned device memory passed by address (e.g. torch data_ptr())."""
+
+    def __init__(self, max_frames: int, atoms_per_frame: int, e0, w_force: float = 10.0):
+        p = mdpf_train_params()
+        p.max_frames = int(max_frames)
+        p.atoms_per_frame = int(atoms_per_frame)
+        p.w_force = float(w_force)
+        for e in range(4):
+            p.e0[e] = float(e0[e])
+        h = _vp()
+        rc = lib().mdpf_trainer_create(ctypes.byref(p), ctypes.byref(h))
+        if rc != MDPF_OK:
+            raise MdpfError(rc, lib().mdpf_trainer_last_error(None).decode())
+        self._h = h
+        self.max_frames = max_frames
+        self.atoms_per_frame = atoms_per_frame
+
+    def _check(self, rc):
+        if rc != MDPF_OK:
+            raise MdpfError(rc, lib().mdpf_trainer_last_error(self._h).decode())
+
+    def loss_grad(self, d_params: int, d_grad: int, n_frames: int, d_pos: int, d_element: int, d_E_ref: int,
+                  d_F_ref: int, d_loss3: int, stream: int = 0):
+        self._check(lib().mdpf_trainer_loss_grad(self._h, _vp(d_params), _vp(d_grad), int(n_frames), _vp(d_pos),
+                                                 _vp(d_element), _vp(d_E_ref), _vp(d_F_ref), _vp(d_loss3),
+                                                 _vp(stream)))
+
+    def status(self) -> int:
+        st = ctypes.c_uint32()
+        self._check(lib().mdpf_trainer_status(self._h, ctypes.byref(st)))
+        return st.value
+
+    def feature_range(self):
+        lo = np.zeros((4, 384), dtype=np.float32)
+        hi = np.zeros((4, 384), dtype=np.float32)
+        self._check(lib().mdpf_trainer_feature_range(self._h, _ptr(lo), _ptr(hi)))
+        return lo, hi
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mdpf_trainer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adamw_step(d_params: int, d_grad: int, d_m: int, d_v: int, n: int, step: int, lr: float, beta1: float = 0.9,
+               beta2: float = 0.999, eps: float = 1e-8, weight_decay: float = 0.01, stream: int = 0) -> None:
+    rc = lib().mdpf_adamw_step(_vp(d_params), _vp(d_grad), _vp(d_m), _vp(d_v), int(n), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), float(weight_decay), _vp(stream))
+    if rc != MDPF_OK:
+        raise MdpfError(rc, "mdpf_adamw_step failed")

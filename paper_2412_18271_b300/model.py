@@ -106,6 +106,32 @@ class Model:
         return Model.unpack(self.pack())
 
 
+PARAMS_PER_ELEMENT = H1 * N_FEAT + H1 + H2 * H1 + H2 + H2 + 1   # 131,585
+
+
+def to_flat(m: Model) -> np.ndarray:
+    """FP32 parameter vector in the trainer's layout: per element W1, b1, W2, b2, W3, b3."""
+    parts = []
+    for e in range(N_ELEM):
+        parts += [np.asarray(m.W1[e], np.float32).ravel(), np.asarray(m.b1[e], np.float32),
+                  np.asarray(m.W2[e], np.float32).ravel(), np.asarray(m.b2[e], np.float32),
+                  np.asarray(m.W3[e], np.float32), np.asarray([m.b3[e]], np.float32)]
+    return np.concatenate(parts)
+
+
+def from_flat(flat, e0, lo=None, hi=None) -> Model:
+    """Model from an FP32 parameter vector (W1, W2 keep their FP32 values; pack() rounds them to BF16)."""
+    flat = np.asarray(flat, dtype=np.float32).reshape(N_ELEM, PARAMS_PER_ELEMENT)
+    o1 = H1 * N_FEAT
+    o2 = o1 + H1
+    o3 = o2 + H2 * H1
+    o4 = o3 + H2
+    o5 = o4 + H2
+    return Model(flat[:, :o1].reshape(N_ELEM, H1, N_FEAT).copy(), flat[:, o1:o2].copy(),
+                 flat[:, o2:o3].reshape(N_ELEM, H2, H1).copy(), flat[:, o3:o4].copy(), flat[:, o4:o5].copy(),
+                 flat[:, o5].copy(), np.asarray(e0, dtype=np.float64), lo, hi)
+
+
 def init_model(seed: int) -> Model:
     """Kaiming-uniform weights U(+-sqrt(6/fan_in)), zero biases, zero e0 (seeded)."""
     rng = np.random.default_rng(seed)

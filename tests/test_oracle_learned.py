@@ -244,3 +244,15 @@ def test_model_blob_roundtrip(mdl):
     r = model.bf16_to_f32(model.bf16_bits(x))
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == np.float32(1.0078125)
     assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8)
+
+
+def test_flat_parameter_layout_roundtrip(mdl):
+    flat = model.to_flat(mdl)
+    assert flat.shape == (4 * model.PARAMS_PER_ELEMENT,) and flat.dtype == np.float32
+    assert 4 * model.PARAMS_PER_ELEMENT == 526340
+    back = model.from_flat(flat, mdl.e0)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert np.array_equal(np.asarray(getattr(back, k), np.float32), np.asarray(getattr(mdl, k), np.float32)), k
+    # element 2's W2[5][7] sits at 2 * P + 256*384 + 256 + 5*256 + 7
+    P = model.PARAMS_PER_ELEMENT
+    assert flat[2 * P + 256 * 384 + 256 + 5 * 256 + 7] == np.float32(mdl.W2[2][5][7])
