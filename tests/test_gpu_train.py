@@ -66,7 +66,7 @@ def _grad_via_autograd(m, frames, trainer):
     L, parts = AG.ForceMatchingLoss.apply(params, trainer, pos, el, E, F)
     L.backward()
     assert trainer.status() == 0
-    return float(L), parts.cpu().numpy(), params.grad.cpu().numpy()
+    return float(L.detach()), parts.cpu().numpy(), params.grad.cpu().numpy()
 
 
 # ------------------------------------------------------------ feature JVP
