@@ -30,8 +30,10 @@ namespace {
 
 constexpr int kOW1 = 0, kOb1 = kH1 * kNFeat, kOW2 = kOb1 + kH1, kOb2 = kOW2 + kH2 * kH1, kOW3 = kOb2 + kH2,
               kOb3 = kOW3 + kH2, kPPE = kOb3 + 1;
-constexpr int kSplits = 8;
-constexpr int kTrRows = 8;   // rows per block of the training MLP kernel
+constexpr int kSplits = 8;     // row-range splits of the weight-matrix gradients
+constexpr int kVSplits = 64;   // row-range splits of the bias / output-weight gradients
+constexpr int kTrRows = 16;    // rows per block of the training MLP kernel
+constexpr int kTrSmem = (2 * kTrRows * kNFeat + 2 * kTrRows * kH1) * 4;
 
 // ------------------------------------------------------------ batch layout
 
@@ -266,11 +268,17 @@ struct RowOut {
 
 // kTrRows rows of one element per block, thread t = hidden unit.  FP32
 // arithmetic on the BF16-valued weights; FP32 features G and tangents U.
+// Each weight loaded from global memory feeds 2 x kTrRows FMAs; the row
+// operands come from shared memory four at a time.
 __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U, const float *c_row, RowOut o) {
     const int r0 = blockIdx.x * kTrRows;
     if (r0 >= *L.n_tiles_live * kRowTile) return;
-    __shared__ float sX[2][kTrRows][kNFeat];    // G, U; later the layer-2 adjoints
-    __shared__ float sA1[kTrRows][kH1], sTA1[kTrRows][kH1];
+    extern __shared__ float4 tr_smem4[];
+    float *sm = reinterpret_cast<float *>(tr_smem4);
+    float (*sG)[kNFeat] = reinterpret_cast<float (*)[kNFeat]>(sm);
+    float (*sU)[kNFeat] = reinterpret_cast<float (*)[kNFeat]>(sm + kTrRows * kNFeat);
+    float (*sA1)[kH1] = reinterpret_cast<float (*)[kH1]>(sm + 2 * kTrRows * kNFeat);
+    float (*sTA1)[kH1] = reinterpret_cast<float (*)[kH1]>(sm + 2 * kTrRows * kNFeat + kTrRows * kH1);
     __shared__ float sc[kTrRows];
     __shared__ int sreal[kTrRows];
     const int t = threadIdx.x;
@@ -280,11 +288,12 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
         sc[t] = c_row[r0 + t];
     }
     __syncthreads();
-    for (int q = t; q < kTrRows * kNFeat; q += 256) {
-        const int r = q / kNFeat, f = q % kNFeat;
+    for (int q = t; q < kTrRows * kNFeat / 4; q += 256) {
+        const int r = q / (kNFeat / 4), f4 = q % (kNFeat / 4);
         const bool re = sreal[r];
-        sX[0][r][f] = re ? L.G32[(size_t)(r0 + r) * kNFeat + f] : 0.f;
-        sX[1][r][f] = re ? U[(size_t)(r0 + r) * kNFeat + f] : 0.f;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(sG[r])[f4] = re ? reinterpret_cast<const float4 *>(L.G32 + (size_t)(r0 + r) * kNFeat)[f4] : z;
+        reinterpret_cast<float4 *>(sU[r])[f4] = re ? reinterpret_cast<const float4 *>(U + (size_t)(r0 + r) * kNFeat)[f4] : z;
     }
     __syncthreads();
     // layer 1 (thread = unit a): h1 = W1 G + b1, t1 = W1 U
@@ -297,12 +306,16 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
             h1[r] = b;
             t1[r] = 0.f;
         }
-        for (int f = 0; f < kNFeat; ++f) {
-            const float wv = __bfloat162float(W[(size_t)f * kH1 + t]);
+        for (int f = 0; f < kNFeat; f += 4) {
+            float wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(f + u) * kH1 + t]);
 #pragma unroll
             for (int r = 0; r < kTrRows; ++r) {
-                h1[r] = fmaf(sX[0][r][f], wv, h1[r]);
-                t1[r] = fmaf(sX[1][r][f], wv, t1[r]);
+                const float4 g = *reinterpret_cast<const float4 *>(&sG[r][f]);
+                const float4 x = *reinterpret_cast<const float4 *>(&sU[r][f]);
+                h1[r] = fmaf(g.x, wv[0], fmaf(g.y, wv[1], fmaf(g.z, wv[2], fmaf(g.w, wv[3], h1[r]))));
+                t1[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], t1[r]))));
             }
         }
 #pragma unroll
@@ -315,8 +328,8 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
         }
     }
     __syncthreads();
-    float (*sBT2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sX[0][0][0]);
-    float (*sBH2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sX[1][0][0]);
+    float (*sBT2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sG[0][0]);
+    float (*sBH2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sU[0][0]);
     // layer 2 and its reverse (thread = unit b < 128): J = c E - W3 . ta2
     if (t < kH2) {
         const __nv_bfloat16 *W = L.W2T + (size_t)e * kH1 * kH2;
@@ -327,12 +340,16 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
             h2[r] = b;
             t2[r] = 0.f;
         }
-        for (int a = 0; a < kH1; ++a) {
-            const float wv = __bfloat162float(W[(size_t)a * kH2 + t]);
+        for (int a = 0; a < kH1; a += 4) {
+            float wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(a + u) * kH2 + t]);
 #pragma unroll
             for (int r = 0; r < kTrRows; ++r) {
-                h2[r] = fmaf(sA1[r][a], wv, h2[r]);
-                t2[r] = fmaf(sTA1[r][a], wv, t2[r]);
+                const float4 x = *reinterpret_cast<const float4 *>(&sA1[r][a]);
+                const float4 y = *reinterpret_cast<const float4 *>(&sTA1[r][a]);
+                h2[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], h2[r]))));
+                t2[r] = fmaf(y.x, wv[0], fmaf(y.y, wv[1], fmaf(y.z, wv[2], fmaf(y.w, wv[3], t2[r]))));
             }
         }
 #pragma unroll
@@ -355,12 +372,16 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
         float bta1[kTrRows], ba1[kTrRows];
 #pragma unroll
         for (int r = 0; r < kTrRows; ++r) bta1[r] = ba1[r] = 0.f;
-        for (int b = 0; b < kH2; ++b) {
-            const float wv = __bfloat162float(W[(size_t)b * kH1 + t]);
+        for (int b = 0; b < kH2; b += 4) {
+            float wv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(b + u) * kH1 + t]);
 #pragma unroll
             for (int r = 0; r < kTrRows; ++r) {
-                bta1[r] = fmaf(sBT2[r][b], wv, bta1[r]);
-                ba1[r] = fmaf(sBH2[r][b], wv, ba1[r]);
+                const float4 x = *reinterpret_cast<const float4 *>(&sBT2[r][b]);
+                const float4 y = *reinterpret_cast<const float4 *>(&sBH2[r][b]);
+                bta1[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], bta1[r]))));
+                ba1[r] = fmaf(y.x, wv[0], fmaf(y.y, wv[1], fmaf(y.z, wv[2], fmaf(y.w, wv[3], ba1[r]))));
             }
         }
 #pragma unroll
@@ -380,8 +401,8 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
 template <int M, int N>
 __global__ void __launch_bounds__(256) k_wgrad(LearnedDev L, const float *A0, const float *A1, const float *B0,
                                                const float *B1, int tiles_max, float *out) {
-    __shared__ float As[32][64 + 4];
-    __shared__ float Bs[32][64 + 4];
+    __shared__ __align__(16) float As[32][64 + 4];
+    __shared__ __align__(16) float Bs[32][64 + 4];
     const int mt = blockIdx.x, nt = blockIdx.y;
     const int e = blockIdx.z / kSplits, sp = blockIdx.z % kSplits;
     const int live = *L.n_tiles_live;
@@ -404,12 +425,9 @@ __global__ void __launch_bounds__(256) k_wgrad(LearnedDev L, const float *A0, co
             __syncthreads();
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
-                float a[4], b[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    a[u] = As[kk][ty * 4 + u];
-                    b[u] = Bs[kk][tx * 4 + u];
-                }
+                const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+                const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+                const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -427,11 +445,11 @@ __global__ void __launch_bounds__(256) k_wgrad(LearnedDev L, const float *A0, co
 
 // out[split][e][j] = sum over the split's rows of element e of X[r][j] (X = null: c_row), fixed order.
 __global__ void k_vgrad(LearnedDev L, const float *X, const float *c_row, int len, int tiles_max, float *out) {
-    const int e = blockIdx.y / kSplits, sp = blockIdx.y % kSplits;
+    const int e = blockIdx.y / kVSplits, sp = blockIdx.y % kVSplits;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= len) return;
     const int live = *L.n_tiles_live;
-    const int t0 = (int)((long long)tiles_max * sp / kSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kSplits);
+    const int t0 = (int)((long long)tiles_max * sp / kVSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kVSplits);
     float s = 0.f;
     for (int tile = t0; tile < t1 && tile < live; ++tile) {
         if (L.tile_el[tile] != e) continue;
@@ -442,12 +460,12 @@ __global__ void k_vgrad(LearnedDev L, const float *X, const float *c_row, int le
 }
 
 // grad[e][off + j] = sum_s part[s][e][j] (in split order)
-__global__ void k_reduce_splits(const float *part, int len, int off, float *grad) {
+__global__ void k_reduce_splits(const float *part, int len, int off, int splits, float *grad) {
     const int e = blockIdx.y;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= len) return;
     float s = 0.f;
-    for (int sp = 0; sp < kSplits; ++sp) s += part[((size_t)sp * 4 + e) * len + j];
+    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * 4 + e) * len + j];
     grad[(size_t)e * kPPE + off + j] = s;
 }
 
@@ -663,9 +681,10 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
         return tr_fail(nullptr, MDPF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
     e1 = learned_mlp_tc_prepare();
+    if (e1 == cudaSuccess) e1 = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
     if (e1 != cudaSuccess) {
         tr_free(t);
-        return tr_cuda(nullptr, e1, "learned_mlp_tc_prepare");
+        return tr_cuda(nullptr, e1, "training kernel attributes");
     }
     *out = t;
     return MDPF_OK;
@@ -718,22 +737,23 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     k_tr_loss_total<<<1, 32, 0, s>>>(B, t->d_lparts, d_loss3);
     learned_jvp(L, t->d_pos4, t->d_v, t->d_U, s);
     // 5. per-row reverse over the tangent pass
-    k_mlp_train<<<t->rows_max / kTrRows, 256, 0, s>>>(L, t->d_U, t->d_c, t->ro);
+    k_mlp_train<<<t->rows_max / kTrRows, 256, kTrSmem, s>>>(L, t->d_U, t->d_c, t->ro);
     // 6. weight gradients (split over the row range, splits summed in order)
     k_wgrad<kH1, kNFeat><<<dim3(kH1 / 64, kNFeat / 64, 4 * kSplits), 256, 0, s>>>(
         L, t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH1 * kNFeat, kOW1, d_grad);
+    k_reduce_splits<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH1 * kNFeat, kOW1, kSplits,
+                                                                         d_grad);
     k_wgrad<kH2, kH1><<<dim3(kH2 / 64, kH1 / 64, 4 * kSplits), 256, 0, s>>>(
         L, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3((kH2 * kH1 + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH2 * kH1, kOW2, d_grad);
-    k_vgrad<<<dim3(1, 4 * kSplits), 256, 0, s>>>(L, t->ro.bh1, nullptr, kH1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 256, 0, s>>>(t->d_part, kH1, kOb1, d_grad);
-    k_vgrad<<<dim3(1, 4 * kSplits), 128, 0, s>>>(L, t->ro.bh2, nullptr, kH2, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOb2, d_grad);
-    k_vgrad<<<dim3(1, 4 * kSplits), 128, 0, s>>>(L, t->ro.w3g, nullptr, kH2, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOW3, d_grad);
-    k_vgrad<<<dim3(1, 4 * kSplits), 32, 0, s>>>(L, nullptr, t->d_c, 1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 32, 0, s>>>(t->d_part, 1, kOb3, d_grad);
+    k_reduce_splits<<<dim3((kH2 * kH1 + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH2 * kH1, kOW2, kSplits, d_grad);
+    k_vgrad<<<dim3(1, 4 * kVSplits), 256, 0, s>>>(L, t->ro.bh1, nullptr, kH1, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 256, 0, s>>>(t->d_part, kH1, kOb1, kVSplits, d_grad);
+    k_vgrad<<<dim3(1, 4 * kVSplits), 128, 0, s>>>(L, t->ro.bh2, nullptr, kH2, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOb2, kVSplits, d_grad);
+    k_vgrad<<<dim3(1, 4 * kVSplits), 128, 0, s>>>(L, t->ro.w3g, nullptr, kH2, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOW3, kVSplits, d_grad);
+    k_vgrad<<<dim3(1, 4 * kVSplits), 32, 0, s>>>(L, nullptr, t->d_c, 1, t->tiles_max, t->d_part);
+    k_reduce_splits<<<dim3(1, 4), 32, 0, s>>>(t->d_part, 1, kOb3, kVSplits, d_grad);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return tr_cuda(t, ce, "training launches");
     return MDPF_OK;
