@@ -115,6 +115,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(value: float, device=None) -> float:
+    """The maximum of a per-rank value over all ranks (the value itself in a
+    single process).  Works with any torch.distributed backend."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world_size: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / (ms_max / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -340,12 +357,8 @@ def run_ours(args):
     c = ctx.counters()
     if c["status"] != 0:
         raise RuntimeError("device status %#x after timed region" % c["status"])
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
-    total_md = args.steps * md * ws
-    rate = total_md / (ms / 1000.0)
+    ms = reduce_max(ms, dev)
+    rate = job_rate(args.steps * md, ws, ms)
 
     # e2e: host buffers through the public API, copies inside the timed region
     pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()

@@ -103,6 +103,8 @@ static void free_ctx(mdpf_ctx *c) {
                     c->frames.step};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto &g : c->lgraph)
+        if (g) cudaGraphExecDestroy(g);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -384,17 +386,15 @@ int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles) {
 
 // Force evaluation into (fx, efx) at the FP32 positions pos4 (learned mode:
 // with a fresh neighbour list).
-static void enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
-                           uint32_t *status, bool energy, cudaStream_t s) {
+static int enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
+                          uint32_t *status, bool energy, cudaStream_t s) {
     launch_zero_fx(fx, 3 * c->n_pad, efx, s);
-    if (c->mode == MDPF_MODE_LEARNED) {
-        learned_enqueue_forces(c, pos4, fx, efx, status, true, false, s);
-        return;
-    }
+    if (c->mode == MDPF_MODE_LEARNED) return learned_enqueue_forces(c, pos4, fx, efx, status, true, false, s);
     PlainDev p = plain_dev(c, pos4);
     p.status = status;
     launch_bonded(p, fx, energy ? efx : nullptr, s);
     launch_nonbonded(p, fx, efx, energy, s);
+    return MDPF_OK;
 }
 
 int mdpf_compute_device(mdpf_ctx *c, const double *d_pos, double *d_energy, float *d_forces, void *stream) {
@@ -402,7 +402,10 @@ int mdpf_compute_device(mdpf_ctx *c, const double *d_pos, double *d_energy, floa
     if (!d_pos) return fail(c, MDPF_ERR_INVALID_ARG, "d_pos is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     launch_pos4_from_x(d_pos, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, s);
-    enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+    {
+        const int rc = enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+        if (rc != MDPF_OK) return rc;
+    }
     if (d_forces) launch_fx_to_forces(c->d_fx_c, c->n, nullptr, d_forces, s);
     launch_energy_out(c->d_efx_c, c->d_scalar + 2, s);
     if (d_energy) CK(c, cudaMemcpyAsync(d_energy, c->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -417,7 +420,10 @@ int mdpf_compute(mdpf_ctx *c, const double *pos, double *energy, double *forces,
     CK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), s));
     CK(c, cudaMemcpyAsync(c->d_xc, pos, sizeof(double) * 3 * c->n, cudaMemcpyHostToDevice, s));
     launch_pos4_from_x(c->d_xc, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, s);
-    enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+    {
+        const int rc = enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+        if (rc != MDPF_OK) return rc;
+    }
     launch_fx_to_forces(c->d_fx_c, c->n, c->d_fc, nullptr, s);
     launch_energy_out(c->d_efx_c, c->d_scalar + 2, s);
     CK(c, cudaGetLastError());
@@ -445,7 +451,10 @@ int mdpf_set_state(mdpf_ctx *c, const double *pos, const double *vel) {
     CK(c, cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), s));
     CK(c, cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), s));
     launch_pos4_from_x(c->d_x, c->d_charge_s, c->d_pos4, c->n, c->n_pad, s);
-    enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, true, s);
+    {
+        const int rc = enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, true, s);
+        if (rc != MDPF_OK) return rc;
+    }
     launch_kinetic(c, s);
     launch_energy_out(c->d_efx, c->d_scalar + 2, s);
     CK(c, cudaGetLastError());
@@ -476,6 +485,46 @@ int mdpf_get_state(mdpf_ctx *c, double *pos, double *vel) {
     return MDPF_OK;
 }
 
+// One learned-mode MD step: kick-drift, rebuild check, learned forces, kick.
+static int enqueue_learned_step(mdpf_ctx *c, bool energy, cudaStream_t s) {
+    launch_kick_drift(c, s);
+    learned_enqueue_step_prologue(c, s);
+    cudaEvent_t pn = prof_begin(c, s);
+    const int rc = learned_enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, false, false, s);
+    if (rc != MDPF_OK) return rc;
+    prof_end(c, MDPF_PROF_NONBONDED, pn, s);
+    launch_kick_finish(c, energy, s);
+    return MDPF_OK;
+}
+
+// The learned step as a CUDA graph (index 1: energy step), captured once on
+// the context's own stream; null when capture is not available, in which
+// case the same kernels are launched one by one.
+static cudaGraphExec_t learned_step_graph(mdpf_ctx *c, bool energy) {
+    const int k = energy ? 1 : 0;
+    if (c->lgraph[k] != nullptr || c->lgraph_failed) return c->lgraph[k];
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const int rc = enqueue_learned_step(c, energy, c->stream);
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        ok = rc == MDPF_OK && e == cudaSuccess && g != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // capture errors are not sticky; clear them
+    if (!ok) {
+        if (ex) cudaGraphExecDestroy(ex);
+        c->lgraph_failed = true;
+        c->err.clear();
+        c->sticky = false;
+        return nullptr;
+    }
+    c->lgraph[k] = ex;
+    return ex;
+}
+
 static int enqueue_steps(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     if (n_steps == 0) return MDPF_OK;
     if (c->stepper == MDPF_STEPPER_PERSISTENT) {
@@ -489,15 +538,17 @@ static int enqueue_steps(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     cudaEvent_t ps = prof_begin(c, s);
     for (int64_t k = 0; k < n_steps; ++k) {
         const bool energy = (c->steps + k + 1) % c->energy_every == 0;
-        launch_kick_drift(c, s);
         if (c->mode == MDPF_MODE_LEARNED) {
-            learned_enqueue_step_prologue(c, s);
-            cudaEvent_t pn = prof_begin(c, s);
-            learned_enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, false, false, s);
-            prof_end(c, MDPF_PROF_NONBONDED, pn, s);
-            launch_kick_finish(c, energy, s);
+            cudaGraphExec_t ex = c->profiling ? nullptr : learned_step_graph(c, energy);
+            if (ex != nullptr) {
+                CK(c, cudaGraphLaunch(ex, s));
+            } else {
+                const int rc = enqueue_learned_step(c, energy, s);
+                if (rc != MDPF_OK) return rc;
+            }
             continue;
         }
+        launch_kick_drift(c, s);
         PlainDev p = plain_dev(c, c->d_pos4);
         launch_bonded(p, c->d_fx, energy ? c->d_efx : nullptr, s);
         cudaEvent_t pn = prof_begin(c, s);

@@ -45,41 +45,69 @@ __device__ __forceinline__ float unord_f(unsigned int u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
-__device__ __forceinline__ bool gate_open(const LearnedDev &L, int forced) { return forced || L.lflags[0] != 0u; }
-
 // ------------------------------------------------------------------ neighbour list
+//
+// One cooperative kernel: it returns at once unless a rebuild is requested
+// (or forced); otherwise four phases separated by grid barriers:
+//   A  bounding box (block min/max, then global ordered-int atomics)
+//   B  cell grid from the box (computed identically by every block), cells cleared
+//   C  cell fill (atomic slot per atom; overflow flagged, never written)
+//   D  rows: every j != i in the 27 surrounding cells with
+//      fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl32(rc^2), sorted ascending.
+// The barrier counter is monotonic; its base for the next build is stored
+// after the last barrier, so no reset is needed between launches.  Each wait
+// gives up after limit_ns (MDPF_STATUS_TIMEOUT).
 
-__global__ void k_nb_begin(LearnedDev L, int forced) {
-    if (!gate_open(L, forced)) return;
-    const int t = threadIdx.x;
-    if (t < 3) L.bbox[t] = 0xFFFFFFFFu;       // min
-    if (t >= 3 && t < 6) L.bbox[t] = 0u;      // max
+__device__ __forceinline__ unsigned long long nb_atom_add_release(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long nb_ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long nb_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-__global__ void k_nb_bbox(LearnedDev L, const float4 *pos4, int forced) {
-    if (!gate_open(L, forced)) return;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= L.n) return;
-    const float4 p = pos4[a];
-    atomicMin(&L.bbox[0], ord_f(p.x));
-    atomicMin(&L.bbox[1], ord_f(p.y));
-    atomicMin(&L.bbox[2], ord_f(p.z));
-    atomicMax(&L.bbox[3], ord_f(p.x));
-    atomicMax(&L.bbox[4], ord_f(p.y));
-    atomicMax(&L.bbox[5], ord_f(p.z));
+__device__ __forceinline__ bool nb_barrier(unsigned long long *bar, unsigned long long target, uint32_t *status,
+                                           long long limit_ns, int *s_fail) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        if (gridDim.x > 1) {
+            __threadfence();
+            nb_atom_add_release(bar, 1ull);
+            const unsigned long long t0 = nb_timer();
+            unsigned int spins = 0;
+            while (nb_ld_acquire(bar) < target) {
+                if ((++spins & 31u) == 0u && (long long)(nb_timer() - t0) > limit_ns) {
+                    atomicOr(status, MDPF_STATUS_TIMEOUT);
+                    fail = 1;
+                    break;
+                }
+            }
+        }
+        *s_fail = fail;
+    }
+    __syncthreads();
+    return *s_fail == 0;
 }
 
-__global__ void k_nb_grid(LearnedDev L, int forced) {
-    if (!gate_open(L, forced) || threadIdx.x != 0) return;
+__device__ __forceinline__ CellGrid make_grid(const unsigned int *bb, float rc_list) {
     float lo[3], ext = 0.f, e3[3];
     for (int d = 0; d < 3; ++d) {
-        lo[d] = unord_f(L.bbox[d]);
-        e3[d] = unord_f(L.bbox[3 + d]) - lo[d];
+        lo[d] = unord_f(bb[d]);
+        e3[d] = unord_f(bb[3 + d]) - lo[d];
         ext = fmaxf(ext, e3[d]);
     }
     // cells a little wider than the list radius, so that rounding in the cell
     // index never puts two atoms within the radius more than one cell apart
-    const float cs = fmaxf(L.rc_list * 1.001f, ext / (float)kMaxCellDim);
+    const float cs = fmaxf(rc_list * 1.001f, ext / (float)kMaxCellDim);
     CellGrid g;
     int nc = 1;
     for (int d = 0; d < 3; ++d) {
@@ -89,13 +117,7 @@ __global__ void k_nb_grid(LearnedDev L, int forced) {
     }
     g.cs = cs;
     g.ncell = nc;
-    *L.grid = g;
-}
-
-__global__ void k_nb_clear(LearnedDev L, int max_cells, int forced) {
-    if (!gate_open(L, forced)) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < max_cells) L.cell_cnt[c] = 0;
+    return g;
 }
 
 __device__ __forceinline__ void cell_of(const CellGrid &g, float4 p, int &cx, int &cy, int &cz) {
@@ -104,26 +126,7 @@ __device__ __forceinline__ void cell_of(const CellGrid &g, float4 p, int &cx, in
     cz = min(max((int)floorf((p.z - g.lo[2]) / g.cs), 0), g.dim[2] - 1);
 }
 
-__global__ void k_nb_fill(LearnedDev L, const float4 *pos4, int forced) {
-    if (!gate_open(L, forced)) return;
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= L.n) return;
-    const CellGrid g = *L.grid;
-    int cx, cy, cz;
-    cell_of(g, pos4[a], cx, cy, cz);
-    const int c = (cz * g.dim[1] + cy) * g.dim[0] + cx;
-    const int slot = atomicAdd(&L.cell_cnt[c], 1);
-    if (slot < kCellCap) L.cell_atoms[(size_t)c * kCellCap + slot] = a;
-    else atomicOr(&L.lflags[2], 1u);
-}
-
-// Row of atom i: every j != i in the 27 surrounding cells with
-// fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl32(rc^2), sorted ascending.
-__global__ void k_nb_build(LearnedDev L, const float4 *pos4, uint32_t *status, int forced) {
-    if (!gate_open(L, forced)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L.n) return;
-    const CellGrid g = *L.grid;
+__device__ void build_row(const LearnedDev &L, const float4 *pos4, const CellGrid &g, int i, uint32_t *status) {
     const float4 pi = pos4[i];
     int cx, cy, cz;
     cell_of(g, pi, cx, cy, cz);
@@ -159,19 +162,66 @@ __global__ void k_nb_build(LearnedDev L, const float4 *pos4, uint32_t *status, i
     for (int p = 0; p < m; ++p) out[p] = row[p];
     L.nb_count[i] = m;
     L.pos_build[i] = pi;
-    if (over) {
-        atomicOr(&L.lflags[2], 1u);
-        atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
-    }
+    if (over) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
     atomicMax((unsigned long long *)&L.lcount[2], (unsigned long long)(over ? kKmax + 1 : m));
 }
 
-__global__ void k_nb_done(LearnedDev L, uint32_t *status, int forced) {
-    if (!gate_open(L, forced) || threadIdx.x != 0) return;
-    if (L.lflags[2]) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
-    L.lflags[0] = 0u;
-    L.lflags[2] = 0u;
-    L.lcount[0] += 1;
+constexpr int kNbThreads = 256;
+
+__global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float4 *pos4, uint32_t *status,
+                                                        int forced, long long limit_ns) {
+    if (!forced && L.lflags[0] == 0u) return;   // the same decision in every block
+    __shared__ unsigned long long s_base;
+    __shared__ int s_fail;
+    __shared__ unsigned int s_bb[6];
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (threadIdx.x == 0) s_base = *(volatile unsigned long long *)&L.nb_bar[1];
+    if (threadIdx.x < 6) s_bb[threadIdx.x] = threadIdx.x < 3 ? 0xFFFFFFFFu : 0u;
+    __syncthreads();
+    const unsigned long long base = s_base;
+    // A: bounding box (the global box was reset to empty by the previous build)
+    for (int a = tid; a < L.n; a += stride) {
+        const float4 p = pos4[a];
+        atomicMin(&s_bb[0], ord_f(p.x));
+        atomicMin(&s_bb[1], ord_f(p.y));
+        atomicMin(&s_bb[2], ord_f(p.z));
+        atomicMax(&s_bb[3], ord_f(p.x));
+        atomicMax(&s_bb[4], ord_f(p.y));
+        atomicMax(&s_bb[5], ord_f(p.z));
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) atomicMin(&L.bbox[threadIdx.x], s_bb[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicMax(&L.bbox[threadIdx.x], s_bb[threadIdx.x]);
+    if (!nb_barrier(L.nb_bar, base + nb, status, limit_ns, &s_fail)) return;
+    // B: the grid (identical in every block), cells cleared
+    unsigned int bb[6];
+    for (int d = 0; d < 6; ++d) bb[d] = *(volatile unsigned int *)&L.bbox[d];
+    const CellGrid g = make_grid(bb, L.rc_list);
+    for (int c = tid; c < g.ncell; c += stride) L.cell_cnt[c] = 0;
+    if (!nb_barrier(L.nb_bar, base + 2ull * nb, status, limit_ns, &s_fail)) return;
+    // every block has read the box: reset it for the next build
+    if (blockIdx.x == 0 && threadIdx.x < 6) L.bbox[threadIdx.x] = threadIdx.x < 3 ? 0xFFFFFFFFu : 0u;
+    // C: cell fill
+    for (int a = tid; a < L.n; a += stride) {
+        int cx, cy, cz;
+        cell_of(g, pos4[a], cx, cy, cz);
+        const int c = (cz * g.dim[1] + cy) * g.dim[0] + cx;
+        const int slot = atomicAdd(&L.cell_cnt[c], 1);
+        if (slot < kCellCap) L.cell_atoms[(size_t)c * kCellCap + slot] = a;
+        else atomicOr(&L.lflags[2], 1u);
+    }
+    if (!nb_barrier(L.nb_bar, base + 3ull * nb, status, limit_ns, &s_fail)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (*(volatile unsigned int *)&L.lflags[2]) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+        L.lflags[2] = 0u;
+        L.lflags[0] = 0u;
+        L.lcount[0] += 1;
+        L.nb_bar[1] = base + 3ull * nb;
+        *L.grid = g;
+    }
+    // D: rows
+    for (int i = tid; i < L.n; i += stride) build_row(L, pos4, g, i, status);
 }
 
 // Request a rebuild when an atom moved more than skin/2 since the last build,
@@ -684,6 +734,7 @@ __global__ void k_learn_begin(LearnedDev L) {
 __global__ void k_learn_end(LearnedDev L, uint32_t *status, int fallback) {
     if (threadIdx.x != 0 || L.lflags[1] == 0u) return;
     L.lcount[1] += 1;
+    L.lflags[1] = 0u;   // ready for the next evaluation
     if (!fallback) atomicOr(status, MDPF_STATUS_OUT_OF_RANGE);
 }
 
@@ -712,16 +763,27 @@ void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s)
     k_import_g<<<(L.n * kNFeat + 255) / 256, 256, 0, s>>>(L, G_atoms);
 }
 
-void learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status, cudaStream_t s) {
-    const int f = forced ? 1 : 0;
-    const int max_cells = (kMaxCellDim + 1) * (kMaxCellDim + 1) * (kMaxCellDim + 1);
-    k_nb_begin<<<1, 32, 0, s>>>(L, f);
-    k_nb_bbox<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, f);
-    k_nb_grid<<<1, 32, 0, s>>>(L, f);
-    k_nb_clear<<<(max_cells + 255) / 256, 256, 0, s>>>(L, max_cells, f);
-    k_nb_fill<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, f);
-    k_nb_build<<<(L.n + 127) / 128, 128, 0, s>>>(L, pos4, status, f);
-    k_nb_done<<<1, 32, 0, s>>>(L, status, f);
+int learned_nb_grid() {
+    int dev = 0, sms = 0, occ = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nb_all, kNbThreads, 0) != cudaSuccess || occ < 1)
+        return 0;
+    return sms * (occ < 2 ? occ : 2);
+}
+
+cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status,
+                              cudaStream_t s) {
+    int f = forced ? 1 : 0;
+    long long limit = 1000000000LL;   // 1 s per barrier wait
+    const int want = (L.n + kNbThreads - 1) / kNbThreads;
+    const int grid = want < L.nb_grid ? want : L.nb_grid;
+    LearnedDev Lc = L;
+    const float4 *p = pos4;
+    void *args[] = {&Lc, &p, &status, &f, &limit};
+    return cudaLaunchCooperativeKernel((const void *)k_nb_all, dim3(grid > 0 ? grid : 1), dim3(kNbThreads), args, 0,
+                                       s);
 }
 
 void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s) {

@@ -41,7 +41,9 @@ struct LearnedDev {
     int *cell_cnt;               // [max cells]
     int *cell_atoms;             // [max cells][kCellCap]
     CellGrid *grid;
-    unsigned int *bbox;          // [6] ordered-int min/max
+    unsigned int *bbox;          // [6] ordered-int min/max (empty box between builds)
+    unsigned long long *nb_bar;  // [2] grid-barrier arrival counter, base of the next build
+    int nb_grid;                 // blocks of the cooperative neighbour kernel
     // features and MLP
     __nv_bfloat16 *G16;          // [n_rows][384] GEMM input
     float *G32;                  // [n_rows][384] FP32 features (parity output) or null
@@ -62,7 +64,10 @@ struct MlpMaps {
 };
 
 // launchers (learned.cu)
-void learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status, cudaStream_t s);
+// neighbour list (cooperative launch; learned_nb_grid() gives its grid size, 0 if unavailable)
+int learned_nb_grid();
+cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status,
+                              cudaStream_t s);
 void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s);
 void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s);
 void learned_mlp(const LearnedDev &L, bool gated, cudaStream_t s);

@@ -200,6 +200,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LA(L.cell_atoms, (size_t)max_cells * kCellCap);
     LA(L.grid, 1);
     LA(L.bbox, 8);
+    LA(L.nb_bar, 2);
     LA(L.G16, (size_t)n_rows * kNFeat);
     LA(L.G32, (size_t)n_rows * kNFeat);
     LA(L.g, (size_t)n_rows * kNFeat);
@@ -245,6 +246,13 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LC(cudaMemset(L.lflags, 0, sizeof(unsigned int) * 4));
     LC(cudaMemset(L.lcount, 0, sizeof(long long) * 4));
     LC(cudaMemset(L.nb_count, 0, sizeof(int) * n));
+    LC(cudaMemset(L.nb_bar, 0, sizeof(unsigned long long) * 2));
+    {
+        const unsigned int empty_box[8] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u, 0u};
+        LC(cudaMemcpy(L.bbox, empty_box, sizeof(empty_box), cudaMemcpyHostToDevice));
+    }
+    L.nb_grid = learned_nb_grid();
+    if (L.nb_grid < 1) return fail(c, MDPF_ERR_UNSUPPORTED, "cooperative launch of the neighbour build is not available");
     unsigned int one = 1u;
     LC(cudaMemcpy(L.lflags, &one, sizeof(one), cudaMemcpyHostToDevice));
 #undef LC
@@ -269,9 +277,11 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
                            uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s) {
     LearnedHost *h = lh(c);
     const LearnedDev &L = h->dev;
-    learned_begin(L, s);
+    // the range flag is cleared by the end-of-evaluation kernel; single evaluations clear it first
+    if (forced_build) learned_begin(L, s);
     cudaEvent_t ev = prof_begin(c, s);
-    learned_neighbors(L, pos4, forced_build, status, s);
+    cudaError_t ce = learned_neighbors(L, pos4, forced_build, status, s);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "learned_neighbors");
     prof_end(c, MDPF_PROF_LEARN_NEIGHBORS, ev, s);
     ev = prof_begin(c, s);
     learned_features(L, pos4, write_f32, s);
@@ -335,7 +345,7 @@ int mdpf_learned_neighbors(mdpf_ctx *c, const double *pos, int32_t max_per_atom,
     int rc = stage_positions(c, pos);
     if (rc != MDPF_OK) return rc;
     LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
-    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    LCK(c, learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream));
     std::vector<int> cnt(c->n), rows((size_t)c->n * kKmax);
     uint32_t st = 0;
     LCK(c, cudaMemcpyAsync(cnt.data(), h->dev.nb_count, sizeof(int) * c->n, cudaMemcpyDeviceToHost, c->stream));
@@ -359,7 +369,7 @@ int mdpf_learned_features(mdpf_ctx *c, const double *pos, float *G) {
     if (rc != MDPF_OK) return rc;
     LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
     learned_begin(h->dev, c->stream);
-    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    LCK(c, learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream));
     learned_features(h->dev, c->d_pos4_c, true, c->stream);
     std::vector<float> rows((size_t)h->n_rows * kNFeat);
     uint32_t st = 0;
@@ -413,7 +423,7 @@ int mdpf_learned_jvp(mdpf_ctx *c, const double *pos, const float *v, float *U) {
     if (rc != MDPF_OK) return rc;
     LCK(c, cudaMemcpyAsync(h->d_vin, v, sizeof(float) * 3 * c->n, cudaMemcpyHostToDevice, c->stream));
     LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
-    learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream);
+    LCK(c, learned_neighbors(h->dev, c->d_pos4_c, true, c->d_status + 1, c->stream));
     learned_jvp(h->dev, c->d_pos4_c, h->d_vin, h->d_U, c->stream);
     std::vector<float> rows((size_t)h->n_rows * kNFeat);
     uint32_t st = 0;

@@ -122,6 +122,8 @@ struct mdpf_ctx {
 
     // learned mode (learned_host.cu)
     void *learned = nullptr;               // mdpf::LearnedHost
+    cudaGraphExec_t lgraph[2] = {nullptr, nullptr};   // learned step as a graph: [0] plain step, [1] energy step
+    bool lgraph_failed = false;
 
     int64_t steps = 0, force_evals = 0;
     double h_initial = 0;

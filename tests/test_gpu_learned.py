@@ -405,3 +405,22 @@ def test_learned_split_steps_equal_one_run(mdl):
     ua, ka = a.trace()
     ub, kb = b.trace()
     assert np.array_equal(ua, ub) and np.array_equal(ka, kb)
+
+
+def test_graph_stepping_equals_direct_launches(mdl):
+    # with profiling on, every step is launched kernel by kernel; off, each step is one graph launch
+    s = synth.workload("mol256")
+    vel = synth.velocities(s.mass, s.pos, 300.0, 14)
+    out = []
+    for prof in (False, True):
+        ctx = _ctx(s, mdl, energy_every=5, trace_capacity=64)
+        ctx.set_state(s.pos, vel)
+        ctx.set_profiling(prof)
+        ctx.step(23)
+        ctx.step(17)
+        out.append((ctx.get_state(), ctx.trace(), ctx.learned_counters()))
+    (xa, va), (ua, ka), ca = out[0]
+    (xb, vb), (ub, kb), cb = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(ua, ub) and np.array_equal(ka, kb)
+    assert ca == cb
