@@ -133,10 +133,14 @@ typedef struct mdpf_params {
                                 force field; 0: such a step reports MDPF_ERR_OUT_OF_RANGE */
     int32_t mlp_kernel;      /* MDPF_MLP_TENSOR (0): tcgen05 tensor cores, TMA-fed;
                                 MDPF_MLP_SIMT (1): CUDA cores.  Same rounding points (BF16
-                                GEMM inputs, FP32 accumulation); sums differ in order only. */
+                                GEMM inputs, FP32 accumulation); sums differ in order only.
+                                MDPF_MLP_SIMT_FP32 (2): CUDA cores with FP32 operands (no BF16
+                                rounding of features, activations or deltas), so the forces are
+                                the gradient of the evaluated energy to FP32 rounding. */
 } mdpf_params;
 #define MDPF_MLP_TENSOR 0
 #define MDPF_MLP_SIMT 1
+#define MDPF_MLP_SIMT_FP32 2
 
 /*
  * Learned mode (MDPF_MODE_LEARNED).  Per atom, 384 symmetry-function features

@@ -126,44 +126,56 @@ __device__ __forceinline__ void cell_of(const CellGrid &g, float4 p, int &cx, in
     cz = min(max((int)floorf((p.z - g.lo[2]) / g.cs), 0), g.dim[2] - 1);
 }
 
-__device__ void build_row(const LearnedDev &L, const float4 *pos4, const CellGrid &g, int i, uint32_t *status) {
+// Row of atom i by one warp: candidates of the 27 cells 32 at a time, accepted
+// ones appended in shared memory (ballot order), then written out in ascending
+// order (each entry's rank among the distinct entries).  Returns the row
+// length (kKmax + 1 when the row overflowed).
+__device__ int build_row_warp(const LearnedDev &L, const float4 *pos4, const CellGrid &g, int i, int lane,
+                              int *srow) {
     const float4 pi = pos4[i];
     int cx, cy, cz;
     cell_of(g, pi, cx, cy, cz);
-    int row[kKmax];
     int m = 0;
-    bool over = false;
     for (int z = max(cz - 1, 0); z <= min(cz + 1, g.dim[2] - 1); ++z)
         for (int y = max(cy - 1, 0); y <= min(cy + 1, g.dim[1] - 1); ++y)
             for (int x = max(cx - 1, 0); x <= min(cx + 1, g.dim[0] - 1); ++x) {
                 const int c = (z * g.dim[1] + y) * g.dim[0] + x;
                 const int cnt = min(L.cell_cnt[c], kCellCap);
-                for (int q = 0; q < cnt; ++q) {
-                    const int j = L.cell_atoms[(size_t)c * kCellCap + q];
-                    if (j == i) continue;
-                    const float4 pj = pos4[j];
-                    const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
-                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    if (d2 < L.rc_list2) {
-                        if (m < kKmax) row[m++] = j; else over = true;
+                for (int q0 = 0; q0 < cnt; q0 += 32) {
+                    const int q = q0 + lane;
+                    int j = -1;
+                    bool in = false;
+                    if (q < cnt) {
+                        j = L.cell_atoms[(size_t)c * kCellCap + q];
+                        if (j != i) {
+                            const float4 pj = pos4[j];
+                            const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y),
+                                        dz = __fsub_rn(pj.z, pi.z);
+                            in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <
+                                 L.rc_list2;
+                        }
                     }
+                    const unsigned int bal = __ballot_sync(0xffffffffu, in);
+                    const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                    if (in && pos < kKmax) srow[pos] = j;
+                    m += __popc(bal);
                 }
             }
-    for (int p = 1; p < m; ++p) {
-        const int v = row[p];
-        int q = p - 1;
-        while (q >= 0 && row[q] > v) {
-            row[q + 1] = row[q];
-            --q;
-        }
-        row[q + 1] = v;
-    }
+    __syncwarp();
+    const int mm = min(m, kKmax);
     int *out = L.nb_idx + (size_t)i * kKmax;
-    for (int p = 0; p < m; ++p) out[p] = row[p];
-    L.nb_count[i] = m;
-    L.pos_build[i] = pi;
-    if (over) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
-    atomicMax((unsigned long long *)&L.lcount[2], (unsigned long long)(over ? kKmax + 1 : m));
+    for (int p = lane; p < mm; p += 32) {
+        const int v = srow[p];
+        int rank = 0;
+        for (int q = 0; q < mm; ++q) rank += srow[q] < v;
+        out[rank] = v;
+    }
+    if (lane == 0) {
+        L.nb_count[i] = mm;
+        L.pos_build[i] = pi;
+    }
+    __syncwarp();
+    return m > kKmax ? kKmax + 1 : m;
 }
 
 constexpr int kNbThreads = 256;
@@ -220,8 +232,22 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
         L.nb_bar[1] = base + 3ull * nb;
         *L.grid = g;
     }
-    // D: rows
-    for (int i = tid; i < L.n; i += stride) build_row(L, pos4, g, i, status);
+    // D: rows, one warp per atom
+    __shared__ int srow[kNbThreads / 32][kKmax];
+    __shared__ int s_max[kNbThreads / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int longest = 0;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L.n; i += nwarps)
+        longest = max(longest, build_row_warp(L, pos4, g, i, lane, srow[wib]));
+    if (lane == 0) s_max[wib] = longest;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int mx = 0;
+        for (int w = 0; w < kNbThreads / 32; ++w) mx = max(mx, s_max[w]);
+        if (mx > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+        atomicMax((unsigned long long *)&L.lcount[2], (unsigned long long)mx);
+    }
 }
 
 // Request a rebuild when an atom moved more than skin/2 since the last build,
@@ -370,7 +396,12 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
 
 constexpr int kMlpRows = 8;
 
-__global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
+// BF16 = true: the tensor-core kernel's rounding points (BF16 features,
+// activations and deltas); false: FP32 operands throughout (features from the
+// FP32 copy), so the forces are the gradient of the evaluated energy to FP32
+// rounding.  Weights are the model's (BF16-valued) in both.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated, unsigned long long *efx) {
     if (gated && L.lflags[1]) return;
     if (L.n_tiles_live != nullptr && (int)(blockIdx.x * kMlpRows / kRowTile) >= *L.n_tiles_live) return;
     __shared__ float sG[kMlpRows][kNFeat];
@@ -382,8 +413,10 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
     const int t = threadIdx.x;
     const int r0 = blockIdx.x * kMlpRows;
     const int e = L.tile_el[r0 / kRowTile];
-    for (int q = t; q < kMlpRows * kNFeat; q += 256)
-        sG[q / kNFeat][q % kNFeat] = __bfloat162float(L.G16[(size_t)r0 * kNFeat + q]);
+    for (int q = t; q < kMlpRows * kNFeat; q += 256) {
+        if (BF16) sG[q / kNFeat][q % kNFeat] = __bfloat162float(L.G16[(size_t)r0 * kNFeat + q]);
+        else sG[q / kNFeat][q % kNFeat] = L.atom_of[r0 + q / kNFeat] >= 0 ? L.G32[(size_t)r0 * kNFeat + q] : 0.f;
+    }
     __syncthreads();
     // layer 1: column a = t
     {
@@ -399,7 +432,7 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
         }
 #pragma unroll
         for (int r = 0; r < kMlpRows; ++r) {
-            sA1[r][t] = bf16r(celu(acc[r]));
+            sA1[r][t] = BF16 ? bf16r(celu(acc[r])) : celu(acc[r]);
             sH1d[r][t] = dcelu(acc[r]);
         }
     }
@@ -422,14 +455,20 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
             float ev = w3 * celu(acc[r]);
             for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
             if ((t & 31) == 0) sE[r][t >> 5] = ev;
-            sD2[r][t] = bf16r(w3 * dcelu(acc[r]));
+            sD2[r][t] = BF16 ? bf16r(w3 * dcelu(acc[r])) : w3 * dcelu(acc[r]);
         }
     }
     __syncthreads();
-    if (t < kMlpRows) {
+    if (t < 32) {
         const int row = r0 + t;
-        const double E = (double)(sE[t][0] + sE[t][1] + sE[t][2] + sE[t][3]) + (double)L.b3[e] + L.e0[e];
-        L.E_row[row] = L.atom_of[row] >= 0 ? E : 0.0;
+        double Er = 0.0;
+        if (t < kMlpRows && L.atom_of[row] >= 0)
+            Er = (double)(sE[t][0] + sE[t][1] + sE[t][2] + sE[t][3]) + (double)L.b3[e] + L.e0[e];
+        if (t < kMlpRows) L.E_row[row] = Er;
+        if (efx != nullptr) {   // the block's energy into the fixed-point learned-energy slot
+            const double ws = warp_sum_d(Er);
+            if (t == 0 && ws != 0.0) fx_add_d(&efx[E_LEARN], ws);
+        }
     }
     // backward through layer 2: delta1 = celu'(h1) * (W2^T delta2), column a = t
     {
@@ -443,7 +482,7 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
             for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sD2[r][c], wv, acc[r]);
         }
 #pragma unroll
-        for (int r = 0; r < kMlpRows; ++r) sD1[r][t] = bf16r(acc[r] * sH1d[r][t]);
+        for (int r = 0; r < kMlpRows; ++r) sD1[r][t] = BF16 ? bf16r(acc[r] * sH1d[r][t]) : acc[r] * sH1d[r][t];
     }
     __syncthreads();
     // backward through layer 1: dE/dG = W1^T delta1, columns f = t, t + 256
@@ -469,22 +508,25 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated) {
 // Angular blocks of g are stored 33 floats apart so that lanes working on
 // different element pairs read different banks.
 constexpr int kAngStride = 33;
+constexpr int kTripChunk = 160;   // triplets staged per pass
 
 struct AdjSmem {
     float g[64 + 10 * kAngStride];
-    unsigned long long f[kKmax][3];  // fixed-point forces on the neighbours
+    float f[kKmax][3];                    // force on each neighbour (FP32, fixed summation order)
+    float tj[kTripChunk][3], tk[kTripChunk][3];   // staged triplet contributions to j and k
 };
 
-__device__ __forceinline__ void sadd(unsigned long long *p, float v) {
-    atomicAdd(p, (unsigned long long)fx_from_float(v));
-}
+// Index of the angular pair (a, b), a < b, in the order triplet_ab enumerates.
+__device__ __forceinline__ int triplet_index(int a, int b, int na) { return a * (na - 1) - a * (a - 1) / 2 + (b - a - 1); }
 
 // F = -dE/dx by the chain rule through the features: for every radial pair and
 // angular triplet around atom i, the contraction of g = dE/dG_i with the
-// derivative of the feature terms.  Forces on the neighbours accumulate in
-// shared int64 fixed point (order-free); the force on atom i accumulates in
-// registers per lane in a fixed triplet order and is reduced over the warp in a
-// fixed shuffle order, so the result is reproducible bit for bit.
+// derivative of the feature terms.  No atomics until the final global adds:
+// each neighbour's radial force is written by the one lane that owns the pair;
+// triplet contributions are staged per chunk and each lane then sums, in a
+// fixed order, those of the triplets that contain its neighbour; the force on
+// atom i is summed per lane and reduced over the warp in a fixed order.  The
+// result is reproducible bit for bit.
 __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
                                                              int gated) {
     if (gated && L.lflags[1]) return;
@@ -501,10 +543,10 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
     for (int f = lane; f < 320; f += 32) A.g[64 + (f >> 5) * kAngStride + (f & 31)] = grow[64 + f];
     int cnt, nr, na;
     load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
-    for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0ull;
+    for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0.f;
     __syncwarp();
     float fix = 0.f, fiy = 0.f, fiz = 0.f;
-    // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j -= dE/dr u,  F_i += dE/dr u
+    // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j = -dE/dr u,  F_i += dE/dr u
     for (int u = lane; u < nr; u += 32) {
         const int q = s.rad[u];
         const float4 d = s.d[q];
@@ -520,13 +562,14 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         }
         const float ir = 1.f / r;
         const float sx = dEdr * d.x * ir, sy = dEdr * d.y * ir, sz = dEdr * d.z * ir;
-        sadd(&A.f[q][0], -sx);
-        sadd(&A.f[q][1], -sy);
-        sadd(&A.f[q][2], -sz);
+        A.f[q][0] = -sx;
+        A.f[q][1] = -sy;
+        A.f[q][2] = -sz;
         fix += sx;
         fiy += sy;
         fiz += sz;
     }
+    __syncwarp();
     // angular triplets
     float cpv[8], spv[8];
 #pragma unroll
@@ -536,75 +579,99 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         spv[p] = sinf(thp);
     }
     const int ntrip = na * (na - 1) / 2;
-    for (int t = lane; t < ntrip; t += 32) {
-        int a, b;
-        triplet_ab(t, na, a, b);
-        const int qa = s.ang[a], qb = s.ang[b];
-        const float4 dj = s.d[qa], dk = s.d[qb];
-        const float rj = dj.w, rk = dk.w;
-        const float irj = 1.f / rj, irk = 1.f / rk;
-        const float ujx = dj.x * irj, ujy = dj.y * irj, ujz = dj.z * irj;
-        const float ukx = dk.x * irk, uky = dk.y * irk, ukz = dk.z * irk;
-        const float ct = ujx * ukx + ujy * uky + ujz * ukz;
-        const float cs = kAngScale * ct;
-        const float sn2 = sqrtf(1.f - cs * cs);
-        const float cot = cs / sn2;
-        const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
-        const float dfj = dfcut(rj, kRcAng), dfk = dfcut(rk, kRcAng);
-        const float C = fj * fk;
-        const float ravg = 0.5f * (rj + rk);
-        const float *gp = A.g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
-        // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
-        float Ap[8], dAp[8];
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
-            const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
-            const float b31 = b16 * b8 * b4 * b2 * base;
-            Ap[p] = kTwoPowM31 * b31 * base;
-            dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
-        }
-        float Sc = 0.f, Sr = 0.f, SC = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float x = ravg - (0.9f + (float)m * 0.65f);
-            const float B = expf(-kEtaA * x * x);
-            const float dB = -2.f * kEtaA * x * B;
-            float sa_ = 0.f, sdA = 0.f;
+    for (int t0 = 0; t0 < ntrip; t0 += kTripChunk) {
+        const int t1 = min(t0 + kTripChunk, ntrip);
+        for (int t = t0 + lane; t < t1; t += 32) {
+            int a, b;
+            triplet_ab(t, na, a, b);
+            const int qa = s.ang[a], qb = s.ang[b];
+            const float4 dj = s.d[qa], dk = s.d[qb];
+            const float rj = dj.w, rk = dk.w;
+            const float irj = 1.f / rj, irk = 1.f / rk;
+            const float ujx = dj.x * irj, ujy = dj.y * irj, ujz = dj.z * irj;
+            const float ukx = dk.x * irk, uky = dk.y * irk, ukz = dk.z * irk;
+            const float ct = ujx * ukx + ujy * uky + ujz * ukz;
+            const float cs = kAngScale * ct;
+            const float sn2 = sqrtf(1.f - cs * cs);
+            const float cot = cs / sn2;
+            const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
+            const float dfj = dfcut(rj, kRcAng), dfk = dfcut(rk, kRcAng);
+            const float C = fj * fk;
+            const float ravg = 0.5f * (rj + rk);
+            const float *gp = A.g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
+            // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
+            float Ap[8], dAp[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
-                const float gv = gp[8 * m + p];
-                sa_ = fmaf(gv, Ap[p], sa_);
-                sdA = fmaf(gv, dAp[p], sdA);
+                const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
+                const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
+                const float b31 = b16 * b8 * b4 * b2 * base;
+                Ap[p] = kTwoPowM31 * b31 * base;
+                dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
             }
-            Sc = fmaf(sdA, B * C, Sc);
-            Sr = fmaf(sa_, dB * C, Sr);
-            SC = fmaf(sa_, B, SC);
+            float Sc = 0.f, Sr = 0.f, SC = 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float x = ravg - (0.9f + (float)m * 0.65f);
+                const float B = expf(-kEtaA * x * x);
+                const float dB = -2.f * kEtaA * x * B;
+                float sa_ = 0.f, sdA = 0.f;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const float gv = gp[8 * m + p];
+                    sa_ = fmaf(gv, Ap[p], sa_);
+                    sdA = fmaf(gv, dAp[p], sdA);
+                }
+                Sc = fmaf(sdA, B * C, Sc);
+                Sr = fmaf(sa_, dB * C, Sr);
+                SC = fmaf(sa_, B, SC);
+            }
+            const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
+            const float gc = Sc * kAngScale;
+            const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;
+            const float gjy = gc * (uky - ct * ujy) * irj + dEdrj * ujy;
+            const float gjz = gc * (ukz - ct * ujz) * irj + dEdrj * ujz;
+            const float gkx = gc * (ujx - ct * ukx) * irk + dEdrk * ukx;
+            const float gky = gc * (ujy - ct * uky) * irk + dEdrk * uky;
+            const float gkz = gc * (ujz - ct * ukz) * irk + dEdrk * ukz;
+            float *tj = A.tj[t - t0], *tk = A.tk[t - t0];
+            tj[0] = -gjx;
+            tj[1] = -gjy;
+            tj[2] = -gjz;
+            tk[0] = -gkx;
+            tk[1] = -gky;
+            tk[2] = -gkz;
+            fix += gjx + gkx;
+            fiy += gjy + gky;
+            fiz += gjz + gkz;
         }
-        const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
-        const float gc = Sc * kAngScale;
-        const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;
-        const float gjy = gc * (uky - ct * ujy) * irj + dEdrj * ujy;
-        const float gjz = gc * (ukz - ct * ujz) * irj + dEdrj * ujz;
-        const float gkx = gc * (ujx - ct * ukx) * irk + dEdrk * ukx;
-        const float gky = gc * (ujy - ct * uky) * irk + dEdrk * uky;
-        const float gkz = gc * (ujz - ct * ukz) * irk + dEdrk * ukz;
-        sadd(&A.f[qa][0], -gjx);
-        sadd(&A.f[qa][1], -gjy);
-        sadd(&A.f[qa][2], -gjz);
-        sadd(&A.f[qb][0], -gkx);
-        sadd(&A.f[qb][1], -gky);
-        sadd(&A.f[qb][2], -gkz);
-        fix += gjx + gkx;
-        fiy += gjy + gky;
-        fiz += gjz + gkz;
+        __syncwarp();
+        // each lane: the staged contributions of this chunk to its angular neighbour a, b in order
+        for (int a = lane; a < na; a += 32) {
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            for (int b = 0; b < na; ++b) {
+                if (b == a) continue;
+                const int t = a < b ? triplet_index(a, b, na) : triplet_index(b, a, na);
+                if (t < t0 || t >= t1) continue;
+                const float *v = a < b ? A.tj[t - t0] : A.tk[t - t0];
+                ax += v[0];
+                ay += v[1];
+                az += v[2];
+            }
+            const int q = s.ang[a];
+            A.f[q][0] += ax;
+            A.f[q][1] += ay;
+            A.f[q][2] += az;
+        }
+        __syncwarp();
     }
-    __syncwarp();
     for (int q = lane; q < cnt; q += 32) {
         const int j = s.j[q];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            if (A.f[q][c]) atomicAdd(&fx[3 * j + c], A.f[q][c]);
+        for (int c = 0; c < 3; ++c) {
+            const long long v = fx_from_float(A.f[q][c]);
+            if (v != 0) atomicAdd(&fx[3 * j + c], (unsigned long long)v);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -715,15 +782,6 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
     for (int f = lane; f < kNFeat; f += 32) out[f] = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
 }
 
-// Sum of the per-row energies into the fixed-point learned-energy slot.
-__global__ void k_learn_energy(LearnedDev L, unsigned long long *efx, int gated) {
-    if (gated && L.lflags[1]) return;
-    double e = 0.0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < L.n_rows; r += gridDim.x * blockDim.x) e += L.E_row[r];
-    e = warp_sum_d(e);
-    if ((threadIdx.x & 31) == 0 && e != 0.0) fx_add_d(&efx[E_LEARN], e);
-}
-
 __global__ void k_learn_begin(LearnedDev L) {
     if (threadIdx.x == 0) L.lflags[1] = 0u;
 }
@@ -777,7 +835,7 @@ cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forc
                               cudaStream_t s) {
     int f = forced ? 1 : 0;
     long long limit = 1000000000LL;   // 1 s per barrier wait
-    const int want = (L.n + kNbThreads - 1) / kNbThreads;
+    const int want = (L.n + kNbThreads / 32 - 1) / (kNbThreads / 32);   // one warp per atom in the row phase
     const int grid = want < L.nb_grid ? want : L.nb_grid;
     LearnedDev Lc = L;
     const float4 *p = pos4;
@@ -794,14 +852,14 @@ void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, c
     k_features<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, write_f32 ? 1 : 0);
 }
 
-void learned_mlp(const LearnedDev &L, bool gated, cudaStream_t s) {
-    if (L.n_rows > 0) k_mlp_simt<<<L.n_rows / kMlpRows, 256, 0, s>>>(L, gated ? 1 : 0);
+void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long *efx, cudaStream_t s) {
+    if (L.n_rows <= 0) return;
+    if (fp32) k_mlp_simt<false><<<L.n_rows / kMlpRows, 256, 0, s>>>(L, gated ? 1 : 0, efx);
+    else k_mlp_simt<true><<<L.n_rows / kMlpRows, 256, 0, s>>>(L, gated ? 1 : 0, efx);
 }
 
-void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
-                     bool gated, cudaStream_t s) {
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s) {
     k_adjoint<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0);
-    k_learn_energy<<<8, 256, 0, s>>>(L, efx, gated ? 1 : 0);
 }
 
 }  // namespace mdpf

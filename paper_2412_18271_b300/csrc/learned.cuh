@@ -70,9 +70,9 @@ cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forc
                               cudaStream_t s);
 void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s);
 void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s);
-void learned_mlp(const LearnedDev &L, bool gated, cudaStream_t s);
-void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
-                     bool gated, cudaStream_t s);
+// MLP on the CUDA cores; efx (or null) receives the summed energy in its learned-energy slot
+void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long *efx, cudaStream_t s);
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s);
 void learned_begin(const LearnedDev &L, cudaStream_t s);
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s);
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s);
@@ -81,6 +81,7 @@ void learned_jvp(const LearnedDev &L, const float4 *pos4, const float *v, float 
 
 // tensor-core MLP (mlp_tc.cu): forward energy and dE/dG, one 128-row tile per CTA
 cudaError_t learned_mlp_tc_prepare();
-cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated, cudaStream_t s);
+cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated,
+                           unsigned long long *efx, cudaStream_t s);
 
 }  // namespace mdpf

@@ -55,9 +55,9 @@ static int make_maps(mdpf_ctx *c, LearnedHost *h) {
 }
 
 // The MLP (energy per row and dE/dG) on the selected units.
-static void enqueue_mlp(LearnedHost *h, uint32_t *status, bool gated, cudaStream_t s) {
-    if (h->mlp_kernel == MDPF_MLP_TENSOR) learned_mlp_tc(h->dev, h->maps, status, gated, s);
-    else learned_mlp(h->dev, gated, s);
+static void enqueue_mlp(LearnedHost *h, uint32_t *status, bool gated, unsigned long long *efx, cudaStream_t s) {
+    if (h->mlp_kernel == MDPF_MLP_TENSOR) learned_mlp_tc(h->dev, h->maps, status, gated, efx, s);
+    else learned_mlp(h->dev, gated, h->mlp_kernel == MDPF_MLP_SIMT_FP32, efx, s);
 }
 
 static LearnedHost *lh(const mdpf_ctx *c) { return static_cast<LearnedHost *>(c->learned); }
@@ -284,17 +284,18 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     if (ce != cudaSuccess) return cuda_fail(c, ce, "learned_neighbors");
     prof_end(c, MDPF_PROF_LEARN_NEIGHBORS, ev, s);
     ev = prof_begin(c, s);
-    learned_features(L, pos4, write_f32, s);
+    learned_features(L, pos4, write_f32 || h->mlp_kernel == MDPF_MLP_SIMT_FP32, s);
     prof_end(c, MDPF_PROF_LEARN_FEATURES, ev, s);
     // with the fallback on, a step that left the range skips the model and runs the plain force field;
     // with it off, the model's forces are used and the step reports MDPF_STATUS_OUT_OF_RANGE
     const bool gated = h->fallback != 0;
     ev = prof_begin(c, s);
-    enqueue_mlp(h, status, gated, s);
+    enqueue_mlp(h, status, gated, efx, s);
     prof_end(c, MDPF_PROF_LEARN_MLP, ev, s);
     ev = prof_begin(c, s);
-    learned_adjoint(L, pos4, fx, efx, gated, s);
+    learned_adjoint(L, pos4, fx, gated, s);
     prof_end(c, MDPF_PROF_LEARN_ADJOINT, ev, s);
+    if (L.lo == nullptr) return MDPF_OK;   // no feature ranges: no evaluation can leave them
     if (gated) {
         PlainDev p = plain_dev(c, pos4);
         p.status = status;
@@ -391,7 +392,11 @@ int mdpf_learned_mlp(mdpf_ctx *c, const float *G, double *E_atom, float *dEdG) {
     LCK(c, cudaMemcpyAsync(h->d_Gin, G, sizeof(float) * (size_t)c->n * kNFeat, cudaMemcpyHostToDevice, c->stream));
     LCK(c, cudaMemsetAsync(c->d_status + 1, 0, sizeof(uint32_t), c->stream));
     learned_import_g(h->dev, h->d_Gin, c->stream);
-    enqueue_mlp(h, c->d_status + 1, false, c->stream);
+    if (h->mlp_kernel == MDPF_MLP_SIMT_FP32)
+        for (int i = 0; i < c->n; ++i)
+            LCK(c, cudaMemcpyAsync(h->dev.G32 + (size_t)h->row_of[i] * kNFeat, G + (size_t)i * kNFeat,
+                                   sizeof(float) * kNFeat, cudaMemcpyHostToDevice, c->stream));
+    enqueue_mlp(h, c->d_status + 1, false, nullptr, c->stream);
     std::vector<double> E(h->n_rows);
     std::vector<float> g((size_t)h->n_rows * kNFeat);
     if (h->n_rows > 0) {

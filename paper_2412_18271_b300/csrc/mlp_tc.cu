@@ -183,7 +183,7 @@ __device__ __forceinline__ void chunk_of(int c, int &g, int &kc) {
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, int gated) {
+k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, int gated, unsigned long long *efx) {
     if (gated && L.lflags[1]) return;
     if (L.n_tiles_live != nullptr && (int)blockIdx.x >= *L.n_tiles_live) return;
     extern __shared__ unsigned char smem_raw[];
@@ -350,7 +350,12 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         epi_sync();   // energy partials of the four column groups are in shared memory
         if (ok && cg == 0) {
             const float E = ((sEp[r] + sEp[128 + r]) + sEp[256 + r]) + sEp[384 + r];
-            L.E_row[row] = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
+            const double Er = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
+            L.E_row[row] = Er;
+            if (efx != nullptr) {   // the tile's energy into the fixed-point learned-energy slot
+                const double ws = warp_sum_d(Er);
+                if (lane == 0 && ws != 0.0) fx_add_d(&efx[E_LEARN], ws);
+            }
         }
         // epi3: d1 = bf16(P1 * celu'(H1 + b1)), columns 64 cg .. 64 cg + 63
         if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {
@@ -418,8 +423,10 @@ cudaError_t learned_mlp_tc_prepare() {
     return cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
-cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated, cudaStream_t s) {
-    if (L.n_rows > 0) k_mlp_tc<<<L.n_rows / kRowTile, kTcThreads, kSmemBytes, s>>>(L, maps, status, gated ? 1 : 0);
+cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated,
+                           unsigned long long *efx, cudaStream_t s) {
+    if (L.n_rows > 0)
+        k_mlp_tc<<<L.n_rows / kRowTile, kTcThreads, kSmemBytes, s>>>(L, maps, status, gated ? 1 : 0, efx);
     return cudaGetLastError();
 }
 

@@ -727,10 +727,10 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     cudaMemsetAsync(L.G16, 0, sizeof(__nv_bfloat16) * (size_t)t->rows_max * kNFeat, s);
     learned_features(L, t->d_pos4, true, s);
     k_tr_range<<<t->tiles_max, kNFeat, 0, s>>>(L, t->d_rmin, t->d_rmax);
-    cudaError_t ce = learned_mlp_tc(L, t->maps, t->d_status, false, s);
+    cudaError_t ce = learned_mlp_tc(L, t->maps, t->d_status, false, nullptr, s);
     if (ce != cudaSuccess) return tr_cuda(t, ce, "learned_mlp_tc");
     cudaMemsetAsync(t->d_fx, 0, sizeof(unsigned long long) * 3 * (size_t)n, s);
-    learned_adjoint(L, t->d_pos4, t->d_fx, t->d_efx, false, s);
+    learned_adjoint(L, t->d_pos4, t->d_fx, false, s);
     // 4. loss, c, v; U = J v
     k_tr_loss<<<B, 256, 0, s>>>(L, N, B, t->w_force, t->d_tile_off, d_E_ref, d_F_ref, t->d_fx, t->d_c, t->d_v,
                                  t->d_lparts);

@@ -36,6 +36,7 @@ MDPF_STEPPER_PERSISTENT = 0
 MDPF_STEPPER_KERNELS = 1
 MDPF_MLP_TENSOR = 0
 MDPF_MLP_SIMT = 1
+MDPF_MLP_SIMT_FP32 = 2
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32

@@ -424,3 +424,39 @@ def test_graph_stepping_equals_direct_launches(mdl):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert np.array_equal(ua, ub) and np.array_equal(ka, kb)
     assert ca == cb
+
+
+def test_fallback_every_step_reproduces_the_plain_trajectory(mdl):
+    # ranges that every feature violates: each learned step is a plain force-field step
+    s = synth.workload("mol256")
+    r = model.Model(mdl.W1, mdl.b1, mdl.W2, mdl.b2, mdl.W3, mdl.b3, mdl.e0,
+                    np.full((4, 384), -2.0, np.float32), np.full((4, 384), -1.0, np.float32))
+    vel = synth.velocities(s.mass, s.pos, 300.0, 15)
+    a = _ctx(s, r, energy_every=1)
+    a.set_state(s.pos, vel)
+    a.step(40)
+    b = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_KERNELS, energy_every=1)
+    b.set_state(s.pos, vel)
+    b.step(40)
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert a.learned_counters()["fallback_steps"] == 41
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    ua, ka = a.trace()
+    ub, kb = b.trace()
+    assert np.allclose(ua, ub, rtol=1e-12, atol=1e-9) and np.array_equal(ka, kb)
+
+
+def test_fp32_mlp_kernel_matches_the_oracle_tightly(mdl):
+    # FP32 operands throughout: FP32 rounding only, against the FP64 oracle
+    s = synth.workload("mol256")
+    ctx = _ctx(s, mdl, mlp_kernel=mdpf.MDPF_MLP_SIMT_FP32)
+    Go = O.features(s.element, s.pos)
+    E, dG = ctx.learned_mlp(Go.astype(np.float32))
+    _, Eo, dGo = O.Learned(mdl).mlp(s.element, Go)
+    assert np.max(np.abs(E - Eo)) <= 1e-5 * max(1.0, np.max(np.abs(Eo)))
+    assert np.sqrt(((dG - dGo) ** 2).mean()) <= 1e-4 * np.sqrt((dGo ** 2).mean())
+    e, f, _ = ctx.compute(s.pos)
+    eo, fo, _ = O.Learned(mdl).energy_forces(s.element, s.pos)
+    assert abs(e - eo) / s.n_atoms <= 1e-5
+    assert np.sqrt(((f - fo) ** 2).mean()) <= 1e-4 * np.sqrt((fo ** 2).mean())

@@ -178,7 +178,7 @@ def test_training_reduces_the_loss(mdl):
         L, _ = AG.ForceMatchingLoss.apply(params, tr, pos, el, E, F)
         L.backward()
         opt.step()
-        losses.append(float(L))
+        losses.append(float(L.detach()))
     assert tr.status() == 0
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
 
