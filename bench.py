@@ -244,7 +244,9 @@ def learned_leg(args, dev, stream, flush):
     # every bench step starts from the same state (reset outside the timed region): the
     # trained potential keeps this cluster intact for a few thousand steps only
     with torch.cuda.stream(stream):
+        # set_state runs on the context's own stream: the previous steps (on `stream`) must be done
         for _ in range(args.warmup):
+            stream.synchronize()
             ctx.set_state(s.pos, v0)
             ctx.step_async(md, stream.cuda_stream)
         stream.synchronize()
@@ -254,6 +256,7 @@ def learned_leg(args, dev, stream, flush):
         torch.cuda.synchronize()
         with ClockSampler(dev.index) as clk:
             for k in range(args.steps):
+                stream.synchronize()
                 ctx.set_state(s.pos, v0)
                 flush.zero_()
                 evs[k][0].record(stream)
@@ -265,6 +268,7 @@ def learned_leg(args, dev, stream, flush):
         # launch stream (profiling launches each step kernel by kernel instead of as one graph)
         ctx.set_profiling(True)
         for k in range(args.steps):
+            stream.synchronize()
             ctx.set_state(s.pos, v0)
             flush.zero_()
             ctx.step_async(md, stream.cuda_stream)

@@ -244,7 +244,13 @@ MDPF_API int mdpf_get_state(mdpf_ctx *ctx, double *pos, double *vel);
  */
 MDPF_API int mdpf_step(mdpf_ctx *ctx, int64_t n_steps);
 
-/* Asynchronous mdpf_step on cuda_stream; status is checked by the next synchronous call. */
+/*
+ * Asynchronous mdpf_step on cuda_stream; status is checked by the next
+ * synchronous call.  The synchronous calls run on the context's own stream:
+ * the caller must let work enqueued on cuda_stream finish (or order the
+ * streams) before calling mdpf_set_state, mdpf_get_state or mdpf_compute on
+ * the same context.
+ */
 MDPF_API int mdpf_step_async(mdpf_ctx *ctx, int64_t n_steps, void *cuda_stream);
 
 /* Counters, energies of the current state and the device status word. */

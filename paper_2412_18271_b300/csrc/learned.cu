@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
     __shared__ NbrSmem sn[kFeatWarps];
     __shared__ float accR[kFeatWarps][2][64];
     __shared__ float accA[kFeatWarps][320];
-    __shared__ float tcs[kFeatWarps][32], tsn[kFeatWarps][32], tC[kFeatWarps][32], tB[kFeatWarps][32][4];
-    __shared__ int tP[kFeatWarps][32];
+    __shared__ float4 tQ[kFeatWarps][32];     // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
+    __shared__ float tB[kFeatWarps][32][4];   // radial-shell factors
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
@@ -340,40 +340,67 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
             accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * fcut(r, kRcRad);
         }
     }
-    // angular: lane = 8 m + p owns the (m, p) column of every pair block
+    // angular: lane = 8 m + p owns the (m, p) column of every pair block.  Each
+    // batch of 32 triplets is staged sorted by pair type (stable), so a lane
+    // keeps its column sum in a register and writes it back when the type changes.
     {
         const int m = lane >> 3, p = lane & 7;
         const float thp = (float)(2 * p + 1) * (kPi / 16.f);
         const float cp = cosf(thp), sp = sinf(thp);
         const int ntrip = na * (na - 1) / 2;
+        const unsigned int below = (1u << lane) - 1u;
+        float acc = 0.f;
+        int curP = -1;
         for (int base = 0; base < ntrip; base += 32) {
             const int t = base + lane;
+            int P = 15;   // no triplet
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            float bm[4] = {0.f, 0.f, 0.f, 0.f};
             if (t < ntrip) {
                 int a, b;
                 triplet_ab(t, na, a, b);
                 const float4 dj = s.d[s.ang[a]], dk = s.d[s.ang[b]];
                 const float ct = (dj.x * dk.x + dj.y * dk.y + dj.z * dk.z) / (dj.w * dk.w);
                 const float cs = kAngScale * ct;
-                tcs[w][lane] = cs;
-                tsn[w][lane] = sqrtf(1.f - cs * cs);
-                tC[w][lane] = fcut(dj.w, kRcAng) * fcut(dk.w, kRcAng);
+                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * fcut(dj.w, kRcAng) * fcut(dk.w, kRcAng), 0.f);
                 const float ravg = 0.5f * (dj.w + dk.w);
 #pragma unroll
                 for (int mm = 0; mm < 4; ++mm) {
                     const float x = ravg - (0.9f + (float)mm * 0.65f);
-                    tB[w][lane][mm] = expf(-kEtaA * x * x);
+                    bm[mm] = expf(-kEtaA * x * x);
                 }
-                tP[w][lane] = pair_index(s.el[s.ang[a]], s.el[s.ang[b]]);
+                P = pair_index(s.el[s.ang[a]], s.el[s.ang[b]]);
+            }
+            int pos = 0, before = 0;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                const unsigned int bal = __ballot_sync(0xffffffffu, P == k);
+                if (P == k) pos = before + __popc(bal & below);
+                before += __popc(bal);
+            }
+            if (t < ntrip) {
+                q.w = __int_as_float(P);
+                tQ[w][pos] = q;
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) tB[w][pos][mm] = bm[mm];
             }
             __syncwarp();
             const int nt = min(32, ntrip - base);
             for (int u = 0; u < nt; ++u) {
-                float x = 1.f + tcs[w][u] * cp + tsn[w][u] * sp;
+                const float4 qq = tQ[w][u];
+                const int Pu = __float_as_int(qq.w);
+                if (Pu != curP) {   // the same in every lane
+                    if (curP >= 0) accA[w][32 * curP + lane] += acc;
+                    acc = 0.f;
+                    curP = Pu;
+                }
+                float x = 1.f + qq.x * cp + qq.y * sp;
                 x *= x; x *= x; x *= x; x *= x; x *= x;  // ^32
-                accA[w][32 * tP[w][u] + lane] += kTwoPowM31 * x * tB[w][u][m] * tC[w][u];
+                acc = fmaf(x * qq.z, tB[w][u][m], acc);
             }
             __syncwarp();
         }
+        if (curP >= 0) accA[w][32 * curP + lane] += acc;
     }
     __syncwarp();
     const int row = L.row_of[i];
