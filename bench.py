@@ -54,6 +54,9 @@ FEAT_FLOPS_PER_PAIR = 110       # radial: 16 Gaussians x (sub, mul, mul, exp, mu
 FEAT_FLOPS_PER_TRIPLET = 460    # angular: cos/sin of theta, 4 shells x exp, 32 columns x (2 fma + ^32 + 3 mul + add)
 ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
+# DRAM bytes (read + write) per launch of each learned kernel on this workload, from the ncu capture in
+# profiles/learned_step_cluster16384.md (valid for the kernels as captured there)
+LEARNED_TRAFFIC = {"adjoint": 28266240, "features": 2696960, "mlp": 15011840}
 
 
 def peaks():
@@ -331,7 +334,7 @@ def learned_leg(args, dev, stream, flush):
         "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": prof[dom][1],
-                     "traffic": None},
+                     "traffic": LEARNED_TRAFFIC.get(dom)},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
                 "d2h_bytes_per_step": 2 * n * 3 * 8 + 48},
         "clocks": clk.summary(),

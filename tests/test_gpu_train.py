@@ -204,5 +204,5 @@ def test_learned_energy_autograd_gives_minus_forces(mdl):
     E = AG.LearnedEnergy.apply(pos, ctx)
     E.backward()
     torch.cuda.synchronize()
-    assert abs(float(E) - e) <= 1e-9 * max(1.0, abs(e))
+    assert abs(float(E.detach()) - e) <= 1e-9 * max(1.0, abs(e))
     assert np.allclose(pos.grad.cpu().numpy(), -f, rtol=1e-6, atol=1e-6)
