@@ -268,7 +268,8 @@ constexpr int kFeatWarps = 4;
 struct NbrSmem {
     int j[kKmax];
     int el[kKmax];
-    float4 d[kKmax];      // dx, dy, dz, r
+    float4 d[kKmax];      // unit vector from i to j (x, y, z) and r
+    float4 fc[kKmax];     // fc(r; 5.2), fc'(r; 5.2), fc(r; 3.5), fc'(r; 3.5)
     int rad[kKmax];       // neighbours within the radial cutoff, in row order
     int ang[kKmax];       // neighbours within the angular cutoff, in row order
 };
@@ -285,9 +286,11 @@ __device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float
         const int j = L.nb_idx[(size_t)i * kKmax + q];
         const float4 pj = pos4[j];
         const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
         s.j[q] = j;
         s.el[q] = L.el[j];
-        s.d[q] = make_float4(dx, dy, dz, sqrtf(dx * dx + dy * dy + dz * dz));
+        s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        s.fc[q] = make_float4(fcut(r, kRcRad), dfcut(r, kRcRad), fcut(r, kRcAng), dfcut(r, kRcAng));
     }
     __syncwarp();
     nr = 0;
@@ -319,8 +322,8 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
     __shared__ NbrSmem sn[kFeatWarps];
     __shared__ float accR[kFeatWarps][2][64];
     __shared__ float accA[kFeatWarps][320];
-    __shared__ float4 tQ[kFeatWarps][32];     // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
-    __shared__ float tB[kFeatWarps][32][4];   // radial-shell factors
+    __shared__ float4 tQ[kFeatWarps][64];     // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
+    __shared__ float4 tB[kFeatWarps][64];     // radial-shell factors of the 4 shells
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
@@ -337,70 +340,104 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
             const int q = s.rad[u];
             const float r = s.d[q].w;
             const float x = r - Rk;
-            accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * fcut(r, kRcRad);
+            accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * s.fc[q].x;
         }
     }
-    // angular: lane = 8 m + p owns the (m, p) column of every pair block.  Each
-    // batch of 32 triplets is staged sorted by pair type (stable), so a lane
-    // keeps its column sum in a register and writes it back when the type changes.
+    // angular.  Each batch of 32 triplets is staged sorted by element pair (stable),
+    // each pair's run padded to a multiple of 4 with empty triplets; then lane
+    // 8 t4 + p takes triplet t4 of every group of 4 (all of one pair type),
+    // computes its angular factor for section p once and adds it, times the 4
+    // shell factors, to its 4 column sums (m = 0..3).  When the pair type changes
+    // the 4 triplet slots are combined in a fixed shuffle order into the pair's
+    // (m, p) columns.
     {
-        const int m = lane >> 3, p = lane & 7;
+        const int t4 = lane >> 3, p = lane & 7;
         const float thp = (float)(2 * p + 1) * (kPi / 16.f);
         const float cp = cosf(thp), sp = sinf(thp);
         const int ntrip = na * (na - 1) / 2;
         const unsigned int below = (1u << lane) - 1u;
-        float acc = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         int curP = -1;
         for (int base = 0; base < ntrip; base += 32) {
             const int t = base + lane;
             int P = 15;   // no triplet
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            float bm[4] = {0.f, 0.f, 0.f, 0.f};
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f), bq = make_float4(0.f, 0.f, 0.f, 0.f);
             if (t < ntrip) {
                 int a, b;
                 triplet_ab(t, na, a, b);
-                const float4 dj = s.d[s.ang[a]], dk = s.d[s.ang[b]];
-                const float ct = (dj.x * dk.x + dj.y * dk.y + dj.z * dk.z) / (dj.w * dk.w);
+                const int qa = s.ang[a], qb = s.ang[b];
+                const float4 dj = s.d[qa], dk = s.d[qb];
+                const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
                 const float cs = kAngScale * ct;
-                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * fcut(dj.w, kRcAng) * fcut(dk.w, kRcAng), 0.f);
+                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * s.fc[qa].z * s.fc[qb].z, 0.f);
                 const float ravg = 0.5f * (dj.w + dk.w);
+                float bm[4];
 #pragma unroll
                 for (int mm = 0; mm < 4; ++mm) {
                     const float x = ravg - (0.9f + (float)mm * 0.65f);
                     bm[mm] = expf(-kEtaA * x * x);
                 }
-                P = pair_index(s.el[s.ang[a]], s.el[s.ang[b]]);
+                bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
+                P = pair_index(s.el[qa], s.el[qb]);
             }
+            // padded, stable counting sort by pair type; empty slots of a run stay zero (no contribution)
             int pos = 0, before = 0;
 #pragma unroll
             for (int k = 0; k < 10; ++k) {
                 const unsigned int bal = __ballot_sync(0xffffffffu, P == k);
+                const int cnt_k = __popc(bal);
                 if (P == k) pos = before + __popc(bal & below);
-                before += __popc(bal);
+                // the run's padding slots: empty triplets of type k
+                const int padded = (cnt_k + 3) & ~3;
+                if (lane >= cnt_k && lane < padded) {
+                    tQ[w][before + lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
+                    tB[w][before + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                before += padded;
             }
             if (t < ntrip) {
                 q.w = __int_as_float(P);
                 tQ[w][pos] = q;
-#pragma unroll
-                for (int mm = 0; mm < 4; ++mm) tB[w][pos][mm] = bm[mm];
+                tB[w][pos] = bq;
             }
             __syncwarp();
-            const int nt = min(32, ntrip - base);
-            for (int u = 0; u < nt; ++u) {
-                const float4 qq = tQ[w][u];
-                const int Pu = __float_as_int(qq.w);
-                if (Pu != curP) {   // the same in every lane
-                    if (curP >= 0) accA[w][32 * curP + lane] += acc;
-                    acc = 0.f;
+            const int ng = before;   // padded length, a multiple of 4
+            for (int u = 0; u < ng; u += 4) {
+                const float4 qq = tQ[w][u + t4];
+                const int Pu = __float_as_int(tQ[w][u].w);   // the group's pair type, the same in every lane
+                if (Pu != curP) {
+                    if (curP >= 0) {
+#pragma unroll
+                        for (int mm = 0; mm < 4; ++mm) {
+                            float v = acc[mm];
+                            v += __shfl_xor_sync(0xffffffffu, v, 8);
+                            v += __shfl_xor_sync(0xffffffffu, v, 16);
+                            if (t4 == 0) accA[w][32 * curP + 8 * mm + p] += v;
+                            acc[mm] = 0.f;
+                        }
+                    }
                     curP = Pu;
                 }
                 float x = 1.f + qq.x * cp + qq.y * sp;
                 x *= x; x *= x; x *= x; x *= x; x *= x;  // ^32
-                acc = fmaf(x * qq.z, tB[w][u][m], acc);
+                const float xc = x * qq.z;
+                const float4 bb = tB[w][u + t4];
+                acc[0] = fmaf(xc, bb.x, acc[0]);
+                acc[1] = fmaf(xc, bb.y, acc[1]);
+                acc[2] = fmaf(xc, bb.z, acc[2]);
+                acc[3] = fmaf(xc, bb.w, acc[3]);
             }
             __syncwarp();
         }
-        if (curP >= 0) accA[w][32 * curP + lane] += acc;
+        if (curP >= 0) {
+#pragma unroll
+            for (int mm = 0; mm < 4; ++mm) {
+                float v = acc[mm];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                if (t4 == 0) accA[w][32 * curP + 8 * mm + p] += v;
+            }
+        }
     }
     __syncwarp();
     const int row = L.row_of[i];
@@ -535,7 +572,7 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated, unsig
 // Angular blocks of g are stored 33 floats apart so that lanes working on
 // different element pairs read different banks.
 constexpr int kAngStride = 33;
-constexpr int kTripChunk = 160;   // triplets staged per pass
+constexpr int kTripChunk = 80;    // triplets staged per pass
 
 struct AdjSmem {
     float g[64 + 10 * kAngStride];
@@ -578,7 +615,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
         const int q = s.rad[u];
         const float4 d = s.d[q];
         const float r = d.w;
-        const float fc = fcut(r, kRcRad), dfc = dfcut(r, kRcRad);
+        const float fc = s.fc[q].x, dfc = s.fc[q].y;
         const float *gz = A.g + 16 * s.el[q];
         float dEdr = 0.f;
 #pragma unroll 4
@@ -587,8 +624,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
             const float ex = expf(-kEtaR * x * x);
             dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
         }
-        const float ir = 1.f / r;
-        const float sx = dEdr * d.x * ir, sy = dEdr * d.y * ir, sz = dEdr * d.z * ir;
+        const float sx = dEdr * d.x, sy = dEdr * d.y, sz = dEdr * d.z;
         A.f[q][0] = -sx;
         A.f[q][1] = -sy;
         A.f[q][2] = -sz;
@@ -615,14 +651,14 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
             const float4 dj = s.d[qa], dk = s.d[qb];
             const float rj = dj.w, rk = dk.w;
             const float irj = 1.f / rj, irk = 1.f / rk;
-            const float ujx = dj.x * irj, ujy = dj.y * irj, ujz = dj.z * irj;
-            const float ukx = dk.x * irk, uky = dk.y * irk, ukz = dk.z * irk;
+            const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
+            const float ukx = dk.x, uky = dk.y, ukz = dk.z;
             const float ct = ujx * ukx + ujy * uky + ujz * ukz;
             const float cs = kAngScale * ct;
             const float sn2 = sqrtf(1.f - cs * cs);
             const float cot = cs / sn2;
-            const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
-            const float dfj = dfcut(rj, kRcAng), dfk = dfcut(rk, kRcAng);
+            const float fj = s.fc[qa].z, fk = s.fc[qb].z;
+            const float dfj = s.fc[qa].w, dfk = s.fc[qb].w;
             const float C = fj * fk;
             const float ravg = 0.5f * (rj + rk);
             const float *gp = A.g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
@@ -743,10 +779,10 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
             const float4 d = s.d[q];
             const int j = s.j[q];
             const float r = d.w;
-            const float rdot = (d.x * (v[3 * j] - vix) + d.y * (v[3 * j + 1] - viy) + d.z * (v[3 * j + 2] - viz)) / r;
+            const float rdot = d.x * (v[3 * j] - vix) + d.y * (v[3 * j + 1] - viy) + d.z * (v[3 * j + 2] - viz);
             const float x = r - Rk;
             const float ex = expf(-kEtaR * x * x);
-            accR[w][h][16 * s.el[q] + k] += ex * (-2.f * kEtaR * x * fcut(r, kRcRad) + dfcut(r, kRcRad)) * rdot;
+            accR[w][h][16 * s.el[q] + k] += ex * (-2.f * kEtaR * x * s.fc[q].x + s.fc[q].y) * rdot;
         }
     }
     {
@@ -763,11 +799,11 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
                 const float4 dj = s.d[qa], dk = s.d[qb];
                 const int ja = s.j[qa], jb = s.j[qb];
                 const float rj = dj.w, rk = dk.w;
-                const float ujx = dj.x / rj, ujy = dj.y / rj, ujz = dj.z / rj;
-                const float ukx = dk.x / rk, uky = dk.y / rk, ukz = dk.z / rk;
+                const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
+                const float ukx = dk.x, uky = dk.y, ukz = dk.z;
                 const float wjx = v[3 * ja] - vix, wjy = v[3 * ja + 1] - viy, wjz = v[3 * ja + 2] - viz;
                 const float wkx = v[3 * jb] - vix, wky = v[3 * jb + 1] - viy, wkz = v[3 * jb + 2] - viz;
-                const float ct = (dj.x * dk.x + dj.y * dk.y + dj.z * dk.z) / (rj * rk);
+                const float ct = ujx * ukx + ujy * uky + ujz * ukz;
                 const float rjd = ujx * wjx + ujy * wjy + ujz * wjz, rkd = ukx * wkx + uky * wky + ukz * wkz;
                 const float ctd = ((ukx - ct * ujx) * wjx + (uky - ct * ujy) * wjy + (ukz - ct * ujz) * wjz) / rj +
                                   ((ujx - ct * ukx) * wkx + (ujy - ct * uky) * wky + (ujz - ct * ukz) * wkz) / rk;
@@ -777,9 +813,9 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
                 tsn[w][lane] = sn2;
                 tcot[w][lane] = cs / sn2;
                 tcsd[w][lane] = kAngScale * ctd;
-                const float fj = fcut(rj, kRcAng), fk = fcut(rk, kRcAng);
+                const float fj = s.fc[qa].z, fk = s.fc[qb].z;
                 tC[w][lane] = fj * fk;
-                tCd[w][lane] = dfcut(rj, kRcAng) * fk * rjd + fj * dfcut(rk, kRcAng) * rkd;
+                tCd[w][lane] = s.fc[qa].w * fk * rjd + fj * s.fc[qb].w * rkd;
                 const float ravg = 0.5f * (rj + rk), ravgd = 0.5f * (rjd + rkd);
 #pragma unroll
                 for (int mm = 0; mm < 4; ++mm) {
