@@ -299,6 +299,28 @@ def learned_leg(args, dev, stream, flush):
     e2e_rate = e2e_steps * md / (time.perf_counter() - t0)
     ctx.close()
 
+    # the plain force field on the same cluster (all pairs, persistent stepper), for the comparison
+    plain_md = max(10, md // 4)
+    pctx = mdpf.Context(s, dt_fs=DT_FS, energy_every=RECORD_EVERY, trace_capacity=plain_md)
+    pctx.set_state(s.pos, v0)
+    pctx.step(plain_md)
+    pms = 0.0
+    for _ in range(args.steps):
+        pctx.set_state(s.pos, v0)
+        torch.cuda.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0_.record(stream)
+            pctx.step_async(plain_md, stream.cuda_stream)
+            e1_.record(stream)
+        torch.cuda.synchronize()
+        pms += e0_.elapsed_time(e1_)
+    if pctx.counters()["status"] != 0:
+        raise RuntimeError("device status after the plain run on the learned workload")
+    pctx.close()
+    plain_rate = args.steps * plain_md / (pms / 1000.0)
+
     pk, pk_kind = peaks()
     mhz = pk.get("sm_max_mhz", 2032.0)
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -322,6 +344,11 @@ def learned_leg(args, dev, stream, flush):
         "dtype": "bf16 GEMM operands / f32 features and forces / f64 state",
         "model": model_desc,
         "force_rmse_vs_plain_kcal_mol_A": rmse_vs_plain, "rms_plain_force_kcal_mol_A": rms_plain,
+        "plain_same_workload": {"value": plain_rate, "unit": UNIT, "ms_per_md_step": pms / args.steps / plain_md,
+                                "md_steps_per_bench_step": plain_md,
+                                "what": "plain force field (all pairs, no cutoff) on the same cluster, persistent "
+                                        "stepper, same start state"},
+        "learned_over_plain": rate / plain_rate,
         "force_rmse_vs_oracle": "<= 1e-2 x RMS(F) against the FP64 oracle (BF16 parity tests)",
         "stepper": "one CUDA graph launch per MD step (fused neighbour check/build, features, tensor-core MLP, "
                    "adjoint, integration); every bench step restarts from the cluster's initial state",
