@@ -368,6 +368,51 @@ def learned_leg(args, dev, stream, flush):
     }
 
 
+def provider_leg(args, dev, stream):
+    """The 64-atom molecule stepped three ways: one persistent launch per bench step, one kernel sequence
+    per MD step, and the external-provider path (a Python callable called by the library every step,
+    here wrapping the in-library force field), which measures what the callback costs per step."""
+    import torch
+    from paper_2412_18271_b300 import mdpf, synth
+    s = synth.workload("mol64")
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED["mol64"])
+    plain = mdpf.Context(s, dt_fs=DT_FS, stepper=mdpf.MDPF_STEPPER_KERNELS)
+
+    def prov(pos):
+        E = torch.empty(1, dtype=torch.float64, device=pos.device)
+        F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device=pos.device)
+        plain.compute_device(pos.data_ptr(), E.data_ptr(), F.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        return E[0], F
+
+    out = {}
+    for name, kw, md in (("persistent", dict(stepper=mdpf.MDPF_STEPPER_PERSISTENT), 1000),
+                         ("kernel_sequence", dict(stepper=mdpf.MDPF_STEPPER_KERNELS), 500),
+                         ("python_provider", dict(mode=mdpf.MDPF_MODE_CALLBACK, provider=prov), 200)):
+        ctx = mdpf.Context(s, dt_fs=DT_FS, energy_every=10, trace_capacity=md, **kw)
+        ctx.set_state(s.pos, v0)
+        with torch.cuda.stream(stream):
+            ctx.step_async(md, stream.cuda_stream)
+            stream.synchronize()
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0_.record(stream)
+            t0 = time.perf_counter()
+            ctx.step_async(md, stream.cuda_stream)
+            e1_.record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        if ctx.counters()["status"] != 0:
+            raise RuntimeError("device status in the %s run" % name)
+        ms = e0_.elapsed_time(e1_)
+        out[name] = {"value": md / (ms / 1000.0), "unit": UNIT, "us_per_md_step": 1000.0 * ms / md,
+                     "host_wall_us_per_md_step": 1e6 * wall / md}
+        ctx.close()
+    plain.close()
+    out["provider_overhead_us_per_md_step"] = (out["python_provider"]["us_per_md_step"] -
+                                               out["kernel_sequence"]["us_per_md_step"])
+    out["workload"] = "64-atom molecule, plain force field (the provider wraps the library's own force field)"
+    return out
+
+
 def run_learned_only(args):
     import torch
     dev = torch.device("cuda", 0)
@@ -478,6 +523,8 @@ def run_ours(args):
     }
     if not args.no_learned:
         line["learned"] = learned_leg(args, dev, stream, flush)
+    if not args.no_learned:
+        line["provider"] = provider_leg(args, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
     if rank == 0:

@@ -51,6 +51,7 @@ extern "C" {
 #define MDPF_ERR_NONFINITE (-5)         /* energy or state became NaN/Inf */
 #define MDPF_ERR_TIMEOUT (-6)           /* a bounded device-side wait gave up */
 #define MDPF_ERR_OUT_OF_RANGE (-7)      /* learned features left the training range and fallback is off */
+#define MDPF_ERR_CALLBACK (-9)          /* the external force provider reported an error */
 #define MDPF_ERR_UNSUPPORTED (-8)       /* feature not available in this build or mode */
 
 /* device status-word bits (mdpf_counters.status), one per failure kind */
@@ -61,6 +62,7 @@ extern "C" {
 
 #define MDPF_MODE_PLAIN 0   /* analytic bonded + all-pairs LJ + Coulomb */
 #define MDPF_MODE_LEARNED 1 /* symmetry-function features + per-element MLP */
+#define MDPF_MODE_CALLBACK 2 /* forces from a caller-supplied force provider (mdpf_force_fn) */
 
 typedef struct mdpf_ctx mdpf_ctx;
 
@@ -115,6 +117,23 @@ typedef struct mdpf_topology {
  */
 #define MDPF_STEPPER_PERSISTENT 0
 #define MDPF_STEPPER_KERNELS 1
+
+/*
+ * External force provider (MDPF_MODE_CALLBACK), the callable the MD engine
+ * calls for energy and forces each step.  For every force evaluation the
+ * library copies the positions (FP64 [N][3], A) into the caller's device
+ * buffer provider_pos on cuda_stream, then calls fn(user, cuda_stream) on the
+ * host.  The provider enqueues its work on cuda_stream (or finishes it before
+ * returning) and writes the potential energy (one FP64, kcal/mol) to
+ * provider_energy and the forces (FP32 [N][3], kcal/mol/A) to provider_forces,
+ * both caller-owned device buffers; the library then turns them into its
+ * fixed-point sums on the same stream.  A nonzero return aborts the call with
+ * MDPF_ERR_CALLBACK.  Steps run one kernel sequence per step with the provider
+ * called between its kick-drift and kick (no graph, no persistent kernel).  The
+ * function and the buffers must stay valid for the context's lifetime.
+ */
+typedef int (*mdpf_force_fn)(void *user, void *cuda_stream);
+
 typedef struct mdpf_params {
     int32_t mode;
     double dt_fs;
@@ -137,6 +156,12 @@ typedef struct mdpf_params {
                                 MDPF_MLP_SIMT_FP32 (2): CUDA cores with FP32 operands (no BF16
                                 rounding of features, activations or deltas), so the forces are
                                 the gradient of the evaluated energy to FP32 rounding. */
+    /* callback mode only */
+    mdpf_force_fn provider;
+    void *provider_user;
+    double *provider_pos;     /* device [N][3] FP64, written by the library */
+    double *provider_energy;  /* device, 1 FP64, written by the provider */
+    float *provider_forces;   /* device [N][3] FP32, written by the provider */
 } mdpf_params;
 #define MDPF_MLP_TENSOR 0
 #define MDPF_MLP_SIMT 1

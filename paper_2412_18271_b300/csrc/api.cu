@@ -128,8 +128,11 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     if (!t->element || !t->mass || !t->charge) return fail(nullptr, MDPF_ERR_INVALID_ARG, "NULL per-atom array");
     if (t->n_bonds < 0 || (t->n_bonds > 0 && (!t->bonds || !t->bond_r0 || !t->bond_k)))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "bad bond arrays");
-    if (prm->mode != MDPF_MODE_PLAIN && prm->mode != MDPF_MODE_LEARNED)
+    if (prm->mode != MDPF_MODE_PLAIN && prm->mode != MDPF_MODE_LEARNED && prm->mode != MDPF_MODE_CALLBACK)
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "unknown mode");
+    if (prm->mode == MDPF_MODE_CALLBACK &&
+        (!prm->provider || !prm->provider_pos || !prm->provider_energy || !prm->provider_forces))
+        return fail(nullptr, MDPF_ERR_INVALID_ARG, "callback mode needs the provider function and its three buffers");
     if (prm->mode == MDPF_MODE_LEARNED && (!(prm->skin >= 0.0) || !std::isfinite(prm->skin) || prm->skin > 10.0 ||
                                            prm->rebuild_every < 0))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "skin must be in [0, 10] and rebuild_every >= 0");
@@ -184,8 +187,15 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     c->trace_cap = prm->trace_capacity > 0 ? prm->trace_capacity : 4096;
     c->record_every = prm->record_every;
     c->max_frames = prm->max_frames;
-    // learned mode always steps with the per-step kernel sequence
-    c->stepper = prm->mode == MDPF_MODE_LEARNED ? MDPF_STEPPER_KERNELS : prm->stepper;
+    // learned and callback modes always step with the per-step kernel sequence
+    c->stepper = prm->mode == MDPF_MODE_PLAIN ? prm->stepper : MDPF_STEPPER_KERNELS;
+    if (prm->mode == MDPF_MODE_CALLBACK) {
+        c->prov_fn = prm->provider;
+        c->prov_user = prm->provider_user;
+        c->prov_pos = prm->provider_pos;
+        c->prov_energy = prm->provider_energy;
+        c->prov_forces = prm->provider_forces;
+    }
     c->energy_every = prm->energy_every > 0 ? prm->energy_every : 1;
     c->angle_k = (float)t->angle_k;
     c->angle_theta0 = (float)(t->angle_theta0_deg * M_PI / 180.0);
@@ -385,6 +395,20 @@ int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles) {
     return MDPF_OK;
 }
 
+// External provider evaluation at the FP64 device positions x into (fx, efx)
+// (zeroed first when `zero`): positions into the caller's buffer, the host
+// call, then the provider's FP32 forces and FP64 energy into fixed point.
+static int enqueue_provider(mdpf_ctx *c, const double *x, unsigned long long *fx, unsigned long long *efx,
+                            uint32_t *status, bool zero, cudaStream_t s) {
+    if (zero) launch_zero_fx(fx, 3 * c->n_pad, efx, s);
+    CK(c, cudaMemcpyAsync(c->prov_pos, x, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, s));
+    const int rc = c->prov_fn(c->prov_user, (void *)s);
+    if (rc != 0) return fail(c, MDPF_ERR_CALLBACK, "the force provider returned " + std::to_string(rc));
+    launch_provider_to_fx(c->prov_forces, c->prov_energy, c->n, fx, efx, status, s);
+    CK(c, cudaGetLastError());
+    return MDPF_OK;
+}
+
 // Force evaluation into (fx, efx) at the FP32 positions pos4 (learned mode:
 // with a fresh neighbour list).
 static int enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
@@ -404,7 +428,9 @@ int mdpf_compute_device(mdpf_ctx *c, const double *d_pos, double *d_energy, floa
     cudaStream_t s = (cudaStream_t)stream;
     launch_pos4_from_x(d_pos, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, s);
     {
-        const int rc = enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+        const int rc = c->mode == MDPF_MODE_CALLBACK
+                           ? enqueue_provider(c, d_pos, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s)
+                           : enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
         if (rc != MDPF_OK) return rc;
     }
     if (d_forces) launch_fx_to_forces(c->d_fx_c, c->n, nullptr, d_forces, s);
@@ -422,7 +448,9 @@ int mdpf_compute(mdpf_ctx *c, const double *pos, double *energy, double *forces,
     CK(c, cudaMemcpyAsync(c->d_xc, pos, sizeof(double) * 3 * c->n, cudaMemcpyHostToDevice, s));
     launch_pos4_from_x(c->d_xc, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, s);
     {
-        const int rc = enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+        const int rc = c->mode == MDPF_MODE_CALLBACK
+                           ? enqueue_provider(c, c->d_xc, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s)
+                           : enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
         if (rc != MDPF_OK) return rc;
     }
     launch_fx_to_forces(c->d_fx_c, c->n, c->d_fc, nullptr, s);
@@ -453,7 +481,9 @@ int mdpf_set_state(mdpf_ctx *c, const double *pos, const double *vel) {
     CK(c, cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), s));
     launch_pos4_from_x(c->d_x, c->d_charge_s, c->d_pos4, c->n, c->n_pad, s);
     {
-        const int rc = enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, true, s);
+        const int rc = c->mode == MDPF_MODE_CALLBACK
+                           ? enqueue_provider(c, c->d_x, c->d_fx, c->d_efx, c->d_status, true, s)
+                           : enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, true, s);
         if (rc != MDPF_OK) return rc;
     }
     launch_kinetic(c, s);
@@ -539,6 +569,13 @@ static int enqueue_steps(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     cudaEvent_t ps = prof_begin(c, s);
     for (int64_t k = 0; k < n_steps; ++k) {
         const bool energy = (c->steps + k + 1) % c->energy_every == 0;
+        if (c->mode == MDPF_MODE_CALLBACK) {
+            launch_kick_drift(c, s);   // also zeroes the force and energy sums
+            const int rc = enqueue_provider(c, c->d_x, c->d_fx, c->d_efx, c->d_status, false, s);
+            if (rc != MDPF_OK) return rc;
+            launch_kick_finish(c, energy, s);
+            continue;
+        }
         if (c->mode == MDPF_MODE_LEARNED) {
             cudaGraphExec_t ex = c->profiling ? nullptr : learned_step_graph(c, energy);
             if (ex != nullptr) {

@@ -26,6 +26,7 @@ constexpr int kPad = 64;           // atoms are padded to a multiple of 64 (two 
 constexpr int kMaxExclPerAtom = 255;
 
 // Energy slot layout (int64 fixed point): bond, angle, LJ, Coulomb, kinetic, learned.
+// E_LEARN holds the learned model's energy, or the external provider's in callback mode.
 enum { E_BOND = 0, E_ANGLE = 1, E_LJ = 2, E_COUL = 3, E_KIN = 4, E_LEARN = 5, E_SLOTS = 8 };
 
 __host__ __device__ inline int64_t tile_pair_index(int I, int J, int T) {
@@ -120,6 +121,12 @@ struct mdpf_ctx {
     int *d_touch_off = nullptr, *d_touch = nullptr;  // other tiles touched by those terms
     int step_grid = 0;                     // blocks of the persistent stepper
 
+    // callback mode: the caller's force provider and its device buffers
+    mdpf_force_fn prov_fn = nullptr;
+    void *prov_user = nullptr;
+    double *prov_pos = nullptr, *prov_energy = nullptr;
+    float *prov_forces = nullptr;
+
     // learned mode (learned_host.cu)
     void *learned = nullptr;               // mdpf::LearnedHost
     cudaGraphExec_t lgraph[2] = {nullptr, nullptr};   // learned step as a graph: [0] plain step, [1] energy step
@@ -171,6 +178,8 @@ void launch_energy_out(const unsigned long long *efx, double *out6, cudaStream_t
 void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s);
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s);
 void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s);
+void launch_provider_to_fx(const float *forces, const double *energy, int n, unsigned long long *fx,
+                           unsigned long long *efx, uint32_t *status, cudaStream_t s);
 void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s);
 
 // learned_host.cu

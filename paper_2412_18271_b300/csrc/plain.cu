@@ -48,6 +48,22 @@ __global__ void k_energy_out(const unsigned long long *efx, double *out) {
                  fx_val(efx[E_LEARN]);
 }
 
+// An external provider's FP32 forces and FP64 energy into the fixed-point sums.
+__global__ void k_provider_to_fx(const float *forces, const double *energy, int n, unsigned long long *fx,
+                                 unsigned long long *efx, uint32_t *status) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < 3 * n) {
+        const float f = forces[q];
+        if (!isfinite(f)) atomicOr(status, MDPF_STATUS_NONFINITE);
+        fx_add(&fx[q], f);
+    }
+    if (q == 0) {
+        const double e = *energy;
+        if (!isfinite(e) || fabs(e) > 1e9) atomicOr(status, MDPF_STATUS_NONFINITE);
+        else fx_add_d(&efx[E_LEARN], e);
+    }
+}
+
 // ------------------------------------------------------------------ bonded
 
 __global__ void k_bonded(PlainDev p, unsigned long long *fx, unsigned long long *efx) {
@@ -283,6 +299,11 @@ void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s) {
 }
 
 // Kinetic energy of the current velocities into efx[E_KIN] (no kick).
+void launch_provider_to_fx(const float *forces, const double *energy, int n, unsigned long long *fx,
+                           unsigned long long *efx, uint32_t *status, cudaStream_t s) {
+    k_provider_to_fx<<<(3 * n + 255) / 256, 256, 0, s>>>(forces, energy, n, fx, efx, status);
+}
+
 void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s) {
     k_kick<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(ctx->n, ctx->d_hdt_m, ctx->d_mass,
                                                                               ctx->d_v, ctx->d_fx, ctx->d_efx, 0, 1);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmdpf.so")
 MDPF_OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NEIGHBOR_OVERFLOW", -5: "NONFINITE", -6: "TIMEOUT",
-    -7: "OUT_OF_RANGE", -8: "UNSUPPORTED",
+    -7: "OUT_OF_RANGE", -8: "UNSUPPORTED", -9: "CALLBACK",
 }
 MDPF_STATUS_NONFINITE = 0x1
 MDPF_STATUS_NEIGHBOR_OVERFLOW = 0x2
@@ -25,6 +25,8 @@ MDPF_STATUS_TIMEOUT = 0x4
 MDPF_STATUS_OUT_OF_RANGE = 0x8
 MDPF_MODE_PLAIN = 0
 MDPF_MODE_LEARNED = 1
+MDPF_MODE_CALLBACK = 2
+FORCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 MDPF_PROF_NONBONDED = 0
 MDPF_PROF_STEPPER = 1
 MDPF_PROF_STEP = 2
@@ -66,6 +68,8 @@ class mdpf_params(ctypes.Structure):
         ("record_every", _i32), ("max_frames", _i32), ("stepper", _i32), ("energy_every", _i32),
         ("model", _vp), ("model_bytes", ctypes.c_uint64), ("skin", _f64), ("rebuild_every", _i32),
         ("fallback", _i32), ("mlp_kernel", _i32),
+        ("provider", _vp), ("provider_user", _vp), ("provider_pos", _vp), ("provider_energy", _vp),
+        ("provider_forces", _vp),
     ]
 
 
@@ -150,8 +154,16 @@ class Context:
                  trace_capacity: int = 0, record_every: int = 0, max_frames: int = 0,
                  stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1, model: bytes | None = None,
                  skin: float = 0.0, rebuild_every: int = 0, fallback: bool = True,
-                 mlp_kernel: int = MDPF_MLP_TENSOR):
-        """mode MDPF_MODE_LEARNED needs ``model`` (a packed model blob, see model.Model.pack)."""
+                 mlp_kernel: int = MDPF_MLP_TENSOR, provider=None, provider_kind: str = "energy_forces"):
+        """mode MDPF_MODE_LEARNED needs ``model`` (a packed model blob, see model.Model.pack).
+
+        mode MDPF_MODE_CALLBACK needs ``provider``, a Python callable the library calls for every
+        force evaluation with the positions as a CUDA float64 tensor [N, 3] (A):
+          provider_kind "energy_forces": provider(pos) -> (energy, forces[N, 3]) (kcal/mol, kcal/mol/A);
+          provider_kind "energy":        provider(pos) -> energy (a differentiable torch scalar); the
+                                         forces are -d energy / d pos by torch autograd.
+        Its work runs on the library's stream (torch's current stream inside the call).
+        """
         L = lib()
         s = system
         self.n = int(s.element.shape[0])
@@ -195,6 +207,8 @@ class Context:
         p.rebuild_every = rebuild_every
         p.fallback = 1 if fallback else 0
         p.mlp_kernel = mlp_kernel
+        if mode == MDPF_MODE_CALLBACK:
+            self._setup_provider(p, provider, provider_kind)
         h = _vp()
         rc = L.mdpf_create(ctypes.byref(t), ctypes.byref(p), ctypes.byref(h))
         if rc != MDPF_OK:
@@ -203,6 +217,47 @@ class Context:
         self.dt_fs = dt_fs
         self.record_every = record_every
         self.max_frames = max_frames
+
+    # -- external force provider
+    def _setup_provider(self, p, provider, kind):
+        import torch
+        if provider is None or kind not in ("energy", "energy_forces"):
+            raise ValueError("callback mode needs provider= and provider_kind 'energy' or 'energy_forces'")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self._prov_pos = torch.zeros((self.n, 3), dtype=torch.float64, device=dev)
+        self._prov_energy = torch.zeros(1, dtype=torch.float64, device=dev)
+        self._prov_forces = torch.zeros((self.n, 3), dtype=torch.float32, device=dev)
+        self._prov_error = None
+
+        def call(user, stream):
+            try:
+                with torch.cuda.stream(torch.cuda.ExternalStream(stream)):
+                    if kind == "energy":
+                        with torch.enable_grad():
+                            x = self._prov_pos.detach().clone().requires_grad_(True)
+                            e = provider(x)
+                            (g,) = torch.autograd.grad(e, x)
+                        self._prov_forces.copy_(-g)
+                    else:
+                        e, f = provider(self._prov_pos)
+                        self._prov_forces.copy_(f)
+                    self._prov_energy.copy_(torch.as_tensor(e, dtype=torch.float64, device=dev).detach().reshape(1))
+                return 0
+            except Exception as exc:   # reported to the caller as MdpfError CALLBACK
+                self._prov_error = exc
+                return 1
+
+        self._prov_fn = FORCE_FN(call)   # kept alive with the context
+        p.provider = ctypes.cast(self._prov_fn, _vp)
+        p.provider_user = None
+        p.provider_pos = self._prov_pos.data_ptr()
+        p.provider_energy = self._prov_energy.data_ptr()
+        p.provider_forces = self._prov_forces.data_ptr()
+
+    @property
+    def provider_error(self):
+        """The exception the provider raised in the last failed call, if any."""
+        return getattr(self, "_prov_error", None)
 
     # -- lifetime
     def close(self):
@@ -224,7 +279,12 @@ class Context:
 
     def _check(self, rc):
         if rc != MDPF_OK:
-            raise MdpfError(rc, lib().mdpf_last_error(self._h).decode())
+            err = MdpfError(rc, lib().mdpf_last_error(self._h).decode())
+            cause = getattr(self, "_prov_error", None) if rc == -9 else None
+            if cause is not None:
+                self._prov_error = None
+                raise err from cause
+            raise err
 
     @property
     def handle(self):

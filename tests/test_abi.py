@@ -61,7 +61,7 @@ def _topo(n=3):
 
 @pytest.mark.parametrize("case", ["null_out", "zero_atoms", "bad_dt", "bad_mode", "bad_bond", "bad_mass",
                                   "bad_stepper", "bad_record_every", "learned_no_model", "learned_bad_magic",
-                                  "learned_short", "learned_bad_alpha", "learned_bad_skin"])
+                                  "learned_short", "learned_bad_alpha", "learned_bad_skin", "callback_no_provider"])
 def test_create_rejects_bad_arguments_without_gpu(lib, case):
     t, keep = _topo()
     p = mdpf.mdpf_params()
@@ -98,6 +98,8 @@ def test_create_rejects_bad_arguments_without_gpu(lib, case):
     elif case == "learned_bad_skin":
         p.mode = mdpf.MDPF_MODE_LEARNED
         p.skin = -1.0
+    elif case == "callback_no_provider":
+        p.mode = mdpf.MDPF_MODE_CALLBACK
     elif case == "bad_bond":
         b = np.array([[0, 5]], dtype=np.int32)
         r = np.array([1.0])
