@@ -409,6 +409,25 @@ def provider_leg(args, dev, stream):
     plain.close()
     out["provider_overhead_us_per_md_step"] = (out["python_provider"]["us_per_md_step"] -
                                                out["kernel_sequence"]["us_per_md_step"])
+    # an ethanol-sized molecule (9 atoms) on the learned path: the per-step latency floor of the
+    # graph-launched learned step
+    blob, _ = learned_model()
+    t9 = synth.molecule(9, seed=9)
+    ctx = mdpf.Context(t9, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, energy_every=10,
+                       trace_capacity=1000)
+    ctx.set_state(t9.pos, synth.velocities(t9.mass, t9.pos, 300.0, seed=9))
+    with torch.cuda.stream(stream):
+        ctx.step_async(100, stream.cuda_stream)
+        stream.synchronize()
+        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0_.record(stream)
+        ctx.step_async(1000, stream.cuda_stream)
+        e1_.record(stream)
+        stream.synchronize()
+    ms = e0_.elapsed_time(e1_)
+    out["learned_9_atoms"] = {"value": 1000 / (ms / 1000.0), "unit": UNIT, "us_per_md_step": ms,
+                              "what": "9-atom seeded molecule, learned potential, one graph launch per MD step"}
+    ctx.close()
     out["workload"] = "64-atom molecule, plain force field (the provider wraps the library's own force field)"
     return out
 
