@@ -156,6 +156,15 @@ typedef struct mdpf_params {
                                 MDPF_MLP_SIMT_FP32 (2): CUDA cores with FP32 operands (no BF16
                                 rounding of features, activations or deltas), so the forces are
                                 the gradient of the evaluated energy to FP32 rounding. */
+    /* integrator: MDPF_INTEGRATOR_VERLET (0, NVE) or MDPF_INTEGRATOR_LANGEVIN (1): BAOAB
+     *   v += dt/2 a;  x += dt/2 v;  v = c1 v + c2 R;  x += dt/2 v;  F = F(x);  v += dt/2 a
+     * with c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kB T / m) and R three normals per atom and step
+     * from Philox4x32-10 (counter: atom, step index, tag; key: seed) by Box-Muller.  Langevin runs
+     * the per-step kernel sequence (the persistent stepper is velocity Verlet only). */
+    int32_t integrator;
+    double friction_per_ps;   /* gamma in 1/ps (> 0 for Langevin) */
+    double temperature_K;     /* bath temperature */
+    uint64_t seed;            /* noise stream */
     /* callback mode only */
     mdpf_force_fn provider;
     void *provider_user;
@@ -163,6 +172,8 @@ typedef struct mdpf_params {
     double *provider_energy;  /* device, 1 FP64, written by the provider */
     float *provider_forces;   /* device [N][3] FP32, written by the provider */
 } mdpf_params;
+#define MDPF_INTEGRATOR_VERLET 0
+#define MDPF_INTEGRATOR_LANGEVIN 1
 #define MDPF_MLP_TENSOR 0
 #define MDPF_MLP_SIMT 1
 #define MDPF_MLP_SIMT_FP32 2

@@ -605,3 +605,88 @@ void orc_mlp_param_grad(const orc_mlp *M, int32_t n, const int32_t *el, const do
     free(h1); free(a1); free(t1); free(ta1); free(h2); free(a2); free(t2); free(ta2);
     free(bt2); free(bh2); free(bt1); free(bh1); free(bta1); free(ba1);
 }
+
+/* ---------------------------------------------------------------- Langevin dynamics */
+
+/*
+ * Philox4x32-10 counter-based generator (Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of
+ *   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+ * with M0 = 0xD2511F53, M1 = 0xCD9E8D57, the key advanced by the Weyl
+ * constants (0x9E3779B9, 0xBB67AE85) before every round after the first.
+ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c[0] = hi1 ^ c[1] ^ k0;
+        c[1] = lo1;
+        c[2] = hi0 ^ c[3] ^ k1;
+        c[3] = lo0;
+    }
+    for (int q = 0; q < 4; ++q) out[q] = c[q];
+}
+
+/*
+ * Three standard normal deviates for atom `atom` at step `step`: Philox with
+ * counter (atom, step low word, step high word, 0x4C414E47) and key (seed low,
+ * seed high); uniforms u = (x + 1/2) 2^-32; Box-Muller on (u0, u1) and (u2, u3).
+ */
+void orc_langevin_normals(uint64_t seed, int64_t step, int32_t atom, double z[3]) {
+    const uint32_t ctr[4] = {(uint32_t)atom, (uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), 0x4C414E47u};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    double u[4];
+    for (int q = 0; q < 4; ++q) u[q] = ((double)x[q] + 0.5) * (1.0 / 4294967296.0);
+    const double two_pi = 6.283185307179586476925286766559;
+    const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+    z[0] = r0 * cos(two_pi * u[1]);
+    z[1] = r0 * sin(two_pi * u[1]);
+    z[2] = r1 * cos(two_pi * u[3]);
+}
+
+/*
+ * Langevin dynamics, BAOAB splitting (Leimkuhler and Matthews 2013), n_steps of
+ * dt fs from step index step0, in place on x and v:
+ *   v <- v + dt/2 a(x);  x <- x + dt/2 v;
+ *   v <- c1 v + c2 R,  c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kB T / m)  (R from orc_langevin_normals);
+ *   x <- x + dt/2 v;  v <- v + dt/2 a(x).
+ * gamma in 1/ps, T in K; U[s], K[s] after step s+1.
+ */
+void orc_langevin_run(const orc_system *s, double dt, int32_t n_steps, double gamma_ps, double temp_K,
+                      uint64_t seed, int64_t step0, double *x, double *v, double *U, double *K) {
+    const int n = s->n;
+    const double kB = 0.0019872041;  /* kcal/mol/K */
+    const double c1 = exp(-gamma_ps * 1e-3 * dt);
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    orc_plain_energy_forces(s, x, f, NULL);
+    for (int st = 0; st < n_steps; ++st) {
+        for (int i = 0; i < n; ++i) {
+            const double c2 = sqrt((1.0 - c1 * c1) * kB * temp_K * ORC_ACC / s->mass[i]);
+            double z[3];
+            orc_langevin_normals(seed, step0 + st, i, z);
+            for (int c = 0; c < 3; ++c) {
+                double vc = v[3 * i + c] + 0.5 * dt * ORC_ACC * f[3 * i + c] / s->mass[i];
+                double xc = x[3 * i + c] + 0.5 * dt * vc;
+                vc = c1 * vc + c2 * z[c];
+                x[3 * i + c] = xc + 0.5 * dt * vc;
+                v[3 * i + c] = vc;
+            }
+        }
+        double u = orc_plain_energy_forces(s, x, f, NULL);
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * dt * ORC_ACC * f[3 * i + c] / s->mass[i];
+        if (U) U[st] = u;
+        if (K) K[st] = orc_kinetic(n, s->mass, v);
+    }
+    free(f);
+}

@@ -149,6 +149,20 @@ class Plain:
         v = np.ascontiguousarray(vel, dtype=np.float64)
         return lib().orc_kinetic(self.n, _p(self.mass), _p(v))
 
+    def langevin(self, pos, vel, dt: float, n_steps: int, gamma_ps: float, temp_K: float, seed: int,
+                 step0: int = 0):
+        """BAOAB Langevin dynamics with Philox normals; returns (x, v, U[n_steps], K[n_steps])."""
+        L = lib()
+        L.orc_langevin_run.restype = None
+        x = np.array(pos, dtype=np.float64, copy=True).reshape(self.n, 3)
+        v = np.array(vel, dtype=np.float64, copy=True).reshape(self.n, 3)
+        U = np.zeros(max(n_steps, 1))
+        K = np.zeros(max(n_steps, 1))
+        L.orc_langevin_run(ctypes.byref(self._st), ctypes.c_double(dt), n_steps, ctypes.c_double(gamma_ps),
+                           ctypes.c_double(temp_K), ctypes.c_uint64(seed), ctypes.c_int64(step0), _p(x), _p(v),
+                           _p(U), _p(K))
+        return x, v, U[:n_steps], K[:n_steps]
+
     def vv(self, pos, vel, dt: float, n_steps: int):
         """Velocity Verlet; returns (x, v, U[n_steps], K[n_steps], F at final x)."""
         x = np.array(pos, dtype=np.float64, copy=True).reshape(self.n, 3)
@@ -339,3 +353,20 @@ def adamw_step(theta, grad, m, v, t: int, lr: float, betas=(0.9, 0.999), eps=1e-
     vh = v / (1.0 - b2 ** t)
     theta -= lr * (mh / (np.sqrt(vh) + eps) + wd * theta)
     return theta
+
+
+# ---------------------------------------------------------------- counter-based normals
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of counter (4 x uint32) and key (2 x uint32) -> 4 x uint32."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    out = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, out)
+    return [int(v) for v in out]
+
+
+def langevin_normals(seed: int, step: int, atom: int):
+    z = (ctypes.c_double * 3)()
+    lib().orc_langevin_normals(ctypes.c_uint64(seed), ctypes.c_int64(step), ctypes.c_int32(atom), z)
+    return np.array(list(z))

@@ -99,7 +99,8 @@ static void free_ctx(mdpf_ctx *c) {
                     c->d_tile_mask, c->d_tile_flag, c->d_items, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
                     c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_step, c->d_status,
                     c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e, c->d_tile_cnt,
-                    c->d_tile_expect, c->d_own_off, c->d_own, c->d_touch_off, c->d_touch, c->frames.pos, c->frames.energy, c->frames.forces,
+                    c->d_tile_expect, c->d_own_off, c->d_own, c->d_touch_off, c->d_touch, c->d_lang_c2, c->frames.pos,
+                    c->frames.energy, c->frames.forces,
                     c->frames.step};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -130,6 +131,12 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "bad bond arrays");
     if (prm->mode != MDPF_MODE_PLAIN && prm->mode != MDPF_MODE_LEARNED && prm->mode != MDPF_MODE_CALLBACK)
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "unknown mode");
+    if (prm->integrator != MDPF_INTEGRATOR_VERLET && prm->integrator != MDPF_INTEGRATOR_LANGEVIN)
+        return fail(nullptr, MDPF_ERR_INVALID_ARG, "unknown integrator");
+    if (prm->integrator == MDPF_INTEGRATOR_LANGEVIN &&
+        (!(prm->friction_per_ps > 0.0) || !std::isfinite(prm->friction_per_ps) || !(prm->temperature_K >= 0.0) ||
+         !std::isfinite(prm->temperature_K)))
+        return fail(nullptr, MDPF_ERR_INVALID_ARG, "Langevin needs friction_per_ps > 0 and temperature_K >= 0");
     if (prm->mode == MDPF_MODE_CALLBACK &&
         (!prm->provider || !prm->provider_pos || !prm->provider_energy || !prm->provider_forces))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "callback mode needs the provider function and its three buffers");
@@ -187,8 +194,9 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     c->trace_cap = prm->trace_capacity > 0 ? prm->trace_capacity : 4096;
     c->record_every = prm->record_every;
     c->max_frames = prm->max_frames;
-    // learned and callback modes always step with the per-step kernel sequence
-    c->stepper = prm->mode == MDPF_MODE_PLAIN ? prm->stepper : MDPF_STEPPER_KERNELS;
+    // learned and callback modes, and Langevin dynamics, always step with the per-step kernel sequence
+    c->stepper = prm->mode == MDPF_MODE_PLAIN && prm->integrator == MDPF_INTEGRATOR_VERLET ? prm->stepper
+                                                                                          : MDPF_STEPPER_KERNELS;
     if (prm->mode == MDPF_MODE_CALLBACK) {
         c->prov_fn = prm->provider;
         c->prov_user = prm->provider_user;
@@ -251,6 +259,16 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     CKC(dalloc(&c->d_element, n));
     CKC(dalloc(&c->d_mass, n));
     CKC(dalloc(&c->d_hdt_m, n));
+    if (prm->integrator == MDPF_INTEGRATOR_LANGEVIN) {
+        const double kB = 0.0019872041;   // kcal/mol/K
+        c->lang_c1 = std::exp(-prm->friction_per_ps * 1e-3 * c->dt);
+        c->lang_seed = prm->seed;
+        std::vector<double> c2(n);
+        for (int i = 0; i < n; ++i)
+            c2[i] = std::sqrt((1.0 - c->lang_c1 * c->lang_c1) * kB * prm->temperature_K * kAcc / t->mass[i]);
+        CKC(dalloc(&c->d_lang_c2, n));
+        CKC(cudaMemcpy(c->d_lang_c2, c2.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    }
     CKC(dalloc(&c->d_pos4, np));
     CKC(dalloc(&c->d_pos4_c, np));
     CKC(dalloc(&c->d_lj, np));

@@ -52,6 +52,14 @@ struct PlainDev {
     const unsigned int *gate;   // if set, the kernels run only when *gate != 0 (learned-mode fallback)
 };
 
+// Langevin (BAOAB) parameters for the kick-drift kernel; c2 == null: velocity Verlet.
+struct LangevinDev {
+    const double *c2;        // [n] sqrt((1 - c1^2) kB T / m) in A/fs
+    double c1;               // exp(-gamma dt)
+    unsigned long long seed;
+    const int64_t *step;     // completed steps (the noise counter)
+};
+
 struct Frames {
     double *pos;      // [cap][n][3]
     double *energy;   // [cap]
@@ -120,6 +128,11 @@ struct mdpf_ctx {
     int *d_own_off = nullptr, *d_own = nullptr;      // bonded terms owned by each tile
     int *d_touch_off = nullptr, *d_touch = nullptr;  // other tiles touched by those terms
     int step_grid = 0;                     // blocks of the persistent stepper
+
+    // Langevin (BAOAB) integrator: per-atom noise amplitude, damping factor, seed
+    double *d_lang_c2 = nullptr;
+    double lang_c1 = 1.0;
+    unsigned long long lang_seed = 0;
 
     // callback mode: the caller's force provider and its device buffers
     mdpf_force_fn prov_fn = nullptr;

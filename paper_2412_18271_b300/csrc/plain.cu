@@ -110,9 +110,43 @@ __global__ void __launch_bounds__(kNbThreads, 2) k_nonbonded(PlainDev p, unsigne
 
 // ------------------------------------------------------------------ integrator
 
-// v += dt/2 a(F);  x += dt v;  refresh the FP32 copy; clear the force accumulators.
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor round
+// with the Weyl-advanced key.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned int lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned int lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Langevin O step (BAOAB): atom a, step index `step`: three Box-Muller normals
+// from Philox with counter (a, step low, step high, tag) and key = seed.
+__device__ __forceinline__ void langevin_normals(unsigned long long seed, long long step, int a, double z[3]) {
+    const uint4 r = philox4x32_10(make_uint4((unsigned int)a, (unsigned int)(unsigned long long)step,
+                                             (unsigned int)((unsigned long long)step >> 32), 0x4C414E47u),
+                                  make_uint2((unsigned int)seed, (unsigned int)(seed >> 32)));
+    const double inv = 1.0 / 4294967296.0, two_pi = 6.283185307179586476925286766559;
+    const double u0 = ((double)r.x + 0.5) * inv, u1 = ((double)r.y + 0.5) * inv;
+    const double u2 = ((double)r.z + 0.5) * inv, u3 = ((double)r.w + 0.5) * inv;
+    const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+    z[0] = r0 * cos(two_pi * u1);
+    z[1] = r0 * sin(two_pi * u1);
+    z[2] = r1 * cos(two_pi * u3);
+}
+
+// Velocity Verlet:  v += dt/2 a(F);  x += dt v.
+// Langevin (lang != null), BAOAB:  v += dt/2 a(F);  x += dt/2 v;  v = c1 v + c2 R;  x += dt/2 v.
+// Then the FP32 copy is refreshed and the force accumulators cleared.
 __global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over_m, double *x, double *v,
-                             unsigned long long *fx, float4 *pos4, const float *qs, unsigned long long *efx) {
+                             unsigned long long *fx, float4 *pos4, const float *qs, unsigned long long *efx,
+                             LangevinDev lang) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < E_SLOTS && efx != nullptr) efx[a] = 0ull;
     if (a >= n) {
@@ -124,14 +158,31 @@ __global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over
     }
     const double h = hdt_over_m[a];
     double p[3];
+    if (lang.c2 != nullptr) {
+        double z[3];
+        langevin_normals(lang.seed, *lang.step, a, z);
+        const double c2 = lang.c2[a], hdt = 0.5 * dt;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double vc = fma(h, fx_val(fx[3 * a + c]), v[3 * a + c]);
-        double xc = fma(dt, vc, x[3 * a + c]);
-        v[3 * a + c] = vc;
-        x[3 * a + c] = xc;
-        p[c] = xc;
-        fx[3 * a + c] = 0ull;
+        for (int c = 0; c < 3; ++c) {
+            double vc = fma(h, fx_val(fx[3 * a + c]), v[3 * a + c]);
+            double xc = fma(hdt, vc, x[3 * a + c]);
+            vc = fma(lang.c1, vc, c2 * z[c]);
+            xc = fma(hdt, vc, xc);
+            v[3 * a + c] = vc;
+            x[3 * a + c] = xc;
+            p[c] = xc;
+            fx[3 * a + c] = 0ull;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double vc = fma(h, fx_val(fx[3 * a + c]), v[3 * a + c]);
+            double xc = fma(dt, vc, x[3 * a + c]);
+            v[3 * a + c] = vc;
+            x[3 * a + c] = xc;
+            p[c] = xc;
+            fx[3 * a + c] = 0ull;
+        }
     }
     pos4[a] = make_float4((float)p[0], (float)p[1], (float)p[2], qs[a]);
 }
@@ -284,7 +335,7 @@ void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s) {
     int m = ctx->n_pad > E_SLOTS ? ctx->n_pad : E_SLOTS;
     k_kick_drift<<<(m + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(
         ctx->n, ctx->n_pad, ctx->dt, ctx->d_hdt_m, ctx->d_x, ctx->d_v, ctx->d_fx, ctx->d_pos4, ctx->d_charge_s,
-        ctx->d_efx);
+        ctx->d_efx, LangevinDev{ctx->d_lang_c2, ctx->lang_c1, ctx->lang_seed, ctx->d_step});
 }
 
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s) {

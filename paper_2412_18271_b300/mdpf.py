@@ -36,6 +36,8 @@ MDPF_PROF_LEARN_MLP = 5
 MDPF_PROF_LEARN_ADJOINT = 6
 MDPF_STEPPER_PERSISTENT = 0
 MDPF_STEPPER_KERNELS = 1
+MDPF_INTEGRATOR_VERLET = 0
+MDPF_INTEGRATOR_LANGEVIN = 1
 MDPF_MLP_TENSOR = 0
 MDPF_MLP_SIMT = 1
 MDPF_MLP_SIMT_FP32 = 2
@@ -68,6 +70,7 @@ class mdpf_params(ctypes.Structure):
         ("record_every", _i32), ("max_frames", _i32), ("stepper", _i32), ("energy_every", _i32),
         ("model", _vp), ("model_bytes", ctypes.c_uint64), ("skin", _f64), ("rebuild_every", _i32),
         ("fallback", _i32), ("mlp_kernel", _i32),
+        ("integrator", _i32), ("friction_per_ps", _f64), ("temperature_K", _f64), ("seed", ctypes.c_uint64),
         ("provider", _vp), ("provider_user", _vp), ("provider_pos", _vp), ("provider_energy", _vp),
         ("provider_forces", _vp),
     ]
@@ -154,7 +157,8 @@ class Context:
                  trace_capacity: int = 0, record_every: int = 0, max_frames: int = 0,
                  stepper: int = MDPF_STEPPER_PERSISTENT, energy_every: int = 1, model: bytes | None = None,
                  skin: float = 0.0, rebuild_every: int = 0, fallback: bool = True,
-                 mlp_kernel: int = MDPF_MLP_TENSOR, provider=None, provider_kind: str = "energy_forces"):
+                 mlp_kernel: int = MDPF_MLP_TENSOR, provider=None, provider_kind: str = "energy_forces",
+                 friction_per_ps: float = 0.0, temperature_K: float = 300.0, seed: int = 0):
         """mode MDPF_MODE_LEARNED needs ``model`` (a packed model blob, see model.Model.pack).
 
         mode MDPF_MODE_CALLBACK needs ``provider``, a Python callable the library calls for every
@@ -207,6 +211,11 @@ class Context:
         p.rebuild_every = rebuild_every
         p.fallback = 1 if fallback else 0
         p.mlp_kernel = mlp_kernel
+        if friction_per_ps > 0.0:   # Langevin (BAOAB); zero friction keeps velocity Verlet
+            p.integrator = MDPF_INTEGRATOR_LANGEVIN
+            p.friction_per_ps = friction_per_ps
+            p.temperature_K = temperature_K
+            p.seed = seed
         if mode == MDPF_MODE_CALLBACK:
             self._setup_provider(p, provider, provider_kind)
         h = _vp()
