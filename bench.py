@@ -40,6 +40,10 @@ DT_FS = 0.5
 FLOPS_PER_PAIR = 35          # algorithmic FP32 flops per pair (forces only), FMA counted as 2
 FLOPS_PER_PAIR_ENERGY = 3    # extra flops per pair on energy steps
 RECORD_EVERY = 10            # frames and energies every 10 steps (the workload's recording cadence)
+# DRAM bytes (read + write) per launch of k_plain_persistent from the ncu capture in
+# profiles/k_plain_persistent_cluster2048.md: the L2-resident working set read once from a cold L2
+# (the bench flushes L2 between launches), independent of the MD steps per launch
+PLAIN_TRAFFIC = 456448
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -56,7 +60,7 @@ ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 # DRAM bytes (read + write) per launch of each learned kernel on this workload, from the ncu capture in
 # profiles/learned_step_cluster16384.md (valid for the kernels as captured there)
-LEARNED_TRAFFIC = {"adjoint": 28266240, "features": 2696960, "mlp": 15011840}
+LEARNED_TRAFFIC = {"adjoint": 28260864, "features": 2702080, "mlp": 15012864}
 
 
 def peaks():
@@ -534,7 +538,7 @@ def run_ours(args):
                      "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (%s max clock)"
                                   % (N_SM, FP32_LANES_PER_SM, mhz, pk_kind),
                      "flops_per_launch": per_launch_flops, "avg_launch_us": avg_launch_s * 1e6,
-                     "launches": st_n, "traffic": None},
+                     "launches": st_n, "traffic": PLAIN_TRAFFIC},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
                 "d2h_bytes_per_step": 2 * n * 3 * 8 + 48},
         "gpu_launches": args.steps,
