@@ -271,6 +271,7 @@ def learned_leg(args, dev, stream, flush):
                 evs[k][1].record(stream)
             torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in evs)
+        x_end, _ = ctx.get_state()
         # per-stage durations: the same steps again with CUDA events around every stage on the
         # launch stream (profiling launches each step kernel by kernel instead of as one graph)
         ctx.set_profiling(True)
@@ -302,6 +303,7 @@ def learned_leg(args, dev, stream, flush):
         ctx.counters()
     e2e_rate = e2e_steps * md / (time.perf_counter() - t0)
     ctx.close()
+    fused = fused_arm(args, s, v0, blob, stream, flush, x_end)
 
     # the plain force field on the same cluster (all pairs, persistent stepper), for the comparison
     plain_md = max(10, md // 4)
@@ -369,7 +371,59 @@ def learned_leg(args, dev, stream, flush):
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
                 "d2h_bytes_per_step": 2 * n * 3 * 8 + 48},
         "clocks": clk.summary(),
+        "fused": dict(fused, vs_stagewise=fused["value"] / rate,
+                      fused_kernel_over_stages=fused["fused_kernel_us"] / 1e3 /
+                      sum(prof[k][0] / max(prof[k][1], 1) for k in ("features", "mlp", "adjoint"))),
     }
+
+
+def fused_arm(args, s, v0, blob, stream, flush, x_ref):
+    """The same learned MD, timed the same way, with the fused features -> MLP -> adjoint kernel
+    (MDPF_MLP_FUSED: one kernel per force evaluation, features and dE/dG kept on chip)."""
+    import numpy as np
+    import torch
+    from paper_2412_18271_b300 import mdpf
+    md = args.learned_md_steps
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, trace_capacity=md,
+                       energy_every=RECORD_EVERY, record_every=RECORD_EVERY, max_frames=max(1, md // RECORD_EVERY),
+                       mlp_kernel=mdpf.MDPF_MLP_FUSED)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            stream.synchronize()
+            ctx.set_state(s.pos, v0)
+            ctx.step_async(md, stream.cuda_stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            stream.synchronize()
+            ctx.set_state(s.pos, v0)
+            flush.zero_()
+            evs[k][0].record(stream)
+            ctx.step_async(md, stream.cuda_stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        x_end, _ = ctx.get_state()
+        ctx.set_profiling(True)
+        for k in range(args.steps):
+            stream.synchronize()
+            ctx.set_state(s.pos, v0)
+            flush.zero_()
+            ctx.step_async(md, stream.cuda_stream)
+        torch.cuda.synchronize()
+    f_ms, f_n = ctx.profile(mdpf.MDPF_PROF_LEARN_FUSED)
+    nb_ms, nb_n = ctx.profile(mdpf.MDPF_PROF_LEARN_NEIGHBORS)
+    ctx.set_profiling(False)
+    if ctx.counters()["status"] != 0:
+        raise RuntimeError("device status after the fused learned run")
+    ctx.close()
+    rate = args.steps * md / (ms / 1000.0)
+    return {"value": rate, "unit": UNIT, "ms_per_md_step": ms / args.steps / md,
+            "fused_kernel_us": 1e3 * f_ms / max(f_n, 1), "fused_launches": f_n,
+            "neighbors_us": 1e3 * nb_ms / max(nb_n, 1),
+            "same_trajectory_as_stagewise": bool(np.array_equal(x_end, x_ref)),
+            "what": "features, tensor-core MLP and adjoint in one kernel per force evaluation (one CTA per tile "
+                    "of <= 128 atoms of one element, tiles balanced over the SMs); no [N,384] array in HBM"}
 
 
 def provider_leg(args, dev, stream):

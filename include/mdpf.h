@@ -155,7 +155,11 @@ typedef struct mdpf_params {
                                 GEMM inputs, FP32 accumulation); sums differ in order only.
                                 MDPF_MLP_SIMT_FP32 (2): CUDA cores with FP32 operands (no BF16
                                 rounding of features, activations or deltas), so the forces are
-                                the gradient of the evaluated energy to FP32 rounding. */
+                                the gradient of the evaluated energy to FP32 rounding.
+                                MDPF_MLP_FUSED (3): features, tensor-core MLP and force adjoint
+                                in one kernel, one CTA per tile of at most 128 atoms of one
+                                element; the features and dE/dG stay on chip.  Same arithmetic
+                                as MDPF_MLP_TENSOR: identical energies and forces. */
     /* integrator: MDPF_INTEGRATOR_VERLET (0, NVE) or MDPF_INTEGRATOR_LANGEVIN (1): BAOAB
      *   v += dt/2 a;  x += dt/2 v;  v = c1 v + c2 R;  x += dt/2 v;  F = F(x);  v += dt/2 a
      * with c1 = exp(-gamma dt), c2 = sqrt((1 - c1^2) kB T / m) and R three normals per atom and step
@@ -177,6 +181,7 @@ typedef struct mdpf_params {
 #define MDPF_MLP_TENSOR 0
 #define MDPF_MLP_SIMT 1
 #define MDPF_MLP_SIMT_FP32 2
+#define MDPF_MLP_FUSED 3
 
 /*
  * Learned mode (MDPF_MODE_LEARNED).  Per atom, 384 symmetry-function features
@@ -413,7 +418,8 @@ MDPF_API int mdpf_learned_jvp(mdpf_ctx *ctx, const double *pos, const float *v, 
  * the kernel-sequence stepper), MDPF_PROF_STEPPER (persistent step-loop
  * kernel), MDPF_PROF_STEP (one whole mdpf_step call on the device); learned
  * mode: MDPF_PROF_NONBONDED times the whole learned force evaluation, and
- * MDPF_PROF_LEARN_NEIGHBORS / _FEATURES / _MLP / _ADJOINT its stages.
+ * MDPF_PROF_LEARN_NEIGHBORS / _FEATURES / _MLP / _ADJOINT its stages, or
+ * MDPF_PROF_LEARN_FUSED the fused features-MLP-adjoint kernel.
  * mdpf_get_profile synchronises the recorded events and returns the summed
  * duration in ms and the number of launches since mdpf_set_profiling(ctx, 1).
  */
@@ -424,6 +430,7 @@ MDPF_API int mdpf_learned_jvp(mdpf_ctx *ctx, const double *pos, const float *v, 
 #define MDPF_PROF_LEARN_FEATURES 4
 #define MDPF_PROF_LEARN_MLP 5
 #define MDPF_PROF_LEARN_ADJOINT 6
+#define MDPF_PROF_LEARN_FUSED 7
 #define MDPF_PROF_SLOTS 8
 MDPF_API int mdpf_set_profiling(mdpf_ctx *ctx, int32_t enable);
 MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);

@@ -144,7 +144,7 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
                                            prm->rebuild_every < 0))
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "skin must be in [0, 10] and rebuild_every >= 0");
     if (prm->mode == MDPF_MODE_LEARNED && prm->mlp_kernel != MDPF_MLP_TENSOR && prm->mlp_kernel != MDPF_MLP_SIMT &&
-        prm->mlp_kernel != MDPF_MLP_SIMT_FP32)
+        prm->mlp_kernel != MDPF_MLP_SIMT_FP32 && prm->mlp_kernel != MDPF_MLP_FUSED)
         return fail(nullptr, MDPF_ERR_INVALID_ARG, "unknown mlp_kernel");
     if (prm->mode == MDPF_MODE_LEARNED) {
         std::string msg;

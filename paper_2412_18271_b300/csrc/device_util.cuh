@@ -32,6 +32,15 @@ __device__ __forceinline__ void fx_add_d(unsigned long long *p, double v) {
 }
 __device__ __forceinline__ double fx_val(unsigned long long u) { return (double)(long long)u * kFxInv; }
 
+// Per-lane values of a warp, each rounded to fixed point and then summed as
+// integers (exact, so the total does not depend on how values are grouped
+// into warps), added by lane 0.
+__device__ __forceinline__ void fx_warp_add_d(unsigned long long *p, double v) {
+    long long q = __double2ll_rn(v * 4294967296.0);
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if ((threadIdx.x & 31) == 0 && q != 0) atomicAdd(p, (unsigned long long)q);
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

@@ -1,41 +1,25 @@
 // Learned-potential kernels: cell-list neighbour build, symmetry-function
-// features, per-element MLP (forward and input gradient), feature adjoint.
+// features, per-element MLP (forward and input gradient), feature adjoint,
+// feature JVP.  The per-atom feature and adjoint arithmetic is in
+// learned_terms.cuh (shared with the fused tile kernel).
 //
-//   radial    G[i, 16 Zj + k]           = sum_j  exp(-16 (r_ij - R_k)^2) fc(r_ij; 5.2)
-//   angular   G[i, 64 + 32 P + 8 m + p] = sum_{j<k} 2^-31 (1 + cos(theta - theta_p))^32
-//                                         exp(-8 ((r_ij + r_ik)/2 - R_m)^2) fc(r_ij; 3.5) fc(r_ik; 3.5)
-//   theta = acos(0.95 cos theta_ijk), cos(theta - theta_p) = c cos theta_p + sqrt(1 - c^2) sin theta_p
 //   E_i = W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0,  celu(x) = max(x, 0.1 (exp(10 x) - 1))
 // Every accumulation that feeds a result is done in a fixed order per lane, and
 // forces are int64 fixed-point sums, so results are reproducible bit for bit.
 #include <cuda_bf16.h>
 
 #include "learned.cuh"
+#include "learned_terms.cuh"
 
 namespace mdpf {
 namespace {
 
-constexpr float kPi = 3.14159265358979f;
-constexpr float kEtaR = 16.f, kEtaA = 8.f;
-constexpr float kAngScale = 0.95f;
 constexpr float kCeluAlpha = 0.1f;
-constexpr float kTwoPowM31 = 4.656612873077393e-10f;  // 2^-31 = 2^(1 - zeta), zeta = 32
 
-__device__ __forceinline__ float fcut(float r, float rc) { return r < rc ? 0.5f * cosf(kPi * r / rc) + 0.5f : 0.f; }
-__device__ __forceinline__ float dfcut(float r, float rc) { return r < rc ? -0.5f * kPi / rc * sinf(kPi * r / rc) : 0.f; }
 // CELU(0.1) and its derivative, exp(10 x) from the fast exponential (as in the tensor-core MLP)
 __device__ __forceinline__ float celu(float x) { return x > 0.f ? x : kCeluAlpha * (__expf(10.f * x) - 1.f); }
 __device__ __forceinline__ float dcelu(float x) { return x >= 0.f ? 1.f : __expf(10.f * x); }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-__device__ __forceinline__ int pair_index(int a, int b) {
-    if (a > b) {
-        int t = a;
-        a = b;
-        b = t;
-    }
-    return (a == 0 ? 0 : (a == 1 ? 4 : (a == 2 ? 7 : 9))) + (b - a);
-}
 
 __device__ __forceinline__ unsigned int ord_f(float f) {
     unsigned int u = __float_as_uint(f);
@@ -265,189 +249,27 @@ __global__ void k_nb_disp(LearnedDev L, const float4 *pos4, const int64_t *step,
 
 constexpr int kFeatWarps = 4;
 
-struct NbrSmem {
-    int j[kKmax];
-    int el[kKmax];
-    float4 d[kKmax];      // unit vector from i to j (x, y, z) and r
-    float4 fc[kKmax];     // fc(r; 5.2), fc'(r; 5.2), fc(r; 3.5), fc'(r; 3.5)
-    int rad[kKmax];       // neighbours within the radial cutoff, in row order
-    int ang[kKmax];       // neighbours within the angular cutoff, in row order
-};
-
-// Load atom i's neighbours into shared memory; returns the row length and the
-// numbers of neighbours within the radial and angular cutoffs.  The compacted
-// in-cutoff lists do not depend on how far the list radius reaches beyond the
-// cutoffs, so neither does any summation order below.
-__device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
-                                                int &cnt, int &nr, int &na) {
-    const float4 pi = pos4[i];
-    cnt = L.nb_count[i];
-    for (int q = lane; q < cnt; q += 32) {
-        const int j = L.nb_idx[(size_t)i * kKmax + q];
-        const float4 pj = pos4[j];
-        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
-        s.j[q] = j;
-        s.el[q] = L.el[j];
-        s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
-        s.fc[q] = make_float4(fcut(r, kRcRad), dfcut(r, kRcRad), fcut(r, kRcAng), dfcut(r, kRcAng));
-    }
-    __syncwarp();
-    nr = 0;
-    na = 0;
-    for (int base = 0; base < cnt; base += 32) {
-        const int q = base + lane;
-        const float r = q < cnt ? s.d[q].w : 1e30f;
-        const unsigned int below = (1u << lane) - 1u;
-        const unsigned int br = __ballot_sync(0xffffffffu, r < kRcRad);
-        if (r < kRcRad) s.rad[nr + __popc(br & below)] = q;
-        nr += __popc(br);
-        const unsigned int ba = __ballot_sync(0xffffffffu, r < kRcAng);
-        if (r < kRcAng) s.ang[na + __popc(ba & below)] = q;
-        na += __popc(ba);
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void triplet_ab(int t, int na, int &a, int &b) {
-    a = 0;
-    while (t >= na - 1 - a) {
-        t -= na - 1 - a;
-        ++a;
-    }
-    b = a + 1 + t;
-}
-
+// One warp per atom: neighbours, features (learned_terms.cuh), then the BF16
+// GEMM input row (and the FP32 row when asked) and the range check.
 __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, const float4 *pos4, int write_f32) {
     __shared__ NbrSmem sn[kFeatWarps];
-    __shared__ float accR[kFeatWarps][2][64];
-    __shared__ float accA[kFeatWarps][320];
-    __shared__ float4 tQ[kFeatWarps][64];     // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
-    __shared__ float4 tB[kFeatWarps][64];     // radial-shell factors of the 4 shells
+    __shared__ TripStage st[kFeatWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
-    NbrSmem &s = sn[w];
-    for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
-    for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
     int cnt, nr, na;
-    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
-    // radial: lane = 16 h + k takes the in-cutoff neighbours u = h, h + 2, ...
-    {
-        const int h = lane >> 4, k = lane & 15;
-        const float Rk = 0.9f + (float)k * (4.3f / 16.f);
-        for (int u = h; u < nr; u += 2) {
-            const int q = s.rad[u];
-            const float r = s.d[q].w;
-            const float x = r - Rk;
-            accR[w][h][16 * s.el[q] + k] += expf(-kEtaR * x * x) * s.fc[q].x;
-        }
-    }
-    // angular.  Each batch of 32 triplets is staged sorted by element pair (stable),
-    // each pair's run padded to a multiple of 4 with empty triplets; then lane
-    // 8 t4 + p takes triplet t4 of every group of 4 (all of one pair type),
-    // computes its angular factor for section p once and adds it, times the 4
-    // shell factors, to its 4 column sums (m = 0..3).  When the pair type changes
-    // the 4 triplet slots are combined in a fixed shuffle order into the pair's
-    // (m, p) columns.
-    {
-        const int t4 = lane >> 3, p = lane & 7;
-        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
-        const float cp = cosf(thp), sp = sinf(thp);
-        const int ntrip = na * (na - 1) / 2;
-        const unsigned int below = (1u << lane) - 1u;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        int curP = -1;
-        for (int base = 0; base < ntrip; base += 32) {
-            const int t = base + lane;
-            int P = 15;   // no triplet
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f), bq = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (t < ntrip) {
-                int a, b;
-                triplet_ab(t, na, a, b);
-                const int qa = s.ang[a], qb = s.ang[b];
-                const float4 dj = s.d[qa], dk = s.d[qb];
-                const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
-                const float cs = kAngScale * ct;
-                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * s.fc[qa].z * s.fc[qb].z, 0.f);
-                const float ravg = 0.5f * (dj.w + dk.w);
-                float bm[4];
-#pragma unroll
-                for (int mm = 0; mm < 4; ++mm) {
-                    const float x = ravg - (0.9f + (float)mm * 0.65f);
-                    bm[mm] = expf(-kEtaA * x * x);
-                }
-                bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
-                P = pair_index(s.el[qa], s.el[qb]);
-            }
-            // padded, stable counting sort by pair type; empty slots of a run stay zero (no contribution)
-            int pos = 0, before = 0;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                const unsigned int bal = __ballot_sync(0xffffffffu, P == k);
-                const int cnt_k = __popc(bal);
-                if (P == k) pos = before + __popc(bal & below);
-                // the run's padding slots: empty triplets of type k
-                const int padded = (cnt_k + 3) & ~3;
-                if (lane >= cnt_k && lane < padded) {
-                    tQ[w][before + lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
-                    tB[w][before + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                before += padded;
-            }
-            if (t < ntrip) {
-                q.w = __int_as_float(P);
-                tQ[w][pos] = q;
-                tB[w][pos] = bq;
-            }
-            __syncwarp();
-            const int ng = before;   // padded length, a multiple of 4
-            for (int u = 0; u < ng; u += 4) {
-                const float4 qq = tQ[w][u + t4];
-                const int Pu = __float_as_int(tQ[w][u].w);   // the group's pair type, the same in every lane
-                if (Pu != curP) {
-                    if (curP >= 0) {
-#pragma unroll
-                        for (int mm = 0; mm < 4; ++mm) {
-                            float v = acc[mm];
-                            v += __shfl_xor_sync(0xffffffffu, v, 8);
-                            v += __shfl_xor_sync(0xffffffffu, v, 16);
-                            if (t4 == 0) accA[w][32 * curP + 8 * mm + p] += v;
-                            acc[mm] = 0.f;
-                        }
-                    }
-                    curP = Pu;
-                }
-                float x = 1.f + qq.x * cp + qq.y * sp;
-                x *= x; x *= x; x *= x; x *= x; x *= x;  // ^32
-                const float xc = x * qq.z;
-                const float4 bb = tB[w][u + t4];
-                acc[0] = fmaf(xc, bb.x, acc[0]);
-                acc[1] = fmaf(xc, bb.y, acc[1]);
-                acc[2] = fmaf(xc, bb.z, acc[2]);
-                acc[3] = fmaf(xc, bb.w, acc[3]);
-            }
-            __syncwarp();
-        }
-        if (curP >= 0) {
-#pragma unroll
-            for (int mm = 0; mm < 4; ++mm) {
-                float v = acc[mm];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                if (t4 == 0) accA[w][32 * curP + 8 * mm + p] += v;
-            }
-        }
-    }
-    __syncwarp();
+    load_neighbours(L, pos4, i, sn[w], lane, cnt, nr, na);
+    float v[12];
+    feature_row(sn[w], nr, na, st[w], lane, v);
     const int row = L.row_of[i];
     const int z = L.el[i];
     bool out = false;
-    for (int f = lane; f < kNFeat; f += 32) {
-        const float v = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
-        if (L.lo != nullptr) out |= (v < L.lo[z * kNFeat + f]) || (v > L.hi[z * kNFeat + f]);
-        L.G16[(size_t)row * kNFeat + f] = __float2bfloat16_rn(v);
-        if (write_f32) L.G32[(size_t)row * kNFeat + f] = v;
+#pragma unroll
+    for (int b = 0; b < 12; ++b) {
+        const int f = 32 * b + lane;
+        if (L.lo != nullptr) out |= (v[b] < L.lo[z * kNFeat + f]) || (v[b] > L.hi[z * kNFeat + f]);
+        L.G16[(size_t)row * kNFeat + f] = __float2bfloat16_rn(v[b]);
+        if (write_f32) L.G32[(size_t)row * kNFeat + f] = v[b];
     }
     if (__any_sync(0xffffffffu, out) && lane == 0) atomicOr(&L.lflags[1], 1u);
 }
@@ -569,184 +391,24 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated, unsig
 
 // ------------------------------------------------------------------ adjoint
 
-// Angular blocks of g are stored 33 floats apart so that lanes working on
-// different element pairs read different banks.
-constexpr int kAngStride = 33;
-constexpr int kTripChunk = 80;    // triplets staged per pass
+constexpr int kAdjChunk = 128;  // triplets staged per pass
 
-struct AdjSmem {
-    float g[64 + 10 * kAngStride];
-    float f[kKmax][3];                    // force on each neighbour (FP32, fixed summation order)
-    float tj[kTripChunk][3], tk[kTripChunk][3];   // staged triplet contributions to j and k
-};
-
-// Index of the angular pair (a, b), a < b, in the order triplet_ab enumerates.
-__device__ __forceinline__ int triplet_index(int a, int b, int na) { return a * (na - 1) - a * (a - 1) / 2 + (b - a - 1); }
-
-// F = -dE/dx by the chain rule through the features: for every radial pair and
-// angular triplet around atom i, the contraction of g = dE/dG_i with the
-// derivative of the feature terms.  No atomics until the final global adds:
-// each neighbour's radial force is written by the one lane that owns the pair;
-// triplet contributions are staged per chunk and each lane then sums, in a
-// fixed order, those of the triplets that contain its neighbour; the force on
-// atom i is summed per lane and reduced over the warp in a fixed order.  The
-// result is reproducible bit for bit.
+// One warp per atom: g row into the padded per-warp layout, neighbours, then
+// the chain rule of learned_terms.cuh (fixed-point force sums).
 __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
                                                              int gated) {
     if (gated && L.lflags[1]) return;
     __shared__ NbrSmem sn[kFeatWarps];
-    __shared__ AdjSmem sa[kFeatWarps];
+    __shared__ AdjScratch<kAdjChunk> sa[kFeatWarps];
+    __shared__ float sg[kFeatWarps][kGRow];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
-    NbrSmem &s = sn[w];
-    AdjSmem &A = sa[w];
-    const int row = L.row_of[i];
-    const float *grow = L.g + (size_t)row * kNFeat;
-    for (int f = lane; f < 64; f += 32) A.g[f] = grow[f];
-    for (int f = lane; f < 320; f += 32) A.g[64 + (f >> 5) * kAngStride + (f & 31)] = grow[64 + f];
+    const float *grow = L.g + (size_t)L.row_of[i] * kNFeat;
+    for (int f = lane; f < kNFeat; f += 32) sg[w][g_col(f)] = grow[f];
     int cnt, nr, na;
-    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
-    for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0.f;
-    __syncwarp();
-    float fix = 0.f, fiy = 0.f, fiz = 0.f;
-    // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j = -dE/dr u,  F_i += dE/dr u
-    for (int u = lane; u < nr; u += 32) {
-        const int q = s.rad[u];
-        const float4 d = s.d[q];
-        const float r = d.w;
-        const float fc = s.fc[q].x, dfc = s.fc[q].y;
-        const float *gz = A.g + 16 * s.el[q];
-        float dEdr = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            const float x = r - (0.9f + (float)k * (4.3f / 16.f));
-            const float ex = expf(-kEtaR * x * x);
-            dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
-        }
-        const float sx = dEdr * d.x, sy = dEdr * d.y, sz = dEdr * d.z;
-        A.f[q][0] = -sx;
-        A.f[q][1] = -sy;
-        A.f[q][2] = -sz;
-        fix += sx;
-        fiy += sy;
-        fiz += sz;
-    }
-    __syncwarp();
-    // angular triplets
-    float cpv[8], spv[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
-        cpv[p] = cosf(thp);
-        spv[p] = sinf(thp);
-    }
-    const int ntrip = na * (na - 1) / 2;
-    for (int t0 = 0; t0 < ntrip; t0 += kTripChunk) {
-        const int t1 = min(t0 + kTripChunk, ntrip);
-        for (int t = t0 + lane; t < t1; t += 32) {
-            int a, b;
-            triplet_ab(t, na, a, b);
-            const int qa = s.ang[a], qb = s.ang[b];
-            const float4 dj = s.d[qa], dk = s.d[qb];
-            const float rj = dj.w, rk = dk.w;
-            const float irj = 1.f / rj, irk = 1.f / rk;
-            const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
-            const float ukx = dk.x, uky = dk.y, ukz = dk.z;
-            const float ct = ujx * ukx + ujy * uky + ujz * ukz;
-            const float cs = kAngScale * ct;
-            const float sn2 = sqrtf(1.f - cs * cs);
-            const float cot = cs / sn2;
-            const float fj = s.fc[qa].z, fk = s.fc[qb].z;
-            const float dfj = s.fc[qa].w, dfk = s.fc[qb].w;
-            const float C = fj * fk;
-            const float ravg = 0.5f * (rj + rk);
-            const float *gp = A.g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
-            // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
-            float Ap[8], dAp[8];
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
-                const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
-                const float b31 = b16 * b8 * b4 * b2 * base;
-                Ap[p] = kTwoPowM31 * b31 * base;
-                dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
-            }
-            float Sc = 0.f, Sr = 0.f, SC = 0.f;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const float x = ravg - (0.9f + (float)m * 0.65f);
-                const float B = expf(-kEtaA * x * x);
-                const float dB = -2.f * kEtaA * x * B;
-                float sa_ = 0.f, sdA = 0.f;
-#pragma unroll
-                for (int p = 0; p < 8; ++p) {
-                    const float gv = gp[8 * m + p];
-                    sa_ = fmaf(gv, Ap[p], sa_);
-                    sdA = fmaf(gv, dAp[p], sdA);
-                }
-                Sc = fmaf(sdA, B * C, Sc);
-                Sr = fmaf(sa_, dB * C, Sr);
-                SC = fmaf(sa_, B, SC);
-            }
-            const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
-            const float gc = Sc * kAngScale;
-            const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;
-            const float gjy = gc * (uky - ct * ujy) * irj + dEdrj * ujy;
-            const float gjz = gc * (ukz - ct * ujz) * irj + dEdrj * ujz;
-            const float gkx = gc * (ujx - ct * ukx) * irk + dEdrk * ukx;
-            const float gky = gc * (ujy - ct * uky) * irk + dEdrk * uky;
-            const float gkz = gc * (ujz - ct * ukz) * irk + dEdrk * ukz;
-            float *tj = A.tj[t - t0], *tk = A.tk[t - t0];
-            tj[0] = -gjx;
-            tj[1] = -gjy;
-            tj[2] = -gjz;
-            tk[0] = -gkx;
-            tk[1] = -gky;
-            tk[2] = -gkz;
-            fix += gjx + gkx;
-            fiy += gjy + gky;
-            fiz += gjz + gkz;
-        }
-        __syncwarp();
-        // each lane: the staged contributions of this chunk to its angular neighbour a, b in order
-        for (int a = lane; a < na; a += 32) {
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            for (int b = 0; b < na; ++b) {
-                if (b == a) continue;
-                const int t = a < b ? triplet_index(a, b, na) : triplet_index(b, a, na);
-                if (t < t0 || t >= t1) continue;
-                const float *v = a < b ? A.tj[t - t0] : A.tk[t - t0];
-                ax += v[0];
-                ay += v[1];
-                az += v[2];
-            }
-            const int q = s.ang[a];
-            A.f[q][0] += ax;
-            A.f[q][1] += ay;
-            A.f[q][2] += az;
-        }
-        __syncwarp();
-    }
-    for (int q = lane; q < cnt; q += 32) {
-        const int j = s.j[q];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long long v = fx_from_float(A.f[q][c]);
-            if (v != 0) atomicAdd(&fx[3 * j + c], (unsigned long long)v);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fix += __shfl_xor_sync(0xffffffffu, fix, o);
-        fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
-        fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&fx[3 * i + 0], (unsigned long long)fx_from_float(fix));
-        atomicAdd(&fx[3 * i + 1], (unsigned long long)fx_from_float(fiy));
-        atomicAdd(&fx[3 * i + 2], (unsigned long long)fx_from_float(fiz));
-    }
+    load_neighbours(L, pos4, i, sn[w], lane, cnt, nr, na);
+    adjoint_atom(i, sn[w], cnt, nr, na, sg[w], sa[w], fx, lane);
 }
 
 // ------------------------------------------------------------------ feature JVP
@@ -859,6 +521,13 @@ __global__ void k_learn_end(LearnedDev L, uint32_t *status, int fallback) {
     if (!fallback) atomicOr(status, MDPF_STATUS_OUT_OF_RANGE);
 }
 
+__global__ void k_fallback_clear(LearnedDev L, unsigned long long *fx, unsigned long long *efx) {
+    if (L.lflags[1] == 0u) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < 3 * L.n) fx[q] = 0ull;
+    if (q == 0 && efx != nullptr) efx[E_LEARN] = 0ull;
+}
+
 __global__ void k_import_g(LearnedDev L, const float *G) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= L.n * kNFeat) return;
@@ -871,6 +540,10 @@ __global__ void k_import_g(LearnedDev L, const float *G) {
 // ------------------------------------------------------------------ launchers
 
 void learned_begin(const LearnedDev &L, cudaStream_t s) { k_learn_begin<<<1, 32, 0, s>>>(L); }
+
+void learned_fallback_clear(const LearnedDev &L, unsigned long long *fx, unsigned long long *efx, cudaStream_t s) {
+    k_fallback_clear<<<(3 * L.n + 255) / 256 + 1, 256, 0, s>>>(L, fx, efx);
+}
 
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s) {
     k_learn_end<<<1, 32, 0, s>>>(L, status, fallback);

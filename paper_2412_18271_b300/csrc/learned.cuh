@@ -63,6 +63,13 @@ struct MlpMaps {
     CUtensorMap g, w1, w2, w2t, w1t;
 };
 
+// Tiles of the fused kernel: tile t covers MLP rows first[t] .. first[t] + count[t] - 1,
+// 1 <= count[t] <= kRowTile, all atoms of element el[t].
+struct FusedTiles {
+    const int *first, *count, *el;
+    int n;
+};
+
 // launchers (learned.cu)
 // neighbour list (cooperative launch; learned_nb_grid() gives its grid size, 0 if unavailable)
 int learned_nb_grid();
@@ -74,6 +81,8 @@ void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, c
 void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long *efx, cudaStream_t s);
 void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s);
 void learned_begin(const LearnedDev &L, cudaStream_t s);
+// a step that left the feature range: drop the model's forces and energy (fused path, before the plain force field)
+void learned_fallback_clear(const LearnedDev &L, unsigned long long *fx, unsigned long long *efx, cudaStream_t s);
 void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream_t s);
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s);
 // feature JVP: U [n_rows][384] (rows of the atoms) = sum_a dG/dx_a . v_a, v [n][3]
@@ -83,5 +92,11 @@ void learned_jvp(const LearnedDev &L, const float4 *pos4, const float *v, float 
 cudaError_t learned_mlp_tc_prepare();
 cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated,
                            unsigned long long *efx, cudaStream_t s);
+
+// fused features -> MLP -> adjoint (fused.cu): energies per row, the energy slot of efx and fixed-point
+// forces fx, with G and dE/dG kept on chip; sets the range flag like the feature kernel
+cudaError_t learned_fused_prepare();
+cudaError_t learned_fused(const LearnedDev &L, const FusedTiles &T, const MlpMaps &maps, const float4 *pos4,
+                          unsigned long long *fx, unsigned long long *efx, uint32_t *status, cudaStream_t s);
 
 }  // namespace mdpf

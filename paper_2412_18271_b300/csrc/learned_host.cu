@@ -25,7 +25,37 @@ struct LearnedHost {
     float *d_U = nullptr;       // [n_rows][384] JVP output (allocated on first use)
     int mlp_kernel = MDPF_MLP_TENSOR;
     MlpMaps maps{};
+    FusedTiles ft{};
 };
+
+static int fused_tile_count(const std::vector<int> &cnt, int run) {
+    int t = 0;
+    for (int c : cnt) t += (c + run - 1) / run;
+    return t;
+}
+
+// Tiles of the fused kernel: each element's atoms (rows start[e] .. start[e] + cnt[e] - 1) in
+// near-equal runs of at most kRowTile.  The run length is the smallest one that keeps the tiles
+// within one wave over the SMs (one CTA per SM), or kRowTile when even that needs more waves.
+static void fused_tiling(const std::vector<int> &cnt, const std::vector<int> &start, int sms, std::vector<int> &first,
+                         std::vector<int> &count, std::vector<int> &el) {
+    int run = kRowTile;
+    if (sms > 0 && fused_tile_count(cnt, kRowTile) <= sms) {
+        run = 1;
+        while (fused_tile_count(cnt, run) > sms) ++run;
+    }
+    for (int e = 0; e < (int)cnt.size(); ++e) {
+        if (cnt[e] == 0) continue;
+        const int nt = (cnt[e] + run - 1) / run, base = cnt[e] / nt, rem = cnt[e] % nt;
+        for (int t = 0, off = 0; t < nt; ++t) {
+            const int len = base + (t < rem ? 1 : 0);
+            first.push_back(start[e] + off);
+            count.push_back(len);
+            el.push_back(e);
+            off += len;
+        }
+    }
+}
 
 // 2-D BF16 tensor maps with 64 x 128 boxes and 128-byte swizzle for the MLP operands.
 static int make_maps(mdpf_ctx *c, LearnedHost *h) {
@@ -51,12 +81,15 @@ static int make_maps(mdpf_ctx *c, LearnedHost *h) {
         return fail(c, MDPF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     e = learned_mlp_tc_prepare();
     if (e != cudaSuccess) return cuda_fail(c, e, "learned_mlp_tc_prepare");
+    e = learned_fused_prepare();
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned_fused_prepare");
     return MDPF_OK;
 }
 
 // The MLP (energy per row and dE/dG) on the selected units.
 static void enqueue_mlp(LearnedHost *h, uint32_t *status, bool gated, unsigned long long *efx, cudaStream_t s) {
-    if (h->mlp_kernel == MDPF_MLP_TENSOR) learned_mlp_tc(h->dev, h->maps, status, gated, efx, s);
+    if (h->mlp_kernel == MDPF_MLP_TENSOR || h->mlp_kernel == MDPF_MLP_FUSED)
+        learned_mlp_tc(h->dev, h->maps, status, gated, efx, s);
     else learned_mlp(h->dev, gated, h->mlp_kernel == MDPF_MLP_SIMT_FP32, efx, s);
 }
 
@@ -168,6 +201,13 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     }
     for (int e = 0; e < 4; ++e)
         for (int r = start[e]; r < start[e + 1]; r += kRowTile) tile_el[r / kRowTile] = e;
+    std::vector<int> ft_first, ft_count, ft_el;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 0;
+        fused_tiling(cnt, start, sms, ft_first, ft_count, ft_el);
+    }
 
     LearnedDev &L = h->dev;
     L.n = n;
@@ -221,6 +261,10 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LA(L.lflags, 4);
     LA(L.lcount, 4);
     LA(h->d_Gin, (size_t)n * kNFeat);
+    int *d_ft_first, *d_ft_count, *d_ft_el;
+    LA(d_ft_first, ft_first.size());
+    LA(d_ft_count, ft_count.size());
+    LA(d_ft_el, ft_el.size());
 #undef LA
 #define LC(x)                                                         \
     do {                                                              \
@@ -242,7 +286,14 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
         LC(cudaMemcpy(dlo, lo.data(), 4 * lo.size(), cudaMemcpyHostToDevice));
         LC(cudaMemcpy(dhi, hi.data(), 4 * hi.size(), cudaMemcpyHostToDevice));
     }
+    if (!ft_first.empty()) {
+        LC(cudaMemcpy(d_ft_first, ft_first.data(), sizeof(int) * ft_first.size(), cudaMemcpyHostToDevice));
+        LC(cudaMemcpy(d_ft_count, ft_count.data(), sizeof(int) * ft_count.size(), cudaMemcpyHostToDevice));
+        LC(cudaMemcpy(d_ft_el, ft_el.data(), sizeof(int) * ft_el.size(), cudaMemcpyHostToDevice));
+    }
+    h->ft = FusedTiles{d_ft_first, d_ft_count, d_ft_el, (int)ft_first.size()};
     LC(cudaMemset(L.G16, 0, sizeof(__nv_bfloat16) * (size_t)n_rows * kNFeat));
+    LC(cudaMemset(L.E_row, 0, sizeof(double) * (size_t)(n_rows > 0 ? n_rows : 1)));
     LC(cudaMemset(L.lflags, 0, sizeof(unsigned int) * 4));
     LC(cudaMemset(L.lcount, 0, sizeof(long long) * 4));
     LC(cudaMemset(L.nb_count, 0, sizeof(int) * n));
@@ -283,12 +334,31 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     cudaError_t ce = learned_neighbors(L, pos4, forced_build, status, s);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "learned_neighbors");
     prof_end(c, MDPF_PROF_LEARN_NEIGHBORS, ev, s);
-    ev = prof_begin(c, s);
-    learned_features(L, pos4, write_f32 || h->mlp_kernel == MDPF_MLP_SIMT_FP32, s);
-    prof_end(c, MDPF_PROF_LEARN_FEATURES, ev, s);
     // with the fallback on, a step that left the range skips the model and runs the plain force field;
     // with it off, the model's forces are used and the step reports MDPF_STATUS_OUT_OF_RANGE
     const bool gated = h->fallback != 0;
+    if (h->mlp_kernel == MDPF_MLP_FUSED && !write_f32) {
+        // one kernel; the range is known only when it ends, so a step that left it drops the model's
+        // forces and energy afterwards
+        ev = prof_begin(c, s);
+        ce = learned_fused(L, h->ft, h->maps, pos4, fx, efx, status, s);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "learned_fused");
+        prof_end(c, MDPF_PROF_LEARN_FUSED, ev, s);
+        if (L.lo == nullptr) return MDPF_OK;
+        if (gated) {
+            learned_fallback_clear(L, fx, efx, s);
+            PlainDev p = plain_dev(c, pos4);
+            p.status = status;
+            p.gate = L.lflags + 1;
+            launch_bonded(p, fx, efx, s);
+            launch_nonbonded(p, fx, efx, true, s);
+        }
+        learned_end(L, status, h->fallback, s);
+        return MDPF_OK;
+    }
+    ev = prof_begin(c, s);
+    learned_features(L, pos4, write_f32 || h->mlp_kernel == MDPF_MLP_SIMT_FP32, s);
+    prof_end(c, MDPF_PROF_LEARN_FEATURES, ev, s);
     ev = prof_begin(c, s);
     enqueue_mlp(h, status, gated, efx, s);
     prof_end(c, MDPF_PROF_LEARN_MLP, ev, s);

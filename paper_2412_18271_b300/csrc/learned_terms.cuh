@@ -1,0 +1,425 @@
+// Per-atom device code of the learned potential, shared by the per-stage
+// kernels (learned.cu) and the fused tile kernel (fused.cu): the neighbour
+// geometry of one atom, its symmetry-function features, and the chain rule
+// from dE/dG back to forces.  Both callers run the same code, so the two paths
+// give the same bits.
+//
+//   radial    G[i, 16 Zj + k]           = sum_j  exp(-16 (r_ij - R_k)^2) fc(r_ij; 5.2)
+//   angular   G[i, 64 + 32 P + 8 m + p] = sum_{j<k} 2^-31 (1 + cos(theta - theta_p))^32
+//                                         exp(-8 ((r_ij + r_ik)/2 - R_m)^2) fc(r_ij; 3.5) fc(r_ik; 3.5)
+//   theta = acos(0.95 cos theta_ijk), cos(theta - theta_p) = c cos theta_p + sqrt(1 - c^2) sin theta_p
+//   R_k = 0.9 + 4.3 k / 16,  R_m = 0.9 + 0.65 m,  theta_p = (2 p + 1) pi / 16
+#pragma once
+
+#include "learned.cuh"
+
+namespace mdpf {
+namespace {
+
+constexpr float kPi = 3.14159265358979f;
+constexpr float kEtaR = 16.f, kEtaA = 8.f;
+constexpr float kAngScale = 0.95f;
+constexpr float kTwoPowM31 = 4.656612873077393e-10f;  // 2^-31 = 2^(1 - zeta), zeta = 32
+
+__device__ __forceinline__ float fcut(float r, float rc) { return r < rc ? 0.5f * cosf(kPi * r / rc) + 0.5f : 0.f; }
+__device__ __forceinline__ float dfcut(float r, float rc) { return r < rc ? -0.5f * kPi / rc * sinf(kPi * r / rc) : 0.f; }
+
+__device__ __forceinline__ int pair_index(int a, int b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return (a == 0 ? 0 : (a == 1 ? 4 : (a == 2 ? 7 : 9))) + (b - a);
+}
+
+// One atom's neighbours, per warp (4,992 bytes).
+struct NbrSmem {
+    int j[kKmax];
+    float4 d[kKmax];              // unit vector from i to j (x, y, z) and r
+    float4 fc[kKmax];             // fc(r; 5.2), fc'(r; 5.2), fc(r; 3.5), fc'(r; 3.5)
+    signed char el[kKmax];
+    unsigned char rad[kKmax];     // neighbours within the radial cutoff, in row order
+    unsigned char ang[kKmax];     // neighbours within the angular cutoff, in row order
+};
+
+// Load atom i's neighbours into shared memory; returns the row length and the
+// numbers of neighbours within the radial and angular cutoffs.  The compacted
+// in-cutoff lists do not depend on how far the list radius reaches beyond the
+// cutoffs, so neither does any summation order below.
+__device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
+                                                int &cnt, int &nr, int &na) {
+    const float4 pi = pos4[i];
+    cnt = L.nb_count[i];
+    for (int q = lane; q < cnt; q += 32) {
+        const int j = L.nb_idx[(size_t)i * kKmax + q];
+        const float4 pj = pos4[j];
+        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
+        s.j[q] = j;
+        s.el[q] = (signed char)L.el[j];
+        s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        s.fc[q] = make_float4(fcut(r, kRcRad), dfcut(r, kRcRad), fcut(r, kRcAng), dfcut(r, kRcAng));
+    }
+    __syncwarp();
+    nr = 0;
+    na = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int q = base + lane;
+        const float r = q < cnt ? s.d[q].w : 1e30f;
+        const unsigned int below = (1u << lane) - 1u;
+        const unsigned int br = __ballot_sync(0xffffffffu, r < kRcRad);
+        if (r < kRcRad) s.rad[nr + __popc(br & below)] = (unsigned char)q;
+        nr += __popc(br);
+        const unsigned int ba = __ballot_sync(0xffffffffu, r < kRcAng);
+        if (r < kRcAng) s.ang[na + __popc(ba & below)] = (unsigned char)q;
+        na += __popc(ba);
+    }
+    __syncwarp();
+}
+
+// Triplet t of the pairs (a, b), a < b, of na angular neighbours, in row-major order.
+__device__ __forceinline__ void triplet_ab(int t, int na, int &a, int &b) {
+    a = 0;
+    while (t >= na - 1 - a) {
+        t -= na - 1 - a;
+        ++a;
+    }
+    b = a + 1 + t;
+}
+// Inverse of triplet_ab.
+__device__ __forceinline__ int triplet_index(int a, int b, int na) { return a * (na - 1) - a * (a - 1) / 2 + (b - a - 1); }
+
+// ------------------------------------------------------------------ features
+
+// Per-warp staging of one batch of 32 triplets, sorted by pair type (2,048 bytes).
+struct TripStage {
+    float4 q[64];   // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
+    float4 b[64];   // radial-shell factors of the 4 shells
+};
+
+// Features of one atom whose neighbours are in s.  On return lane l holds
+// G[32 b + l] in v[b], b = 0..11.
+//   radial: lane 16 h + k sums the in-cutoff neighbours u = h, h + 2, ... into
+//     its four per-element sums (registers), then the two halves are added;
+//   angular: each batch of 32 triplets is staged sorted by element pair
+//     (stable), each pair's run padded to a multiple of 4 with empty triplets;
+//     lane 8 t4 + p takes triplet t4 of every group of 4 (all of one pair
+//     type), computes its angular factor for section p once and adds it, times
+//     the 4 shell factors, to its 4 column sums (m = 0..3).  When the pair type
+//     changes, the 4 triplet slots are combined in a fixed shuffle order and
+//     lane 8 m + p adds sum m to its register for that pair, column
+//     64 + 32 P + 8 m + p.
+// Every sum is taken in a fixed order, so the result does not depend on the
+// caller.
+__device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, TripStage &ts, int lane, float (&v)[12]) {
+    {
+        const int h = lane >> 4, k = lane & 15;
+        const float Rk = 0.9f + (float)k * (4.3f / 16.f);
+        float racc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int u = h; u < nr; u += 2) {
+            const int q = s.rad[u];
+            const float x = s.d[q].w - Rk;
+            const float t = expf(-kEtaR * x * x);
+            const float fc = s.fc[q].x;
+            const int e = s.el[q];
+#pragma unroll
+            for (int ee = 0; ee < 4; ++ee)
+                if (ee == e) racc[ee] = fmaf(t, fc, racc[ee]);
+        }
+        float tot[4];
+#pragma unroll
+        for (int ee = 0; ee < 4; ++ee) tot[ee] = racc[ee] + __shfl_xor_sync(0xffffffffu, racc[ee], 16);
+        v[0] = h ? tot[1] : tot[0];   // column l      = 16 h + k:       element h
+        v[1] = h ? tot[3] : tot[2];   // column 32 + l = 16 (2 + h) + k: element 2 + h
+    }
+    {
+        const int t4 = lane >> 3, p = lane & 7;
+        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+        const float cp = cosf(thp), sp = sinf(thp);
+        const int ntrip = na * (na - 1) / 2;
+        const unsigned int below = (1u << lane) - 1u;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float areg[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) areg[k] = 0.f;
+        int curP = -1;
+        auto flush = [&]() {
+            float red[4];
+#pragma unroll
+            for (int mm = 0; mm < 4; ++mm) {
+                float x = acc[mm];
+                x += __shfl_xor_sync(0xffffffffu, x, 8);
+                x += __shfl_xor_sync(0xffffffffu, x, 16);
+                red[mm] = x;
+                acc[mm] = 0.f;
+            }
+            const float mine = t4 == 0 ? red[0] : (t4 == 1 ? red[1] : (t4 == 2 ? red[2] : red[3]));
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+                if (k == curP) areg[k] += mine;
+        };
+        for (int base = 0; base < ntrip; base += 32) {
+            const int t = base + lane;
+            int P = 15;   // no triplet
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f), bq = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < ntrip) {
+                int a, b;
+                triplet_ab(t, na, a, b);
+                const int qa = s.ang[a], qb = s.ang[b];
+                const float4 dj = s.d[qa], dk = s.d[qb];
+                const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
+                const float cs = kAngScale * ct;
+                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * s.fc[qa].z * s.fc[qb].z, 0.f);
+                const float ravg = 0.5f * (dj.w + dk.w);
+                float bm[4];
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) {
+                    const float x = ravg - (0.9f + (float)mm * 0.65f);
+                    bm[mm] = expf(-kEtaA * x * x);
+                }
+                bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
+                P = pair_index(s.el[qa], s.el[qb]);
+            }
+            // padded, stable counting sort by pair type; empty slots of a run stay zero (no contribution)
+            int pos = 0, before = 0;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                const unsigned int bal = __ballot_sync(0xffffffffu, P == k);
+                const int cnt_k = __popc(bal);
+                if (P == k) pos = before + __popc(bal & below);
+                const int padded = (cnt_k + 3) & ~3;
+                if (lane >= cnt_k && lane < padded) {
+                    ts.q[before + lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
+                    ts.b[before + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                before += padded;
+            }
+            if (t < ntrip) {
+                q.w = __int_as_float(P);
+                ts.q[pos] = q;
+                ts.b[pos] = bq;
+            }
+            __syncwarp();
+            const int ng = before;   // padded length, a multiple of 4
+            for (int u = 0; u < ng; u += 4) {
+                const float4 qq = ts.q[u + t4];
+                const int Pu = __float_as_int(ts.q[u].w);   // the group's pair type, the same in every lane
+                if (Pu != curP) {
+                    if (curP >= 0) flush();
+                    curP = Pu;
+                }
+                float x = 1.f + qq.x * cp + qq.y * sp;
+                x *= x; x *= x; x *= x; x *= x; x *= x;  // ^32
+                const float xc = x * qq.z;
+                const float4 bb = ts.b[u + t4];
+                acc[0] = fmaf(xc, bb.x, acc[0]);
+                acc[1] = fmaf(xc, bb.y, acc[1]);
+                acc[2] = fmaf(xc, bb.z, acc[2]);
+                acc[3] = fmaf(xc, bb.w, acc[3]);
+            }
+            __syncwarp();
+        }
+        if (curP >= 0) flush();
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v[2 + k] = areg[k];
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+
+// Angular blocks of a g row are stored kAngStride floats apart, so that lanes
+// working on different element pairs read different banks.
+constexpr int kAngStride = 33;
+constexpr int kGRow = 64 + 10 * kAngStride;   // floats of one g row in that layout
+
+// Per-warp scratch of the adjoint: Chunk triplets are staged per pass (a
+// multiple of 32; the result does not depend on it).
+template <int Chunk>
+struct AdjScratch {
+    static_assert(Chunk % 32 == 0, "triplet t is always taken by lane t mod 32");
+    float f[kKmax][3];                  // force on each neighbour (FP32, fixed summation order)
+    float tj[Chunk][3], tk[Chunk][3];   // staged triplet contributions to j and k
+};
+
+// Column of feature f of a g row in the padded layout.
+__device__ __forceinline__ int g_col(int f) { return f < 64 ? f : 64 + kAngStride * ((f - 64) >> 5) + ((f - 64) & 31); }
+
+// F = -dE/dx by the chain rule through the features of atom i (neighbours in
+// s, g = dE/dG_i in the padded layout): for every radial pair and angular
+// triplet around atom i, the contraction of g with the derivative of the
+// feature terms.  Each neighbour's radial force is written by the one lane
+// that owns the pair; triplet contributions are staged per chunk and each lane
+// then sums, in a fixed order, those of the triplets that contain its
+// neighbour; the force on atom i is summed per lane and reduced over the warp
+// in a fixed order.  Triplet t is taken by lane t mod 32 and each neighbour's
+// force is one running sum (radial term, then its triplets in index order), so
+// no sum depends on the chunk size.  The sums go to fx as int64 fixed point,
+// so the result is reproducible bit for bit.
+template <int Chunk>
+__device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, int nr, int na, const float *g,
+                                             AdjScratch<Chunk> &A, unsigned long long *fx, int lane) {
+    for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0.f;
+    __syncwarp();
+    float fix = 0.f, fiy = 0.f, fiz = 0.f;
+    // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j = -dE/dr u,  F_i += dE/dr u
+    for (int u = lane; u < nr; u += 32) {
+        const int q = s.rad[u];
+        const float4 d = s.d[q];
+        const float r = d.w;
+        const float fc = s.fc[q].x, dfc = s.fc[q].y;
+        const float *gz = g + 16 * s.el[q];
+        float dEdr = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+            const float x = r - (0.9f + (float)k * (4.3f / 16.f));
+            const float ex = expf(-kEtaR * x * x);
+            dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
+        }
+        const float sx = dEdr * d.x, sy = dEdr * d.y, sz = dEdr * d.z;
+        A.f[q][0] = -sx;
+        A.f[q][1] = -sy;
+        A.f[q][2] = -sz;
+        fix += sx;
+        fiy += sy;
+        fiz += sz;
+    }
+    __syncwarp();
+    // angular triplets
+    float cpv[8], spv[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
+        cpv[p] = cosf(thp);
+        spv[p] = sinf(thp);
+    }
+    const int ntrip = na * (na - 1) / 2;
+    int kcur[kKmax / 32] = {0, 0, 0, 0};
+    for (int t0 = 0; t0 < ntrip; t0 += Chunk) {
+        const int t1 = min(t0 + Chunk, ntrip);
+        for (int t = t0 + lane; t < t1; t += 32) {
+            int a, b;
+            triplet_ab(t, na, a, b);
+            const int qa = s.ang[a], qb = s.ang[b];
+            const float4 dj = s.d[qa], dk = s.d[qb];
+            const float rj = dj.w, rk = dk.w;
+            const float irj = 1.f / rj, irk = 1.f / rk;
+            const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
+            const float ukx = dk.x, uky = dk.y, ukz = dk.z;
+            const float ct = ujx * ukx + ujy * uky + ujz * ukz;
+            const float cs = kAngScale * ct;
+            const float sn2 = sqrtf(1.f - cs * cs);
+            const float cot = cs / sn2;
+            const float fj = s.fc[qa].z, fk = s.fc[qb].z;
+            const float dfj = s.fc[qa].w, dfk = s.fc[qb].w;
+            const float C = fj * fk;
+            const float ravg = 0.5f * (rj + rk);
+            const float *gp = g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
+            // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
+            float Ap[8], dAp[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
+                const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
+                const float b31 = b16 * b8 * b4 * b2 * base;
+                Ap[p] = kTwoPowM31 * b31 * base;
+                dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
+            }
+            float Sc = 0.f, Sr = 0.f, SC = 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const float x = ravg - (0.9f + (float)m * 0.65f);
+                const float B = expf(-kEtaA * x * x);
+                const float dB = -2.f * kEtaA * x * B;
+                float sa_ = 0.f, sdA = 0.f;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const float gv = gp[8 * m + p];
+                    sa_ = fmaf(gv, Ap[p], sa_);
+                    sdA = fmaf(gv, dAp[p], sdA);
+                }
+                Sc = fmaf(sdA, B * C, Sc);
+                Sr = fmaf(sa_, dB * C, Sr);
+                SC = fmaf(sa_, B, SC);
+            }
+            const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
+            const float gc = Sc * kAngScale;
+            const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;
+            const float gjy = gc * (uky - ct * ujy) * irj + dEdrj * ujy;
+            const float gjz = gc * (ukz - ct * ujz) * irj + dEdrj * ujz;
+            const float gkx = gc * (ujx - ct * ukx) * irk + dEdrk * ukx;
+            const float gky = gc * (ujy - ct * uky) * irk + dEdrk * uky;
+            const float gkz = gc * (ujz - ct * ukz) * irk + dEdrk * ukz;
+            float *tj = A.tj[t - t0], *tk = A.tk[t - t0];
+            tj[0] = -gjx;
+            tj[1] = -gjy;
+            tj[2] = -gjz;
+            tk[0] = -gkx;
+            tk[1] = -gky;
+            tk[2] = -gkz;
+            fix += gjx + gkx;
+            fiy += gjy + gky;
+            fiz += gjz + gkz;
+        }
+        __syncwarp();
+        // each lane, for its angular neighbours a = lane + 32 sl: the staged contributions of
+        // this chunk, in triplet order.  Those of the triplets (b, a), b < a, come first (their
+        // indices grow with b; kcur carries the next b across chunks), then those of (a, b),
+        // b > a, whose indices are contiguous.  Over all chunks this is one running sum per
+        // neighbour in triplet index order, whatever the chunk size.
+#pragma unroll
+        for (int sl = 0; sl < kKmax / 32; ++sl) {
+            const int a = lane + 32 * sl;
+            if (a >= na) break;
+            const int q = s.ang[a];
+            float ax = A.f[q][0], ay = A.f[q][1], az = A.f[q][2];
+            int b = kcur[sl];
+            for (; b < a; ++b) {
+                const int t = triplet_index(b, a, na);
+                if (t >= t1) break;
+                const float *v = A.tk[t - t0];
+                ax += v[0];
+                ay += v[1];
+                az += v[2];
+            }
+            kcur[sl] = b;
+            if (a + 1 < na) {
+                const int ra = triplet_index(a, a + 1, na);
+                const int lo = max(ra, t0), hi = min(ra + (na - a - 2), t1 - 1);
+                for (int t = lo; t <= hi; ++t) {
+                    const float *v = A.tj[t - t0];
+                    ax += v[0];
+                    ay += v[1];
+                    az += v[2];
+                }
+            }
+            A.f[q][0] = ax;
+            A.f[q][1] = ay;
+            A.f[q][2] = az;
+        }
+        __syncwarp();
+    }
+    for (int q = lane; q < cnt; q += 32) {
+        const int j = s.j[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long v = fx_from_float(A.f[q][c]);
+            if (v != 0) atomicAdd(&fx[3 * j + c], (unsigned long long)v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fix += __shfl_xor_sync(0xffffffffu, fix, o);
+        fiy += __shfl_xor_sync(0xffffffffu, fiy, o);
+        fiz += __shfl_xor_sync(0xffffffffu, fiz, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&fx[3 * i + 0], (unsigned long long)fx_from_float(fix));
+        atomicAdd(&fx[3 * i + 1], (unsigned long long)fx_from_float(fiy));
+        atomicAdd(&fx[3 * i + 2], (unsigned long long)fx_from_float(fiz));
+    }
+    __syncwarp();
+}
+
+}  // namespace
+}  // namespace mdpf

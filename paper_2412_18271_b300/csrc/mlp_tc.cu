@@ -18,13 +18,14 @@
 // Warps 0-15: epilogue (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. those
 // tile rows, and column group w / 4); warp 16: TMA producer; warp 17: TMEM
 // allocation and MMA issue.
-// Every wait is bounded (kWaitNs): on expiry the CTA records
+// Every wait is bounded (kTcWaitNs): on expiry the CTA records
 // MDPF_STATUS_TIMEOUT, drains its copies and MMAs in flight, frees its tensor
 // memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "learned.cuh"
+#include "tc_util.cuh"
 
 namespace mdpf {
 namespace {
@@ -42,138 +43,11 @@ constexpr int kOffBar = kOffPar + 4096;
 constexpr int kGStride = 36;                   // padded row of a 32 x 32 FP32 staging block of g
 constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
 constexpr int kChunks = 16;                    // 6 + 4 + 2 + 4 K-chunks of 64
-constexpr long long kWaitNs = 200000000LL;     // 200 ms; a tile takes microseconds
-constexpr float kCeluAlphaTc = 0.1f;
 
 // barrier block: full[2] empty[2] acc epi drain, then tmem address, abort flag, issued, consumed
 enum { B_FULL = 0, B_EMPTY = 2, B_ACC = 4, B_EPI = 5, B_DRAIN = 6 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ long long gtimer() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait; false when the CTA aborted (here or elsewhere).
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort) {
-    if (mbar_try(a, parity)) return true;
-    const long long t0 = gtimer();
-    for (;;) {
-        if (mbar_try(a, parity)) return true;
-        if (*abort) return false;
-        if (gtimer() - t0 > kWaitNs) {
-            *abort = 1;
-            return false;
-        }
-    }
-}
-// Bounded wait used during teardown (ignores the abort flag).
-__device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity) {
-    const long long t0 = gtimer();
-    while (!mbar_try(a, parity) && gtimer() - t0 < kWaitNs) {
-    }
-}
-
-// Bounded wait by every lane of a warp, with a warp-uniform result (the
-// tensor-memory loads that follow are warp-collective).
-__device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, volatile int *abort) {
-    const bool ok = mbar_wait(a, parity, abort);
-    return __all_sync(0xffffffffu, ok);
-}
-
-__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (load and wait in one statement).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// CELU(0.1) and its derivative; exp(10 x) from the fast exponential (its error
-// is far below the BF16 rounding that follows on every operand path)
-__device__ __forceinline__ float celu_tc(float x) { return x > 0.f ? x : kCeluAlphaTc * (__expf(10.f * x) - 1.f); }
-__device__ __forceinline__ float dcelu_tc(float x) { return x >= 0.f ? 1.f : __expf(10.f * x); }
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&p);
-}
-
-// Store 32 BF16 values (columns c0..c0+31 of row r, c0 a multiple of 32) into a
-// swizzled K-major operand whose 64-column chunks are 16 KB apart.
-__device__ __forceinline__ void st_operand32(unsigned char *res, int r, int c0, const float (&v)[32]) {
-    unsigned char *blk = res + (c0 >> 6) * 16384 + r * 128;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int unit = ((c0 & 63) >> 3) + q;
-        uint4 w;
-        w.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-        w.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-        w.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-        w.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-        *reinterpret_cast<uint4 *>(blk + ((unit ^ (r & 7)) << 4)) = w;
-    }
-}
 
 __device__ __forceinline__ void chunk_of(int c, int &g, int &kc) {
     if (c < 6) { g = 0; kc = c; }
@@ -352,10 +226,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             const float E = ((sEp[r] + sEp[128 + r]) + sEp[256 + r]) + sEp[384 + r];
             const double Er = L.atom_of[row] >= 0 ? (double)E + (double)L.b3[e] + L.e0[e] : 0.0;
             L.E_row[row] = Er;
-            if (efx != nullptr) {   // the tile's energy into the fixed-point learned-energy slot
-                const double ws = warp_sum_d(Er);
-                if (lane == 0 && ws != 0.0) fx_add_d(&efx[E_LEARN], ws);
-            }
+            if (efx != nullptr) fx_warp_add_d(&efx[E_LEARN], Er);
         }
         // epi3: d1 = bf16(P1 * celu'(H1 + b1)), columns 64 cg .. 64 cg + 63
         if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {

@@ -34,6 +34,7 @@ MDPF_PROF_LEARN_NEIGHBORS = 3
 MDPF_PROF_LEARN_FEATURES = 4
 MDPF_PROF_LEARN_MLP = 5
 MDPF_PROF_LEARN_ADJOINT = 6
+MDPF_PROF_LEARN_FUSED = 7
 MDPF_STEPPER_PERSISTENT = 0
 MDPF_STEPPER_KERNELS = 1
 MDPF_INTEGRATOR_VERLET = 0
@@ -41,6 +42,7 @@ MDPF_INTEGRATOR_LANGEVIN = 1
 MDPF_MLP_TENSOR = 0
 MDPF_MLP_SIMT = 1
 MDPF_MLP_SIMT_FP32 = 2
+MDPF_MLP_FUSED = 3
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
