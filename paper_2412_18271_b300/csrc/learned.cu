@@ -404,10 +404,17 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
-    const float *grow = L.g + (size_t)L.row_of[i] * kNFeat;
-    for (int f = lane; f < kNFeat; f += 32) sg[w][g_col(f)] = grow[f];
+    // all global loads first (neighbour row, then its positions alongside the g row), then the stores
+    const int row = L.row_of[i];
+    NbrFetch nf;
+    fetch_neighbours(L, pos4, i, lane, nf);
+    float gv[kNFeat / 32];
+#pragma unroll
+    for (int b = 0; b < kNFeat / 32; ++b) gv[b] = L.g[(size_t)row * kNFeat + 32 * b + lane];
+#pragma unroll
+    for (int b = 0; b < kNFeat / 32; ++b) sg[w][g_col(32 * b + lane)] = gv[b];
     int cnt, nr, na;
-    load_neighbours(L, pos4, i, sn[w], lane, cnt, nr, na);
+    store_neighbours(nf, sn[w], lane, cnt, nr, na);
     adjoint_atom(i, sn[w], cnt, nr, na, sg[w], sa[w], fx, lane);
 }
 

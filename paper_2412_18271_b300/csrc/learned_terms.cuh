@@ -21,8 +21,6 @@ constexpr float kEtaR = 16.f, kEtaA = 8.f;
 constexpr float kAngScale = 0.95f;
 constexpr float kTwoPowM31 = 4.656612873077393e-10f;  // 2^-31 = 2^(1 - zeta), zeta = 32
 
-__device__ __forceinline__ float fcut(float r, float rc) { return r < rc ? 0.5f * cosf(kPi * r / rc) + 0.5f : 0.f; }
-__device__ __forceinline__ float dfcut(float r, float rc) { return r < rc ? -0.5f * kPi / rc * sinf(kPi * r / rc) : 0.f; }
 
 __device__ __forceinline__ int pair_index(int a, int b) {
     if (a > b) {
@@ -43,23 +41,65 @@ struct NbrSmem {
     unsigned char ang[kKmax];     // neighbours within the angular cutoff, in row order
 };
 
-// Load atom i's neighbours into shared memory; returns the row length and the
-// numbers of neighbours within the radial and angular cutoffs.  The compacted
-// in-cutoff lists do not depend on how far the list radius reaches beyond the
-// cutoffs, so neither does any summation order below.
-__device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
-                                                int &cnt, int &nr, int &na) {
-    const float4 pi = pos4[i];
-    cnt = L.nb_count[i];
-    for (int q = lane; q < cnt; q += 32) {
-        const int j = L.nb_idx[(size_t)i * kKmax + q];
-        const float4 pj = pos4[j];
-        const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
-        s.j[q] = j;
-        s.el[q] = (signed char)L.el[j];
-        s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
-        s.fc[q] = make_float4(fcut(r, kRcRad), dfcut(r, kRcRad), fcut(r, kRcAng), dfcut(r, kRcAng));
+// Cosine cutoff and its derivative at both cutoffs from one sincospi each:
+// fc(r; rc) = (1 + cos(pi r / rc)) / 2, fc' = -pi / (2 rc) sin(pi r / rc), zero from rc on.
+__device__ __forceinline__ float4 cutoffs(float r) {
+    float sr, cr, sa, ca;
+    sincospif(r * (1.f / kRcRad), &sr, &cr);
+    sincospif(r * (1.f / kRcAng), &sa, &ca);
+    const bool inr = r < kRcRad, ina = r < kRcAng;
+    return make_float4(inr ? 0.5f * cr + 0.5f : 0.f, inr ? (-0.5f * kPi / kRcRad) * sr : 0.f,
+                       ina ? 0.5f * ca + 0.5f : 0.f, ina ? (-0.5f * kPi / kRcAng) * sa : 0.f);
+}
+
+// Atom i's neighbour row in registers: lane l holds entries l, l + 32, ...
+struct NbrFetch {
+    float4 pi;
+    int cnt;
+    int j[kKmax / 32];
+    float4 pj[kKmax / 32];
+    int ej[kKmax / 32];
+};
+
+// Issue every global load of atom i's neighbours: the count and the whole
+// index row at once (the row is allocated at full length, so this needs no
+// count), then the positions and elements of the entries below the count.
+// Two dependent memory round trips in all.
+__device__ __forceinline__ void fetch_neighbours(const LearnedDev &L, const float4 *pos4, int i, int lane,
+                                                 NbrFetch &f) {
+    f.pi = pos4[i];
+    f.cnt = L.nb_count[i];
+    const int *row = L.nb_idx + (size_t)i * kKmax;
+#pragma unroll
+    for (int k = 0; k < kKmax / 32; ++k) f.j[k] = row[lane + 32 * k];
+#pragma unroll
+    for (int k = 0; k < kKmax / 32; ++k) {
+        if (lane + 32 * k < f.cnt) {
+            f.pj[k] = pos4[f.j[k]];
+            f.ej[k] = L.el[f.j[k]];
+        }
+    }
+}
+
+// The fetched row into shared memory (geometry and cutoff values per entry);
+// returns the row length and the numbers of neighbours within the radial and
+// angular cutoffs.  The compacted in-cutoff lists do not depend on how far the
+// list radius reaches beyond the cutoffs, so neither does any summation order
+// below.
+__device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, int lane, int &cnt, int &nr,
+                                                 int &na) {
+    cnt = f.cnt;
+#pragma unroll
+    for (int k = 0; k < kKmax / 32; ++k) {
+        const int q = lane + 32 * k;
+        if (q < cnt) {
+            const float dx = f.pj[k].x - f.pi.x, dy = f.pj[k].y - f.pi.y, dz = f.pj[k].z - f.pi.z;
+            const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
+            s.j[q] = f.j[k];
+            s.el[q] = (signed char)f.ej[k];
+            s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
+            s.fc[q] = cutoffs(r);
+        }
     }
     __syncwarp();
     nr = 0;
@@ -76,6 +116,13 @@ __device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float
         na += __popc(ba);
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
+                                                int &cnt, int &nr, int &na) {
+    NbrFetch f;
+    fetch_neighbours(L, pos4, i, lane, f);
+    store_neighbours(f, s, lane, cnt, nr, na);
 }
 
 // Triplet t of the pairs (a, b), a < b, of na angular neighbours, in row-major order.
@@ -285,14 +332,9 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
         fiz += sz;
     }
     __syncwarp();
-    // angular triplets
-    float cpv[8], spv[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const float thp = (float)(2 * p + 1) * (kPi / 16.f);
-        cpv[p] = cosf(thp);
-        spv[p] = sinf(thp);
-    }
+    // angular triplets; cos and sin of theta_p = (2 p + 1) pi / 16 as literals (immediate operands)
+    constexpr float cpv[8] = {9.807852804e-01f, 8.314696123e-01f, 5.555702330e-01f, 1.950903220e-01f, -1.950903220e-01f, -5.555702330e-01f, -8.314696123e-01f, -9.807852804e-01f};
+    constexpr float spv[8] = {1.950903220e-01f, 5.555702330e-01f, 8.314696123e-01f, 9.807852804e-01f, 9.807852804e-01f, 8.314696123e-01f, 5.555702330e-01f, 1.950903220e-01f};
     const int ntrip = na * (na - 1) / 2;
     int kcur[kKmax / 32] = {0, 0, 0, 0};
     for (int t0 = 0; t0 < ntrip; t0 += Chunk) {
@@ -370,7 +412,7 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
 #pragma unroll
         for (int sl = 0; sl < kKmax / 32; ++sl) {
             const int a = lane + 32 * sl;
-            if (a >= na) break;
+            if (a >= na) continue;
             const int q = s.ang[a];
             float ax = A.f[q][0], ay = A.f[q][1], az = A.f[q][2];
             int b = kcur[sl];
