@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(kFuThreads, 1)
 k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const float4 *pos4,
         unsigned long long *fx, unsigned long long *efx, uint32_t *status) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned base (128-byte swizzle atoms), by pointer arithmetic on the shared array so that
+    // the compiler keeps the shared address space for every access through it
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(sm);
     unsigned char *res = sm;
     float *sb1 = (float *)(sm + kFuOffPar), *sb2 = sb1 + 256, *sw3 = sb2 + 128, *sEp = sw3 + 128;
@@ -242,8 +244,13 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = celu_tc(v[j] + sb1[cc * 32 + j]);
+                for (int j = 0; j < 32; ++j) {
+                    const float x = v[j] + sb1[cc * 32 + j], ex = exp10x_neg(x);
+                    v[j] = celu_e(x, ex);
+                    h[j] = dcelu_e(x, ex);
+                }
                 st_operand32(res, r, cc * 32, v);
+                tmem_st32(tl + cc * 32, h);   // celu'(H1 + b1) replaces H1 (read again by epi3)
             }
             proxy_fence();
             tc_fence_before();
@@ -257,9 +264,9 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int c = cg * 32 + j;
-                const float hv = v[j] + sb2[c];
-                E = fmaf(sw3[c], celu_tc(hv), E);
-                v[j] = sw3[c] * dcelu_tc(hv);
+                const float hv = v[j] + sb2[c], ex = exp10x_neg(hv);
+                E = fmaf(sw3[c], celu_e(hv, ex), E);
+                v[j] = sw3[c] * dcelu_e(hv, ex);
             }
             st_operand32(res, r, cg * 32, v);
             sEp[cg * 128 + r] = E;
@@ -280,9 +287,9 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
 #pragma unroll 1
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + 256 + cc * 32, v);
-                tmem_ld32(tl + cc * 32, h);
+                tmem_ld32(tl + cc * 32, h);   // celu'(H1 + b1), stored by epi1
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = v[j] * dcelu_tc(h[j] + sb1[cc * 32 + j]);
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * h[j];
                 st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();

@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
             const float r = d.w;
             const float rdot = d.x * (v[3 * j] - vix) + d.y * (v[3 * j + 1] - viy) + d.z * (v[3 * j + 2] - viz);
             const float x = r - Rk;
-            const float ex = expf(-kEtaR * x * x);
+            const float ex = __expf(-kEtaR * x * x);
             accR[w][h][16 * s.el[q] + k] += ex * (-2.f * kEtaR * x * s.fc[q].x + s.fc[q].y) * rdot;
         }
     }
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
 #pragma unroll
                 for (int mm = 0; mm < 4; ++mm) {
                     const float x = ravg - (0.9f + (float)mm * 0.65f);
-                    const float B = expf(-kEtaA * x * x);
+                    const float B = __expf(-kEtaA * x * x);
                     tB[w][lane][mm] = B;
                     tBd[w][lane][mm] = -2.f * kEtaA * x * B * ravgd;
                 }

@@ -2,18 +2,18 @@
 // input gradient dE/dG for one 128-row tile of same-element atoms per CTA.
 //
 //   GEMM1  H1 = G  W1^T      [128 x 256], K = 384   (TMEM columns   0..255)
-//   epi1   a1 = bf16(celu(H1 + b1))                  -> shared A operand
+//   epi1   a1 = bf16(celu(H1 + b1))                  -> shared A operand; celu'(H1 + b1) -> TMEM 0..255
 //   GEMM2  H2 = a1 W2^T      [128 x 128], K = 256   (TMEM columns 256..383)
 //   epi2   E  = W3 . celu(H2 + b2) + b3 + e0;  d2 = bf16(W3 * celu'(H2 + b2))
 //   GEMM3  P1 = d2 W2        [128 x 256], K = 128   (TMEM columns 256..511)
-//   epi3   d1 = bf16(P1 * celu'(H1 + b1))
+//   epi3   d1 = bf16(P1 * celu'(H1 + b1))           (celu' read back from TMEM, no exponential)
 //   GEMM4  g  = d1 W1        [128 x 384], K = 256   (TMEM columns 0..255, 256..383)
 //   epi4   g -> global FP32
 //
 // Operands are BF16 in shared memory in the 128-byte-swizzled K-major layout
 // (8-row x 128-byte atoms, the 16-byte unit index XOR-ed with the row index
-// mod 8); weight and feature K-chunks of 64 arrive by TMA through a two-stage
-// ring, the intermediate operands (a1, d2, d1) are written by the epilogue
+// mod 8); weight and feature K-chunks of 64 arrive by TMA through a three-stage
+// ring of 48 KB, the intermediate operands (a1, d2, d1) are written by the epilogue
 // warps straight into that layout.  Accumulation is FP32 in tensor memory.
 // Warps 0-15: epilogue (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. those
 // tile rows, and column group w / 4); warp 16: TMA producer; warp 17: TMEM
@@ -34,18 +34,22 @@ constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kTcThreads = kEpiThreads + 64;
 constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
-constexpr int kStageBytes = 64 * 1024;     // [A 16 KB][B 48 KB]
-constexpr int kStages = 2;
+constexpr int kStageBytes = 48 * 1024;     // GEMM1: [G 16 KB][W1 32 KB]; GEMM2-4: [W 16/32/48 KB]
+constexpr int kStages = 3;
 constexpr int kResBytes = 64 * 1024;       // resident A operand: a1 / d2 / d1
 constexpr int kOffRes = kStages * kStageBytes;
 constexpr int kOffPar = kOffRes + kResBytes;   // b1[256] b2[128] w3[128] E partials[4][128], FP32
 constexpr int kOffBar = kOffPar + 4096;
 constexpr int kGStride = 36;                   // padded row of a 32 x 32 FP32 staging block of g
 constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
+static_assert(kSmemBytes <= 232448, "shared memory");
+static_assert(kEpiWarps * 32 * kGStride * 4 <= kStages * kStageBytes, "g staging fits in the ring");
 constexpr int kChunks = 16;                    // 6 + 4 + 2 + 4 K-chunks of 64
 
-// barrier block: full[2] empty[2] acc epi drain, then tmem address, abort flag, issued, consumed
-enum { B_FULL = 0, B_EMPTY = 2, B_ACC = 4, B_EPI = 5, B_DRAIN = 6 };
+// barrier block: full[kStages] empty[kStages] acc epi drain, then (from byte 96) tmem address, abort
+// flag, issued, consumed
+enum { B_FULL = 0, B_EMPTY = kStages, B_ACC = 2 * kStages, B_EPI = 2 * kStages + 1, B_DRAIN = 2 * kStages + 2 };
+static_assert(8 * (B_DRAIN + 1) <= 96, "barrier block");
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
 
@@ -61,15 +65,17 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
     if (gated && L.lflags[1]) return;
     if (L.n_tiles_live != nullptr && (int)blockIdx.x >= *L.n_tiles_live) return;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned base (128-byte swizzle atoms), by pointer arithmetic on the shared array so that
+    // the compiler keeps the shared address space for every access through it
+    unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(sm);
     float *sb1 = (float *)(sm + kOffPar), *sb2 = sb1 + 256, *sw3 = sb2 + 128, *sEp = sw3 + 128;
     const uint32_t bar0 = sbase + kOffBar;
     auto bar = [&](int k) { return bar0 + 8u * (uint32_t)k; };
-    volatile uint32_t *s_tmem = (volatile uint32_t *)(sm + kOffBar + 64);
-    volatile int *s_abort = (volatile int *)(sm + kOffBar + 68);
-    volatile int *s_issued = (volatile int *)(sm + kOffBar + 72);
-    volatile int *s_consumed = (volatile int *)(sm + kOffBar + 76);
+    volatile uint32_t *s_tmem = (volatile uint32_t *)(sm + kOffBar + 96);
+    volatile int *s_abort = (volatile int *)(sm + kOffBar + 100);
+    volatile int *s_issued = (volatile int *)(sm + kOffBar + 104);
+    volatile int *s_consumed = (volatile int *)(sm + kOffBar + 108);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x;
@@ -77,10 +83,10 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
     const int e = L.tile_el[tile];
 
     if (tid == 0) {
-        mbar_init(bar(B_FULL), 1);
-        mbar_init(bar(B_FULL + 1), 1);
-        mbar_init(bar(B_EMPTY), 1);
-        mbar_init(bar(B_EMPTY + 1), 1);
+        for (int k = 0; k < kStages; ++k) {
+            mbar_init(bar(B_FULL + k), 1);
+            mbar_init(bar(B_EMPTY + k), 1);
+        }
         mbar_init(bar(B_ACC), 1);
         mbar_init(bar(B_EPI), kEpiThreads);
         mbar_init(bar(B_DRAIN), 1);
@@ -109,11 +115,11 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         // ---------------- TMA producer
         if (lane == 0) {
             for (int c = 0; c < kChunks; ++c) {
-                const int s = c & 1;
-                if (c >= 2 && !mbar_wait(bar(B_EMPTY + s), ((c >> 1) - 1) & 1, s_abort)) break;
+                const int s = c % kStages;
+                if (c >= kStages && !mbar_wait(bar(B_EMPTY + s), ((c / kStages) - 1) & 1, s_abort)) break;
                 int g, kc;
                 chunk_of(c, g, kc);
-                const uint32_t A = sbase + s * kStageBytes, B = A + 16384;
+                const uint32_t A = sbase + s * kStageBytes, B = g == 0 ? A + 16384 : A;
                 const int x = kc * 64;
                 const uint32_t fb = bar(B_FULL + s);
                 if (g == 0) {
@@ -151,14 +157,14 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
                 }
                 const int nk = g == 0 ? 6 : (g == 2 ? 2 : 4);
                 for (int kc = 0; kc < nk; ++kc, ++c) {
-                    const int s = c & 1;
-                    if (!mbar_wait(bar(B_FULL + s), (c >> 1) & 1, s_abort)) {
+                    const int s = c % kStages;
+                    if (!mbar_wait(bar(B_FULL + s), (c / kStages) & 1, s_abort)) {
                         ok = false;
                         break;
                     }
                     *s_consumed = c + 1;
                     tc_fence_after();
-                    const uint32_t A = sbase + s * kStageBytes, B = A + 16384;
+                    const uint32_t A = sbase + s * kStageBytes, B = g == 0 ? A + 16384 : A;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const uint32_t acc = (kc | k) != 0;
@@ -196,8 +202,13 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = celu_tc(v[j] + sb1[cc * 32 + j]);
+                for (int j = 0; j < 32; ++j) {
+                    const float x = v[j] + sb1[cc * 32 + j], ex = exp10x_neg(x);
+                    v[j] = celu_e(x, ex);
+                    h[j] = dcelu_e(x, ex);
+                }
                 st_operand32(res, r, cc * 32, v);
+                tmem_st32(tl + cc * 32, h);   // celu'(H1 + b1) replaces H1 (read again by epi3)
             }
             proxy_fence();
             tc_fence_before();
@@ -211,9 +222,9 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int c = cg * 32 + j;
-                const float hv = v[j] + sb2[c];
-                E = fmaf(sw3[c], celu_tc(hv), E);
-                v[j] = sw3[c] * dcelu_tc(hv);
+                const float hv = v[j] + sb2[c], ex = exp10x_neg(hv);
+                E = fmaf(sw3[c], celu_e(hv, ex), E);
+                v[j] = sw3[c] * dcelu_e(hv, ex);
             }
             st_operand32(res, r, cg * 32, v);
             sEp[cg * 128 + r] = E;
@@ -234,9 +245,9 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
 #pragma unroll 1
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + 256 + cc * 32, v);
-                tmem_ld32(tl + cc * 32, h);
+                tmem_ld32(tl + cc * 32, h);   // celu'(H1 + b1), stored by epi1
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = v[j] * dcelu_tc(h[j] + sb1[cc * 32 + j]);
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * h[j];
                 st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();
@@ -272,7 +283,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
     if (*s_abort) {
         // teardown after a timeout: let copies and MMAs in flight finish before freeing tensor memory
         if (tid == 0) {
-            for (int c = *s_consumed; c < *s_issued; ++c) mbar_drain(bar(B_FULL + (c & 1)), (c >> 1) & 1);
+            for (int c = *s_consumed; c < *s_issued; ++c) mbar_drain(bar(B_FULL + c % kStages), (c / kStages) & 1);
             atomicOr(status, MDPF_STATUS_TIMEOUT);
             atomicOr(&L.lflags[3], 1u);
         }

@@ -117,10 +117,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// CELU(0.1) and its derivative; exp(10 x) from the fast exponential (its error
-// is far below the BF16 rounding that follows on every operand path)
-__device__ __forceinline__ float celu_tc(float x) { return x > 0.f ? x : kCeluAlphaTc * (__expf(10.f * x) - 1.f); }
-__device__ __forceinline__ float dcelu_tc(float x) { return x >= 0.f ? 1.f : __expf(10.f * x); }
+// exp(10 x) = 2^(10 log2(e) x) for x <= 0, one ex2.approx instruction (subnormal
+// results flush to zero); its error is far below the BF16 rounding that follows
+// on every operand path.
+__device__ __forceinline__ float exp10x_neg(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fminf(x, 0.f) * 14.426950408889634f));
+    return y;
+}
+// CELU(0.1) and its derivative from one exponential: e = exp(10 min(x, 0)).
+__device__ __forceinline__ float celu_e(float x, float e) { return x > 0.f ? x : kCeluAlphaTc * (e - 1.f); }
+__device__ __forceinline__ float dcelu_e(float x, float e) { return x >= 0.f ? 1.f : e; }
+
+// 32 consecutive FP32 columns into this thread's TMEM lane (store and wait in one statement).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
+}
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
