@@ -13,7 +13,9 @@
 // (subnormal results flush to zero): the relative error grows with |x| but
 // stays below ~2e-6 wherever exp(x) is not negligible (x > -30), far inside
 // the FP32 feature tolerance, and the features and the adjoint use the same
-// one.
+// one.  Square roots and reciprocals are the approximate single-instruction
+// forms (a few ulp): every argument is bounded away from zero (distances
+// between distinct atoms, 1 - (0.95 cos)^2 >= 0.0975).
 #pragma once
 
 #include "learned.cuh"
@@ -42,14 +44,15 @@ __device__ __forceinline__ int pair_index(int a, int b) {
     return (a == 0 ? 0 : (a == 1 ? 4 : (a == 2 ? 7 : 9))) + (b - a);
 }
 
-// One atom's neighbours, per warp (4,992 bytes).
+// One atom's neighbours, per warp (5,008 bytes).
 struct NbrSmem {
     int j[kKmax];
     float4 d[kKmax];              // unit vector from i to j (x, y, z) and r
     float4 fc[kKmax];             // fc(r; 5.2), fc'(r; 5.2), fc(r; 3.5), fc'(r; 3.5)
     signed char el[kKmax];
     unsigned char rad[kKmax];     // neighbours within the radial cutoff, in row order
-    unsigned char ang[kKmax];     // neighbours within the angular cutoff, in row order
+    unsigned char ang[kKmax];     // neighbours within the angular cutoff, by element, in row order within one
+    int nae[4];                   // angular neighbours of each element
 };
 
 // Cosine cutoff and its derivative at both cutoffs from one sincospi each:
@@ -105,7 +108,7 @@ __device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, 
         const int q = lane + 32 * k;
         if (q < cnt) {
             const float dx = f.pj[k].x - f.pi.x, dy = f.pj[k].y - f.pi.y, dz = f.pj[k].z - f.pi.z;
-            const float r = sqrtf(dx * dx + dy * dy + dz * dz), ir = 1.f / r;
+            const float d2 = dx * dx + dy * dy + dz * dz, ir = rsqrtf(d2), r = d2 * ir;
             s.j[q] = f.j[k];
             s.el[q] = (signed char)f.ej[k];
             s.d[q] = make_float4(dx * ir, dy * ir, dz * ir, r);
@@ -113,19 +116,34 @@ __device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, 
         }
     }
     __syncwarp();
+    // radial list in row order; angular neighbours counted per element, then listed element by element
+    const unsigned int below = (1u << lane) - 1u;
     nr = 0;
-    na = 0;
+    int ne[4] = {0, 0, 0, 0};
     for (int base = 0; base < cnt; base += 32) {
         const int q = base + lane;
         const float r = q < cnt ? s.d[q].w : 1e30f;
-        const unsigned int below = (1u << lane) - 1u;
         const unsigned int br = __ballot_sync(0xffffffffu, r < kRcRad);
         if (r < kRcRad) s.rad[nr + __popc(br & below)] = (unsigned char)q;
         nr += __popc(br);
-        const unsigned int ba = __ballot_sync(0xffffffffu, r < kRcAng);
-        if (r < kRcAng) s.ang[na + __popc(ba & below)] = (unsigned char)q;
-        na += __popc(ba);
+        const int e = q < cnt ? s.el[q] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ne[k] += __popc(__ballot_sync(0xffffffffu, r < kRcAng && e == k));
     }
+    int at[4] = {0, ne[0], ne[0] + ne[1], ne[0] + ne[1] + ne[2]};
+    na = at[3] + ne[3];
+    for (int base = 0; base < cnt; base += 32) {
+        const int q = base + lane;
+        const bool in = q < cnt && s.d[q].w < kRcAng;
+        const int e = q < cnt ? s.el[q] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned int b = __ballot_sync(0xffffffffu, in && e == k);
+            if (in && e == k) s.ang[at[k] + __popc(b & below)] = (unsigned char)q;
+            at[k] += __popc(b);
+        }
+    }
+    if (lane < 4) s.nae[lane] = lane == 0 ? ne[0] : (lane == 1 ? ne[1] : (lane == 2 ? ne[2] : ne[3]));
     __syncwarp();
 }
 
@@ -150,23 +168,30 @@ __device__ __forceinline__ int triplet_index(int a, int b, int na) { return a * 
 
 // ------------------------------------------------------------------ features
 
-// Per-warp staging of one batch of 32 triplets, sorted by pair type (2,048 bytes).
+// Per-warp staging of one batch of 32 triplet slots, and the atom's pair-type
+// table (1,232 bytes).
 struct TripStage {
-    float4 q[64];   // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
-    float4 b[64];   // radial-shell factors of the 4 shells
+    float4 q[32];    // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
+    float4 b[32];    // radial-shell factors of the 4 shells
+    int4 type[10];   // per pair type: first slot, triplets, first angular index of e1 | of e2 << 8 | count of
+                     // e2 << 16, e1 == e2
+    float rcp[12];   // 1 / (count of e2)
 };
 
 // Features of one atom whose neighbours are in s.  On return lane l holds
 // G[32 b + l] in v[b], b = 0..11.
 //   radial: lane 16 h + k sums the in-cutoff neighbours u = h, h + 2, ... into
 //     its four per-element sums (registers), then the two halves are added;
-//   angular: each batch of 32 triplets is staged sorted by element pair
-//     (stable), each pair's run padded to a multiple of 4 with empty triplets;
-//     lane 8 t4 + p takes triplet t4 of every group of 4 (all of one pair
-//     type), computes its angular factor for section p once and adds it, times
-//     the 4 shell factors, to its 4 column sums (m = 0..3).  When the pair type
-//     changes, the 4 triplet slots are combined in a fixed shuffle order and
-//     lane 8 m + p adds sum m to its register for that pair, column
+//   angular: the angular neighbours are listed by element, so the triplets of
+//     pair type (e1, e2) are the pairs (a, b) with a in e1's range and b in
+//     e2's (a < b when e1 = e2).  The atom's triplets are laid out type by
+//     type, each type's run padded to a multiple of 4 slots with empty
+//     triplets, and processed in batches of 32 slots: each lane stages one
+//     slot's geometry; then lane 8 t4 + p takes slot t4 of every group of 4
+//     (all of one type), computes its angular factor for section p once and
+//     adds it, times the 4 shell factors, to its 4 column sums (m = 0..3).
+//     When the type changes the 4 slots are combined in a fixed shuffle order
+//     and lane 8 m + p adds sum m to its register for that pair, column
 //     64 + 32 P + 8 m + p.
 // Every sum is taken in a fixed order, so the result does not depend on the
 // caller.
@@ -195,8 +220,29 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
         const int t4 = lane >> 3, p = lane & 7;
         const float thp = (float)(2 * p + 1) * (kPi / 16.f);
         const float cp = cosf(thp), sp = sinf(thp);
-        const int ntrip = na * (na - 1) / 2;
-        const unsigned int below = (1u << lane) - 1u;
+        // the pair-type table (lane P writes type P) and the padded run starts (every lane)
+        int ne[4], st[4], off[10];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ne[e] = s.nae[e];
+        st[0] = 0;
+        st[1] = ne[0];
+        st[2] = st[1] + ne[1];
+        st[3] = st[2] + ne[2];
+        int total = 0;
+#pragma unroll
+        for (int P = 0; P < 10; ++P) {
+            // elements (e1 <= e2) of pair type P, in the column order of the angular blocks
+            constexpr int e1s[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3}, e2s[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+            const int e1 = e1s[P], e2 = e2s[P];
+            const int n = e1 == e2 ? ne[e1] * (ne[e1] - 1) / 2 : ne[e1] * ne[e2];
+            if (lane == P) {
+                ts.type[P] = make_int4(total, n, st[e1] | (st[e2] << 8) | (ne[e2] << 16), e1 == e2 ? 1 : 0);
+                ts.rcp[P] = ne[e2] > 0 ? 1.f / (float)ne[e2] : 0.f;
+            }
+            off[P] = total;
+            total += (n + 3) & ~3;
+        }
+        __syncwarp();
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         float areg[10];
 #pragma unroll
@@ -217,49 +263,48 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
             for (int k = 0; k < 10; ++k)
                 if (k == curP) areg[k] += mine;
         };
-        for (int base = 0; base < ntrip; base += 32) {
-            const int t = base + lane;
-            int P = 15;   // no triplet
+        for (int base = 0; base < total; base += 32) {
+            const int slot = base + lane;
+            int P = 0;
+#pragma unroll
+            for (int k = 1; k < 10; ++k) P += slot >= off[k] ? 1 : 0;
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f), bq = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (t < ntrip) {
-                int a, b;
-                triplet_ab(t, na, a, b);
-                const int qa = s.ang[a], qb = s.ang[b];
-                const float4 dj = s.d[qa], dk = s.d[qb];
-                const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
-                const float cs = kAngScale * ct;
-                q = make_float4(cs, sqrtf(1.f - cs * cs), kTwoPowM31 * s.fc[qa].z * s.fc[qb].z, 0.f);
-                const float ravg = 0.5f * (dj.w + dk.w);
-                float bm[4];
+            if (slot < total) {
+                const int4 ty = ts.type[P];
+                const int l = slot - ty.x;
+                if (l < ty.y) {
+                    const int a0 = ty.z & 255, b0 = (ty.z >> 8) & 255, c2 = ty.z >> 16;
+                    int a, b;
+                    if (ty.w) {   // both neighbours of one element: pairs a < b of its range
+                        triplet_ab(l, c2, a, b);
+                        a += a0;
+                        b += a0;
+                    } else {      // a in e1's range, b in e2's (exact: l < 2^14)
+                        a = (int)(((float)l + 0.5f) * ts.rcp[P]);
+                        b = b0 + (l - a * c2);
+                        a += a0;
+                    }
+                    const int qa = s.ang[a], qb = s.ang[b];
+                    const float4 dj = s.d[qa], dk = s.d[qb];
+                    const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
+                    const float cs = kAngScale * ct;
+                    const float s2 = 1.f - cs * cs;   // >= 1 - 0.95^2
+                    q = make_float4(cs, s2 * rsqrtf(s2), kTwoPowM31 * s.fc[qa].z * s.fc[qb].z, 0.f);
+                    const float ravg = 0.5f * (dj.w + dk.w);
+                    float bm[4];
 #pragma unroll
-                for (int mm = 0; mm < 4; ++mm) {
-                    const float x = ravg - (0.9f + (float)mm * 0.65f);
-                    bm[mm] = exp_neg(-kEtaA * x * x);
+                    for (int mm = 0; mm < 4; ++mm) {
+                        const float x = ravg - (0.9f + (float)mm * 0.65f);
+                        bm[mm] = exp_neg(-kEtaA * x * x);
+                    }
+                    bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
                 }
-                bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
-                P = pair_index(s.el[qa], s.el[qb]);
             }
-            // padded, stable counting sort by pair type; empty slots of a run stay zero (no contribution)
-            int pos = 0, before = 0;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                const unsigned int bal = __ballot_sync(0xffffffffu, P == k);
-                const int cnt_k = __popc(bal);
-                if (P == k) pos = before + __popc(bal & below);
-                const int padded = (cnt_k + 3) & ~3;
-                if (lane >= cnt_k && lane < padded) {
-                    ts.q[before + lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(k));
-                    ts.b[before + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                before += padded;
-            }
-            if (t < ntrip) {
-                q.w = __int_as_float(P);
-                ts.q[pos] = q;
-                ts.b[pos] = bq;
-            }
+            q.w = __int_as_float(P);   // empty slots of a run carry its type and contribute zero
+            ts.q[lane] = q;
+            ts.b[lane] = bq;
             __syncwarp();
-            const int ng = before;   // padded length, a multiple of 4
+            const int ng = min(32, total - base);   // a multiple of 4
             for (int u = 0; u < ng; u += 4) {
                 const float4 qq = ts.q[u + t4];
                 const int Pu = __float_as_int(ts.q[u].w);   // the group's pair type, the same in every lane
@@ -356,13 +401,14 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
             const int qa = s.ang[a], qb = s.ang[b];
             const float4 dj = s.d[qa], dk = s.d[qb];
             const float rj = dj.w, rk = dk.w;
-            const float irj = 1.f / rj, irk = 1.f / rk;
+            const float irj = __fdividef(1.f, rj), irk = __fdividef(1.f, rk);
             const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
             const float ukx = dk.x, uky = dk.y, ukz = dk.z;
             const float ct = ujx * ukx + ujy * uky + ujz * ukz;
             const float cs = kAngScale * ct;
-            const float sn2 = sqrtf(1.f - cs * cs);
-            const float cot = cs / sn2;
+            const float s2 = 1.f - cs * cs, isn = rsqrtf(s2);   // s2 >= 1 - 0.95^2
+            const float sn2 = s2 * isn;
+            const float cot = cs * isn;
             const float fj = s.fc[qa].z, fk = s.fc[qb].z;
             const float dfj = s.fc[qa].w, dfk = s.fc[qb].w;
             const float C = fj * fk;
