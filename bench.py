@@ -60,7 +60,7 @@ ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 # DRAM bytes (read + write) per launch of each learned kernel on this workload, from the ncu capture in
 # profiles/learned_step_cluster16384.md (valid for the kernels as captured there)
-LEARNED_TRAFFIC = {"adjoint": 28260864, "features": 2702080, "mlp": 15012864}
+LEARNED_TRAFFIC = {"adjoint": 34463232, "features": 8897024, "mlp": 14992384, "fused": 11452672}
 
 
 def peaks():
@@ -420,6 +420,7 @@ def fused_arm(args, s, v0, blob, stream, flush, x_ref):
     rate = args.steps * md / (ms / 1000.0)
     return {"value": rate, "unit": UNIT, "ms_per_md_step": ms / args.steps / md,
             "fused_kernel_us": 1e3 * f_ms / max(f_n, 1), "fused_launches": f_n,
+            "traffic": LEARNED_TRAFFIC["fused"],
             "neighbors_us": 1e3 * nb_ms / max(nb_n, 1),
             "same_trajectory_as_stagewise": bool(np.array_equal(x_end, x_ref)),
             "what": "features, tensor-core MLP and adjoint in one kernel per force evaluation (one CTA per tile "
