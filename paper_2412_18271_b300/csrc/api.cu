@@ -536,8 +536,7 @@ int mdpf_get_state(mdpf_ctx *c, double *pos, double *vel) {
 
 // One learned-mode MD step: kick-drift, rebuild check, learned forces, kick.
 static int enqueue_learned_step(mdpf_ctx *c, bool energy, cudaStream_t s) {
-    launch_kick_drift(c, s);
-    learned_enqueue_step_prologue(c, s);
+    launch_kick_drift(c, s);   // also requests a list rebuild when one is due
     cudaEvent_t pn = prof_begin(c, s);
     const int rc = learned_enqueue_forces(c, c->d_pos4, c->d_fx, c->d_efx, c->d_status, false, false, s);
     if (rc != MDPF_OK) return rc;

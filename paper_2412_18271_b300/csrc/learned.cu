@@ -234,17 +234,6 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
     }
 }
 
-// Request a rebuild when an atom moved more than skin/2 since the last build,
-// or when the completed-step count is a multiple of rebuild_every.
-__global__ void k_nb_disp(LearnedDev L, const float4 *pos4, const int64_t *step, int rebuild_every) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a == 0 && rebuild_every > 0 && (*step % rebuild_every) == 0) atomicOr(&L.lflags[0], 1u);
-    if (a >= L.n) return;
-    const float4 p = pos4[a], b = L.pos_build[a];
-    const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
-    if (dx * dx + dy * dy + dz * dz > L.half_skin2) atomicOr(&L.lflags[0], 1u);
-}
-
 // ------------------------------------------------------------------ features
 
 constexpr int kFeatWarps = 4;
@@ -585,10 +574,6 @@ cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forc
     void *args[] = {&Lc, &p, &status, &f, &limit};
     return cudaLaunchCooperativeKernel((const void *)k_nb_all, dim3(grid > 0 ? grid : 1), dim3(kNbThreads), args, 0,
                                        s);
-}
-
-void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s) {
-    k_nb_disp<<<(L.n + 255) / 256, 256, 0, s>>>(L, pos4, step, rebuild_every);
 }
 
 void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s) {

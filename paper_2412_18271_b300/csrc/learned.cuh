@@ -75,7 +75,6 @@ struct FusedTiles {
 int learned_nb_grid();
 cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status,
                               cudaStream_t s);
-void learned_displacement(const LearnedDev &L, const float4 *pos4, int64_t *step, int rebuild_every, cudaStream_t s);
 void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s);
 // MLP on the CUDA cores; efx (or null) receives the summed energy in its learned-energy slot
 void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long *efx, cudaStream_t s);

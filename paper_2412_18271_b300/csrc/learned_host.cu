@@ -377,11 +377,11 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     return MDPF_OK;
 }
 
-// Per step, before the force evaluation: request a list rebuild when due.
-int learned_enqueue_step_prologue(mdpf_ctx *c, cudaStream_t s) {
-    LearnedHost *h = lh(c);
-    learned_displacement(h->dev, c->d_pos4, c->d_step, h->rebuild_every, s);
-    return MDPF_OK;
+// The per-step rebuild request, checked by the kick-drift kernel: an atom moved more than skin/2 since the
+// last build, or the completed-step count is a multiple of rebuild_every.
+DispCheck learned_disp_check(const mdpf_ctx *c) {
+    const LearnedHost *h = lh(c);
+    return DispCheck{h->dev.pos_build, h->dev.lflags, h->dev.half_skin2, h->rebuild_every};
 }
 
 }  // namespace mdpf

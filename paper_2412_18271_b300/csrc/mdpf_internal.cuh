@@ -60,6 +60,14 @@ struct LangevinDev {
     const int64_t *step;     // completed steps (the noise counter)
 };
 
+// Learned mode: the neighbour-list displacement check done in the kick-drift kernel.
+struct DispCheck {
+    const float4 *pos_build;   // positions at the last list build, or null (no check)
+    unsigned int *flag;        // set to request a rebuild
+    float half_skin2;          // (skin / 2)^2
+    int rebuild_every;         // also request one when the completed-step count is a multiple of this
+};
+
 struct Frames {
     double *pos;      // [cap][n][3]
     double *energy;   // [cap]
@@ -113,7 +121,7 @@ struct mdpf_ctx {
     double *d_trace_u = nullptr, *d_trace_k = nullptr;
     int64_t *d_trace_step = nullptr;
     int64_t *d_step = nullptr;             // device step counter
-    uint32_t *d_status = nullptr;          // [0] state, [1] compute()
+    uint32_t *d_status = nullptr;          // [0] state, [1] compute(), [3] block ticket of the kick-finish kernel
     double *d_xc = nullptr;                // compute() FP64 position staging [n][3]
     double *d_fc = nullptr;                // compute() FP64 forces out [n][3]
     double *d_scalar = nullptr;            // [16]: [0] U, [1] K of the state; [2..7] compute outputs
@@ -201,7 +209,7 @@ int learned_create(mdpf_ctx *ctx, const mdpf_topology *t, const mdpf_params *prm
 void learned_free(mdpf_ctx *ctx);
 int learned_enqueue_forces(mdpf_ctx *ctx, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
                            uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s);
-int learned_enqueue_step_prologue(mdpf_ctx *ctx, cudaStream_t s);
+DispCheck learned_disp_check(const mdpf_ctx *ctx);
 
 // stepper.cu
 int stepper_grid(const mdpf_ctx *ctx);

@@ -143,10 +143,13 @@ __device__ __forceinline__ void langevin_normals(unsigned long long seed, long l
 
 // Velocity Verlet:  v += dt/2 a(F);  x += dt v.
 // Langevin (lang != null), BAOAB:  v += dt/2 a(F);  x += dt/2 v;  v = c1 v + c2 R;  x += dt/2 v.
-// Then the FP32 copy is refreshed and the force accumulators cleared.
+// Then the FP32 copy is refreshed and the force accumulators cleared.  With a
+// displacement check (learned mode), a neighbour-list rebuild is requested
+// when the new FP32 position is more than skin/2 from the one at the last
+// build, or when the completed-step count is a multiple of rebuild_every.
 __global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over_m, double *x, double *v,
                              unsigned long long *fx, float4 *pos4, const float *qs, unsigned long long *efx,
-                             LangevinDev lang) {
+                             LangevinDev lang, DispCheck dc) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < E_SLOTS && efx != nullptr) efx[a] = 0ull;
     if (a >= n) {
@@ -184,7 +187,14 @@ __global__ void k_kick_drift(int n, int n_pad, double dt, const double *hdt_over
             fx[3 * a + c] = 0ull;
         }
     }
-    pos4[a] = make_float4((float)p[0], (float)p[1], (float)p[2], qs[a]);
+    const float4 p4 = make_float4((float)p[0], (float)p[1], (float)p[2], qs[a]);
+    pos4[a] = p4;
+    if (dc.pos_build != nullptr) {
+        if (a == 0 && dc.rebuild_every > 0 && (*lang.step % dc.rebuild_every) == 0) atomicOr(dc.flag, 1u);
+        const float4 b = dc.pos_build[a];
+        const float dx = p4.x - b.x, dy = p4.y - b.y, dz = p4.z - b.z;
+        if (dx * dx + dy * dy + dz * dz > dc.half_skin2) atomicOr(dc.flag, 1u);
+    }
 }
 
 // v += dt/2 a(F_new) (when do_kick); kinetic energy into the fixed-point slot (when energy).
@@ -210,45 +220,76 @@ __global__ void k_kick(int n, const double *hdt_over_m, const double *mass, doub
     if ((threadIdx.x & 31) == 0 && ke != 0.0) fx_add_d(&efx[E_KIN], ke);
 }
 
-// After a step: counters; on energy steps the trace entry and the non-finite
-// check.  One thread.
-__global__ void k_finish_step(const unsigned long long *efx, double *trace_u, double *trace_k,
-                              int64_t *trace_step, int cap, int energy_every, int64_t *step, uint32_t *status,
-                              double *scalars, int energy) {
-    if (threadIdx.x != 0) return;
-    const int64_t s = *step + 1;
-    *step = s;
-    if (!energy) return;
-    double U = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]) +
-               fx_val(efx[E_LEARN]);
-    double K = fx_val(efx[E_KIN]);
-    const int64_t e = s / energy_every - 1;
-    trace_u[e % cap] = U;
-    trace_k[e % cap] = K;
-    trace_step[e % cap] = s;
-    scalars[0] = U;
-    scalars[1] = K;
-    // fixed-point slots saturate rather than turn NaN: treat huge values as non-finite too
-    bool bad = !isfinite(U) || !isfinite(K) || fabs(U) > 1e9 || fabs(K) > 1e9;
-    if (bad) atomicOr(status, MDPF_STATUS_NONFINITE);
-}
+// End of a step, one kernel: v += dt/2 a(F_new); the kinetic energy on energy
+// steps; the frame (positions, forces) when the completed step is recorded.
+// The last block to finish (a ticket counter, reset by that block) then does
+// the single-thread part: the step counter, and on energy steps the trace
+// entry, the scalars and the non-finite check; the recorded frame's energy and
+// step.
+struct FinishArgs {
+    const double *x;
+    double *trace_u, *trace_k;
+    int64_t *trace_step;
+    int cap, energy_every, record_every;
+    int64_t *step;
+    uint32_t *status;
+    double *scalars;
+    unsigned int *ticket;
+    Frames frames;
+};
 
-__global__ void k_record(int n, int every, const int64_t *step, const double *x, const unsigned long long *fx,
-                         const double *scalars, Frames fr) {
-    const int64_t s = *step;  // steps completed
-    if (every <= 0 || s % every != 0) return;
-    const int64_t f = s / every - 1;
-    const int slot = (int)(f % fr.cap);
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_kick_finish(int n, const double *hdt_over_m, const double *mass, double *v,
+                              const unsigned long long *fx, unsigned long long *efx, int energy, FinishArgs f) {
+    __shared__ int s_last;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = *f.step + 1;   // the step being completed
+    const bool rec = f.record_every > 0 && f.frames.cap > 0 && s % f.record_every == 0;
+    const int slot = rec ? (int)((s / f.record_every - 1) % f.frames.cap) : 0;
+    double ke = 0.0;
     if (a < n) {
+        const double h = hdt_over_m[a];
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            fr.pos[((size_t)slot * n + a) * 3 + c] = x[3 * a + c];
-            fr.forces[((size_t)slot * n + a) * 3 + c] = (float)fx_val(fx[3 * a + c]);
+            const double fc = fx_val(fx[3 * a + c]);
+            const double vc = fma(h, fc, v[3 * a + c]);
+            v[3 * a + c] = vc;
+            ke += vc * vc;
+            if (rec) {
+                f.frames.pos[((size_t)slot * n + a) * 3 + c] = f.x[3 * a + c];
+                f.frames.forces[((size_t)slot * n + a) * 3 + c] = (float)fc;
+            }
         }
+        ke *= 0.5 * mass[a] / kAcc;
     }
-    if (a == 0) {
-        fr.energy[slot] = scalars[0];
-        fr.step[slot] = s;
+    if (energy) {
+        ke = warp_sum_d(ke);
+        if ((threadIdx.x & 31) == 0 && ke != 0.0) fx_add_d(&efx[E_KIN], ke);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(f.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    *f.ticket = 0u;
+    __threadfence();
+    *f.step = s;
+    if (energy) {
+        const double U = fx_val(__ldcg(&efx[E_BOND])) + fx_val(__ldcg(&efx[E_ANGLE])) + fx_val(__ldcg(&efx[E_LJ])) +
+                         fx_val(__ldcg(&efx[E_COUL])) + fx_val(__ldcg(&efx[E_LEARN]));
+        const double K = fx_val(__ldcg(&efx[E_KIN]));
+        const int64_t e = s / f.energy_every - 1;
+        f.trace_u[e % f.cap] = U;
+        f.trace_k[e % f.cap] = K;
+        f.trace_step[e % f.cap] = s;
+        f.scalars[0] = U;
+        f.scalars[1] = K;
+        // fixed-point slots saturate rather than turn NaN: treat huge values as non-finite too
+        const bool bad = !isfinite(U) || !isfinite(K) || fabs(U) > 1e9 || fabs(K) > 1e9;
+        if (bad) atomicOr(f.status, MDPF_STATUS_NONFINITE);
+    }
+    if (rec) {
+        f.frames.energy[slot] = f.scalars[0];
+        f.frames.step[slot] = s;
     }
 }
 
@@ -333,20 +374,17 @@ constexpr int kIntThreads = 32;
 
 void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s) {
     int m = ctx->n_pad > E_SLOTS ? ctx->n_pad : E_SLOTS;
+    const DispCheck dc = ctx->mode == MDPF_MODE_LEARNED ? learned_disp_check(ctx) : DispCheck{nullptr, nullptr, 0.f, 0};
     k_kick_drift<<<(m + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(
         ctx->n, ctx->n_pad, ctx->dt, ctx->d_hdt_m, ctx->d_x, ctx->d_v, ctx->d_fx, ctx->d_pos4, ctx->d_charge_s,
-        ctx->d_efx, LangevinDev{ctx->d_lang_c2, ctx->lang_c1, ctx->lang_seed, ctx->d_step});
+        ctx->d_efx, LangevinDev{ctx->d_lang_c2, ctx->lang_c1, ctx->lang_seed, ctx->d_step}, dc);
 }
 
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s) {
-    k_kick<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(ctx->n, ctx->d_hdt_m, ctx->d_mass,
-                                                                              ctx->d_v, ctx->d_fx, ctx->d_efx, 1,
-                                                                              energy ? 1 : 0);
-    k_finish_step<<<1, 32, 0, s>>>(ctx->d_efx, ctx->d_trace_u, ctx->d_trace_k, ctx->d_trace_step, ctx->trace_cap,
-                                   ctx->energy_every, ctx->d_step, ctx->d_status, ctx->d_scalar, energy ? 1 : 0);
-    if (ctx->record_every > 0 && ctx->frames.cap > 0)
-        k_record<<<(ctx->n + 255) / 256, 256, 0, s>>>(ctx->n, ctx->record_every, ctx->d_step, ctx->d_x, ctx->d_fx,
-                                                      ctx->d_scalar, ctx->frames);
+    FinishArgs f{ctx->d_x, ctx->d_trace_u, ctx->d_trace_k, ctx->d_trace_step, ctx->trace_cap, ctx->energy_every,
+                 ctx->record_every, ctx->d_step, ctx->d_status, ctx->d_scalar, ctx->d_status + 3, ctx->frames};
+    k_kick_finish<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(
+        ctx->n, ctx->d_hdt_m, ctx->d_mass, ctx->d_v, ctx->d_fx, ctx->d_efx, energy ? 1 : 0, f);
 }
 
 // Kinetic energy of the current velocities into efx[E_KIN] (no kick).
