@@ -135,7 +135,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
             if (r < cnt) {
                 const int i = L.atom_of[row0 + r];
                 int nc, nr, na;
-                load_neighbours(L, pos4, i, sn, lane, nc, nr, na);
+                load_neighbours<true>(L, pos4, i, sn, lane, nc, nr, na);
                 feature_row(sn, nr, na, ts, lane, v);
                 if (L.lo != nullptr) {
 #pragma unroll
@@ -326,7 +326,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                 if (k >= 64 || rr >= cnt || *s_abort) break;
                 const int i = L.atom_of[row0 + rr];
                 int nc, nr, na;
-                load_neighbours(L, pos4, i, sn, lane, nc, nr, na);
+                load_neighbours<false>(L, pos4, i, sn, lane, nc, nr, na);
                 adjoint_atom(i, sn, nc, nr, na, gst + k * kGRow, A, fx, lane);
             }
             fu_sync();   // the half's g rows are no longer read

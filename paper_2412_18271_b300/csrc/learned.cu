@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
     const int i = blockIdx.x * kFeatWarps + w;
     if (i >= L.n) return;
     int cnt, nr, na;
-    load_neighbours(L, pos4, i, sn[w], lane, cnt, nr, na);
+    load_neighbours<true>(L, pos4, i, sn[w], lane, cnt, nr, na);
     float v[12];
     feature_row(sn[w], nr, na, st[w], lane, v);
     const int row = L.row_of[i];
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
 #pragma unroll
     for (int b = 0; b < kNFeat / 32; ++b) sg[w][g_col(32 * b + lane)] = gv[b];
     int cnt, nr, na;
-    store_neighbours(nf, sn[w], lane, cnt, nr, na);
+    store_neighbours<false>(nf, sn[w], lane, cnt, nr, na);
     adjoint_atom(i, sn[w], cnt, nr, na, sg[w], sa[w], fx, lane);
 }
 
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const flo
     for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
     for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
     int cnt, nr, na;
-    load_neighbours(L, pos4, i, s, lane, cnt, nr, na);
+    load_neighbours<false>(L, pos4, i, s, lane, cnt, nr, na);
     const float vix = v[3 * i], viy = v[3 * i + 1], viz = v[3 * i + 2];
     {
         const int h = lane >> 4, k = lane & 15;

@@ -51,8 +51,8 @@ struct NbrSmem {
     float4 fc[kKmax];             // fc(r; 5.2), fc'(r; 5.2), fc(r; 3.5), fc'(r; 3.5)
     signed char el[kKmax];
     unsigned char rad[kKmax];     // neighbours within the radial cutoff, in row order
-    unsigned char ang[kKmax];     // neighbours within the angular cutoff, by element, in row order within one
-    int nae[4];                   // angular neighbours of each element
+    unsigned char ang[kKmax];     // neighbours within the angular cutoff (by element for the features)
+    int nae[4];                   // angular neighbours of each element (features)
 };
 
 // Cosine cutoff and its derivative at both cutoffs from one sincospi each:
@@ -97,9 +97,11 @@ __device__ __forceinline__ void fetch_neighbours(const LearnedDev &L, const floa
 
 // The fetched row into shared memory (geometry and cutoff values per entry);
 // returns the row length and the numbers of neighbours within the radial and
-// angular cutoffs.  The compacted in-cutoff lists do not depend on how far the
+// angular cutoffs.  ByElement: the angular list element by element (and the
+// per-element counts), as the features need; otherwise in row order.  The compacted in-cutoff lists do not depend on how far the
 // list radius reaches beyond the cutoffs, so neither does any summation order
 // below.
+template <bool ByElement>
 __device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, int lane, int &cnt, int &nr,
                                                  int &na) {
     cnt = f.cnt;
@@ -116,8 +118,24 @@ __device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, 
         }
     }
     __syncwarp();
-    // radial list in row order; angular neighbours counted per element, then listed element by element
     const unsigned int below = (1u << lane) - 1u;
+    if (!ByElement) {   // both lists in row order
+        nr = 0;
+        na = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            const int q = base + lane;
+            const float r = q < cnt ? s.d[q].w : 1e30f;
+            const unsigned int br = __ballot_sync(0xffffffffu, r < kRcRad);
+            if (r < kRcRad) s.rad[nr + __popc(br & below)] = (unsigned char)q;
+            nr += __popc(br);
+            const unsigned int ba = __ballot_sync(0xffffffffu, r < kRcAng);
+            if (r < kRcAng) s.ang[na + __popc(ba & below)] = (unsigned char)q;
+            na += __popc(ba);
+        }
+        __syncwarp();
+        return;
+    }
+    // radial list in row order; angular neighbours counted per element, then listed element by element
     nr = 0;
     int ne[4] = {0, 0, 0, 0};
     for (int base = 0; base < cnt; base += 32) {
@@ -147,11 +165,12 @@ __device__ __forceinline__ void store_neighbours(const NbrFetch &f, NbrSmem &s, 
     __syncwarp();
 }
 
+template <bool ByElement>
 __device__ __forceinline__ void load_neighbours(const LearnedDev &L, const float4 *pos4, int i, NbrSmem &s, int lane,
                                                 int &cnt, int &nr, int &na) {
     NbrFetch f;
     fetch_neighbours(L, pos4, i, lane, f);
-    store_neighbours(f, s, lane, cnt, nr, na);
+    store_neighbours<ByElement>(f, s, lane, cnt, nr, na);
 }
 
 // Triplet t of the pairs (a, b), a < b, of na angular neighbours, in row-major order.
@@ -461,6 +480,38 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
             fiz += gjz + gkz;
         }
         __syncwarp();
+        if (ntrip <= Chunk) {
+            // one chunk holds every triplet: the same sums, with partner loops of fixed length
+#pragma unroll
+            for (int sl = 0; sl < kKmax / 32; ++sl) {
+                const int a = lane + 32 * sl;
+                if (a >= na) continue;
+                const int q = s.ang[a];
+                float ax = A.f[q][0], ay = A.f[q][1], az = A.f[q][2];
+                int t = a - 1;   // triplet (0, a); it grows by na - 2 - b from partner b to b + 1
+#pragma unroll 4
+                for (int b = 0; b < a; ++b) {
+                    const float *v = A.tk[t];
+                    ax += v[0];
+                    ay += v[1];
+                    az += v[2];
+                    t += na - 2 - b;
+                }
+                const int ra = triplet_index(a, a + 1, na), rb = ra + (na - a - 1);
+#pragma unroll 4
+                for (int u = ra; u < rb; ++u) {
+                    const float *v = A.tj[u];
+                    ax += v[0];
+                    ay += v[1];
+                    az += v[2];
+                }
+                A.f[q][0] = ax;
+                A.f[q][1] = ay;
+                A.f[q][2] = az;
+            }
+            __syncwarp();
+            continue;
+        }
         // each lane, for its angular neighbours a = lane + 32 sl: the staged contributions of
         // this chunk, in triplet order.  Those of the triplets (b, a), b < a, come first (their
         // indices grow with b; kcur carries the next b across chunks), then those of (a, b),
