@@ -92,6 +92,24 @@ cudaError_t learned_mlp_tc_prepare();
 cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *status, bool gated,
                            unsigned long long *efx, cudaStream_t s);
 
+// training (wgrad_tc.cu): dW1 and dW2 of the force-matching loss on the tensor cores, as K-split GEMMs
+// over each element's row tiles, the splits summed in order into grad[e * per_element + off + ...]
+constexpr int kWgSplits = 24;
+struct WgradIn {
+    const float *bh1, *bt1, *G, *U;       // [rows][256], [rows][256], [rows][384], [rows][384]
+    const float *bh2, *bt2, *a1, *ta1;    // [rows][128], [rows][128], [rows][256], [rows][256]
+    const int *atom_of, *tile_el, *n_live;
+    int tiles_max;
+    int *etiles;                          // scratch [4][tiles_max]
+    int4 *split;                          // scratch [kWgSplits]
+    float *part;                          // scratch kWgSplits * (256 * 384 + 128 * 256) floats
+    float *grad;
+    int per_element, off_w1, off_w2;
+    uint32_t *status;
+};
+cudaError_t learned_wgrad_tc_prepare();
+cudaError_t learned_wgrad_tc(const WgradIn &w, cudaStream_t s);
+
 // fused features -> MLP -> adjoint (fused.cu): energies per row, the energy slot of efx and fixed-point
 // forces fx, with G and dE/dG kept on chip; sets the range flag like the feature kernel
 cudaError_t learned_fused_prepare();

@@ -395,54 +395,6 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
 
 // ------------------------------------------------------------ weight gradients
 
-// out[split][e][m][n] = sum over the split's rows of element e of
-//   A0[r][m] B0[r][n] + A1[r][m] B1[r][n]
-// (rows of padding atoms skipped), 64 x 64 output tile per block, FP32, fixed order.
-template <int M, int N>
-__global__ void __launch_bounds__(256) k_wgrad(LearnedDev L, const float *A0, const float *A1, const float *B0,
-                                               const float *B1, int tiles_max, float *out) {
-    __shared__ __align__(16) float As[32][64 + 4];
-    __shared__ __align__(16) float Bs[32][64 + 4];
-    const int mt = blockIdx.x, nt = blockIdx.y;
-    const int e = blockIdx.z / kSplits, sp = blockIdx.z % kSplits;
-    const int live = *L.n_tiles_live;
-    const int t0 = (int)((long long)tiles_max * sp / kSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kSplits);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[4][4] = {};
-    for (int tile = t0; tile < t1 && tile < live; ++tile) {
-        if (L.tile_el[tile] != e) continue;
-        for (int k0 = tile * kRowTile; k0 < (tile + 1) * kRowTile; k0 += 16) {
-            // 16 rows x (A0 | A1) and (B0 | B1) -> 32 K-slices
-            for (int q = threadIdx.x; q < 32 * 64; q += 256) {
-                const int kk = q >> 6, c = q & 63;
-                const int r = k0 + (kk & 15);
-                const bool re = L.atom_of[r] >= 0;
-                const float *A = kk < 16 ? A0 : A1;
-                const float *Bp = kk < 16 ? B0 : B1;
-                As[kk][c] = re ? A[(size_t)r * M + mt * 64 + c] : 0.f;
-                Bs[kk][c] = re ? Bp[(size_t)r * N + nt * 64 + c] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < 32; ++kk) {
-                const float4 av = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-                const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-                const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(a[u], b[w], acc[u][w]);
-            }
-            __syncthreads();
-        }
-    }
-    float *o = out + ((size_t)(sp * 4 + e) * M) * N;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) o[(size_t)(mt * 64 + ty * 4 + u) * N + nt * 64 + tx * 4 + w] = acc[u][w];
-}
-
 // out[split][e][j] = sum over the split's rows of element e of X[r][j] (X = null: c_row), fixed order.
 __global__ void k_vgrad(LearnedDev L, const float *X, const float *c_row, int len, int tiles_max, float *out) {
     const int e = blockIdx.y / kVSplits, sp = blockIdx.y % kVSplits;
@@ -504,6 +456,8 @@ struct mdpf_trainer {
     float *d_c = nullptr, *d_v = nullptr, *d_U = nullptr;
     RowOut ro{};
     float *d_part = nullptr;
+    int *d_etiles = nullptr;
+    int4 *d_wsplit = nullptr;
     double *d_lparts = nullptr;
     unsigned int *d_rmin = nullptr, *d_rmax = nullptr;
     std::string err;
@@ -621,6 +575,10 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     TA(t->ro.bt2, R * kH2);
     TA(t->ro.w3g, R * kH2);
     TA(t->d_part, (size_t)kSplits * 4 * kH1 * kNFeat);
+    static_assert((size_t)kWgSplits * (kH1 * kNFeat + kH2 * kH1) <= (size_t)kSplits * 4 * kH1 * kNFeat,
+                  "partial buffer");
+    TA(t->d_etiles, 4 * (size_t)t->tiles_max);
+    TA(t->d_wsplit, kWgSplits);
     TA(t->d_lparts, 2 * (size_t)t->max_frames);
     TA(t->d_rmin, 4 * kNFeat);
     TA(t->d_rmax, 4 * kNFeat);
@@ -681,6 +639,7 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
         return tr_fail(nullptr, MDPF_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
     e1 = learned_mlp_tc_prepare();
+    if (e1 == cudaSuccess) e1 = learned_wgrad_tc_prepare();
     if (e1 == cudaSuccess) e1 = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
     if (e1 != cudaSuccess) {
         tr_free(t);
@@ -738,14 +697,13 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     learned_jvp(L, t->d_pos4, t->d_v, t->d_U, s);
     // 5. per-row reverse over the tangent pass
     k_mlp_train<<<t->rows_max / kTrRows, 256, kTrSmem, s>>>(L, t->d_U, t->d_c, t->ro);
-    // 6. weight gradients (split over the row range, splits summed in order)
-    k_wgrad<kH1, kNFeat><<<dim3(kH1 / 64, kNFeat / 64, 4 * kSplits), 256, 0, s>>>(
-        L, t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH1 * kNFeat, kOW1, kSplits,
-                                                                         d_grad);
-    k_wgrad<kH2, kH1><<<dim3(kH2 / 64, kH1 / 64, 4 * kSplits), 256, 0, s>>>(
-        L, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3((kH2 * kH1 + 255) / 256, 4), 256, 0, s>>>(t->d_part, kH2 * kH1, kOW2, kSplits, d_grad);
+    // 6. weight-matrix gradients on the tensor cores (K splits over each element's row tiles, summed in
+    //    order); bias and output-weight gradients as split row sums
+    WgradIn wg{t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1,
+               L.atom_of, L.tile_el, L.n_tiles_live, t->tiles_max, t->d_etiles, t->d_wsplit, t->d_part,
+               d_grad, kPPE, kOW1, kOW2, t->d_status};
+    ce = learned_wgrad_tc(wg, s);
+    if (ce != cudaSuccess) return tr_cuda(t, ce, "learned_wgrad_tc");
     k_vgrad<<<dim3(1, 4 * kVSplits), 256, 0, s>>>(L, t->ro.bh1, nullptr, kH1, t->tiles_max, t->d_part);
     k_reduce_splits<<<dim3(1, 4), 256, 0, s>>>(t->d_part, kH1, kOb1, kVSplits, d_grad);
     k_vgrad<<<dim3(1, 4 * kVSplits), 128, 0, s>>>(L, t->ro.bh2, nullptr, kH2, t->tiles_max, t->d_part);
