@@ -42,8 +42,9 @@ FLOPS_PER_PAIR_ENERGY = 3    # extra flops per pair on energy steps
 RECORD_EVERY = 10            # frames and energies every 10 steps (the workload's recording cadence)
 # DRAM bytes (read + write) per launch of k_plain_persistent from the ncu capture in
 # profiles/k_plain_persistent_cluster2048.md: the L2-resident working set read once from a cold L2
-# (the bench flushes L2 between launches), independent of the MD steps per launch
-PLAIN_TRAFFIC = 456448
+# (the bench flushes L2 between launches), independent of the MD steps per launch; None until the
+# current kernel has been captured
+PLAIN_TRAFFIC = None
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -588,7 +589,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) between bench steps; within a bench step the ~1 MB state "
                          "stays L2-resident across MD steps as in any MD engine"},
         "roofline": {"bound": "alu", "kernel": "k_plain_persistent (whole MD loop: all-pairs tiles, bonded, "
-                                               "velocity Verlet, one grid barrier per step)",
+                                               "velocity Verlet, two grid barriers per step)",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (%s max clock)"
                                   % (N_SM, FP32_LANES_PER_SM, mhz, pk_kind),

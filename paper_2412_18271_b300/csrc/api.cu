@@ -98,8 +98,8 @@ static void free_ctx(mdpf_ctx *c) {
                     c->d_charge_s, c->d_bonds, c->d_bond_par, c->d_angles, c->d_excl_off, c->d_excl_idx,
                     c->d_tile_mask, c->d_tile_flag, c->d_items, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
                     c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_step, c->d_status,
-                    c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e, c->d_tile_cnt,
-                    c->d_tile_expect, c->d_own_off, c->d_own, c->d_touch_off, c->d_touch, c->d_lang_c2, c->frames.pos,
+                    c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e,
+                    c->d_own_off, c->d_own, c->d_lang_c2, c->frames.pos,
                     c->frames.energy, c->frames.forces,
                     c->frames.step};
     for (void *p : ptrs)
@@ -330,69 +330,26 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
             fail(c, MDPF_ERR_UNSUPPORTED, "cooperative launch of the persistent stepper is not available");
             return bail(MDPF_ERR_UNSUPPORTED);
         }
-        // contributions per tile per step
-        std::vector<int> expect(T, 0);
-        for (const int4 &it : items) {
-            if (it.x == ITEM_OFF64) {
-                expect[2 * it.y]++;
-                expect[2 * it.y + 1]++;
-                expect[it.z]++;
-            } else if (it.x == ITEM_OFF32) {
-                expect[it.y]++;
-                expect[it.z]++;
-            } else {
-                expect[it.y]++;
-            }
-        }
-        // bonded terms by owning tile (bond: first atom; angle: vertex) and the other tiles they touch;
-        // the angle list comes from the device
+        // bonded terms by owning tile (bond: first atom; angle: vertex); the angle list comes from the device
         std::vector<int4> angles(c->n_angles);
         if (c->n_angles > 0)
             CKC(cudaMemcpy(angles.data(), c->d_angles, sizeof(int4) * c->n_angles, cudaMemcpyDeviceToHost));
-        std::vector<std::vector<int>> own(T), touch(T);
-        auto add_touch = [&](int t, int atom) {
-            const int u = atom / kTile;
-            if (u == t) return;
-            for (int v : touch[t])
-                if (v == u) return;
-            touch[t].push_back(u);
-        };
-        for (int b = 0; b < t->n_bonds; ++b) {
-            const int owner = t->bonds[2 * b] / kTile;
-            own[owner].push_back(b);
-            add_touch(owner, t->bonds[2 * b + 1]);
-        }
-        for (int k = 0; k < c->n_angles; ++k) {
-            const int owner = angles[k].y / kTile;
-            own[owner].push_back(t->n_bonds + k);
-            add_touch(owner, angles[k].x);
-            add_touch(owner, angles[k].z);
-        }
-        std::vector<int> own_off(T + 1, 0), touch_off(T + 1, 0), own_flat, touch_flat;
+        std::vector<std::vector<int>> own(T);
+        for (int b = 0; b < t->n_bonds; ++b) own[t->bonds[2 * b] / kTile].push_back(b);
+        for (int k = 0; k < c->n_angles; ++k) own[angles[k].y / kTile].push_back(t->n_bonds + k);
+        std::vector<int> own_off(T + 1, 0), own_flat;
         for (int tt = 0; tt < T; ++tt) {
             own_flat.insert(own_flat.end(), own[tt].begin(), own[tt].end());
-            touch_flat.insert(touch_flat.end(), touch[tt].begin(), touch[tt].end());
             own_off[tt + 1] = (int)own_flat.size();
-            touch_off[tt + 1] = (int)touch_flat.size();
-            for (int u : touch[tt]) expect[u]++;  // the self item of tt also contributes to u
         }
         own_flat.push_back(0);
-        touch_flat.push_back(0);
         CKC(dalloc(&c->d_part, 2 * (size_t)c->step_grid * 4));
         CKC(dalloc(&c->d_tile_e, 2 * (size_t)T * 4));
-        CKC(dalloc(&c->d_tile_cnt, T));
-        CKC(dalloc(&c->d_tile_expect, T));
         CKC(dalloc(&c->d_own_off, T + 1));
         CKC(dalloc(&c->d_own, own_flat.size()));
-        CKC(dalloc(&c->d_touch_off, T + 1));
-        CKC(dalloc(&c->d_touch, touch_flat.size()));
         CKC(dalloc(&c->d_pos4_b, np));
-        CKC(cudaMemcpy(c->d_tile_expect, expect.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(c->d_own_off, own_off.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(c->d_own, own_flat.data(), sizeof(int) * own_flat.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_touch_off, touch_off.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_touch, touch_flat.data(), sizeof(int) * touch_flat.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemset(c->d_tile_cnt, 0, sizeof(unsigned int) * T));
         CKC(cudaMemset(c->d_tile_e, 0, sizeof(double) * 2 * T * 4));
     }
 #undef CKC

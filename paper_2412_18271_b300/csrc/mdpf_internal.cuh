@@ -131,10 +131,7 @@ struct mdpf_ctx {
     // persistent stepper
     double *d_part = nullptr;              // [2][step_grid][4] per-block energies
     double *d_tile_e = nullptr;            // [2][n_tiles][4] per-tile kinetic energies
-    unsigned int *d_tile_cnt = nullptr;    // [n_tiles] contribution counters
-    int *d_tile_expect = nullptr;          // [n_tiles] contributions per step
     int *d_own_off = nullptr, *d_own = nullptr;      // bonded terms owned by each tile
-    int *d_touch_off = nullptr, *d_touch = nullptr;  // other tiles touched by those terms
     int step_grid = 0;                     // blocks of the persistent stepper
 
     // Langevin (BAOAB) integrator: per-atom noise amplitude, damping factor, seed

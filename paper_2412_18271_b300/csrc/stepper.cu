@@ -5,15 +5,17 @@
 // small systems launch overhead, not arithmetic, decides the step time; CUDA
 // graphs were its remedy, a single resident kernel is the one used here).
 //
-// Each MD step costs one grid barrier:
-//   phase B(s)   every warp evaluates its all-pairs work items at x_{s+1}
+// Each MD step costs two grid barriers:
+//   forces       every warp evaluates its all-pairs work items at x_{s+1}
 //                (FP32 copy P[s & 1]) and adds the forces into buffer
-//                buf(s) (int64 fixed point); the warp of a tile's self item
-//                also evaluates the bonded terms that tile owns (bond: first
-//                atom; angle: vertex).  After each item the warp bumps the
-//                contribution counter of every 32-atom tile the item touched
-//                (release); the warp that brings a tile's counter to its
-//                expected value (acquire) owns the tile's completion:
+//                buf(s) (int64 fixed point).  The bonded terms a tile owns
+//                (bond: first atom; angle: vertex) go with the tile's items
+//                on the diagonal: the first kSelfBonded with its self item,
+//                the rest with the 32x32 item of its pair of tiles, the
+//                shortest items, which sit beside the two self items.
+//   grid barrier
+//   integration  tile t by warp t / G of block t % G (one tile per SM while
+//                the tiles fit), because FP64 throughput is the limit here:
 //                  v_{s+1} = v_{s+1/2} + dt/2 a          (end of step s, K)
 //                  v_{s+3/2} = v_{s+1} + dt/2 a; x_{s+2} = x_{s+1} + dt v
 //                  FP32 copy of x_{s+2} into P[(s + 1) & 1]  (start of step s+1)
@@ -48,10 +50,7 @@ struct StepArgs {
     double *x, *v;
     unsigned long long *fxA;      // state forces F(x) on entry and exit; accumulator of odd steps
     unsigned long long *fxB;      // accumulator of even steps
-    unsigned int *tile_cnt;       // [T] contributions seen this step
-    const int *tile_expect;       // [T] contributions per step
     const int *own_off, *own;     // bonded terms owned by each tile (CSR over tiles)
-    const int *touch_off, *touch; // other tiles those terms touch (CSR over tiles)
     double *part;                 // [2][grid][4] per-block energies (bond, angle, LJ, Coulomb)
     double *tile_e;               // [2][T][4] per-tile kinetic energy (slot 2)
     double *trace_u, *trace_k;
@@ -114,8 +113,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
 
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
+constexpr int kSelfBonded = 64;  // bonded terms of a tile evaluated with its self item
 
-// Completion of tile t by the warp that delivered its last contribution.
+// Integration of tile t (one atom per lane) after all forces of the step are in.
 __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t s, float4 *Pnext,
                                               unsigned long long *acc, bool energy, bool rec, int slot) {
     const int lane = threadIdx.x & 31;
@@ -175,46 +175,6 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
     }
 }
 
-// Bump the counters of the tiles an item touched (one lane per tile, in
-// parallel); complete every tile whose last contribution this warp delivered.
-__device__ __forceinline__ void item_done(const StepArgs &a, const int4 &item, int64_t s, float4 *Pnext,
-                                          unsigned long long *acc, bool energy, bool rec, int slot) {
-    const int lane = threadIdx.x & 31;
-    int base = 0, cnt;
-    if (item.x == ITEM_OFF64) {
-        cnt = 3;
-    } else if (item.x == ITEM_OFF32) {
-        cnt = 2;
-    } else {
-        base = a.touch_off[item.y];
-        cnt = 1 + a.touch_off[item.y + 1] - base;
-    }
-    __syncwarp();
-    for (int c0 = 0; c0 < cnt; c0 += 32) {
-        int t = -1;
-        bool mine = false;
-        const int k = c0 + lane;
-        if (k < cnt) {
-            if (item.x == ITEM_OFF64) t = k == 0 ? 2 * item.y : (k == 1 ? 2 * item.y + 1 : item.z);
-            else if (item.x == ITEM_OFF32) t = k == 0 ? item.y : item.z;
-            else t = k == 0 ? item.y : a.touch[base + k - 1];
-            __threadfence();  // release this warp's force additions (ordered before by __syncwarp)
-            const unsigned int old = atomicAdd(&a.tile_cnt[t], 1u);
-            mine = old + 1 == (unsigned int)a.tile_expect[t];
-        }
-        unsigned int bal = __ballot_sync(0xffffffffu, mine);
-        if (bal) __threadfence();  // acquire: every lane orders its reads of the tile after the counter
-        while (bal) {
-            const int src = __ffs(bal) - 1;
-            bal &= bal - 1;
-            const int tt = __shfl_sync(0xffffffffu, t, src);
-            complete_tile(a, tt, s, Pnext, acc, energy, rec, slot);
-            __syncwarp();
-            if (lane == 0) a.tile_cnt[tt] = 0u;
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a) {
     __shared__ JTile jt[kStepWarps];
     __shared__ double red[kStepWarps][4];
@@ -251,7 +211,6 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             a.fxB[3 * at + q] = 0ull;
         }
     }
-    for (int t = gtid; t < a.n_tiles; t += nthreads) a.tile_cnt[t] = 0u;
     if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
 
     for (int64_t s = 0; s < a.n_steps; ++s) {
@@ -271,11 +230,17 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
                 nonbonded_item<true>(p, it, lane, jt[w], acc, elj, ec, bad);
             else
                 nonbonded_item<false>(p, it, lane, jt[w], acc, elj, ec, bad);
+            // bonded terms: the first kSelfBonded of a tile with its self item, the rest with the (shorter)
+            // 32x32 item of the tile's diagonal pair, which runs beside the two self items
             const int4 item = p.items[it];
-            if (item.x == ITEM_SELF)
-                for (int q = a.own_off[item.y] + lane; q < a.own_off[item.y + 1]; q += 32)
-                    bonded_term(p, a.own[q], acc, eb, ea);
-            item_done(a, item, s, Pnext, acc, energy, rec, slot);
+            if (item.x == ITEM_SELF) {
+                const int q0 = a.own_off[item.y], q1 = min(a.own_off[item.y + 1], q0 + kSelfBonded);
+                for (int q = q0 + lane; q < q1; q += 32) bonded_term(p, a.own[q], acc, eb, ea);
+            } else if (item.x == ITEM_OFF32) {
+                for (int t = item.y; t <= item.z; ++t)
+                    for (int q = a.own_off[t] + kSelfBonded + lane; q < a.own_off[t + 1]; q += 32)
+                        bonded_term(p, a.own[q], acc, eb, ea);
+            }
         }
         bad |= !isfinite(eb + ea);
         if (bad) atomicOr(a.status, MDPF_STATUS_NONFINITE);
@@ -292,6 +257,10 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
                 a.part[((size_t)(s & 1) * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = sum;
             }
         }
+        if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
+        // ---- integration: tile t by warp t / G of block t % G (G blocks), one tile per SM while T <= G
+        for (int t = blockIdx.x + gridDim.x * w; t < a.n_tiles; t += gridDim.x * kStepWarps)
+            complete_tile(a, t, s, Pnext, acc, energy, rec, slot);
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
         // ---- energies of step `done` (block 0, warp 0), read after the barrier
         if (energy && blockIdx.x == 0 && w == 0) {
@@ -361,12 +330,8 @@ cudaError_t launch_plain_persistent(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t
     a.v = ctx->d_v;
     a.fxA = ctx->d_fx_base;
     a.fxB = ctx->d_fx_base + 3 * (size_t)ctx->n_pad;
-    a.tile_cnt = ctx->d_tile_cnt;
-    a.tile_expect = ctx->d_tile_expect;
     a.own_off = ctx->d_own_off;
     a.own = ctx->d_own;
-    a.touch_off = ctx->d_touch_off;
-    a.touch = ctx->d_touch;
     a.part = ctx->d_part;
     a.tile_e = ctx->d_tile_e;
     a.trace_u = ctx->d_trace_u;

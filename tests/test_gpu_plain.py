@@ -246,6 +246,62 @@ def test_steppers_agree_and_split_calls_agree():
     assert np.abs(Ua - Uc).max() / s.n_atoms < 1e-7
 
 
+def _hub_system():
+    # two hub atoms with 30 bonded neighbours each: the tile of a hub owns 30 bonds and 435 angles, so
+    # the persistent stepper evaluates most of them with the tile pair's 32x32 item, and they touch
+    # four tiles
+    rng = np.random.default_rng(11)
+    n = 128
+    pos = np.zeros((n, 3))
+    far = np.array([[x, y, z] for x in range(8) for y in range(8) for z in range(4)], dtype=np.float64) * 6.0
+    pos[:] = far[:n] + 40.0
+    bonds = []
+    for hub, nbrs, centre in ((0, list(range(1, 16)) + list(range(64, 79)), (0.0, 0.0, 0.0)),
+                              (40, list(range(41, 56)) + list(range(96, 111)), (20.0, 0.0, 0.0))):
+        k = np.arange(len(nbrs)) + 0.5
+        phi = np.arccos(1 - 2 * k / len(nbrs))
+        th = np.pi * (1 + 5 ** 0.5) * k
+        dirs = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+        pos[hub] = centre
+        pos[nbrs] = np.asarray(centre) + 1.2 * dirs + 0.02 * rng.standard_normal((len(nbrs), 3))
+        bonds += [(hub, j) for j in nbrs]
+    el = rng.integers(0, 4, n).astype(np.int32)
+    q = rng.uniform(-0.3, 0.3, n)
+    return tiny.system(pos, el, bonds=bonds, charge=q - q.mean(), angle_k=2.0, theta0_deg=90.0)
+
+
+@pytest.mark.parametrize("which", ["hub", "cluster8192"])
+def test_persistent_bonded_split_and_many_items(which):
+    # hub: tiles whose bonded terms are shared between the self item and the diagonal 32x32 item;
+    # cluster8192: more work items than warps, so every warp takes several items per step
+    if which == "hub":
+        s = _hub_system()
+        _check_forces(s, s.pos)
+        steps = 60
+    else:
+        s = synth.cluster(256, 32, 110.0, seed=8)
+        steps = 20
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=5)
+    a = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_PERSISTENT)
+    a.set_state(s.pos, v0)
+    a.step(steps)
+    c = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_KERNELS)
+    c.set_state(s.pos, v0)
+    c.step(steps)
+    xa, va = a.get_state()
+    xc, vc = c.get_state()
+    assert np.abs(xa - xc).max() < 1e-9 and np.abs(va - vc).max() < 1e-9
+    Ua, _ = a.trace()
+    Uc, _ = c.trace()
+    # the persistent stepper sums each warp's pair energies over its items in FP32 before the FP64
+    # block sums, the kernel sequence per item: the totals agree to FP32 accumulation error
+    assert np.abs(Ua - Uc).max() <= 1e-7 * np.abs(Uc).max()
+    if which == "hub":
+        xo, vo, Uo, Ko, _ = O.Plain(s).vv(s.pos, v0, 0.5, steps)
+        assert np.abs(xa - xo).max() < 1e-4
+        assert abs(Ua[-1] - Uo[-1]) / s.n_atoms < 1e-5
+
+
 def test_persistent_is_reproducible():
     s = synth.workload("cluster2048")
     v0 = synth.velocities(s.mass, s.pos, 300.0, seed=7)
