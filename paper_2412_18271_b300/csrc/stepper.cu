@@ -15,7 +15,8 @@
 //                shortest items, which sit beside the two self items.
 //   grid barrier
 //   integration  tile t by warp t / G of block t % G (one tile per SM while
-//                the tiles fit), because FP64 throughput is the limit here:
+//                the tiles fit), because FP64 throughput is the limit here;
+//                the warp keeps its first tile's x, v in registers:
 //                  v_{s+1} = v_{s+1/2} + dt/2 a          (end of step s, K)
 //                  v_{s+3/2} = v_{s+1} + dt/2 a; x_{s+2} = x_{s+1} + dt v
 //                  FP32 copy of x_{s+2} into P[(s + 1) & 1]  (start of step s+1)
@@ -115,46 +116,64 @@ constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 constexpr int kSelfBonded = 64;  // bonded terms of a tile evaluated with its self item
 
+// Integration state of one atom (one lane).  A warp keeps the state of the
+// first tile it integrates in registers for the whole launch and writes x, v
+// back only on energy steps (where the status is checked and the launch may
+// stop) and at the last step; further tiles go through memory.
+struct AtomState {
+    double x[3], v[3], h, m;
+    float q;
+};
+
+__device__ __forceinline__ void load_state(const StepArgs &a, int at, AtomState &st) {
+    if (at < a.n) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            st.x[q] = __ldcg(&a.x[3 * at + q]);
+            st.v[q] = __ldcg(&a.v[3 * at + q]);
+        }
+        st.h = a.hdt_m[at];
+        st.m = a.mass[at];
+        st.q = a.qs[at];
+    }
+}
+
 // Integration of tile t (one atom per lane) after all forces of the step are in.
-__device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t s, float4 *Pnext,
-                                              unsigned long long *acc, bool energy, bool rec, int slot) {
+__device__ __forceinline__ void integrate_tile(const StepArgs &a, int t, int64_t s, float4 *Pnext,
+                                               unsigned long long *acc, bool energy, bool rec, int slot,
+                                               AtomState &st, bool store) {
     const int lane = threadIdx.x & 31;
     const int at = t * kTile + lane;
     double kin = 0.0;
     const bool last = s + 1 == a.n_steps;
     if (at < a.n) {
-        const double h = a.hdt_m[at];
+        const double h = st.h;
         unsigned long long fi[3];
-        double f[3], v[3], x[3];
+        double f[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            fi[q] = __ldcg(&acc[3 * at + q]);
-            v[q] = __ldcg(&a.v[3 * at + q]);
-            x[q] = __ldcg(&a.x[3 * at + q]);
-        }
+        for (int q = 0; q < 3; ++q) fi[q] = __ldcg(&acc[3 * at + q]);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             f[q] = fx_val(fi[q]);
-            v[q] = fma(h, f[q], v[q]);  // v_{s+1}
-            kin += v[q] * v[q];
+            st.v[q] = fma(h, f[q], st.v[q]);  // v_{s+1}
+            kin += st.v[q] * st.v[q];
         }
-        kin *= 0.5 * a.mass[at] / kAcc;
+        kin *= 0.5 * st.m / kAcc;
         if (rec) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                a.frames.pos[((size_t)slot * a.n + at) * 3 + q] = x[q];
+                a.frames.pos[((size_t)slot * a.n + at) * 3 + q] = st.x[q];
                 a.frames.forces[((size_t)slot * a.n + at) * 3 + q] = (float)f[q];
             }
         }
         if (!last) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                v[q] = fma(h, f[q], v[q]);
-                x[q] = fma(a.dt, v[q], x[q]);
-                a.x[3 * at + q] = x[q];
+                st.v[q] = fma(h, f[q], st.v[q]);
+                st.x[q] = fma(a.dt, st.v[q], st.x[q]);
                 acc[3 * at + q] = 0ull;
             }
-            Pnext[at] = make_float4((float)x[0], (float)x[1], (float)x[2], a.qs[at]);
+            Pnext[at] = make_float4((float)st.x[0], (float)st.x[1], (float)st.x[2], st.q);
         } else {
             // leave F(x_n) in the state buffer for the next launch
 #pragma unroll
@@ -163,8 +182,13 @@ __device__ __forceinline__ void complete_tile(const StepArgs &a, int t, int64_t 
                 a.fxA[3 * at + q] = fi[q];
             }
         }
+        if (store || last) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) a.v[3 * at + q] = v[q];
+            for (int q = 0; q < 3; ++q) {
+                a.x[3 * at + q] = st.x[q];
+                a.v[3 * at + q] = st.v[q];
+            }
+        }
         if (!isfinite(kin)) atomicOr(a.status, MDPF_STATUS_NONFINITE);
     } else if (at < a.p.n_pad) {
         acc[3 * at] = acc[3 * at + 1] = acc[3 * at + 2] = 0ull;
@@ -212,6 +236,10 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
         }
     }
     if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
+    // integration: tile t by warp t / G of block t % G (G blocks), one tile per SM while T <= G
+    const int t_own = blockIdx.x + gridDim.x * w;
+    AtomState own;
+    if (t_own < a.n_tiles) load_state(a, t_own * kTile + lane, own);
 
     for (int64_t s = 0; s < a.n_steps; ++s) {
         const float4 *Pcur = (s & 1) ? a.P1 : a.P0;
@@ -258,9 +286,12 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             }
         }
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
-        // ---- integration: tile t by warp t / G of block t % G (G blocks), one tile per SM while T <= G
-        for (int t = blockIdx.x + gridDim.x * w; t < a.n_tiles; t += gridDim.x * kStepWarps)
-            complete_tile(a, t, s, Pnext, acc, energy, rec, slot);
+        if (t_own < a.n_tiles) integrate_tile(a, t_own, s, Pnext, acc, energy, rec, slot, own, energy);
+        for (int t = t_own + gridDim.x * kStepWarps; t < a.n_tiles; t += gridDim.x * kStepWarps) {
+            AtomState st;
+            load_state(a, t * kTile + lane, st);
+            integrate_tile(a, t, s, Pnext, acc, energy, rec, slot, st, true);
+        }
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
         // ---- energies of step `done` (block 0, warp 0), read after the barrier
         if (energy && blockIdx.x == 0 && w == 0) {
