@@ -42,9 +42,8 @@ FLOPS_PER_PAIR_ENERGY = 3    # extra flops per pair on energy steps
 RECORD_EVERY = 10            # frames and energies every 10 steps (the workload's recording cadence)
 # DRAM bytes (read + write) per launch of k_plain_persistent from the ncu capture in
 # profiles/k_plain_persistent_cluster2048.md: the L2-resident working set read once from a cold L2
-# (the bench flushes L2 between launches), independent of the MD steps per launch; None until the
-# current kernel has been captured
-PLAIN_TRAFFIC = None
+# (the bench flushes L2 between launches), independent of the MD steps per launch
+PLAIN_TRAFFIC = 466176
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
