@@ -194,65 +194,89 @@ struct JTile {
     float2 ab[32];
 };
 
+// What a work item reads besides positions: its tiles, exclusion masks and
+// LJ parameters (fixed for the lifetime of a context, so a caller that runs
+// the same item many times can keep them).
+struct ItemCtx {
+    int4 item;
+    int I0, J;
+    bool masked;       // some pair of the item is excluded
+    uint32_t m0, m1;   // exclusion masks of this lane's i-atoms (bit j: pair skipped)
+    float2 b0, b1, bj; // LJ parameters of this lane's i-atoms and of j-atom J * 32 + lane
+};
+
+__device__ __forceinline__ void item_ctx(const PlainDev &p, const int4 &item, int lane, ItemCtx &c) {
+    const int T = p.n_tiles;
+    c.item = item;
+    if (item.x == ITEM_OFF64) {
+        c.I0 = 2 * item.y;
+        c.J = item.z;
+    } else if (item.x == ITEM_OFF32) {
+        c.I0 = item.y;
+        c.J = item.z;
+    } else {
+        c.I0 = item.y;
+        c.J = item.y;
+    }
+    const int i0 = c.I0 * kTile + lane;
+    c.bj = p.lj[c.J * kTile + lane];
+    c.b0 = p.lj[i0];
+    c.m0 = c.m1 = 0u;
+    c.b1 = make_float2(0.f, 0.f);
+    if (item.x == ITEM_SELF) {
+        c.masked = true;
+        c.m0 = p.tile_mask[tile_pair_index(c.I0, c.I0, T) * kTile + lane];
+    } else if (item.x == ITEM_OFF32) {
+        const int64_t tp = tile_pair_index(c.I0, c.J, T);
+        c.masked = p.tile_flag[tp] != 0u;
+        if (c.masked) c.m0 = p.tile_mask[tp * kTile + lane];
+    } else {
+        c.b1 = p.lj[i0 + kTile];
+        const int64_t tp0 = tile_pair_index(c.I0, c.J, T), tp1 = tile_pair_index(c.I0 + 1, c.J, T);
+        c.masked = (p.tile_flag[tp0] | p.tile_flag[tp1]) != 0u;
+        if (c.masked) {
+            c.m0 = p.tile_mask[tp0 * kTile + lane];
+            c.m1 = p.tile_mask[tp1 * kTile + lane];
+        }
+    }
+}
+
 // One work item of the all-pairs sum: forces into fx (fixed point), energies
 // added to the lane's FP32 accumulators (elj as 24 eps (s^12 - s^6)).
 template <bool ENERGY>
-__device__ __forceinline__ void nonbonded_item(const PlainDev &p, int it, int lane, JTile &jt,
-                                               unsigned long long *fx, float &elj, float &ec, bool &bad) {
-    const int4 item = p.items[it];
-    const int T = p.n_tiles;
-    int I0, J;
-    if (item.x == ITEM_OFF64) {
-        I0 = 2 * item.y;
-        J = item.z;
-    } else if (item.x == ITEM_OFF32) {
-        I0 = item.y;
-        J = item.z;
-    } else {
-        I0 = item.y;
-        J = item.y;
-    }
-    const int i0 = I0 * kTile + lane, j = J * kTile + lane;
+__device__ __forceinline__ void item_eval(const PlainDev &p, const ItemCtx &c, int lane, JTile &jt,
+                                          unsigned long long *fx, float &elj, float &ec, bool &bad) {
+    const int i0 = c.I0 * kTile + lane, j = c.J * kTile + lane;
     __syncwarp();
     jt.pos[lane] = p.pos4[j];
-    jt.ab[lane] = p.lj[j];
+    jt.ab[lane] = c.bj;
     __syncwarp();
     float3 fi0 = make_float3(0.f, 0.f, 0.f), fj = make_float3(0.f, 0.f, 0.f);
     float el = 0.f, eq = 0.f;
-    if (item.x == ITEM_SELF) {
-        const int64_t tp = tile_pair_index(I0, I0, T);
-        const uint32_t m0 = p.tile_mask[tp * kTile + lane];
-        item_self<ENERGY>(jt.pos, jt.ab, jt.pos[lane], jt.ab[lane], m0, lane, fi0, el, eq);
+    if (c.item.x == ITEM_SELF) {
+        item_self<ENERGY>(jt.pos, jt.ab, jt.pos[lane], jt.ab[lane], c.m0, lane, fi0, el, eq);
         el *= 0.5f;
         eq *= 0.5f;
-    } else if (item.x == ITEM_OFF32) {
+    } else if (c.item.x == ITEM_OFF32) {
         const float4 a0 = p.pos4[i0];
-        const float2 b0 = p.lj[i0];
-        const int64_t tp = tile_pair_index(I0, J, T);
-        if (p.tile_flag[tp]) {
-            const uint32_t m0 = p.tile_mask[tp * kTile + lane];
-            item_off32<true, ENERGY>(jt.pos, jt.ab, a0, b0, m0, lane, fi0, fj, el, eq);
-        } else {
-            item_off32<false, ENERGY>(jt.pos, jt.ab, a0, b0, 0u, lane, fi0, fj, el, eq);
-        }
+        if (c.masked)
+            item_off32<true, ENERGY>(jt.pos, jt.ab, a0, c.b0, c.m0, lane, fi0, fj, el, eq);
+        else
+            item_off32<false, ENERGY>(jt.pos, jt.ab, a0, c.b0, 0u, lane, fi0, fj, el, eq);
     } else {
         const int i1 = i0 + kTile;
         const float4 a0 = p.pos4[i0], a1 = p.pos4[i1];
-        const float2 b0 = p.lj[i0], b1 = p.lj[i1];
-        const int64_t tp0 = tile_pair_index(I0, J, T), tp1 = tile_pair_index(I0 + 1, J, T);
         float3 fi1 = make_float3(0.f, 0.f, 0.f);
-        if (p.tile_flag[tp0] | p.tile_flag[tp1]) {
-            const uint32_t m0 = p.tile_mask[tp0 * kTile + lane], m1 = p.tile_mask[tp1 * kTile + lane];
-            item_off64<true, ENERGY>(jt.pos, jt.ab, a0, b0, a1, b1, m0, m1, lane, fi0, fi1, fj, el, eq);
-        } else {
-            item_off64<false, ENERGY>(jt.pos, jt.ab, a0, b0, a1, b1, 0u, 0u, lane, fi0, fi1, fj, el, eq);
-        }
+        if (c.masked)
+            item_off64<true, ENERGY>(jt.pos, jt.ab, a0, c.b0, a1, c.b1, c.m0, c.m1, lane, fi0, fi1, fj, el, eq);
+        else
+            item_off64<false, ENERGY>(jt.pos, jt.ab, a0, c.b0, a1, c.b1, 0u, 0u, lane, fi0, fi1, fj, el, eq);
         fx_add(&fx[3 * i1 + 0], fi1.x);
         fx_add(&fx[3 * i1 + 1], fi1.y);
         fx_add(&fx[3 * i1 + 2], fi1.z);
         bad |= !isfinite(fi1.x + fi1.y + fi1.z);
     }
-    if (item.x != ITEM_SELF) {
+    if (c.item.x != ITEM_SELF) {
         fx_add(&fx[3 * j + 0], fj.x);
         fx_add(&fx[3 * j + 1], fj.y);
         fx_add(&fx[3 * j + 2], fj.z);
@@ -265,6 +289,14 @@ __device__ __forceinline__ void nonbonded_item(const PlainDev &p, int it, int la
         elj += el;
         ec += eq;
     }
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ void nonbonded_item(const PlainDev &p, int it, int lane, JTile &jt,
+                                               unsigned long long *fx, float &elj, float &ec, bool &bad) {
+    ItemCtx c;
+    item_ctx(p, p.items[it], lane, c);
+    item_eval<ENERGY>(p, c, lane, jt, fx, elj, ec, bad);
 }
 
 }  // namespace mdpf

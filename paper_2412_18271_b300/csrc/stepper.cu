@@ -240,6 +240,10 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
     const int t_own = blockIdx.x + gridDim.x * w;
     AtomState own;
     if (t_own < a.n_tiles) load_state(a, t_own * kTile + lane, own);
+    // the warp's first work item (its only one unless there are more items than warps): tiles, masks and LJ
+    // parameters stay in registers, so a step loads only positions for it
+    ItemCtx first;
+    if (gwarp < a.p.n_items) item_ctx(a.p, a.p.items[gwarp], lane, first);
 
     for (int64_t s = 0; s < a.n_steps; ++s) {
         const float4 *Pcur = (s & 1) ? a.P1 : a.P0;
@@ -254,13 +258,16 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
         float elj = 0.f, ec = 0.f, eb = 0.f, ea = 0.f;
         bool bad = false;
         for (int it = gwarp; it < p.n_items; it += nwarps) {
+            ItemCtx later;
+            if (it != gwarp) item_ctx(p, p.items[it], lane, later);
+            const ItemCtx &c = it == gwarp ? first : later;
             if (energy)
-                nonbonded_item<true>(p, it, lane, jt[w], acc, elj, ec, bad);
+                item_eval<true>(p, c, lane, jt[w], acc, elj, ec, bad);
             else
-                nonbonded_item<false>(p, it, lane, jt[w], acc, elj, ec, bad);
+                item_eval<false>(p, c, lane, jt[w], acc, elj, ec, bad);
             // bonded terms: the first kSelfBonded of a tile with its self item, the rest with the (shorter)
             // 32x32 item of the tile's diagonal pair, which runs beside the two self items
-            const int4 item = p.items[it];
+            const int4 item = c.item;
             if (item.x == ITEM_SELF) {
                 const int q0 = a.own_off[item.y], q1 = min(a.own_off[item.y + 1], q0 + kSelfBonded);
                 for (int q = q0 + lane; q < q1; q += 32) bonded_term(p, a.own[q], acc, eb, ea);
