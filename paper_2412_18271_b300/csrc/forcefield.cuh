@@ -29,28 +29,56 @@ namespace mdpf {
 
 enum { ITEM_OFF64 = 0, ITEM_OFF32 = 1, ITEM_SELF = 2 };
 
-// One bonded term t: bonds are t < n_bonds, angles follow.  Energies are
-// added to eb / ea, forces to the fixed-point accumulators.
-__device__ __forceinline__ void bonded_term(const PlainDev &p, int t, unsigned long long *fx, float &eb,
-                                            float &ea) {
+// One bonded term t: bonds are t < n_bonds, angles follow.  A term is
+// described by a record r = (i, j, -1, t) for a bond, (a, v, b, t) for an
+// angle with vertex v; its evaluation is split into the record, a gather of
+// what it reads (positions, bond parameters) and the arithmetic, so that a
+// caller can keep records and issue the loads of several terms before
+// evaluating any.  Energies are added to eb / ea, forces to the fixed-point
+// accumulators.
+struct BondedGeom {
+    float4 xa, xb, xc;  // bond: x_i, x_j; angle: x_a, x_v, x_b
+    float2 par;         // bond: r0, k
+};
+
+__device__ __forceinline__ int4 bonded_rec(const PlainDev &p, int t) {
     if (t < p.n_bonds) {
-        int2 b = p.bonds[t];
-        float4 xi = p.pos4[b.x], xj = p.pos4[b.y];
-        float2 par = p.bond_par[t];
+        const int2 b = p.bonds[t];
+        return make_int4(b.x, b.y, -1, t);
+    }
+    const int4 an = p.angles[t - p.n_bonds];
+    return make_int4(an.x, an.y, an.z, t);
+}
+
+__device__ __forceinline__ void bonded_gather(const PlainDev &p, const int4 &r, BondedGeom &g) {
+    g.xa = p.pos4[r.x];
+    g.xb = p.pos4[r.y];
+    if (r.z >= 0) {
+        g.xc = p.pos4[r.z];
+    } else {
+        g.xc = make_float4(0.f, 0.f, 0.f, 0.f);
+        g.par = p.bond_par[r.w];
+    }
+}
+
+__device__ __forceinline__ void bonded_eval(const PlainDev &p, const int4 &r, const BondedGeom &g,
+                                            unsigned long long *fx, float &eb, float &ea) {
+    if (r.z < 0) {
+        const float4 xi = g.xa, xj = g.xb;
+        const float2 par = g.par;
         float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        float dr = r - par.x;
+        float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float dr = rr - par.x;
         eb += 0.5f * par.y * dr * dr;
-        float g = par.y * dr / r;
-        fx_add(&fx[3 * b.x + 0], g * dx);
-        fx_add(&fx[3 * b.x + 1], g * dy);
-        fx_add(&fx[3 * b.x + 2], g * dz);
-        fx_add(&fx[3 * b.y + 0], -g * dx);
-        fx_add(&fx[3 * b.y + 1], -g * dy);
-        fx_add(&fx[3 * b.y + 2], -g * dz);
-    } else if (t < p.n_bonds + p.n_angles) {
-        int4 an = p.angles[t - p.n_bonds];
-        float4 xa = p.pos4[an.x], xv = p.pos4[an.y], xb = p.pos4[an.z];
+        float gg = par.y * dr / rr;
+        fx_add(&fx[3 * r.x + 0], gg * dx);
+        fx_add(&fx[3 * r.x + 1], gg * dy);
+        fx_add(&fx[3 * r.x + 2], gg * dz);
+        fx_add(&fx[3 * r.y + 0], -gg * dx);
+        fx_add(&fx[3 * r.y + 1], -gg * dy);
+        fx_add(&fx[3 * r.y + 2], -gg * dz);
+    } else {
+        const float4 xa = g.xa, xv = g.xb, xb = g.xc;
         float ux = xa.x - xv.x, uy = xa.y - xv.y, uz = xa.z - xv.z;
         float wx = xb.x - xv.x, wy = xb.y - xv.y, wz = xb.z - xv.z;
         float ru = sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz))), rw = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
@@ -68,16 +96,25 @@ __device__ __forceinline__ void bonded_term(const PlainDev &p, int t, unsigned l
         float iu = 1.f / ru, iw = 1.f / rw;
         float fax = ga * (wx * iw - cs * ux * iu), fay = ga * (wy * iw - cs * uy * iu), faz = ga * (wz * iw - cs * uz * iu);
         float fbx = gb * (ux * iu - cs * wx * iw), fby = gb * (uy * iu - cs * wy * iw), fbz = gb * (uz * iu - cs * wz * iw);
-        fx_add(&fx[3 * an.x + 0], fax);
-        fx_add(&fx[3 * an.x + 1], fay);
-        fx_add(&fx[3 * an.x + 2], faz);
-        fx_add(&fx[3 * an.z + 0], fbx);
-        fx_add(&fx[3 * an.z + 1], fby);
-        fx_add(&fx[3 * an.z + 2], fbz);
-        fx_add(&fx[3 * an.y + 0], -(fax + fbx));
-        fx_add(&fx[3 * an.y + 1], -(fay + fby));
-        fx_add(&fx[3 * an.y + 2], -(faz + fbz));
+        fx_add(&fx[3 * r.x + 0], fax);
+        fx_add(&fx[3 * r.x + 1], fay);
+        fx_add(&fx[3 * r.x + 2], faz);
+        fx_add(&fx[3 * r.z + 0], fbx);
+        fx_add(&fx[3 * r.z + 1], fby);
+        fx_add(&fx[3 * r.z + 2], fbz);
+        fx_add(&fx[3 * r.y + 0], -(fax + fbx));
+        fx_add(&fx[3 * r.y + 1], -(fay + fby));
+        fx_add(&fx[3 * r.y + 2], -(faz + fbz));
     }
+}
+
+__device__ __forceinline__ void bonded_term(const PlainDev &p, int t, unsigned long long *fx, float &eb,
+                                            float &ea) {
+    if (t >= p.n_bonds + p.n_angles) return;
+    const int4 r = bonded_rec(p, t);
+    BondedGeom g;
+    bonded_gather(p, r, g);
+    bonded_eval(p, r, g, fx, eb, ea);
 }
 
 // One pair: returns fs (0 when skipped); accumulates energies (elj carries

@@ -115,6 +115,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 constexpr int kSelfBonded = 64;  // bonded terms of a tile evaluated with its self item
+constexpr int kBondRegs = 4;     // bonded terms per lane whose records a warp keeps in registers
 
 // Integration state of one atom (one lane).  A warp keeps the state of the
 // first tile it integrates in registers for the whole launch and writes x, v
@@ -199,6 +200,29 @@ __device__ __forceinline__ void integrate_tile(const StepArgs &a, int t, int64_t
     }
 }
 
+// The bonded terms that go with a work item, as up to two ranges of the
+// owner lists: a self item takes the first kSelfBonded terms of its tile, the
+// 32x32 item of a diagonal pair the rest of both tiles' terms.
+struct BondedList {
+    int a0, na, b0, nb;
+    __device__ __forceinline__ int size() const { return na + nb; }
+    __device__ __forceinline__ int at(const int *own, int e) const { return e < na ? own[a0 + e] : own[b0 + e - na]; }
+};
+
+__device__ __forceinline__ BondedList bonded_list(const StepArgs &a, const int4 &item) {
+    BondedList l{0, 0, 0, 0};
+    if (item.x == ITEM_SELF) {
+        l.a0 = a.own_off[item.y];
+        l.na = min(a.own_off[item.y + 1] - l.a0, kSelfBonded);
+    } else if (item.x == ITEM_OFF32) {
+        l.a0 = a.own_off[item.y] + kSelfBonded;
+        l.na = max(a.own_off[item.y + 1] - l.a0, 0);
+        l.b0 = a.own_off[item.z] + kSelfBonded;
+        l.nb = max(a.own_off[item.z + 1] - l.b0, 0);
+    }
+    return l;
+}
+
 __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a) {
     __shared__ JTile jt[kStepWarps];
     __shared__ double red[kStepWarps][4];
@@ -243,7 +267,21 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
     // the warp's first work item (its only one unless there are more items than warps): tiles, masks and LJ
     // parameters stay in registers, so a step loads only positions for it
     ItemCtx first;
-    if (gwarp < a.p.n_items) item_ctx(a.p, a.p.items[gwarp], lane, first);
+    BondedList first_bl{0, 0, 0, 0};
+    int4 brec[kBondRegs];    // records of the first item's bonded terms lane, lane + 32, ...
+    float2 bpar[kBondRegs];  // and their bond parameters
+    if (gwarp < a.p.n_items) {
+        item_ctx(a.p, a.p.items[gwarp], lane, first);
+        first_bl = bonded_list(a, first.item);
+#pragma unroll
+        for (int k = 0; k < kBondRegs; ++k) {
+            const int e = lane + 32 * k;
+            if (e < first_bl.size()) {
+                brec[k] = bonded_rec(a.p, first_bl.at(a.own, e));
+                bpar[k] = brec[k].z < 0 ? a.p.bond_par[brec[k].w] : make_float2(0.f, 0.f);
+            }
+        }
+    }
 
     for (int64_t s = 0; s < a.n_steps; ++s) {
         const float4 *Pcur = (s & 1) ? a.P1 : a.P0;
@@ -268,13 +306,28 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             // bonded terms: the first kSelfBonded of a tile with its self item, the rest with the (shorter)
             // 32x32 item of the tile's diagonal pair, which runs beside the two self items
             const int4 item = c.item;
-            if (item.x == ITEM_SELF) {
-                const int q0 = a.own_off[item.y], q1 = min(a.own_off[item.y + 1], q0 + kSelfBonded);
-                for (int q = q0 + lane; q < q1; q += 32) bonded_term(p, a.own[q], acc, eb, ea);
-            } else if (item.x == ITEM_OFF32) {
-                for (int t = item.y; t <= item.z; ++t)
-                    for (int q = a.own_off[t] + kSelfBonded + lane; q < a.own_off[t + 1]; q += 32)
-                        bonded_term(p, a.own[q], acc, eb, ea);
+            if (item.x != ITEM_OFF64) {
+                int e0 = 0;
+                BondedList bl = first_bl;
+                if (it == gwarp) {
+                    // records in registers: every position load is issued before the first evaluation
+                    BondedGeom g[kBondRegs];
+#pragma unroll
+                    for (int k = 0; k < kBondRegs; ++k)
+                        if (lane + 32 * k < bl.size()) {
+                            g[k].xa = p.pos4[brec[k].x];
+                            g[k].xb = p.pos4[brec[k].y];
+                            g[k].xc = brec[k].z >= 0 ? p.pos4[brec[k].z] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            g[k].par = bpar[k];
+                        }
+#pragma unroll
+                    for (int k = 0; k < kBondRegs; ++k)
+                        if (lane + 32 * k < bl.size()) bonded_eval(p, brec[k], g[k], acc, eb, ea);
+                    e0 = 32 * kBondRegs;
+                } else {
+                    bl = bonded_list(a, item);
+                }
+                for (int e = e0 + lane; e < bl.size(); e += 32) bonded_term(p, bl.at(a.own, e), acc, eb, ea);
             }
         }
         bad |= !isfinite(eb + ea);
