@@ -280,9 +280,12 @@ __device__ __forceinline__ void item_ctx(const PlainDev &p, const int4 &item, in
 
 // One work item of the all-pairs sum: forces into fx (fixed point), energies
 // added to the lane's FP32 accumulators (elj as 24 eps (s^12 - s^6)).
+// With fi_out set, a 64x32 item returns its two i-forces there (fi_out[0],
+// fi_out[1]) instead of adding them.
 template <bool ENERGY>
 __device__ __forceinline__ void item_eval(const PlainDev &p, const ItemCtx &c, int lane, JTile &jt,
-                                          unsigned long long *fx, float &elj, float &ec, bool &bad) {
+                                          unsigned long long *fx, float &elj, float &ec, bool &bad,
+                                          float3 *fi_out = nullptr) {
     const int i0 = c.I0 * kTile + lane, j = c.J * kTile + lane;
     __syncwarp();
     jt.pos[lane] = p.pos4[j];
@@ -308,9 +311,13 @@ __device__ __forceinline__ void item_eval(const PlainDev &p, const ItemCtx &c, i
             item_off64<true, ENERGY>(jt.pos, jt.ab, a0, c.b0, a1, c.b1, c.m0, c.m1, lane, fi0, fi1, fj, el, eq);
         else
             item_off64<false, ENERGY>(jt.pos, jt.ab, a0, c.b0, a1, c.b1, 0u, 0u, lane, fi0, fi1, fj, el, eq);
-        fx_add(&fx[3 * i1 + 0], fi1.x);
-        fx_add(&fx[3 * i1 + 1], fi1.y);
-        fx_add(&fx[3 * i1 + 2], fi1.z);
+        if (fi_out != nullptr) {
+            fi_out[1] = fi1;
+        } else {
+            fx_add(&fx[3 * i1 + 0], fi1.x);
+            fx_add(&fx[3 * i1 + 1], fi1.y);
+            fx_add(&fx[3 * i1 + 2], fi1.z);
+        }
         bad |= !isfinite(fi1.x + fi1.y + fi1.z);
     }
     if (c.item.x != ITEM_SELF) {
@@ -318,9 +325,13 @@ __device__ __forceinline__ void item_eval(const PlainDev &p, const ItemCtx &c, i
         fx_add(&fx[3 * j + 1], fj.y);
         fx_add(&fx[3 * j + 2], fj.z);
     }
-    fx_add(&fx[3 * i0 + 0], fi0.x);
-    fx_add(&fx[3 * i0 + 1], fi0.y);
-    fx_add(&fx[3 * i0 + 2], fi0.z);
+    if (fi_out != nullptr && c.item.x == ITEM_OFF64) {
+        fi_out[0] = fi0;
+    } else {
+        fx_add(&fx[3 * i0 + 0], fi0.x);
+        fx_add(&fx[3 * i0 + 1], fi0.y);
+        fx_add(&fx[3 * i0 + 2], fi0.z);
+    }
     bad |= !isfinite(fi0.x + fi0.y + fi0.z + fj.x + fj.y + fj.z + el + eq);
     if (ENERGY) {
         elj += el;

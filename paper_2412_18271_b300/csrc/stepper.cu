@@ -226,6 +226,8 @@ __device__ __forceinline__ BondedList bonded_list(const StepArgs &a, const int4 
 __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a) {
     __shared__ JTile jt[kStepWarps];
     __shared__ double red[kStepWarps][4];
+    __shared__ long long ired[kStepWarps][6][kTile];  // the block's i-forces (fixed point) before one add
+    __shared__ int s_uniform;
     __shared__ int s_fail;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -266,6 +268,22 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
     if (t_own < a.n_tiles) load_state(a, t_own * kTile + lane, own);
     // the warp's first work item (its only one unless there are more items than warps): tiles, masks and LJ
     // parameters stay in registers, so a step loads only positions for it
+    // A block whose eight warps each have one 64x32 item on the same pair of i-tiles (the usual case: the
+    // items of a pair of i-tiles are listed together) adds their i-forces in shared memory as integers and
+    // sends one fixed-point add per atom and component instead of eight.
+    if (threadIdx.x == 0) {
+        int u = (long long)nwarps >= a.p.n_items && (blockIdx.x + 1) * kStepWarps <= a.p.n_items;
+        if (u) {
+            const int4 i0 = a.p.items[blockIdx.x * kStepWarps];
+            for (int k = 0; k < kStepWarps && u; ++k) {
+                const int4 ik = a.p.items[blockIdx.x * kStepWarps + k];
+                u = ik.x == ITEM_OFF64 && ik.y == i0.y;
+            }
+        }
+        s_uniform = u;
+    }
+    __syncthreads();
+    const bool uniform = s_uniform != 0;
     ItemCtx first;
     BondedList first_bl{0, 0, 0, 0};
     int4 brec[kBondRegs];    // records of the first item's bonded terms lane, lane + 32, ...
@@ -299,10 +317,30 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             ItemCtx later;
             if (it != gwarp) item_ctx(p, p.items[it], lane, later);
             const ItemCtx &c = it == gwarp ? first : later;
+            float3 fio[2];
             if (energy)
-                item_eval<true>(p, c, lane, jt[w], acc, elj, ec, bad);
+                item_eval<true>(p, c, lane, jt[w], acc, elj, ec, bad, uniform ? fio : nullptr);
             else
-                item_eval<false>(p, c, lane, jt[w], acc, elj, ec, bad);
+                item_eval<false>(p, c, lane, jt[w], acc, elj, ec, bad, uniform ? fio : nullptr);
+            if (uniform) {
+                ired[w][0][lane] = fx_from_float(fio[0].x);
+                ired[w][1][lane] = fx_from_float(fio[0].y);
+                ired[w][2][lane] = fx_from_float(fio[0].z);
+                ired[w][3][lane] = fx_from_float(fio[1].x);
+                ired[w][4][lane] = fx_from_float(fio[1].y);
+                ired[w][5][lane] = fx_from_float(fio[1].z);
+                __syncthreads();
+                // thread k < 192: atom k % 64 of the tile pair, component k / 64
+                if (threadIdx.x < 6 * kTile) {
+                    const int q = threadIdx.x / (2 * kTile), at = threadIdx.x % (2 * kTile);
+                    const int slot = (at / kTile) * 3 + q, l = at % kTile;
+                    long long sum = 0;
+#pragma unroll
+                    for (int k = 0; k < kStepWarps; ++k) sum += ired[k][slot][l];
+                    atomicAdd(&acc[3 * (2 * c.item.y * kTile + at) + q], (unsigned long long)sum);
+                }
+                __syncthreads();
+            }
             // bonded terms: the first kSelfBonded of a tile with its self item, the rest with the (shorter)
             // 32x32 item of the tile's diagonal pair, which runs beside the two self items
             const int4 item = c.item;
