@@ -254,6 +254,9 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
         items.push_back(make_int4(ITEM_SELF, 2 * p, 0, 0));
         items.push_back(make_int4(ITEM_SELF, 2 * p + 1, 0, 0));
     }
+    // the persistent stepper spreads each tile's bonded terms over its diagonal items and one more item
+    if (c->stepper == MDPF_STEPPER_PERSISTENT)
+        for (int tt = 0; tt < T; ++tt) items.push_back(make_int4(ITEM_BONDED, tt, 0, 0));
     c->n_items = (int)items.size();
 
     CKC(dalloc(&c->d_element, n));

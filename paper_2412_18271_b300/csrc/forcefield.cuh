@@ -7,7 +7,10 @@
 //   ITEM_OFF64 (p, J)  tiles 2p and 2p+1 against tile J > 2p+1: every lane
 //                      owns two i-atoms, so each j read serves two pairs;
 //   ITEM_OFF32 (I, J)  tile I against tile J > I, one i-atom per lane;
-//   ITEM_SELF  (I)     the pairs inside tile I.
+//   ITEM_SELF  (I)     the pairs inside tile I;
+//   ITEM_BONDED (I)    no pairs: a share of tile I's bonded terms, for a
+//                      stepper that spreads them over more warps (the
+//                      pair sum skips it).
 // Off-diagonal items apply Newton's third law: the j-tile sits in shared
 // memory, lane l meets j-lane (l + k) & 31 at step k, and the j-force
 // accumulator travels with its j index (one lane down per step, three
@@ -27,7 +30,7 @@
 
 namespace mdpf {
 
-enum { ITEM_OFF64 = 0, ITEM_OFF32 = 1, ITEM_SELF = 2 };
+enum { ITEM_OFF64 = 0, ITEM_OFF32 = 1, ITEM_SELF = 2, ITEM_BONDED = 3 };
 
 // One bonded term t: bonds are t < n_bonds, angles follow.  A term is
 // described by a record r = (i, j, -1, t) for a bond, (a, v, b, t) for an
@@ -245,6 +248,13 @@ struct ItemCtx {
 __device__ __forceinline__ void item_ctx(const PlainDev &p, const int4 &item, int lane, ItemCtx &c) {
     const int T = p.n_tiles;
     c.item = item;
+    if (item.x == ITEM_BONDED) {  // no pair work, nothing to read
+        c.I0 = c.J = item.y;
+        c.masked = false;
+        c.m0 = c.m1 = 0u;
+        c.b0 = c.b1 = c.bj = make_float2(0.f, 0.f);
+        return;
+    }
     if (item.x == ITEM_OFF64) {
         c.I0 = 2 * item.y;
         c.J = item.z;
@@ -286,6 +296,7 @@ template <bool ENERGY>
 __device__ __forceinline__ void item_eval(const PlainDev &p, const ItemCtx &c, int lane, JTile &jt,
                                           unsigned long long *fx, float &elj, float &ec, bool &bad,
                                           float3 *fi_out = nullptr) {
+    if (c.item.x == ITEM_BONDED) return;
     const int i0 = c.I0 * kTile + lane, j = c.J * kTile + lane;
     __syncwarp();
     jt.pos[lane] = p.pos4[j];

@@ -10,9 +10,9 @@
 //                (FP32 copy P[s & 1]) and adds the forces into buffer
 //                buf(s) (int64 fixed point).  The bonded terms a tile owns
 //                (bond: first atom; angle: vertex) go with the tile's items
-//                on the diagonal: the first kSelfBonded with its self item,
-//                the rest with the 32x32 item of its pair of tiles, the
-//                shortest items, which sit beside the two self items.
+//                on the diagonal, the shortest ones: the first kSelfBonded
+//                with its self item, the next kPairBonded with the 32x32 item
+//                of its pair of tiles, the rest with a bonded-only item.
 //   grid barrier
 //   integration  tile t by warp t / G of block t % G (one tile per SM while
 //                the tiles fit), because FP64 throughput is the limit here;
@@ -114,7 +114,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
 
 constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
-constexpr int kSelfBonded = 64;  // bonded terms of a tile evaluated with its self item
+constexpr int kSelfBonded = 16;  // bonded terms of a tile evaluated with its self item ...
+constexpr int kPairBonded = 0;   // ... with the 32x32 item of its pair of tiles; the rest with its bonded item
 constexpr int kBondRegs = 4;     // bonded terms per lane whose records a warp keeps in registers
 
 // Integration state of one atom (one lane).  A warp keeps the state of the
@@ -202,7 +203,8 @@ __device__ __forceinline__ void integrate_tile(const StepArgs &a, int t, int64_t
 
 // The bonded terms that go with a work item, as up to two ranges of the
 // owner lists: a self item takes the first kSelfBonded terms of its tile, the
-// 32x32 item of a diagonal pair the rest of both tiles' terms.
+// 32x32 item of a diagonal pair the next kPairBonded of both tiles, and the
+// tile's bonded item the rest (the shares follow each item's pair work).
 struct BondedList {
     int a0, na, b0, nb;
     __device__ __forceinline__ int size() const { return na + nb; }
@@ -216,9 +218,12 @@ __device__ __forceinline__ BondedList bonded_list(const StepArgs &a, const int4 
         l.na = min(a.own_off[item.y + 1] - l.a0, kSelfBonded);
     } else if (item.x == ITEM_OFF32) {
         l.a0 = a.own_off[item.y] + kSelfBonded;
-        l.na = max(a.own_off[item.y + 1] - l.a0, 0);
+        l.na = min(max(a.own_off[item.y + 1] - l.a0, 0), kPairBonded);
         l.b0 = a.own_off[item.z] + kSelfBonded;
-        l.nb = max(a.own_off[item.z + 1] - l.b0, 0);
+        l.nb = min(max(a.own_off[item.z + 1] - l.b0, 0), kPairBonded);
+    } else if (item.x == ITEM_BONDED) {
+        l.a0 = a.own_off[item.y] + kSelfBonded + kPairBonded;
+        l.na = max(a.own_off[item.y + 1] - l.a0, 0);
     }
     return l;
 }
@@ -341,8 +346,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
                 }
                 __syncthreads();
             }
-            // bonded terms: the first kSelfBonded of a tile with its self item, the rest with the (shorter)
-            // 32x32 item of the tile's diagonal pair, which runs beside the two self items
+            // bonded terms: shares of the tile's list by item type (bonded_list)
             const int4 item = c.item;
             if (item.x != ITEM_OFF64) {
                 int e0 = 0;
