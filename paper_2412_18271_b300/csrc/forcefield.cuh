@@ -160,7 +160,7 @@ __device__ __forceinline__ void item_off64(const float4 *sj, const float2 *sab, 
                                            float3 &fi0, float3 &fi1, float3 &fj, float &elj, float &ec) {
     float3 fa = make_float3(0.f, 0.f, 0.f), fb = make_float3(0.f, 0.f, 0.f);
     const int nxt = (lane + 1) & 31;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < 16; ++k) {
         const int sA = (lane + k) & 31, sB = (lane + k + 16) & 31;
         const float4 ja = sj[sA], jb = sj[sB];
