@@ -114,37 +114,68 @@ __device__ __forceinline__ void cell_of(const CellGrid &g, float4 p, int &cx, in
 // ones appended in shared memory (ballot order), then written out in ascending
 // order (each entry's rank among the distinct entries).  Returns the row
 // length (kKmax + 1 when the row overflowed).
+// Candidates of the 27 cells around atom i, in (z, y, x) cell order and slot
+// order within a cell: lane c < 27 reads cell c's count, a warp scan gives
+// each cell's first candidate index, and the candidates are then taken 32 at
+// a time across cells (three dependent memory trips per 32 candidates instead
+// of per cell).
+struct CellScan {
+    int start[28];  // first candidate index of cell c; start[27] = total
+    int cell[27];   // cell id, or -1 outside the grid
+};
+
 __device__ int build_row_warp(const LearnedDev &L, const float4 *pos4, const CellGrid &g, int i, int lane,
-                              int *srow) {
+                              int *srow, CellScan &cs) {
     const float4 pi = pos4[i];
     int cx, cy, cz;
     cell_of(g, pi, cx, cy, cz);
+    int cid = -1, ccnt = 0;
+    if (lane < 27) {
+        const int z = cz - 1 + lane / 9, y = cy - 1 + (lane / 3) % 3, x = cx - 1 + lane % 3;
+        if (z >= 0 && z < g.dim[2] && y >= 0 && y < g.dim[1] && x >= 0 && x < g.dim[0]) {
+            cid = (z * g.dim[1] + y) * g.dim[0] + x;
+            ccnt = min(L.cell_cnt[cid], kCellCap);
+        }
+    }
+    int incl = ccnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    if (lane < 27) {
+        cs.start[lane] = incl - ccnt;
+        cs.cell[lane] = cid;
+    }
+    if (lane == 27) cs.start[27] = total;
+    __syncwarp();
     int m = 0;
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, g.dim[2] - 1); ++z)
-        for (int y = max(cy - 1, 0); y <= min(cy + 1, g.dim[1] - 1); ++y)
-            for (int x = max(cx - 1, 0); x <= min(cx + 1, g.dim[0] - 1); ++x) {
-                const int c = (z * g.dim[1] + y) * g.dim[0] + x;
-                const int cnt = min(L.cell_cnt[c], kCellCap);
-                for (int q0 = 0; q0 < cnt; q0 += 32) {
-                    const int q = q0 + lane;
-                    int j = -1;
-                    bool in = false;
-                    if (q < cnt) {
-                        j = L.cell_atoms[(size_t)c * kCellCap + q];
-                        if (j != i) {
-                            const float4 pj = pos4[j];
-                            const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y),
-                                        dz = __fsub_rn(pj.z, pi.z);
-                            in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <
-                                 L.rc_list2;
-                        }
-                    }
-                    const unsigned int bal = __ballot_sync(0xffffffffu, in);
-                    const int pos = m + __popc(bal & ((1u << lane) - 1u));
-                    if (in && pos < kKmax) srow[pos] = j;
-                    m += __popc(bal);
-                }
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        int j = -1;
+        bool in = false;
+        if (k < total) {
+            // the cell holding candidate k: the last c with start[c] <= k (empty cells share their start)
+            int lo = 0, hi = 26;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cs.start[mid] <= k) lo = mid;
+                else hi = mid - 1;
             }
+            j = L.cell_atoms[(size_t)cs.cell[lo] * kCellCap + (k - cs.start[lo])];
+            if (j != i) {
+                const float4 pj = pos4[j];
+                const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+                in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < L.rc_list2;
+            }
+        }
+        const unsigned int bal = __ballot_sync(0xffffffffu, in);
+        const int pos = m + __popc(bal & ((1u << lane) - 1u));
+        if (in && pos < kKmax) srow[pos] = j;
+        m += __popc(bal);
+    }
     __syncwarp();
     const int mm = min(m, kKmax);
     int *out = L.nb_idx + (size_t)i * kKmax;
@@ -218,12 +249,13 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
     }
     // D: rows, one warp per atom
     __shared__ int srow[kNbThreads / 32][kKmax];
+    __shared__ CellScan scs[kNbThreads / 32];
     __shared__ int s_max[kNbThreads / 32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     int longest = 0;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < L.n; i += nwarps)
-        longest = max(longest, build_row_warp(L, pos4, g, i, lane, srow[wib]));
+        longest = max(longest, build_row_warp(L, pos4, g, i, lane, srow[wib], scs[wib]));
     if (lane == 0) s_max[wib] = longest;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -560,7 +592,7 @@ int learned_nb_grid() {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nb_all, kNbThreads, 0) != cudaSuccess || occ < 1)
         return 0;
-    return sms * (occ < 2 ? occ : 2);
+    return sms * (occ < 4 ? occ : 4);
 }
 
 cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status,
