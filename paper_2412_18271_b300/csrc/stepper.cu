@@ -13,6 +13,11 @@
 //                on the diagonal, the shortest ones: the first kSelfBonded
 //                with its self item, the next kPairBonded with the 32x32 item
 //                of its pair of tiles, the rest with a bonded-only item.
+//                A block whose eight 64x32 items share their i-tiles sums
+//                those i-forces in shared memory (as integers) and sends one
+//                add per atom and component.  A warp keeps what its first
+//                item reads besides positions (tiles, masks, LJ parameters,
+//                bonded records) in registers for the whole launch.
 //   grid barrier
 //   integration  tile t by warp t / G of block t % G (one tile per SM while
 //                the tiles fit), because FP64 throughput is the limit here;
