@@ -294,12 +294,17 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
     }
     __syncthreads();
     const bool uniform = s_uniform != 0;
+    // Work items: warp w takes the contiguous run [w * per, (w + 1) * per), so that consecutive 64x32 items of
+    // a warp share their i-tiles when there are more items than warps; the warp then sums those i-forces as
+    // integers in registers and sends them once per run of equal i-tiles.
+    const int per = (a.p.n_items + nwarps - 1) / nwarps;
+    const int it_first = gwarp * per, it_end = min(it_first + per, a.p.n_items);
     ItemCtx first;
     BondedList first_bl{0, 0, 0, 0};
     int4 brec[kBondRegs];    // records of the first item's bonded terms lane, lane + 32, ...
     float2 bpar[kBondRegs];  // and their bond parameters
-    if (gwarp < a.p.n_items) {
-        item_ctx(a.p, a.p.items[gwarp], lane, first);
+    if (it_first < a.p.n_items) {
+        item_ctx(a.p, a.p.items[it_first], lane, first);
         first_bl = bonded_list(a, first.item);
 #pragma unroll
         for (int k = 0; k < kBondRegs; ++k) {
@@ -323,15 +328,39 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
         p.pos4 = Pcur;
         float elj = 0.f, ec = 0.f, eb = 0.f, ea = 0.f;
         bool bad = false;
-        for (int it = gwarp; it < p.n_items; it += nwarps) {
+        int run_p = -1;         // i-tile pair of the current run of 64x32 items
+        long long run_f[6] = {0, 0, 0, 0, 0, 0};  // its i-forces (fixed point), atoms 64 run_p + lane (+ 32)
+        auto flush_run = [&]() {
+            if (run_p < 0) return;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    atomicAdd(&acc[3 * ((2 * run_p + h) * kTile + lane) + q], (unsigned long long)run_f[3 * h + q]);
+        };
+        for (int it = it_first; it < it_end; ++it) {
             ItemCtx later;
-            if (it != gwarp) item_ctx(p, p.items[it], lane, later);
-            const ItemCtx &c = it == gwarp ? first : later;
+            if (it != it_first) item_ctx(p, p.items[it], lane, later);
+            const ItemCtx &c = it == it_first ? first : later;
             float3 fio[2];
             if (energy)
-                item_eval<true>(p, c, lane, jt[w], acc, elj, ec, bad, uniform ? fio : nullptr);
+                item_eval<true>(p, c, lane, jt[w], acc, elj, ec, bad, fio);
             else
-                item_eval<false>(p, c, lane, jt[w], acc, elj, ec, bad, uniform ? fio : nullptr);
+                item_eval<false>(p, c, lane, jt[w], acc, elj, ec, bad, fio);
+            if (c.item.x == ITEM_OFF64 && !uniform) {
+                if (c.item.y != run_p) {
+                    flush_run();
+                    run_p = c.item.y;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) run_f[k] = 0;
+                }
+                run_f[0] += fx_from_float(fio[0].x);
+                run_f[1] += fx_from_float(fio[0].y);
+                run_f[2] += fx_from_float(fio[0].z);
+                run_f[3] += fx_from_float(fio[1].x);
+                run_f[4] += fx_from_float(fio[1].y);
+                run_f[5] += fx_from_float(fio[1].z);
+            }
             if (uniform) {
                 ired[w][0][lane] = fx_from_float(fio[0].x);
                 ired[w][1][lane] = fx_from_float(fio[0].y);
@@ -356,7 +385,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             if (item.x != ITEM_OFF64) {
                 int e0 = 0;
                 BondedList bl = first_bl;
-                if (it == gwarp) {
+                if (it == it_first) {
                     // records in registers: every position load is issued before the first evaluation
                     BondedGeom g[kBondRegs];
 #pragma unroll
@@ -377,6 +406,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
                 for (int e = e0 + lane; e < bl.size(); e += 32) bonded_term(p, bl.at(a.own, e), acc, eb, ea);
             }
         }
+        flush_run();
         bad |= !isfinite(eb + ea);
         if (bad) atomicOr(a.status, MDPF_STATUS_NONFINITE);
         if (energy) {
