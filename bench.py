@@ -43,7 +43,7 @@ RECORD_EVERY = 10            # frames and energies every 10 steps (the workload'
 # DRAM bytes (read + write) per launch of k_plain_persistent from the ncu capture in
 # profiles/k_plain_persistent_cluster2048.md: the L2-resident working set read once from a cold L2
 # (the bench flushes L2 between launches), independent of the MD steps per launch
-PLAIN_TRAFFIC = None
+PLAIN_TRAFFIC = 500736
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
