@@ -302,6 +302,27 @@ def test_persistent_bonded_split_and_many_items(which):
         assert abs(Ua[-1] - Uo[-1]) / s.n_atoms < 1e-5
 
 
+@pytest.mark.parametrize("n_mol", [3, 37, 90, 161])
+def test_persistent_matches_kernel_sequence_across_sizes(n_mol):
+    # 96 to 5,152 atoms: one item per warp with blocks that straddle runs of i-tiles, a partly filled grid,
+    # and several items per warp; the persistent stepper must follow the kernel sequence's trajectory
+    s = synth.cluster(n_mol, 32, max(20.0, 60.0 * (n_mol / 64.0) ** (1.0 / 3.0)), seed=50 + n_mol)  # c1's density
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=9)
+    a = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_PERSISTENT, energy_every=5)
+    a.set_state(s.pos, v0)
+    a.step(30)
+    c = mdpf.Context(s, stepper=mdpf.MDPF_STEPPER_KERNELS, energy_every=5)
+    c.set_state(s.pos, v0)
+    c.step(30)
+    xa, va = a.get_state()
+    xc, vc = c.get_state()
+    assert np.abs(xa - xc).max() < 1e-9 and np.abs(va - vc).max() < 1e-9
+    Ua, Ka = a.trace()
+    Uc, Kc = c.trace()
+    assert np.abs(Ua - Uc).max() <= 1e-7 * np.abs(Uc).max()
+    assert np.abs(Ka - Kc).max() <= 1e-9 * np.abs(Kc).max()
+
+
 def test_persistent_is_reproducible():
     s = synth.workload("cluster2048")
     v0 = synth.velocities(s.mass, s.pos, 300.0, seed=7)
