@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
 
 // ------------------------------------------------------------------ features
 
-constexpr int kFeatWarps = 4;
+constexpr int kFeatWarps = 2;   // warps (atoms) per block of k_features ...
+constexpr int kAtomWarps = 4;   // ... and of k_adjoint and k_jvp (each measured best on c4)
 
 // One warp per atom: neighbours, features (learned_terms.cuh), then the BF16
 // GEMM input row (and the FP32 row when asked) and the range check.
@@ -416,14 +417,14 @@ constexpr int kAdjChunk = 128;  // triplets staged per pass
 
 // One warp per atom: g row into the padded per-warp layout, neighbours, then
 // the chain rule of learned_terms.cuh (fixed-point force sums).
-__global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
+__global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
                                                              int gated) {
     if (gated && L.lflags[1]) return;
-    __shared__ NbrSmem sn[kFeatWarps];
-    __shared__ AdjScratch<kAdjChunk> sa[kFeatWarps];
-    __shared__ float sg[kFeatWarps][kGRow];
+    __shared__ NbrSmem sn[kAtomWarps];
+    __shared__ AdjScratch<kAdjChunk> sa[kAtomWarps];
+    __shared__ float sg[kAtomWarps][kGRow];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kFeatWarps + w;
+    const int i = blockIdx.x * kAtomWarps + w;
     if (i >= L.n) return;
     // all global loads first (neighbour row, then its positions alongside the g row), then the stores
     const int row = L.row_of[i];
@@ -445,15 +446,15 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_adjoint(LearnedDev L, const
 // Same lane layout and summation order as k_features; per pair the tangent of
 // r_ij is u_ij . (v_j - v_i), per triplet that of cos(theta) is
 // ((u_k - c u_j)/r_j) . (v_j - v_i) + ((u_j - c u_k)/r_k) . (v_k - v_i).
-__global__ void __launch_bounds__(32 * kFeatWarps) k_jvp(LearnedDev L, const float4 *pos4, const float *v, float *U) {
-    __shared__ NbrSmem sn[kFeatWarps];
-    __shared__ float accR[kFeatWarps][2][64];
-    __shared__ float accA[kFeatWarps][320];
-    __shared__ float tcs[kFeatWarps][32], tsn[kFeatWarps][32], tcot[kFeatWarps][32], tcsd[kFeatWarps][32];
-    __shared__ float tC[kFeatWarps][32], tCd[kFeatWarps][32], tB[kFeatWarps][32][4], tBd[kFeatWarps][32][4];
-    __shared__ int tP[kFeatWarps][32];
+__global__ void __launch_bounds__(32 * kAtomWarps) k_jvp(LearnedDev L, const float4 *pos4, const float *v, float *U) {
+    __shared__ NbrSmem sn[kAtomWarps];
+    __shared__ float accR[kAtomWarps][2][64];
+    __shared__ float accA[kAtomWarps][320];
+    __shared__ float tcs[kAtomWarps][32], tsn[kAtomWarps][32], tcot[kAtomWarps][32], tcsd[kAtomWarps][32];
+    __shared__ float tC[kAtomWarps][32], tCd[kAtomWarps][32], tB[kAtomWarps][32][4], tBd[kAtomWarps][32][4];
+    __shared__ int tP[kAtomWarps][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * kFeatWarps + w;
+    const int i = blockIdx.x * kAtomWarps + w;
     if (i >= L.n) return;
     NbrSmem &s = sn[w];
     for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
@@ -578,7 +579,7 @@ void learned_end(const LearnedDev &L, uint32_t *status, int fallback, cudaStream
 }
 
 void learned_jvp(const LearnedDev &L, const float4 *pos4, const float *v, float *U, cudaStream_t s) {
-    k_jvp<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, v, U);
+    k_jvp<<<(L.n + kAtomWarps - 1) / kAtomWarps, 32 * kAtomWarps, 0, s>>>(L, pos4, v, U);
 }
 
 void learned_import_g(const LearnedDev &L, const float *G_atoms, cudaStream_t s) {
@@ -619,7 +620,7 @@ void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long 
 }
 
 void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s) {
-    k_adjoint<<<(L.n + kFeatWarps - 1) / kFeatWarps, 32 * kFeatWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0);
+    k_adjoint<<<(L.n + kAtomWarps - 1) / kAtomWarps, 32 * kAtomWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0);
 }
 
 }  // namespace mdpf
