@@ -520,6 +520,34 @@ double orc_learned_energy_forces(const orc_mlp *M, int32_t n, const int32_t *el,
     return E;
 }
 
+/*
+ * Repulsive core of the learned potential: for every pair i < j closer than
+ * rc,  E = A (1 - x)^3 / x  with x = r / rc, so E and its first two
+ * derivatives vanish at rc and E grows as 1/r towards r = 0.  Returns the
+ * energy and adds -dE/dx to F [n][3] (F may be NULL).  dE/dr is written out
+ * by hand: dE/dx = -A (1 - x)^2 (3 x + (1 - x)) / x^2 = -A (1 - x)^2 (1 + 2 x) / x^2.
+ */
+double orc_core_energy_forces(int32_t n, const double *x, double A, double rc, double *F) {
+    double E = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+            const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (!(r < rc)) continue;
+            const double u = r / rc, om = 1.0 - u;
+            E += A * om * om * om / u;
+            if (F) {
+                const double dEdr = -A / rc * om * om * (1.0 + 2.0 * u) / (u * u);
+                for (int c = 0; c < 3; ++c) {
+                    /* E depends on x_j - x_i through r: dE/dx_j = dEdr d / r, dE/dx_i = -dEdr d / r */
+                    F[3 * i + c] += dEdr * d[c] / r;
+                    F[3 * j + c] -= dEdr * d[c] / r;
+                }
+            }
+        }
+    return E;
+}
+
 /* ---------------------------------------------------------------- training gradient */
 
 static double orc_d2celu(double z, double a) { return z >= 0 ? 0.0 : exp(z / a) / a; }

@@ -191,8 +191,10 @@ class OrcMLP(ctypes.Structure):
 
 def _learned_lib():
     L = lib()
-    for name in ("orc_mlp_energy", "orc_learned_energy_forces"):
+    for name in ("orc_mlp_energy", "orc_learned_energy_forces", "orc_core_energy_forces"):
         getattr(L, name).restype = ctypes.c_double
+    L.orc_core_energy_forces.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_void_p]
     for name in ("orc_features", "orc_feature_forces", "orc_feature_jvp"):
         getattr(L, name).restype = None
     L.orc_neighbors.restype = ctypes.c_int
@@ -241,8 +243,17 @@ def feature_jvp(element, pos, u):
     return Gd
 
 
+def core_energy_forces(pos, A: float, rc: float):
+    """Repulsive core sum_{i<j, r<rc} A (1 - r/rc)^3 (rc/r): (E, F [N,3])."""
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    F = np.zeros_like(x)
+    E = _learned_lib().orc_core_energy_forces(x.shape[0], _p(x), float(A), float(rc), _p(F))
+    return E, F
+
+
 class Learned:
-    """The learned potential of a ``model.Model`` evaluated in FP64 (weights taken as stored)."""
+    """The learned potential of a ``model.Model`` evaluated in FP64 (weights taken as stored):
+    the per-element MLP on the symmetry functions plus the model's repulsive core, if it has one."""
 
     def __init__(self, model):
         self.m = model
@@ -275,6 +286,10 @@ class Learned:
         F = np.zeros_like(x)
         G = np.zeros((x.shape[0], N_FEAT))
         E = _learned_lib().orc_learned_energy_forces(ctypes.byref(self._st), x.shape[0], _p(el), _p(x), _p(F), _p(G))
+        if getattr(self.m, "core_rc", 0.0) > 0.0:
+            Ec, Fc = core_energy_forces(x, self.m.core_a, self.m.core_rc)
+            E += Ec
+            F += Fc
         return E, F, G
 
 
@@ -306,8 +321,9 @@ def train_loss_grad(model, frames, w_force: float = 10.0):
 
     frames: list of (element [N], pos [N,3], E_ref, F_ref [N,3]).
       L = (1/B) sum_f ((E_f - E_ref,f) / N_f)^2  +  w_force * mean over all force components (F - F_ref)^2
-    Steps per frame: features G; energies and dE/dG; forces F = -J^T dE/dG; the
-    loss terms; v = dL/dF; U = J v (feature JVP); then the MLP parameter
+    Steps per frame: features G; energies and dE/dG; forces F = -J^T dE/dG (plus the
+    model's repulsive core in E and F, which has no parameters); the loss terms;
+    v = dL/dF; U = J v (feature JVP); then the MLP parameter
     gradient of sum_i [c E_i - U_i . dE_i/dG_i] with c = dL/dE_f.
     Returns (L, grads dict, per-frame (E, F)).
     """
@@ -322,6 +338,10 @@ def train_loss_grad(model, frames, w_force: float = 10.0):
         G = features(el, pos)
         E, _, dG = lrn.mlp(el, G)
         F = feature_forces(el, pos, dG)
+        if getattr(model, "core_rc", 0.0) > 0.0:   # no parameters, but part of E and F
+            Ec, Fc = core_energy_forces(pos, model.core_a, model.core_rc)
+            E += Ec
+            F = F + Fc
         loss += ((E - e_ref) / n) ** 2 / B + w_force * float(((F - f_ref) ** 2).sum()) / n_comp
         c = np.full(n, 2.0 * (E - e_ref) / (n * n) / B)
         v = 2.0 * w_force * (F - f_ref) / n_comp

@@ -6,10 +6,20 @@ E_i = W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0_Z.  The weights that
 define the model are the BF16 values of W1 and W2 (the GEMM operands run in
 BF16 with FP32 accumulation); biases, W3, b3 are FP32 and e0 FP64.
 
+Repulsive core: E_core = sum over pairs i < j with r < rc of A (1 - r/rc)^3 (rc/r).
+The symmetry functions vanish as r -> 0 (the first radial shell sits at
+0.9 A with eta = 16 A^-2), so a network on them sees two merging atoms as no
+neighbour at all and cannot hold them apart; without this term, bonded H-H
+pairs of the synthetic molecules fuse in hot NVE runs.  Its value, slope and
+curvature vanish at rc, so it changes nothing above rc.  The default
+(CORE_A = 400 kcal/mol, CORE_RC = 0.8 A) lies below every bond length the
+workloads draw (1.0 to 1.5 A).
+
 Blob layout (little endian):
   header   64 bytes: magic "MDPFMLP1", int32 version=1, n_elem=4, n_feat=384,
-           h1=256, h2=128, flags (bit 0: feature ranges present), float64
-           celu_alpha, 24 bytes reserved
+           h1=256, h2=128, flags (bit 0: feature ranges present, bit 1: core
+           present), float64 celu_alpha, float64 core_A, float64 core_rc,
+           8 bytes reserved
   per element e = 0..3:
            uint16 W1[h1][n_feat] (bf16 bits), float32 b1[h1],
            uint16 W2[h2][h1] (bf16 bits),     float32 b2[h2],
@@ -26,7 +36,9 @@ import numpy as np
 N_ELEM, N_FEAT, H1, H2 = 4, 384, 256, 128
 CELU_ALPHA = 0.1
 MAGIC = b"MDPFMLP1"
-HEADER = struct.Struct("<8s6id24x")
+HEADER = struct.Struct("<8s6iddd8x")
+CORE_A = 400.0     # kcal/mol
+CORE_RC = 0.8      # A
 
 
 def bf16_bits(x: np.ndarray) -> np.ndarray:
@@ -54,10 +66,13 @@ class Model:
     lo: np.ndarray | None = None   # f32 [4, 384] feature range of the training data
     hi: np.ndarray | None = None
     alpha: float = CELU_ALPHA
+    core_a: float = 0.0            # repulsive core A (kcal/mol) and rc (A); core_rc == 0: no core
+    core_rc: float = 0.0
 
     def pack(self) -> bytes:
-        flags = 1 if self.lo is not None else 0
-        out = [HEADER.pack(MAGIC, 1, N_ELEM, N_FEAT, H1, H2, flags, float(self.alpha))]
+        flags = (1 if self.lo is not None else 0) | (2 if self.core_rc > 0 else 0)
+        core = (float(self.core_a), float(self.core_rc)) if self.core_rc > 0 else (0.0, 0.0)
+        out = [HEADER.pack(MAGIC, 1, N_ELEM, N_FEAT, H1, H2, flags, float(self.alpha), *core)]
         for e in range(N_ELEM):
             out.append(bf16_bits(self.W1[e]).tobytes())
             out.append(np.asarray(self.b1[e], dtype="<f4").tobytes())
@@ -65,14 +80,16 @@ class Model:
             out.append(np.asarray(self.b2[e], dtype="<f4").tobytes())
             out.append(np.asarray(self.W3[e], dtype="<f4").tobytes())
             out.append(struct.pack("<ffd", float(self.b3[e]), 0.0, float(self.e0[e])))
-        if flags:
+        if flags & 1:
             out.append(np.asarray(self.lo, dtype="<f4").tobytes())
             out.append(np.asarray(self.hi, dtype="<f4").tobytes())
         return b"".join(out)
 
     @staticmethod
     def unpack(blob: bytes) -> "Model":
-        magic, ver, ne, nf, h1, h2, flags, alpha = HEADER.unpack_from(blob, 0)
+        magic, ver, ne, nf, h1, h2, flags, alpha, core_a, core_rc = HEADER.unpack_from(blob, 0)
+        if not flags & 2:
+            core_a = core_rc = 0.0
         if magic != MAGIC or ver != 1 or (ne, nf, h1, h2) != (N_ELEM, N_FEAT, H1, H2):
             raise ValueError("not an MDPFMLP1 blob of the expected shape")
         off = HEADER.size
@@ -99,7 +116,7 @@ class Model:
             lo = take("<f4", N_ELEM * N_FEAT).reshape(N_ELEM, N_FEAT).copy()
             hi = take("<f4", N_ELEM * N_FEAT).reshape(N_ELEM, N_FEAT).copy()
         return Model(np.stack(W1), np.stack(b1), np.stack(W2), np.stack(b2), np.stack(W3),
-                     np.array(b3, dtype=np.float32), np.array(e0), lo, hi, alpha)
+                     np.array(b3, dtype=np.float32), np.array(e0), lo, hi, alpha, core_a, core_rc)
 
     def rounded(self) -> "Model":
         """Copy whose W1, W2 hold the BF16-rounded values (the values the blob stores)."""
@@ -119,7 +136,7 @@ def to_flat(m: Model) -> np.ndarray:
     return np.concatenate(parts)
 
 
-def from_flat(flat, e0, lo=None, hi=None) -> Model:
+def from_flat(flat, e0, lo=None, hi=None, core_a: float = 0.0, core_rc: float = 0.0) -> Model:
     """Model from an FP32 parameter vector (W1, W2 keep their FP32 values; pack() rounds them to BF16)."""
     flat = np.asarray(flat, dtype=np.float32).reshape(N_ELEM, PARAMS_PER_ELEMENT)
     o1 = H1 * N_FEAT
@@ -129,11 +146,12 @@ def from_flat(flat, e0, lo=None, hi=None) -> Model:
     o5 = o4 + H2
     return Model(flat[:, :o1].reshape(N_ELEM, H1, N_FEAT).copy(), flat[:, o1:o2].copy(),
                  flat[:, o2:o3].reshape(N_ELEM, H2, H1).copy(), flat[:, o3:o4].copy(), flat[:, o4:o5].copy(),
-                 flat[:, o5].copy(), np.asarray(e0, dtype=np.float64), lo, hi)
+                 flat[:, o5].copy(), np.asarray(e0, dtype=np.float64), lo, hi, CELU_ALPHA, core_a, core_rc)
 
 
-def init_model(seed: int) -> Model:
-    """Kaiming-uniform weights U(+-sqrt(6/fan_in)), zero biases, zero e0 (seeded)."""
+def init_model(seed: int, core: bool = True) -> Model:
+    """Kaiming-uniform weights U(+-sqrt(6/fan_in)), zero biases, zero e0 (seeded), with the default
+    repulsive core unless core is False."""
     rng = np.random.default_rng(seed)
 
     def ku(shape, fan_in):
@@ -145,4 +163,6 @@ def init_model(seed: int) -> Model:
     W3 = ku((N_ELEM, H2), H2)
     m = Model(W1, np.zeros((N_ELEM, H1), np.float32), W2, np.zeros((N_ELEM, H2), np.float32), W3,
               np.zeros(N_ELEM, np.float32), np.zeros(N_ELEM))
+    if core:
+        m.core_a, m.core_rc = CORE_A, CORE_RC
     return m.rounded()

@@ -256,3 +256,66 @@ def test_flat_parameter_layout_roundtrip(mdl):
     # element 2's W2[5][7] sits at 2 * P + 256*384 + 256 + 5*256 + 7
     P = model.PARAMS_PER_ELEMENT
     assert flat[2 * P + 256 * 384 + 256 + 5 * 256 + 7] == np.float32(mdl.W2[2][5][7])
+
+
+# ------------------------------------------------------------ repulsive core
+
+CORE_A, CORE_RC = 400.0, 0.8
+
+
+def _dimer(r):
+    return np.array([[0.0, 0.0, 0.0], [0.3 * r, -0.4 * r, math.sqrt(1 - 0.25) * r]])
+
+
+@pytest.mark.parametrize("r,e_hand", [(0.4, 100.0), (0.2, 675.0), (0.6, 25.0 / 3.0), (0.8, 0.0), (1.3, 0.0)])
+def test_core_dimer_values_by_hand(r, e_hand):
+    # A (1 - x)^3 / x at x = 1/2: 400 / 8 * 2 = 100;  x = 1/4: 400 * 27/64 * 4 = 675;
+    # x = 3/4: 400 / 64 * 4/3 = 25/3;  zero from rc on
+    e, f = O.core_energy_forces(_dimer(r), CORE_A, CORE_RC)
+    assert e == pytest.approx(e_hand, rel=1e-12, abs=1e-12)
+    assert np.abs(f.sum(axis=0)).max() < 1e-10
+
+
+def test_core_vanishes_smoothly_at_rc():
+    # a cubic contact: E(rc - d) ~ A (d / rc)^3 (a quadratic or linear one would be 10^2 / 10^4 x larger)
+    d = 1e-3
+    e, f = O.core_energy_forces(_dimer(CORE_RC - d), CORE_A, CORE_RC)
+    assert e == pytest.approx(CORE_A * (d / CORE_RC) ** 3, rel=5e-3)
+    # and its force ~ 3 A d^2 / rc^3, so it vanishes quadratically
+    assert np.linalg.norm(f[0]) == pytest.approx(3 * CORE_A * d * d / CORE_RC ** 3, rel=1e-2)
+
+
+def test_core_repels_and_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    x = np.array([[0, 0, 0], [0.5, 0.1, 0], [0.2, 0.55, 0.1], [1.5, 0.2, 0.3], [0.1, 0.1, 0.7]], dtype=np.float64)
+    x += rng.normal(scale=0.01, size=x.shape)
+    e, f = O.core_energy_forces(x, CORE_A, CORE_RC)
+    h = 1e-6
+    fd = np.zeros_like(x)
+    for a in range(x.shape[0]):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[a, c] += h
+            xm[a, c] -= h
+            fd[a, c] = -(O.core_energy_forces(xp, CORE_A, CORE_RC)[0] - O.core_energy_forces(xm, CORE_A, CORE_RC)[0]) / (2 * h)
+    assert np.abs(f - fd).max() < 1e-5 * np.abs(fd).max()
+    assert np.abs(f.sum(axis=0)).max() < 1e-9 * np.abs(f).max()
+    assert np.abs(np.cross(x, f).sum(axis=0)).max() < 1e-9 * np.abs(f).max()
+    # repulsive: the force on atom 1 of a close dimer points away from atom 0
+    _, fd2 = O.core_energy_forces(_dimer(0.5), CORE_A, CORE_RC)
+    assert float(np.dot(fd2[1], _dimer(0.5)[1])) > 0
+
+
+def test_learned_energy_includes_the_core():
+    s = synth.molecule(5, seed=3)
+    x = s.pos.copy()
+    x[1] = x[0] + np.array([0.45, 0.0, 0.0])   # one pair inside the core radius
+    m_on = model.init_model(7)
+    m_off = model.init_model(7, core=False)
+    e_on, f_on, _ = O.Learned(m_on).energy_forces(s.element, x)
+    e_off, f_off, _ = O.Learned(m_off).energy_forces(s.element, x)
+    ec, fc_ = O.core_energy_forces(x, model.CORE_A, model.CORE_RC)
+    assert ec > 10.0
+    assert e_on - e_off == pytest.approx(ec, rel=1e-12)
+    assert np.abs((f_on - f_off) - fc_).max() < 1e-9 * np.abs(fc_).max()
+    assert model.Model.unpack(m_on.pack()).core_rc == model.CORE_RC
