@@ -191,15 +191,19 @@ typedef struct mdpf_params {
  * R_m = 0.9 + m 2.6/4 (eta 8) x 8 angular sections theta_p = (2p+1) pi/16 of
  * 2^(1-32) (1 + cos(theta - theta_p))^32 with theta = acos(0.95 cos theta_ijk),
  * cutoff 3.5 A) feed a per-element MLP 384 -> 256 -> 128 -> 1 with CELU(0.1):
- * E = sum_i W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0.  Forces are the
- * analytic adjoint -dE/dx.  The GEMM operands run in BF16 (features, CELU
+ * E = sum_i W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0, plus an optional
+ * repulsive pair core E_core = sum_{i<j, r_ij < rc} A (1 - r/rc)^3 (rc/r)
+ * (the features vanish as r -> 0, so the network alone cannot keep two atoms
+ * from merging).  Forces are the analytic adjoint -dE/dx.  The GEMM operands run in BF16 (features, CELU
  * outputs and back-propagated deltas rounded to BF16), accumulations in FP32,
  * energies and the state in FP64.  The plain topology (bonds, charges, LJ) is
  * still required: it is the fallback force field.
  *
  * Model blob (little endian): 64-byte header {char magic[8] = "MDPFMLP1";
  * int32 version = 1, n_elem = 4, n_feat = 384, h1 = 256, h2 = 128, flags
- * (bit 0: feature ranges follow); float64 celu_alpha; 24 reserved bytes},
+ * (bit 0: feature ranges follow; bit 1: repulsive core present); float64
+ * celu_alpha; float64 core_A (kcal/mol, in (0, 1e5]), float64 core_rc (A, in
+ * (0, 2]), both read only with flag bit 1; 8 reserved bytes},
  * then per element: uint16 W1[256][384] (BF16 bits), float32 b1[256],
  * uint16 W2[128][256] (BF16 bits), float32 b2[128], float32 W3[128],
  * float32 b3, float32 pad, float64 e0; then, if flags & 1, float32
@@ -390,6 +394,8 @@ typedef struct mdpf_train_params {
     int32_t atoms_per_frame;   /* N, the same for every frame */
     double w_force;            /* force-loss weight (10) */
     double e0[4];              /* per-element self energies (not trained) */
+    double core_a, core_rc;    /* the model's repulsive core (kcal/mol, A; core_rc 0: none).  It has no
+                                  trained parameters; its energy and forces are part of E_f and F. */
 } mdpf_train_params;
 #define MDPF_TRAIN_PARAMS_PER_ELEMENT 131585
 MDPF_API int mdpf_trainer_create(const mdpf_train_params *params, mdpf_trainer **out);

@@ -327,7 +327,8 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                 const int i = L.atom_of[row0 + rr];
                 int nc, nr, na;
                 load_neighbours<false>(L, pos4, i, sn, lane, nc, nr, na);
-                adjoint_atom(i, sn, nc, nr, na, gst + k * kGRow, A, fx, lane);
+                adjoint_atom(i, sn, nc, nr, na, gst + k * kGRow, A, fx, lane, make_float2(L.core_a, L.core_rc),
+                             efx != nullptr ? efx + E_LEARN : nullptr);
             }
             fu_sync();   // the half's g rows are no longer read
         }

@@ -418,7 +418,7 @@ constexpr int kAdjChunk = 128;  // triplets staged per pass
 // One warp per atom: g row into the padded per-warp layout, neighbours, then
 // the chain rule of learned_terms.cuh (fixed-point force sums).
 __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const float4 *pos4, unsigned long long *fx,
-                                                             int gated) {
+                                                             int gated, unsigned long long *ecore, int ecore_per) {
     if (gated && L.lflags[1]) return;
     __shared__ NbrSmem sn[kAtomWarps];
     __shared__ AdjScratch<kAdjChunk> sa[kAtomWarps];
@@ -437,7 +437,8 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const
     for (int b = 0; b < kNFeat / 32; ++b) sg[w][g_col(32 * b + lane)] = gv[b];
     int cnt, nr, na;
     store_neighbours<false>(nf, sn[w], lane, cnt, nr, na);
-    adjoint_atom(i, sn[w], cnt, nr, na, sg[w], sa[w], fx, lane);
+    adjoint_atom(i, sn[w], cnt, nr, na, sg[w], sa[w], fx, lane, make_float2(L.core_a, L.core_rc),
+                 ecore != nullptr ? ecore + i / ecore_per : nullptr);
 }
 
 // ------------------------------------------------------------------ feature JVP
@@ -619,8 +620,10 @@ void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long 
     else k_mlp_simt<true><<<L.n_rows / kMlpRows, 256, 0, s>>>(L, gated ? 1 : 0, efx);
 }
 
-void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s) {
-    k_adjoint<<<(L.n + kAtomWarps - 1) / kAtomWarps, 32 * kAtomWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0);
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated,
+                     unsigned long long *ecore, int ecore_per, cudaStream_t s) {
+    k_adjoint<<<(L.n + kAtomWarps - 1) / kAtomWarps, 32 * kAtomWarps, 0, s>>>(L, pos4, fx, gated ? 1 : 0, ecore,
+                                                                               ecore_per > 0 ? ecore_per : 1);
 }
 
 }  // namespace mdpf

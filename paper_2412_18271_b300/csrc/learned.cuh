@@ -53,6 +53,7 @@ struct LearnedDev {
     const float *b1, *b2, *W3, *b3;            // [4][256], [4][128], [4][128], [4]
     const double *e0;                          // [4]
     const float *lo, *hi;                      // [4][384] training range, or null
+    float core_a, core_rc;       // short-range repulsive core A (kcal/mol), r_c (A); core_rc == 0: none
     unsigned int *lflags;        // [0] rebuild requested, [1] out of range this step, [2] overflow, [3] MLP timeout
     long long *lcount;           // [0] rebuilds, [1] fallback steps, [2] max row length
 };
@@ -78,7 +79,9 @@ cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forc
 void learned_features(const LearnedDev &L, const float4 *pos4, bool write_f32, cudaStream_t s);
 // MLP on the CUDA cores; efx (or null) receives the summed energy in its learned-energy slot
 void learned_mlp(const LearnedDev &L, bool gated, bool fp32, unsigned long long *efx, cudaStream_t s);
-void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated, cudaStream_t s);
+// forces into fx; the core energy of atom i goes to ecore[i / ecore_per] (fixed point) unless ecore is null
+void learned_adjoint(const LearnedDev &L, const float4 *pos4, unsigned long long *fx, bool gated,
+                     unsigned long long *ecore, int ecore_per, cudaStream_t s);
 void learned_begin(const LearnedDev &L, cudaStream_t s);
 // a step that left the feature range: drop the model's forces and energy (fused path, before the plain force field)
 void learned_fallback_clear(const LearnedDev &L, unsigned long long *fx, unsigned long long *efx, cudaStream_t s);

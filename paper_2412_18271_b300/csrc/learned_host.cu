@@ -129,6 +129,13 @@ int learned_validate(const mdpf_params *prm, std::string &msg) {
     const bool ranges = (hdr[5] & 1) != 0;
     const size_t expect = kHeader + 4 * kPerElement + (ranges ? 2 * 4 * kNFeat * sizeof(float) : 0);
     if (prm->model_bytes != expect) return msg = "model blob: wrong size", MDPF_ERR_INVALID_ARG;
+    if (hdr[5] & 2) {   // repulsive core: A (kcal/mol) and r_c (A) in the header
+        double core[2];
+        std::memcpy(core, blob + 40, sizeof(core));
+        if (!(core[0] > 0.0 && core[0] <= 1e5) || !(core[1] > 0.0 && core[1] <= 2.0))
+            return msg = "model blob: core A must be in (0, 1e5] kcal/mol and r_c in (0, 2] A", MDPF_ERR_INVALID_ARG;
+    }
+    if (hdr[5] & ~3) return msg = "model blob: unknown flag bits", MDPF_ERR_INVALID_ARG;
     return MDPF_OK;
 }
 
@@ -143,6 +150,12 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
 
     LearnedHost *h = new LearnedHost();
     c->learned = h;
+    if (hdr[5] & 2) {
+        double core[2];
+        std::memcpy(core, blob + 40, sizeof(core));
+        h->dev.core_a = (float)core[0];
+        h->dev.core_rc = (float)core[1];
+    }
     h->fallback = prm->fallback != 0;
     h->rebuild_every = prm->rebuild_every > 0 ? prm->rebuild_every : 20;
     h->skin = prm->skin > 0 ? prm->skin : 1.0;
@@ -363,7 +376,7 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
     enqueue_mlp(h, status, gated, efx, s);
     prof_end(c, MDPF_PROF_LEARN_MLP, ev, s);
     ev = prof_begin(c, s);
-    learned_adjoint(L, pos4, fx, gated, s);
+    learned_adjoint(L, pos4, fx, gated, efx != nullptr ? efx + E_LEARN : nullptr, L.n, s);
     prof_end(c, MDPF_PROF_LEARN_ADJOINT, ev, s);
     if (L.lo == nullptr) return MDPF_OK;   // no feature ranges: no evaluation can leave them
     if (gated) {

@@ -9,6 +9,9 @@
 //                                         exp(-8 ((r_ij + r_ik)/2 - R_m)^2) fc(r_ij; 3.5) fc(r_ik; 3.5)
 //   theta = acos(0.95 cos theta_ijk), cos(theta - theta_p) = c cos theta_p + sqrt(1 - c^2) sin theta_p
 //   R_k = 0.9 + 4.3 k / 16,  R_m = 0.9 + 0.65 m,  theta_p = (2 p + 1) pi / 16
+// plus, when the model has one, a repulsive pair core that the features cannot
+// express (they vanish as r -> 0, so no network on them can keep two atoms
+// apart):  E_core = sum_{i<j, r < rc} A (1 - x)^3 / x,  x = r / rc.
 // The Gaussians exp(x), x <= 0, are one ex2.approx instruction on x log2(e)
 // (subnormal results flush to zero): the relative error grows with |x| but
 // stays below ~2e-6 wherever exp(x) is not negligible (x > -30), far inside
@@ -64,6 +67,16 @@ __device__ __forceinline__ float4 cutoffs(float r) {
     const bool inr = r < kRcRad, ina = r < kRcAng;
     return make_float4(inr ? 0.5f * cr + 0.5f : 0.f, inr ? (-0.5f * kPi / kRcRad) * sr : 0.f,
                        ina ? 0.5f * ca + 0.5f : 0.f, ina ? (-0.5f * kPi / kRcAng) * sa : 0.f);
+}
+
+// The repulsive core of one pair at r < rc: energy A (1 - x)^3 / x and its
+// r-derivative -(A / rc) (1 - x)^2 (1 + 2 x) / x^2, x = r / rc (zero with its
+// first two derivatives at rc, growing as 1/r below).
+__device__ __forceinline__ void core_pair(float r, float a, float rc, float &e, float &dedr) {
+    const float x = __fdividef(r, rc), ix = __fdividef(1.f, x), om = 1.f - x;
+    const float om2 = om * om;
+    e = a * om2 * om * ix;
+    dedr = -__fdividef(a, rc) * om2 * (1.f + 2.f * x) * ix * ix;
 }
 
 // Atom i's neighbour row in registers: lane l holds entries l, l + 32, ...
@@ -378,12 +391,19 @@ __device__ __forceinline__ int g_col(int f) { return f < 64 ? f : 64 + kAngStrid
 // force is one running sum (radial term, then its triplets in index order), so
 // no sum depends on the chunk size.  The sums go to fx as int64 fixed point,
 // so the result is reproducible bit for bit.
+// core = (A, rc) of the repulsive core (rc == 0: none).  Every pair sits in
+// both atoms' rows, so each side adds half of the pair's core energy and
+// force; the half energies of atom i go to *ecore (fixed point) when ecore is
+// set.
 template <int Chunk>
 __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, int nr, int na, const float *g,
-                                             AdjScratch<Chunk> &A, unsigned long long *fx, int lane) {
+                                             AdjScratch<Chunk> &A, unsigned long long *fx, int lane,
+                                             float2 core = make_float2(0.f, 0.f),
+                                             unsigned long long *ecore = nullptr) {
     for (int q = lane; q < cnt * 3; q += 32) (&A.f[0][0])[q] = 0.f;
     __syncwarp();
     float fix = 0.f, fiy = 0.f, fiz = 0.f;
+    float ecore_i = 0.f;
     // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j = -dE/dr u,  F_i += dE/dr u
     for (int u = lane; u < nr; u += 32) {
         const int q = s.rad[u];
@@ -397,6 +417,12 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
             const float x = r - (0.9f + (float)k * (4.3f / 16.f));
             const float ex = exp_neg(-kEtaR * x * x);
             dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
+        }
+        if (r < core.y) {
+            float ec, dc;
+            core_pair(r, core.x, core.y, ec, dc);
+            dEdr = fmaf(0.5f, dc, dEdr);
+            ecore_i = fmaf(0.5f, ec, ecore_i);
         }
         const float sx = dEdr * d.x, sy = dEdr * d.y, sz = dEdr * d.z;
         A.f[q][0] = -sx;
@@ -567,6 +593,13 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
         atomicAdd(&fx[3 * i + 0], (unsigned long long)fx_from_float(fix));
         atomicAdd(&fx[3 * i + 1], (unsigned long long)fx_from_float(fiy));
         atomicAdd(&fx[3 * i + 2], (unsigned long long)fx_from_float(fiz));
+    }
+    if (ecore != nullptr && core.y > 0.f) {
+        // the core energy of atom i: lane sums reduced in a fixed order, one fixed-point add when nonzero
+        double e = (double)ecore_i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0 && e != 0.0) fx_add_d(ecore, e);
     }
     __syncwarp();
 }

@@ -6,7 +6,8 @@
 //   1. rows: per frame, atoms grouped by element into 128-row tiles;
 //   2. neighbours per frame (all pairs within 5.2 A, FP32 predicate, ascending);
 //   3. features (FP32 and the BF16 GEMM copy), MLP energies and dE/dG on the
-//      tensor cores, forces by the feature adjoint;
+//      tensor cores, forces by the feature adjoint (with the model's repulsive
+//      core, whose energy and forces have no parameters but enter E_f and F);
 //   4. per frame: c = dL/dE_f, v = dL/dF;  U = J v by the feature JVP;
 //   5. per row: primal and tangent passes of the MLP along U, then one reverse
 //      sweep over both for sum_i [c E_i - U_i . dE_i/dG_i]; the row adjoints
@@ -214,15 +215,15 @@ __device__ double block_sum_d(double v, double *sh) {
 
 // Per frame: energy, energy-loss weight c (per row), force residual -> v, loss parts.
 __global__ void k_tr_loss(LearnedDev L, int N, int B, double w_force, const int *tile_off, const double *E_ref,
-                          const float *F_ref, const unsigned long long *fx, float *c_row, float *v,
-                          double *loss_parts) {
+                          const float *F_ref, const unsigned long long *fx, const unsigned long long *ecore,
+                          float *c_row, float *v, double *loss_parts) {
     __shared__ double sh[32];
     __shared__ double s_c;
     const int f = blockIdx.x;
     const int r0 = tile_off[f] * kRowTile, r1 = tile_off[f + 1] * kRowTile;
     double e = 0.0;
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) e += L.E_row[r];
-    const double Ef = block_sum_d(e, sh);
+    const double Ef = block_sum_d(e, sh) + fx_val(ecore[f]);   // MLP rows + the repulsive core
     if (threadIdx.x == 0) {
         const double d = (Ef - E_ref[f]) / N;
         loss_parts[2 * f] = d * d / B;
@@ -452,6 +453,7 @@ struct mdpf_trainer {
     int *d_cnt = nullptr, *d_ntile = nullptr, *d_tile_off = nullptr, *d_live = nullptr;
     float4 *d_pos4 = nullptr;
     unsigned long long *d_fx = nullptr, *d_efx = nullptr;
+    unsigned long long *d_ecore = nullptr;   // [max_frames] repulsive-core energy per frame (fixed point)
     uint32_t *d_status = nullptr;
     float *d_c = nullptr, *d_v = nullptr, *d_U = nullptr;
     RowOut ro{};
@@ -507,6 +509,8 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     if (p->max_frames < 1 || p->atoms_per_frame < 1 || (int64_t)p->max_frames * p->atoms_per_frame > (1 << 22))
         return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "max_frames, atoms_per_frame out of range");
     if (!(p->w_force >= 0.0)) return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "w_force must be >= 0");
+    if (p->core_rc != 0.0 && (!(p->core_a > 0.0 && p->core_a <= 1e5) || !(p->core_rc > 0.0 && p->core_rc <= 2.0)))
+        return tr_fail(nullptr, MDPF_ERR_INVALID_ARG, "core A must be in (0, 1e5] and r_c in (0, 2] (or r_c 0: none)");
     mdpf_trainer *t = new mdpf_trainer();
     t->max_frames = p->max_frames;
     t->N = p->atoms_per_frame;
@@ -580,6 +584,7 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     TA(t->d_etiles, 4 * (size_t)t->tiles_max);
     TA(t->d_wsplit, kWgSplits);
     TA(t->d_lparts, 2 * (size_t)t->max_frames);
+    TA(t->d_ecore, (size_t)t->max_frames);
     TA(t->d_rmin, 4 * kNFeat);
     TA(t->d_rmax, 4 * kNFeat);
 #undef TA
@@ -603,6 +608,8 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     L.b3 = b3;
     L.e0 = e0;
     L.lo = L.hi = nullptr;
+    L.core_a = (float)p->core_a;
+    L.core_rc = (float)p->core_rc;
     cudaError_t e1 = cudaMemcpy(e0, t->e0, sizeof(double) * 4, cudaMemcpyHostToDevice);
     if (e1 == cudaSuccess) e1 = cudaMemset(atom_of, 0xFF, sizeof(int) * R);
     if (e1 == cudaSuccess) e1 = cudaMemset(L.G16, 0, sizeof(__nv_bfloat16) * R * kNFeat);
@@ -689,10 +696,11 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     cudaError_t ce = learned_mlp_tc(L, t->maps, t->d_status, false, nullptr, s);
     if (ce != cudaSuccess) return tr_cuda(t, ce, "learned_mlp_tc");
     cudaMemsetAsync(t->d_fx, 0, sizeof(unsigned long long) * 3 * (size_t)n, s);
-    learned_adjoint(L, t->d_pos4, t->d_fx, false, s);
+    cudaMemsetAsync(t->d_ecore, 0, sizeof(unsigned long long) * (size_t)B, s);
+    learned_adjoint(L, t->d_pos4, t->d_fx, false, t->d_ecore, N, s);
     // 4. loss, c, v; U = J v
-    k_tr_loss<<<B, 256, 0, s>>>(L, N, B, t->w_force, t->d_tile_off, d_E_ref, d_F_ref, t->d_fx, t->d_c, t->d_v,
-                                 t->d_lparts);
+    k_tr_loss<<<B, 256, 0, s>>>(L, N, B, t->w_force, t->d_tile_off, d_E_ref, d_F_ref, t->d_fx, t->d_ecore, t->d_c,
+                                 t->d_v, t->d_lparts);
     k_tr_loss_total<<<1, 32, 0, s>>>(B, t->d_lparts, d_loss3);
     learned_jvp(L, t->d_pos4, t->d_v, t->d_U, s);
     // 5. per-row reverse over the tangent pass

@@ -79,7 +79,8 @@ class mdpf_params(ctypes.Structure):
 
 
 class mdpf_train_params(ctypes.Structure):
-    _fields_ = [("max_frames", _i32), ("atoms_per_frame", _i32), ("w_force", _f64), ("e0", _f64 * 4)]
+    _fields_ = [("max_frames", _i32), ("atoms_per_frame", _i32), ("w_force", _f64), ("e0", _f64 * 4),
+                ("core_a", _f64), ("core_rc", _f64)]
 
 
 TRAIN_PARAMS_PER_ELEMENT = 131585
@@ -445,13 +446,17 @@ class Trainer:
     """Device-side force-matching loss and gradient (mdpf_trainer_*); all tensors
     are caller-owned device memory passed by address (e.g. torch data_ptr())."""
 
-    def __init__(self, max_frames: int, atoms_per_frame: int, e0, w_force: float = 10.0):
+    def __init__(self, max_frames: int, atoms_per_frame: int, e0, w_force: float = 10.0, core_a: float = 0.0,
+                 core_rc: float = 0.0):
+        """core_a, core_rc: the model's repulsive core (core_rc 0: none), part of the predicted E and F."""
         p = mdpf_train_params()
         p.max_frames = int(max_frames)
         p.atoms_per_frame = int(atoms_per_frame)
         p.w_force = float(w_force)
         for e in range(4):
             p.e0[e] = float(e0[e])
+        p.core_a = float(core_a)
+        p.core_rc = float(core_rc)
         h = _vp()
         rc = lib().mdpf_trainer_create(ctypes.byref(p), ctypes.byref(h))
         if rc != MDPF_OK:

@@ -8,7 +8,9 @@ other its inputs.
 Recipe (the workloads of the benchmark configurations, restated):
 
 * A molecule of ``n`` atoms is a random bonded tree: atom ``i >= 1`` bonds to a
-  parent drawn uniformly from ``[0, i)``.  Elements H/C/N/O are drawn i.i.d.
+  parent drawn uniformly from the atoms ``j < i`` that have fewer than four
+  bonds (a tetrahedral centre at most, so every pair of bonds at an atom can
+  sit at 109.5 deg).  Elements H/C/N/O are drawn i.i.d.
   with probabilities 0.5/0.3/0.1/0.1.  Bond lengths ``r0 ~ U[1.0, 1.5]`` A,
   bond constant 300 kcal/mol/A^2; one harmonic angle per pair of bonds that
   share an atom, k = 50 kcal/mol/rad^2, theta0 = 109.5 deg.  Charges
@@ -19,9 +21,9 @@ Recipe (the workloads of the benchmark configurations, restated):
   parent, at 109.5 deg to the parent's own parent bond, at the azimuth (out of
   48 tried) that keeps it farthest from every atom already placed.  The
   coordinates are then cleaned up by least squares on distances only (bonded
-  pairs at r0, pairs sharing an atom at the 109.5 deg law-of-cosines distance,
-  all other pairs of the molecule at least 3.2 A apart); no force field is
-  evaluated.
+  pairs at r0 with weight 100, pairs sharing an atom at the 109.5 deg
+  law-of-cosines distance with weight 50, all other pairs of the molecule at
+  least 3.2 A apart with weight 50); no force field is evaluated.
 * A cluster places ``m`` such molecules, each with its own random tree, with
   a uniform random rotation and a centre drawn uniformly in a ball of the given
   radius; a placement is rejected if an atom leaves the ball or comes closer
@@ -69,11 +71,19 @@ class System:
         return int(self.element.shape[0])
 
 
+MAX_DEGREE = 4
+
+
 def _tree(rng, n):
     elem = rng.choice(4, size=n, p=ELEMENT_P).astype(np.int32)
     parent = np.full(n, -1, dtype=np.int64)
+    degree = np.zeros(n, dtype=np.int64)
     for i in range(1, n):
-        parent[i] = rng.integers(0, i)
+        free = np.nonzero(degree[:i] < MAX_DEGREE)[0]   # never empty: atom i - 1 has at most one bond yet
+        p = int(free[rng.integers(0, free.size)])
+        parent[i] = p
+        degree[p] += 1
+        degree[i] += 1
     r0 = rng.uniform(1.0, 1.5, size=n - 1)
     q = rng.uniform(-0.5, 0.5, size=n)
     q = q - q.mean()
@@ -146,7 +156,7 @@ def _geometry_terms(n, bonds, r0):
         for p in range(len(nbr[v])):
             for q in range(p + 1, len(nbr[v])):
                 (a, ra), (b, rb) = nbr[v][p], nbr[v][q]
-                tgt[(min(a, b), max(a, b))] = (math.sqrt(ra * ra + rb * rb - 2 * ra * rb * c0), 5.0)
+                tgt[(min(a, b), max(a, b))] = (math.sqrt(ra * ra + rb * rb - 2 * ra * rb * c0), W_13)
     pi, pj = np.triu_indices(n, 1)
     key = {k: t for k, t in tgt.items()}
     d0 = np.full(pi.shape, CONTACT_MIN)
@@ -160,6 +170,7 @@ def _geometry_terms(n, bonds, r0):
 
 
 CONTACT_MIN = 3.2
+W_13 = 50.0
 
 
 def _relax(x, terms):

@@ -103,7 +103,7 @@ def main(argv=None):
     m0 = model.init_model(a.init_seed)
     m0.e0 = e0
     params = torch.tensor(model.to_flat(m0), device=dev, requires_grad=True)
-    trainer = mdpf.Trainer(a.batch, N, e0)
+    trainer = mdpf.Trainer(a.batch, N, e0, core_a=m0.core_a, core_rc=m0.core_rc)
     opt = AG.CosineAdamW([params], lr=a.lr, total_steps=a.iters)
     gen = torch.Generator(device="cpu").manual_seed(a.seed)
     log = []
@@ -130,7 +130,8 @@ def main(argv=None):
 
     lo, hi = trainer.feature_range()
     span = hi - lo
-    trained = model.from_flat(params.detach().cpu().numpy(), e0, lo - 0.02 * span, hi + 0.02 * span)
+    trained = model.from_flat(params.detach().cpu().numpy(), e0, lo - 0.02 * span, hi + 0.02 * span,
+                              m0.core_a, m0.core_rc)
     blob = trained.pack()
     if a.out:
         with open(a.out, "wb") as fh:
@@ -139,7 +140,7 @@ def main(argv=None):
     # test force RMSE against the plain force field (held-out trajectories): the
     # model's own forces (a range-free copy), and how many test frames leave the range
     from . import synth
-    plain_blob = model.from_flat(params.detach().cpu().numpy(), e0).pack()
+    plain_blob = model.from_flat(params.detach().cpu().numpy(), e0, core_a=m0.core_a, core_rc=m0.core_rc).pack()
     se, ss, cnt, n_eval, n_out = 0.0, 0.0, 0, 0, 0
     for t in test:
         s = synth.workload("cluster2048", trajectory=t)

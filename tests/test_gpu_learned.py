@@ -265,6 +265,35 @@ def test_energy_forces_tiny_systems(mdl):
         assert np.sqrt(((f - fo) ** 2).mean()) <= F_RTOL_BF16 * rms + 1e-6
 
 
+def _core_geometry(s, seps=(0.45, 0.6, 0.75)):
+    """The molecule with a few bonded pairs pulled inside the core radius (one
+    atom of each moved along its bond to the given separations)."""
+    pos = s.pos.copy()
+    for (a, b), r in zip(s.bonds[[3, 11, 20]], seps):
+        d = pos[b] - pos[a]
+        pos[b] = pos[a] + d / np.linalg.norm(d) * r
+    return pos
+
+
+@pytest.mark.parametrize("kernel", MLP_KERNELS + [mdpf.MDPF_MLP_SIMT_FP32, mdpf.MDPF_MLP_FUSED])
+def test_core_pairs_match_oracle(kernel, mdl):
+    s = synth.workload("mol64")
+    pos = _core_geometry(s)
+    ec, fc = O.core_energy_forces(pos, mdl.core_a, mdl.core_rc)
+    assert ec > 30.0                      # the core carries real energy here
+    ctx = _ctx(s, mdl, mlp_kernel=kernel)
+    e, f, _ = ctx.compute(pos)
+    eo, fo, _ = O.Learned(mdl).energy_forces(s.element, pos)
+    assert abs(e - eo) / s.n_atoms <= E_TOL_BF16, (e, eo)
+    assert np.sqrt(((f - fo) ** 2).mean()) <= F_RTOL_BF16 * np.sqrt((fo ** 2).mean())
+    # the core part alone: the same model without its core, on the same kernels, differs by the
+    # oracle's core energy and forces (FP32 pair arithmetic: relative 1e-5)
+    off = model.Model(mdl.W1, mdl.b1, mdl.W2, mdl.b2, mdl.W3, mdl.b3, mdl.e0)
+    e_off, f_off, _ = _ctx(s, off, mlp_kernel=kernel).compute(pos)
+    assert abs((e - e_off) - ec) <= 1e-5 * ec
+    assert np.abs((f - f_off) - fc).max() <= 1e-5 * np.abs(fc).max() + 1e-3
+
+
 def test_learned_compute_is_deterministic(mdl):
     s = synth.workload("mol256")
     ctx = _ctx(s, mdl)
@@ -287,7 +316,7 @@ def _ranged(m, s, widen=0.02):
         span = b - a
         lo[e] = a - widen * span - 1e-6
         hi[e] = b + widen * span + 1e-6
-    r = model.Model(m.W1, m.b1, m.W2, m.b2, m.W3, m.b3, m.e0, lo, hi, m.alpha)
+    r = model.Model(m.W1, m.b1, m.W2, m.b2, m.W3, m.b3, m.e0, lo, hi, m.alpha, m.core_a, m.core_rc)
     return r
 
 

@@ -89,9 +89,35 @@ def _rel_rmse(a, b):
     return np.sqrt(((a - b) ** 2).mean()) / max(np.sqrt((b ** 2).mean()), 1e-30)
 
 
+def test_loss_includes_the_repulsive_core(mdl):
+    # one frame with a bonded pair pulled inside the core radius: the loss and gradient follow the
+    # oracle's, whose predicted energy and forces include the core
+    s, frames = _batch()
+    el, pos, e_ref, f_ref = frames[1]
+    pos = pos.copy()
+    a, b = s.bonds[5]
+    d = pos[b] - pos[a]
+    pos[b] = pos[a] + d / np.linalg.norm(d) * 0.5
+    frames[1] = (el, pos, e_ref, f_ref)
+    assert O.core_energy_forces(pos, mdl.core_a, mdl.core_rc)[0] > 30.0
+    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
+    L, parts, g = _grad_via_autograd(mdl, frames, tr)
+    Lo, go, _ = O.train_loss_grad(mdl, frames)
+    assert abs(L - Lo) <= 1e-2 * abs(Lo), (L, Lo)
+    gm = model.from_flat(g, mdl.e0)
+    present = np.unique(s.element)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a_ = np.asarray(getattr(gm, k), dtype=np.float64)[present]
+        assert _rel_rmse(a_, go[k][present]) <= 2e-2, k
+    # without the core the device loss is a different number
+    tr0 = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0)
+    L0, _, _ = _grad_via_autograd(mdl, frames, tr0)
+    assert abs(L0 - L) > 1e-3 * abs(L)
+
+
 def test_loss_and_gradient_match_oracle(mdl):
     s, frames = _batch()
-    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0)
+    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     L, parts, g = _grad_via_autograd(mdl, frames, tr)
     Lo, go, _ = O.train_loss_grad(mdl, frames)
     assert abs(L - Lo) <= 1e-2 * abs(Lo), (L, Lo)
@@ -109,7 +135,7 @@ def test_loss_and_gradient_match_oracle(mdl):
 
 def test_gradient_is_deterministic(mdl):
     s, frames = _batch(seed=6)
-    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0)
+    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     _, _, g1 = _grad_via_autograd(mdl, frames, tr)
     _, _, g2 = _grad_via_autograd(mdl, frames, tr)
     assert np.array_equal(g1, g2)
@@ -122,7 +148,7 @@ def test_zero_residual_gives_near_zero_gradient(mdl):
     for el, pos, _, _ in frames:
         e, f, _ = ctx.compute(pos)
         own.append((el, pos, e, f.astype(np.float32).astype(np.float64)))
-    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0)
+    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     L0, _, g0 = _grad_via_autograd(mdl, own, tr)
     L1, _, g1 = _grad_via_autograd(mdl, frames, tr)
     assert L0 <= 1e-9 * L1
@@ -137,7 +163,7 @@ def test_multi_frame_batch_with_different_molecules(mdl):
         s = synth.molecule(48, seed=seed)
         e, f, _ = O.Plain(s).energy_forces(s.pos)
         frames.append((s.element, s.pos + rng.normal(0, 0.02, s.pos.shape), e, f))
-    tr = mdpf.Trainer(4, 48, mdl.e0)
+    tr = mdpf.Trainer(4, 48, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     L, _, g = _grad_via_autograd(mdl, frames, tr)
     Lo, go, _ = O.train_loss_grad(mdl, frames)
     assert abs(L - Lo) <= 1e-2 * abs(Lo)
@@ -168,7 +194,7 @@ def test_adamw_matches_oracle():
 
 def test_training_reduces_the_loss(mdl):
     s, frames = _batch(n_frames=4, seed=10)
-    tr = mdpf.Trainer(4, s.n_atoms, mdl.e0)
+    tr = mdpf.Trainer(4, s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     params = torch.tensor(model.to_flat(mdl), device="cuda", requires_grad=True)
     opt = AG.CosineAdamW([params], lr=1e-3, total_steps=60)
     pos, el, E, F = _device_batch(frames)
@@ -185,7 +211,7 @@ def test_training_reduces_the_loss(mdl):
 
 def test_feature_range_matches_oracle(mdl):
     s, frames = _batch(seed=12)
-    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0)
+    tr = mdpf.Trainer(len(frames), s.n_atoms, mdl.e0, core_a=mdl.core_a, core_rc=mdl.core_rc)
     _grad_via_autograd(mdl, frames, tr)
     lo, hi = tr.feature_range()
     G = np.concatenate([O.features(f[0], f[1]) for f in frames])
