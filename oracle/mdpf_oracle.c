@@ -25,7 +25,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_ACC 4.184e-4 /* kcal/mol/A/amu -> A/fs^2 (1 kcal/mol = 4.184e-4 amu A^2/fs^2) */
+
+/*
+ * Threads of the O(N^2) and per-atom loops (1 = the serial loops as written;
+ * only the CPU-baseline timing asks for more).  With T > 1 the i loop is split
+ * over T OpenMP threads, cyclically, each with its own force or gradient
+ * accumulator; the accumulators are then added in thread order, so results
+ * differ from the serial ones by rounding only.
+ */
+static int g_threads = 1;
+
+int orc_set_threads(int32_t t) {
+#ifdef _OPENMP
+    g_threads = t < 1 ? 1 : t;
+#else
+    (void)t;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 typedef struct {
     int32_t n;
@@ -190,7 +213,17 @@ double orc_plain_energy_forces(const orc_system *s, const double *x, double *f, 
     }
 
     /* all pairs i < j not excluded: LJ (Lorentz-Berthelot) + Coulomb, no cutoff */
+    const int T = g_threads;
+    double *ft = T > 1 ? (double *)calloc((size_t)T * 3 * n, sizeof(double)) : f;
+    double *et = (double *)calloc(2 * (size_t)T, sizeof(double));
+#pragma omp parallel for schedule(static, 1) num_threads(T) if (T > 1)
     for (int i = 0; i < n; ++i) {
+#ifdef _OPENMP
+        const int tid = T > 1 ? omp_get_thread_num() : 0;
+#else
+        const int tid = 0;
+#endif
+        double *fo = T > 1 ? ft + (size_t)tid * 3 * n : f;
         for (int j = i + 1; j < n; ++j) {
             if (is_excluded(s, i, j)) continue;
             double d[3], r2 = 0;
@@ -202,14 +235,22 @@ double orc_plain_energy_forces(const orc_system *s, const double *x, double *f, 
             double sr12 = sr6 * sr6;
             double e_lj = 4.0 * eps * (sr12 - sr6);
             double e_c = s->coulomb_k * s->charge[i] * s->charge[j] / r;
-            elj += e_lj;
-            ec += e_c;
+            et[2 * tid] += e_lj;
+            et[2 * tid + 1] += e_c;
             /* dE/dr = (-48 eps sr12 + 24 eps sr6)/r - e_c/r */
             double dedr = (-48.0 * eps * sr12 + 24.0 * eps * sr6) / r - e_c / r;
             double g = dedr / r;                   /* F_i = +dE/dr * d/r, F_j = -F_i */
-            for (int c = 0; c < 3; ++c) { f[3 * i + c] += g * d[c]; f[3 * j + c] -= g * d[c]; }
+            for (int c = 0; c < 3; ++c) { fo[3 * i + c] += g * d[c]; fo[3 * j + c] -= g * d[c]; }
         }
     }
+    for (int t = 0; t < T; ++t) {
+        elj += et[2 * t];
+        ec += et[2 * t + 1];
+        if (T > 1)
+            for (int q = 0; q < 3 * n; ++q) f[q] += ft[(size_t)t * 3 * n + q];
+    }
+    if (T > 1) free(ft);
+    free(et);
     if (terms) { terms[0] = eb; terms[1] = ea; terms[2] = elj; terms[3] = ec; }
     return eb + ea + elj + ec;
 }
@@ -328,8 +369,17 @@ int orc_neighbors(int32_t n, const float *x, float rc2, int32_t max_per_atom, in
  * F -= w[i,f] dT/dx; mode 2: JVP Gdot[i,f] += dT/dx . u.
  */
 static void orc_feature_pass(int n, const int32_t *el, const double *x, int mode, const double *w, const double *u,
-                             double *out) {
+                             double *out_all) {
+    /* modes 0 and 2 write row i only; mode 1 adds into every atom's force, so each thread has its own */
+    const int T = g_threads;
+    double *priv = (T > 1 && mode == 1) ? (double *)calloc((size_t)T * 3 * n, sizeof(double)) : NULL;
+#pragma omp parallel for schedule(static, 1) num_threads(T) if (T > 1)
     for (int i = 0; i < n; ++i) {
+#ifdef _OPENMP
+        double *out = priv ? priv + (size_t)omp_get_thread_num() * 3 * n : out_all;
+#else
+        double *out = out_all;
+#endif
         const double *xi = x + 3 * i;
         /* radial */
         for (int j = 0; j < n; ++j) {
@@ -421,6 +471,11 @@ static void orc_feature_pass(int n, const int32_t *el, const double *x, int mode
             }
         }
     }
+    if (priv) {
+        for (int t = 0; t < T; ++t)
+            for (int q = 0; q < 3 * n; ++q) out_all[q] += priv[(size_t)t * 3 * n + q];
+        free(priv);
+    }
 }
 
 /* G [n][384] */
@@ -464,12 +519,17 @@ static double orc_dcelu(double z, double a) { return z >= 0 ? 1.0 : exp(z / a); 
  *   h1 = W1 G + b1, a1 = celu(h1); h2 = W2 a1 + b2, a2 = celu(h2); E = W3 . a2 + b3 + e0
  *   dE/dG = W1^T [celu'(h1) * W2^T (celu'(h2) * W3)]
  */
-double orc_mlp_energy(const orc_mlp *M, int32_t n, const int32_t *el, const double *G, double *Ei, double *dEdG) {
+double orc_mlp_energy(const orc_mlp *M, int32_t n, const int32_t *el, const double *G, double *Ei_out,
+                      double *dEdG) {
     const int F = M->n_feat, H1 = M->h1, H2 = M->h2;
+    const int T = g_threads;
+    double *Ei = Ei_out ? Ei_out : (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+#pragma omp parallel num_threads(T) if (T > 1)
+    {
     double *h1 = (double *)malloc(sizeof(double) * H1), *a1 = (double *)malloc(sizeof(double) * H1);
     double *h2 = (double *)malloc(sizeof(double) * H2), *a2 = (double *)malloc(sizeof(double) * H2);
     double *d2 = (double *)malloc(sizeof(double) * H2), *d1 = (double *)malloc(sizeof(double) * H1);
-    double total = 0;
+#pragma omp for schedule(static, 1)
     for (int i = 0; i < n; ++i) {
         const int e = el[i];
         const double *g = G + (size_t)i * F;
@@ -487,8 +547,7 @@ double orc_mlp_energy(const orc_mlp *M, int32_t n, const int32_t *el, const doub
         }
         double E = M->b3[e] + M->e0[e];
         for (int b = 0; b < H2; ++b) E += M->W3[e][b] * a2[b];
-        if (Ei) Ei[i] = E;
-        total += E;
+        Ei[i] = E;
         if (dEdG) {
             for (int b = 0; b < H2; ++b) d2[b] = M->W3[e][b] * orc_dcelu(h2[b], M->alpha);
             for (int a = 0; a < H1; ++a) {
@@ -504,6 +563,10 @@ double orc_mlp_energy(const orc_mlp *M, int32_t n, const int32_t *el, const doub
         }
     }
     free(h1); free(a1); free(h2); free(a2); free(d2); free(d1);
+    }
+    double total = 0;   /* summed in atom order, whatever the threads */
+    for (int i = 0; i < n; ++i) total += Ei[i];
+    if (!Ei_out) free(Ei);
     return total;
 }
 
@@ -565,10 +628,27 @@ static double orc_d2celu(double z, double a) { return z >= 0 ? 0.0 : exp(z / a) 
  * for z >= 0 and exp(z/alpha)/alpha below.
  */
 void orc_mlp_param_grad(const orc_mlp *M, int32_t n, const int32_t *el, const double *G, const double *U,
-                        const double *c, double *gW1, double *gb1, double *gW2, double *gb2, double *gW3,
-                        double *gb3) {
+                        const double *c, double *gW1_all, double *gb1_all, double *gW2_all, double *gb2_all,
+                        double *gW3_all, double *gb3_all) {
     const int F = M->n_feat, H1 = M->h1, H2 = M->h2;
     const double al = M->alpha;
+    const int T = g_threads;
+    /* per-thread gradient accumulators when threaded (added in thread order at the end) */
+    const size_t nW1 = 4 * (size_t)H1 * F, nW2 = 4 * (size_t)H2 * H1;
+    const size_t per = nW1 + 4 * (size_t)H1 + nW2 + 4 * (size_t)H2 + 4 * (size_t)H2 + 4;
+    double *acc = T > 1 ? (double *)calloc((size_t)T * per, sizeof(double)) : NULL;
+#pragma omp parallel num_threads(T) if (T > 1)
+    {
+#ifdef _OPENMP
+    double *mine = acc ? acc + (size_t)omp_get_thread_num() * per : NULL;
+#else
+    double *mine = NULL;
+#endif
+    double *gW1 = mine ? mine : gW1_all, *gb1 = mine ? mine + nW1 : gb1_all;
+    double *gW2 = mine ? mine + nW1 + 4 * (size_t)H1 : gW2_all;
+    double *gb2 = mine ? mine + nW1 + 4 * (size_t)H1 + nW2 : gb2_all;
+    double *gW3 = mine ? mine + nW1 + 4 * (size_t)H1 + nW2 + 4 * (size_t)H2 : gW3_all;
+    double *gb3 = mine ? mine + nW1 + 4 * (size_t)H1 + nW2 + 8 * (size_t)H2 : gb3_all;
     double *h1 = (double *)malloc(sizeof(double) * H1), *a1 = (double *)malloc(sizeof(double) * H1);
     double *t1 = (double *)malloc(sizeof(double) * H1), *ta1 = (double *)malloc(sizeof(double) * H1);
     double *h2 = (double *)malloc(sizeof(double) * H2), *a2 = (double *)malloc(sizeof(double) * H2);
@@ -576,6 +656,7 @@ void orc_mlp_param_grad(const orc_mlp *M, int32_t n, const int32_t *el, const do
     double *bt2 = (double *)malloc(sizeof(double) * H2), *bh2 = (double *)malloc(sizeof(double) * H2);
     double *bt1 = (double *)malloc(sizeof(double) * H1), *bh1 = (double *)malloc(sizeof(double) * H1);
     double *bta1 = (double *)malloc(sizeof(double) * H1), *ba1 = (double *)malloc(sizeof(double) * H1);
+#pragma omp for schedule(static, 1)
     for (int i = 0; i < n; ++i) {
         const int e = el[i];
         const double *g = G + (size_t)i * F, *u = U + (size_t)i * F;
@@ -632,6 +713,19 @@ void orc_mlp_param_grad(const orc_mlp *M, int32_t n, const int32_t *el, const do
     }
     free(h1); free(a1); free(t1); free(ta1); free(h2); free(a2); free(t2); free(ta2);
     free(bt2); free(bh2); free(bt1); free(bh1); free(bta1); free(ba1);
+    }
+    if (acc) {
+        for (int t = 0; t < T; ++t) {
+            const double *m = acc + (size_t)t * per;
+            for (size_t q = 0; q < nW1; ++q) gW1_all[q] += m[q];
+            for (size_t q = 0; q < 4 * (size_t)H1; ++q) gb1_all[q] += m[nW1 + q];
+            for (size_t q = 0; q < nW2; ++q) gW2_all[q] += m[nW1 + 4 * (size_t)H1 + q];
+            for (size_t q = 0; q < 4 * (size_t)H2; ++q) gb2_all[q] += m[nW1 + 4 * (size_t)H1 + nW2 + q];
+            for (size_t q = 0; q < 4 * (size_t)H2; ++q) gW3_all[q] += m[nW1 + 4 * (size_t)H1 + nW2 + 4 * (size_t)H2 + q];
+            for (int q = 0; q < 4; ++q) gb3_all[q] += m[nW1 + 4 * (size_t)H1 + nW2 + 8 * (size_t)H2 + q];
+        }
+        free(acc);
+    }
 }
 
 /* ---------------------------------------------------------------- Langevin dynamics */
@@ -717,4 +811,92 @@ void orc_langevin_run(const orc_system *s, double dt, int32_t n_steps, double ga
         if (K) K[st] = orc_kinetic(n, s->mass, v);
     }
     free(f);
+}
+
+/* ---------------------------------------------------------------- initial velocities */
+
+/*
+ * Maxwell-Boltzmann velocities (A/fs) at temperature T for masses m [n] at
+ * positions x [n][3], written to v [n][3]:
+ *   1. v_i = sqrt(kB T / m_i) z_i, with z_i three standard normals per atom by
+ *      Box-Muller from Philox4x32-10 with counter (i, 0, 0, 0x4D425630) and
+ *      key (seed low, seed high) (units: kB T / m in kcal/mol/amu, times
+ *      ORC_ACC for A^2/fs^2);
+ *   2. the centre-of-mass velocity P / M is subtracted;
+ *   3. for n >= 3, the rigid rotation w x (x_i - x_com) with I w = L is
+ *      subtracted (L the angular momentum about the centre of mass, I the
+ *      inertia tensor), unless I is singular (collinear atoms);
+ *   4. v is scaled so that K = (3n - 6) kB T / 2 (3n - 6 taken as at least 1).
+ */
+void orc_init_velocities(int32_t n, const double *mass, const double *x, double T, uint64_t seed, double *v) {
+    const double kB = 0.0019872041;  /* kcal/mol/K */
+    const double two_pi = 6.283185307179586476925286766559;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int i = 0; i < n; ++i) {
+        const uint32_t ctr[4] = {(uint32_t)i, 0u, 0u, 0x4D425630u};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        double u[4];
+        for (int q = 0; q < 4; ++q) u[q] = ((double)r[q] + 0.5) * (1.0 / 4294967296.0);
+        const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+        const double z[3] = {r0 * cos(two_pi * u[1]), r0 * sin(two_pi * u[1]), r1 * cos(two_pi * u[3])};
+        const double sd = sqrt(kB * T * ORC_ACC / mass[i]);
+        for (int c = 0; c < 3; ++c) v[3 * i + c] = sd * z[c];
+    }
+    double M = 0, P[3] = {0, 0, 0}, com[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        M += mass[i];
+        for (int c = 0; c < 3; ++c) {
+            P[c] += mass[i] * v[3 * i + c];
+            com[c] += mass[i] * x[3 * i + c];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) v[3 * i + c] -= P[c] / M;
+    if (n >= 3) {
+        double L[3] = {0, 0, 0}, I[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int c = 0; c < 3; ++c) com[c] /= M;
+        for (int i = 0; i < n; ++i) {
+            const double r[3] = {x[3 * i] - com[0], x[3 * i + 1] - com[1], x[3 * i + 2] - com[2]};
+            const double *vi = v + 3 * i;
+            L[0] += mass[i] * (r[1] * vi[2] - r[2] * vi[1]);
+            L[1] += mass[i] * (r[2] * vi[0] - r[0] * vi[2]);
+            L[2] += mass[i] * (r[0] * vi[1] - r[1] * vi[0]);
+            const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) I[a][b] += mass[i] * ((a == b ? rr : 0.0) - r[a] * r[b]);
+        }
+        /* w = I^-1 L by the adjugate */
+        const double det = I[0][0] * (I[1][1] * I[2][2] - I[1][2] * I[2][1]) -
+                           I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
+                           I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
+        const double tr = I[0][0] + I[1][1] + I[2][2];
+        if (fabs(det) > 1e-12 * tr * tr * tr) {
+            double inv[3][3];
+            inv[0][0] = (I[1][1] * I[2][2] - I[1][2] * I[2][1]) / det;
+            inv[0][1] = (I[0][2] * I[2][1] - I[0][1] * I[2][2]) / det;
+            inv[0][2] = (I[0][1] * I[1][2] - I[0][2] * I[1][1]) / det;
+            inv[1][0] = (I[1][2] * I[2][0] - I[1][0] * I[2][2]) / det;
+            inv[1][1] = (I[0][0] * I[2][2] - I[0][2] * I[2][0]) / det;
+            inv[1][2] = (I[0][2] * I[1][0] - I[0][0] * I[1][2]) / det;
+            inv[2][0] = (I[1][0] * I[2][1] - I[1][1] * I[2][0]) / det;
+            inv[2][1] = (I[0][1] * I[2][0] - I[0][0] * I[2][1]) / det;
+            inv[2][2] = (I[0][0] * I[1][1] - I[0][1] * I[1][0]) / det;
+            double w[3];
+            for (int a = 0; a < 3; ++a) w[a] = inv[a][0] * L[0] + inv[a][1] * L[1] + inv[a][2] * L[2];
+            for (int i = 0; i < n; ++i) {
+                const double r[3] = {x[3 * i] - com[0], x[3 * i + 1] - com[1], x[3 * i + 2] - com[2]};
+                v[3 * i] -= w[1] * r[2] - w[2] * r[1];
+                v[3 * i + 1] -= w[2] * r[0] - w[0] * r[2];
+                v[3 * i + 2] -= w[0] * r[1] - w[1] * r[0];
+            }
+        }
+    }
+    const double K = orc_kinetic(n, mass, v);
+    const int dof = 3 * n - 6 > 1 ? 3 * n - 6 : 1;
+    const double target = 0.5 * dof * kB * T;
+    if (K > 0) {
+        const double sc = sqrt(target / K);
+        for (int q = 0; q < 3 * n; ++q) v[q] *= sc;
+    }
 }

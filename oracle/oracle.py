@@ -28,7 +28,7 @@ def build(force: bool = False) -> str:
     """Compile the C oracle into ``libmdpf_oracle.so`` beside its source."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                                "-std=c11", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
@@ -73,6 +73,14 @@ def lib():
 
 def _p(a):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's O(N^2) and per-atom loops (1, the default, runs them serially as
+    written; the CPU-baseline timing uses more).  Returns the count in effect."""
+    L = lib()
+    L.orc_set_threads.restype = ctypes.c_int
+    return int(L.orc_set_threads(ctypes.c_int32(int(n))))
 
 
 def exclusions(n_atoms: int, bonds: np.ndarray):
@@ -384,6 +392,19 @@ def philox4x32_10(ctr, key):
     out = (ctypes.c_uint32 * 4)()
     lib().orc_philox4x32_10(c, k, out)
     return [int(v) for v in out]
+
+
+def init_velocities(mass, pos, temperature: float, seed: int):
+    """Maxwell-Boltzmann velocities [N,3] (A/fs) from counter-based normals, zero linear and angular
+    momentum, K = (3N - 6) kB T / 2."""
+    m = np.ascontiguousarray(mass, dtype=np.float64)
+    x = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    v = np.zeros_like(x)
+    L = lib()
+    L.orc_init_velocities.restype = None
+    L.orc_init_velocities(ctypes.c_int32(m.shape[0]), _p(m), _p(x), ctypes.c_double(temperature),
+                          ctypes.c_uint64(seed), _p(v))
+    return v
 
 
 def langevin_normals(seed: int, step: int, atom: int):
