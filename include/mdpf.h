@@ -219,7 +219,12 @@ typedef struct mdpf_counters {
     uint32_t reserved;
     double potential;       /* U at the last energy step, kcal/mol */
     double kinetic;         /* K at the last energy step, kcal/mol */
-    double h_initial;       /* U + K right after the last set_state */
+    double h_initial;       /* U + K right after the last set_state / init_velocities */
+    double h_now;           /* U + K at the last energy step */
+    int64_t rebuilds;       /* learned mode: neighbour-list builds so far (0 otherwise) */
+    int64_t fallbacks;      /* learned mode: force evaluations whose features left the model's range
+                               (they used the plain force field when the fallback is on) */
+    double max_disp;        /* learned mode: largest displacement of an atom since the last list build, A */
 } mdpf_counters;
 
 /*
@@ -302,12 +307,38 @@ MDPF_API int mdpf_step_async(mdpf_ctx *ctx, int64_t n_steps, void *cuda_stream);
 MDPF_API int mdpf_get_counters(mdpf_ctx *ctx, mdpf_counters *out);
 
 /*
+ * Maxwell-Boltzmann velocities at temperature_K (>= 0) for the current
+ * positions (set them with mdpf_set_state first), drawn on the device:
+ * v_i = sqrt(kB T / m_i) z_i with three standard normals per atom by
+ * Box-Muller from Philox4x32-10 (counter: atom, 0, 0, 0x4D425630; key: seed),
+ * then the centre-of-mass velocity and, for N >= 3 with a non-singular
+ * inertia tensor, the rigid rotation are removed, and the velocities are
+ * scaled so that K = (3N - 6) kB T / 2 (at least one degree of freedom).
+ * Positions, forces and the step counter are unchanged; h_initial becomes
+ * U + K.  These are the starting velocities of the NVE runs the engine
+ * integrates (Results, "Example: Ethanol").  Errors: INVALID_ARG (bad
+ * temperature, no state set), CUDA.  Synchronous.
+ */
+MDPF_API int mdpf_init_velocities(mdpf_ctx *ctx, double temperature_K, uint64_t seed);
+
+/*
  * Energy trace, oldest first: one entry per energy step (every energy_every
  * steps), the most recent min(count, trace_capacity) of them.  U[k], K[k] in
  * kcal/mol after step step[k] (any output may be NULL).  *n_out receives the
  * count written (at most max_n).
  */
 MDPF_API int mdpf_get_trace(mdpf_ctx *ctx, double *U, double *K, int64_t *step, int64_t max_n, int64_t *n_out);
+
+/*
+ * Beside each energy-trace entry (same order and count as mdpf_get_trace):
+ * the number of force evaluations so far, since mdpf_create, whose features
+ * left the learned model's range (fallback evaluations; always 0 outside
+ * learned mode).  Two consecutive entries one step apart that differ show a
+ * step run on the plain force field; a step whose force field differs from
+ * its predecessor's is a switch step, across which H is not conserved (the
+ * two potentials differ), so drift is judged on the steps between switches.
+ */
+MDPF_API int mdpf_get_trace_fallbacks(mdpf_ctx *ctx, int64_t *fallbacks, int64_t max_n, int64_t *n_out);
 
 /*
  * Recorded frames, oldest first (at most max_frames of them): pos [n,N,3]

@@ -97,7 +97,7 @@ static void free_ctx(mdpf_ctx *c) {
     void *ptrs[] = {c->d_element, c->d_mass, c->d_hdt_m, c->d_pos4, c->d_pos4_b, c->d_pos4_c, c->d_lj,
                     c->d_charge_s, c->d_bonds, c->d_bond_par, c->d_angles, c->d_excl_off, c->d_excl_idx,
                     c->d_tile_mask, c->d_tile_flag, c->d_items, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
-                    c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_step, c->d_status,
+                    c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_trace_fb, c->d_step, c->d_status,
                     c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e,
                     c->d_own_off, c->d_own, c->d_lang_c2, c->frames.pos,
                     c->frames.energy, c->frames.forces,
@@ -291,6 +291,8 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     CKC(dalloc(&c->d_trace_u, c->trace_cap));
     CKC(dalloc(&c->d_trace_k, c->trace_cap));
     CKC(dalloc(&c->d_trace_step, c->trace_cap));
+    CKC(dalloc(&c->d_trace_fb, c->trace_cap));
+    CKC(cudaMemset(c->d_trace_fb, 0, sizeof(int64_t) * c->trace_cap));
     CKC(dalloc(&c->d_step, 1));
     CKC(dalloc(&c->d_status, 4));
     CKC(dalloc(&c->d_scalar, 16));
@@ -623,6 +625,33 @@ int mdpf_get_counters(mdpf_ctx *c, mdpf_counters *out) {
     out->potential = uk[0];
     out->kinetic = uk[1];
     out->h_initial = c->h_initial;
+    out->h_now = uk[0] + uk[1];
+    if (c->learned != nullptr) {
+        const int rc = learned_counter_values(c, &out->rebuilds, &out->fallbacks, &out->max_disp);
+        if (rc != MDPF_OK) return rc;
+    }
+    return MDPF_OK;
+}
+
+int mdpf_init_velocities(mdpf_ctx *c, double temperature_K, uint64_t seed) {
+    GUARD(c);
+    if (!(temperature_K >= 0.0) || !std::isfinite(temperature_K))
+        return fail(c, MDPF_ERR_INVALID_ARG, "temperature must be finite and >= 0");
+    if (!c->state_set) return fail(c, MDPF_ERR_INVALID_ARG, "set the state (positions) with mdpf_set_state first");
+    cudaStream_t s = c->stream;
+    launch_init_velocities(c, temperature_K, (unsigned long long)seed, s);
+    // K of the new velocities (fixed-point slot, as everywhere else) and H0 = U + K
+    CK(c, cudaMemsetAsync(c->d_efx + E_KIN, 0, sizeof(unsigned long long), s));
+    launch_kinetic(c, s);
+    CK(c, cudaGetLastError());
+    unsigned long long kfx = 0;
+    double u = 0;
+    CK(c, cudaMemcpyAsync(&kfx, c->d_efx + E_KIN, sizeof(kfx), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(&u, c->d_scalar, sizeof(u), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    const double k = (double)(long long)kfx * kFxInv;
+    CK(c, cudaMemcpy(c->d_scalar + 1, &k, sizeof(k), cudaMemcpyHostToDevice));
+    c->h_initial = u + k;
     return MDPF_OK;
 }
 
@@ -647,6 +676,24 @@ int mdpf_get_trace(mdpf_ctx *c, double *U, double *K, int64_t *step, int64_t max
         if (K) K[k] = hk[slot];
         if (step) step[k] = hs[slot];
     }
+    if (n_out) *n_out = cnt;
+    return MDPF_OK;
+}
+
+int mdpf_get_trace_fallbacks(mdpf_ctx *c, int64_t *fallbacks, int64_t max_n, int64_t *n_out) {
+    GUARD(c);
+    if (max_n < 0) return fail(c, MDPF_ERR_INVALID_ARG, "max_n < 0");
+    int64_t dstep = 0;
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaMemcpy(&dstep, c->d_step, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const int64_t n_energy = dstep / c->energy_every;
+    int64_t cnt = n_energy < c->trace_cap ? n_energy : c->trace_cap;
+    if (cnt > max_n) cnt = max_n;
+    std::vector<int64_t> hf(c->trace_cap);
+    CK(c, cudaMemcpy(hf.data(), c->d_trace_fb, sizeof(int64_t) * c->trace_cap, cudaMemcpyDeviceToHost));
+    const int64_t start = n_energy - cnt;
+    for (int64_t k = 0; k < cnt; ++k)
+        if (fallbacks) fallbacks[k] = hf[(start + k) % c->trace_cap];
     if (n_out) *n_out = cnt;
     return MDPF_OK;
 }

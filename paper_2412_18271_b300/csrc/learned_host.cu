@@ -23,6 +23,7 @@ struct LearnedHost {
     float *d_Gin = nullptr;     // [n][384] staging for mdpf_learned_mlp
     float *d_vin = nullptr;     // [n][3] tangent staging for mdpf_learned_jvp (allocated on first use)
     float *d_U = nullptr;       // [n_rows][384] JVP output (allocated on first use)
+    unsigned int *d_disp = nullptr;   // max squared displacement (float bits) for the counters
     int mlp_kernel = MDPF_MLP_TENSOR;
     MlpMaps maps{};
     FusedTiles ft{};
@@ -272,6 +273,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
         LA(dhi, hi.size());
     }
     LA(L.lflags, 4);
+    LA(h->d_disp, 1);
     LA(L.lcount, 4);
     LA(h->d_Gin, (size_t)n * kNFeat);
     int *d_ft_first, *d_ft_count, *d_ft_el;
@@ -392,6 +394,48 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
 
 // The per-step rebuild request, checked by the kick-drift kernel: an atom moved more than skin/2 since the
 // last build, or the completed-step count is a multiple of rebuild_every.
+__global__ void k_max_disp2(int n, const float4 *pos4, const float4 *pos_build, unsigned int *out) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.f;
+    if (a < n) {
+        const float4 p = pos4[a], b = pos_build[a];
+        const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+        d2 = dx * dx + dy * dy + dz * dz;
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(out, __float_as_uint(d2));
+}
+
+// Counters of the learned path for mdpf_get_counters: list rebuilds, evaluations that left the
+// feature range, and the largest displacement of an atom (FP32 state positions) since the last
+// list build, in A.  Synchronous on the context's stream.
+int learned_counter_values(mdpf_ctx *c, int64_t *rebuilds, int64_t *fallbacks, double *max_disp) {
+    LearnedHost *h = lh(c);
+    long long v[4];
+    unsigned int bits = 0;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(v, h->dev.lcount, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_disp, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) {
+        k_max_disp2<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->n, c->d_pos4, h->dev.pos_build, h->d_disp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, h->d_disp, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned counters");
+    float d2;
+    std::memcpy(&d2, &bits, sizeof(d2));
+    *rebuilds = v[0];
+    *fallbacks = v[1];
+    *max_disp = std::sqrt((double)d2);
+    return MDPF_OK;
+}
+
+const long long *learned_fallback_counter(const mdpf_ctx *c) {
+    return c->learned != nullptr ? lh(c)->dev.lcount + 1 : nullptr;
+}
+
 DispCheck learned_disp_check(const mdpf_ctx *c) {
     const LearnedHost *h = lh(c);
     return DispCheck{h->dev.pos_build, h->dev.lflags, h->dev.half_skin2, h->rebuild_every};

@@ -120,6 +120,7 @@ struct mdpf_ctx {
     unsigned long long *d_efx_c = nullptr;   // compute() energies
     double *d_trace_u = nullptr, *d_trace_k = nullptr;
     int64_t *d_trace_step = nullptr;
+    int64_t *d_trace_fb = nullptr;         // learned mode: fallback evaluations so far, per trace entry
     int64_t *d_step = nullptr;             // device step counter
     uint32_t *d_status = nullptr;          // [0] state, [1] compute(), [3] block ticket of the kick-finish kernel
     double *d_xc = nullptr;                // compute() FP64 position staging [n][3]
@@ -199,6 +200,8 @@ void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s);
 void launch_provider_to_fx(const float *forces, const double *energy, int n, unsigned long long *fx,
                            unsigned long long *efx, uint32_t *status, cudaStream_t s);
 void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s);
+// Maxwell-Boltzmann velocities of the current positions into d_v (one block)
+void launch_init_velocities(mdpf_ctx *ctx, double temperature_K, unsigned long long seed, cudaStream_t s);
 
 // learned_host.cu
 int learned_validate(const mdpf_params *prm, std::string &msg);
@@ -207,6 +210,9 @@ void learned_free(mdpf_ctx *ctx);
 int learned_enqueue_forces(mdpf_ctx *ctx, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
                            uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s);
 DispCheck learned_disp_check(const mdpf_ctx *ctx);
+int learned_counter_values(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fallbacks, double *max_disp);
+// device counter of evaluations that fell back to the plain force field (learned mode), else null
+const long long *learned_fallback_counter(const mdpf_ctx *ctx);
 
 // stepper.cu
 int stepper_grid(const mdpf_ctx *ctx);

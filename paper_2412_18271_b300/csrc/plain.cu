@@ -230,6 +230,8 @@ struct FinishArgs {
     const double *x;
     double *trace_u, *trace_k;
     int64_t *trace_step;
+    int64_t *trace_fb;            // cumulative fallback evaluations per trace entry
+    const long long *fb_count;    // learned mode: the device counter of fallback evaluations, else null
     int cap, energy_every, record_every;
     int64_t *step;
     uint32_t *status;
@@ -281,6 +283,7 @@ __global__ void k_kick_finish(int n, const double *hdt_over_m, const double *mas
         f.trace_u[e % f.cap] = U;
         f.trace_k[e % f.cap] = K;
         f.trace_step[e % f.cap] = s;
+        f.trace_fb[e % f.cap] = f.fb_count != nullptr ? (int64_t)__ldcg(f.fb_count) : 0;
         f.scalars[0] = U;
         f.scalars[1] = K;
         // fixed-point slots saturate rather than turn NaN: treat huge values as non-finite too
@@ -291,6 +294,118 @@ __global__ void k_kick_finish(int n, const double *hdt_over_m, const double *mas
         f.frames.energy[slot] = f.scalars[0];
         f.frames.step[slot] = s;
     }
+}
+
+// Maxwell-Boltzmann initial velocities in one block (runs once per call, so
+// one block of kMbThreads keeps every reduction in a fixed order):
+//   v_a = sqrt(kB T / m_a) z_a, z_a three Box-Muller normals from Philox with
+//   counter (a, 0, 0, 'MBV0') and key = seed; minus the centre-of-mass
+//   velocity; for n >= 3 minus the rigid rotation w x (x_a - x_com), I w = L
+//   (skipped when I is singular); then scaled to K = (3n - 6) kB T / 2.
+constexpr int kMbThreads = 1024;
+
+__device__ double mb_block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kMbThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kMbThreads) k_init_velocities(int n, const double *mass, const double *x,
+                                                                  double *v, double kT_acc, double k_target,
+                                                                  unsigned long long seed) {
+    __shared__ double sh[kMbThreads];
+    __shared__ double s_q[16];
+    const int t = threadIdx.x;
+    const double inv = 1.0 / 4294967296.0, two_pi = 6.283185307179586476925286766559;
+    double M = 0, P[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
+    for (int a = t; a < n; a += kMbThreads) {
+        const uint4 r = philox4x32_10(make_uint4((unsigned int)a, 0u, 0u, 0x4D425630u),
+                                      make_uint2((unsigned int)seed, (unsigned int)(seed >> 32)));
+        const double u0 = ((double)r.x + 0.5) * inv, u1 = ((double)r.y + 0.5) * inv;
+        const double u2 = ((double)r.z + 0.5) * inv, u3 = ((double)r.w + 0.5) * inv;
+        const double r0 = sqrt(-2.0 * log(u0)), r1 = sqrt(-2.0 * log(u2));
+        const double z[3] = {r0 * cos(two_pi * u1), r0 * sin(two_pi * u1), r1 * cos(two_pi * u3)};
+        const double m = mass[a], sd = sqrt(kT_acc / m);
+        M += m;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double vc = sd * z[c];
+            v[3 * a + c] = vc;
+            P[c] += m * vc;
+            mx[c] += m * x[3 * a + c];
+        }
+    }
+    M = mb_block_sum(M, sh);
+    double vcm[3], com[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        vcm[c] = mb_block_sum(P[c], sh) / M;
+        com[c] = mb_block_sum(mx[c], sh) / M;
+    }
+    double L[3] = {0, 0, 0}, I6[6] = {0, 0, 0, 0, 0, 0};   // I: xx yy zz xy xz yz
+    for (int a = t; a < n; a += kMbThreads) {
+        const double m = mass[a];
+        const double r[3] = {x[3 * a] - com[0], x[3 * a + 1] - com[1], x[3 * a + 2] - com[2]};
+        double vv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            vv[c] = v[3 * a + c] - vcm[c];
+            v[3 * a + c] = vv[c];
+        }
+        L[0] += m * (r[1] * vv[2] - r[2] * vv[1]);
+        L[1] += m * (r[2] * vv[0] - r[0] * vv[2]);
+        L[2] += m * (r[0] * vv[1] - r[1] * vv[0]);
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        I6[0] += m * (rr - r[0] * r[0]);
+        I6[1] += m * (rr - r[1] * r[1]);
+        I6[2] += m * (rr - r[2] * r[2]);
+        I6[3] -= m * r[0] * r[1];
+        I6[4] -= m * r[0] * r[2];
+        I6[5] -= m * r[1] * r[2];
+    }
+    if (n >= 3) {
+        double Ls[3], Is[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Ls[c] = mb_block_sum(L[c], sh);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Is[c] = mb_block_sum(I6[c], sh);
+        if (t == 0) {
+            const double a = Is[0], b = Is[1], c = Is[2], d = Is[3], e = Is[4], f = Is[5];
+            // I = [[a d e] [d b f] [e f c]]; w = adj(I) L / det(I)
+            const double A00 = b * c - f * f, A01 = e * f - d * c, A02 = d * f - e * b;
+            const double A11 = a * c - e * e, A12 = d * e - a * f, A22 = a * b - d * d;
+            const double det = a * A00 + d * A01 + e * A02, tr = a + b + c;
+            const bool ok = fabs(det) > 1e-12 * tr * tr * tr;
+            s_q[0] = ok ? (A00 * Ls[0] + A01 * Ls[1] + A02 * Ls[2]) / det : 0.0;
+            s_q[1] = ok ? (A01 * Ls[0] + A11 * Ls[1] + A12 * Ls[2]) / det : 0.0;
+            s_q[2] = ok ? (A02 * Ls[0] + A12 * Ls[1] + A22 * Ls[2]) / det : 0.0;
+        }
+        __syncthreads();
+    } else if (t == 0) {
+        s_q[0] = s_q[1] = s_q[2] = 0.0;
+    }
+    __syncthreads();
+    const double w[3] = {s_q[0], s_q[1], s_q[2]};
+    double K = 0;
+    for (int a = t; a < n; a += kMbThreads) {
+        const double r[3] = {x[3 * a] - com[0], x[3 * a + 1] - com[1], x[3 * a + 2] - com[2]};
+        double vv[3] = {v[3 * a], v[3 * a + 1], v[3 * a + 2]};
+        vv[0] -= w[1] * r[2] - w[2] * r[1];
+        vv[1] -= w[2] * r[0] - w[0] * r[2];
+        vv[2] -= w[0] * r[1] - w[1] * r[0];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[3 * a + c] = vv[c];
+        K += 0.5 * mass[a] * (vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]) / kAcc;
+    }
+    K = mb_block_sum(K, sh);
+    const double sc = K > 0.0 ? sqrt(k_target / K) : 1.0;
+    for (int q = t; q < 3 * n; q += kMbThreads) v[q] *= sc;
 }
 
 // Spin on a flag that nothing sets, for at most limit_ns of globaltimer.
@@ -381,8 +496,9 @@ void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s) {
 }
 
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s) {
-    FinishArgs f{ctx->d_x, ctx->d_trace_u, ctx->d_trace_k, ctx->d_trace_step, ctx->trace_cap, ctx->energy_every,
-                 ctx->record_every, ctx->d_step, ctx->d_status, ctx->d_scalar, ctx->d_status + 3, ctx->frames};
+    FinishArgs f{ctx->d_x,          ctx->d_trace_u,   ctx->d_trace_k,      ctx->d_trace_step, ctx->d_trace_fb,
+                 learned_fallback_counter(ctx), ctx->trace_cap, ctx->energy_every, ctx->record_every,
+                 ctx->d_step,       ctx->d_status,    ctx->d_scalar,       ctx->d_status + 3, ctx->frames};
     k_kick_finish<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(
         ctx->n, ctx->d_hdt_m, ctx->d_mass, ctx->d_v, ctx->d_fx, ctx->d_efx, energy ? 1 : 0, f);
 }
@@ -396,6 +512,13 @@ void launch_provider_to_fx(const float *forces, const double *energy, int n, uns
 void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s) {
     k_kick<<<(ctx->n + kIntThreads - 1) / kIntThreads, kIntThreads, 0, s>>>(ctx->n, ctx->d_hdt_m, ctx->d_mass,
                                                                               ctx->d_v, ctx->d_fx, ctx->d_efx, 0, 1);
+}
+
+void launch_init_velocities(mdpf_ctx *ctx, double temperature_K, unsigned long long seed, cudaStream_t s) {
+    const double kB = 0.0019872041;   // kcal/mol/K
+    const int dof = 3 * ctx->n - 6 > 1 ? 3 * ctx->n - 6 : 1;
+    k_init_velocities<<<1, kMbThreads, 0, s>>>(ctx->n, ctx->d_mass, ctx->d_x, ctx->d_v, kB * temperature_K * kAcc,
+                                               0.5 * dof * kB * temperature_K, seed);
 }
 
 void launch_wait_timeout(uint32_t *status, unsigned int *flag, long long limit_ns, cudaStream_t s) {

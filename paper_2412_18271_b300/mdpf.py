@@ -90,6 +90,7 @@ class mdpf_counters(ctypes.Structure):
     _fields_ = [
         ("steps", _i64), ("force_evals", _i64), ("frames", _i64), ("status", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32), ("potential", _f64), ("kinetic", _f64), ("h_initial", _f64),
+        ("h_now", _f64), ("rebuilds", _i64), ("fallbacks", _i64), ("max_disp", _f64),
     ]
 
 
@@ -109,8 +110,10 @@ def load(path: str = LIB_PATH):
         "mdpf_step": (ctypes.c_int, [_vp, _i64]),
         "mdpf_step_async": (ctypes.c_int, [_vp, _i64, _vp]),
         "mdpf_get_counters": (ctypes.c_int, [_vp, ctypes.POINTER(mdpf_counters)]),
+        "mdpf_init_velocities": (ctypes.c_int, [_vp, _f64, ctypes.c_uint64]),
         "mdpf_get_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
         "mdpf_get_frames": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+        "mdpf_get_trace_fallbacks": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
         "mdpf_get_exclusions": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
         "mdpf_get_angles": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
         "mdpf_debug_set_status": (ctypes.c_int, [_vp, ctypes.c_uint32]),
@@ -321,6 +324,10 @@ class Context:
         v = np.ascontiguousarray(vel, dtype=np.float64).reshape(self.n, 3)
         self._check(lib().mdpf_set_state(self._h, _ptr(x), _ptr(v)))
 
+    def init_velocities(self, temperature_K: float, seed: int):
+        """Maxwell-Boltzmann velocities for the current positions, drawn on the device."""
+        self._check(lib().mdpf_init_velocities(self._h, float(temperature_K), ctypes.c_uint64(int(seed))))
+
     def get_state(self, pos=None, vel=None):
         x = np.zeros((self.n, 3)) if pos is None else pos
         v = np.zeros((self.n, 3)) if vel is None else vel
@@ -348,6 +355,13 @@ class Context:
         if with_steps:
             return U[:n.value], K[:n.value], st[:n.value]
         return U[:n.value], K[:n.value]
+
+    def trace_fallbacks(self, max_n: int = 1 << 20):
+        """Cumulative fallback evaluations beside each energy-trace entry (learned mode)."""
+        fb = np.zeros(max_n, dtype=np.int64)
+        n = ctypes.c_int64()
+        self._check(lib().mdpf_get_trace_fallbacks(self._h, _ptr(fb), max_n, ctypes.byref(n)))
+        return fb[:n.value]
 
     def frames(self, max_n: int | None = None):
         m = self.max_frames if max_n is None else max_n
