@@ -4,16 +4,28 @@ Verlet update on one B300, through the libmdpf C ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One bench step = ``--md-steps`` MD steps (default 1000) of the 2,048-atom
-gas-phase cluster (64 seeded 32-atom molecules in a 60 A ball, plain force
-field: harmonic bonds and angles, all-pairs LJ + Coulomb with 1-2/1-3
-exclusions, no cutoff; FP32 forces, FP64 integration, dt = 0.5 fs), with the
-state resident in HBM; frames and energies are recorded every 10 steps.
-The line's "learned" object times the learned path the same way on the
-16,384-atom cluster (512 molecules in an 80 A ball): cell-list neighbours
-(5.2 A cutoff, 1 A skin, rebuild every 20 steps or on displacement),
-symmetry-function features, per-element BF16 MLP with its input gradient,
-analytic adjoint forces, FP64 velocity Verlet.
+The line's headline (value, e2e, roofline): one bench step = ``--md-steps`` MD
+steps (default 1000) of the 2,048-atom gas-phase cluster (64 seeded 32-atom
+molecules in a 60 A ball, plain force field: harmonic bonds and angles,
+all-pairs LJ + Coulomb with 1-2/1-3 exclusions, no cutoff; FP32 forces, FP64
+integration, dt = 0.5 fs), state resident in HBM, frames and energies every
+10 steps.  Beside it:
+  learned     the 16,384-atom cluster (512 molecules in an 80 A ball) on the
+              learned potential as the workload states it: the trained model
+              with its feature ranges, so steps whose features leave the range
+              run on the plain force field and are counted; 10,000 NVE steps
+              timed in one region, the energy drift over them (switch steps
+              apart); then, as a labelled secondary, the same model without its
+              ranges (per-stage times, the learned kernels' roofline), the
+              fused-kernel variant and the plain force field on that cluster;
+  mol256      one learned energy + force evaluation of the 256-atom molecule
+              (seeded model), its time and its error against the FP64 oracle;
+  training    one force-matching iteration on 64 frames x 2,048 atoms;
+  provider    the 64-atom molecule: persistent stepper, kernel sequence, the
+              Python force-provider callback, the empty-loop floor, and the
+              9-atom learned molecule;
+  cpu_oracle  the FP64 oracle single-threaded and on all host cores, per workload.
+Every result carries its measured error against the FP64 oracle.
 Prints one JSON line.  For N > 1 (torchrun) each rank runs an independent
 replica (weak scaling, no collective on the data path).
 """
@@ -40,9 +52,9 @@ DT_FS = 0.5
 FLOPS_PER_PAIR = 35          # algorithmic FP32 flops per pair (forces only), FMA counted as 2
 FLOPS_PER_PAIR_ENERGY = 3    # extra flops per pair on energy steps
 RECORD_EVERY = 10            # frames and energies every 10 steps (the workload's recording cadence)
-# DRAM bytes (read + write) per launch of k_plain_persistent from the ncu capture in
-# profiles/k_plain_persistent_cluster2048.md: the L2-resident working set read once from a cold L2
-# (the bench flushes L2 between launches), independent of the MD steps per launch
+# DRAM bytes (read + write) per launch of k_plain_persistent, from an ncu capture of this workload:
+# the L2-resident working set read once from a cold L2 (the bench flushes L2 between launches),
+# independent of the MD steps per launch
 PLAIN_TRAFFIC = 500736
 FP32_LANES_PER_SM = 128
 N_SM = 148
@@ -58,9 +70,10 @@ FEAT_FLOPS_PER_PAIR = 110       # radial: 16 Gaussians x (sub, mul, mul, exp, mu
 FEAT_FLOPS_PER_TRIPLET = 460    # angular: cos/sin of theta, 4 shells x exp, 32 columns x (2 fma + ^32 + 3 mul + add)
 ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
-# DRAM bytes (read + write) per launch of each learned kernel on this workload, from the ncu capture in
-# profiles/learned_step_cluster16384.md (valid for the kernels as captured there)
+# DRAM bytes (read + write) per launch of each learned kernel on this workload, from an ncu capture of
+# the kernels (valid for the kernels as captured)
 LEARNED_TRAFFIC = {"adjoint": 34463232, "features": 8897024, "mlp": 14992384, "fused": 11452672}
+LEARNED_MD_STEPS = 10000         # the learned workload's NVE run, timed as one region
 
 
 def peaks():
@@ -190,7 +203,8 @@ def cpu_baseline(sample_steps: int):
     dt = time.perf_counter() - t0
     return {"value": sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d velocity-Verlet steps of the same 2048-atom cluster (%d force evaluations), "
-                      "single-threaded FP64 C oracle, %.1f s" % (sample_steps, sample_steps + 1, dt)}
+                      "single-threaded FP64 C oracle, %.1f s" % (sample_steps, sample_steps + 1, dt),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def _pair_triplet_counts(pos):
@@ -206,76 +220,207 @@ def _pair_triplet_counts(pos):
 
 
 TRAINED_MODEL = os.path.join(ROOT, "paper_2412_18271_b300", "data", "learned_c3.mdpfmlp")
+TRAINED_DESC = ("trained on 45,000 frames of 2048-atom plain-force-field cluster trajectories "
+                "(paper_2412_18271_b300/train.py defaults), repulsive core A = 400 kcal/mol, rc = 0.8 A")
 
 
-def learned_model():
-    """The model the learned leg runs: the one trained on the plain-force-field
-    cluster trajectories (with its feature ranges, so out-of-range steps fall
-    back to the plain force field and are counted), else the seeded init."""
+def learned_model(ranges: bool = True):
+    """The trained model (with or without its feature ranges) as a blob, its description, and the Model."""
     from paper_2412_18271_b300 import model
     if os.path.exists(TRAINED_MODEL):
         with open(TRAINED_MODEL, "rb") as fh:
             m = model.Model.unpack(fh.read())
-        # without its feature ranges: every step runs the model (on this cluster some atom leaves the
-        # range of the 2048-atom training clusters at nearly every step, and the fallback would time
-        # the plain force field instead)
-        m.lo = m.hi = None
-        return m.pack(), ("trained on 45,000 frames of 2048-atom plain-force-field cluster trajectories "
-                          "(paper_2412_18271_b300/train.py defaults); run without its feature ranges, so every "
-                          "step evaluates the model")
-    return model.init_model(7).pack(), "seeded Kaiming-uniform init (untrained), no feature ranges"
+        if not ranges:
+            m.lo = m.hi = None
+        return m.pack(), TRAINED_DESC + ("; with its feature ranges (fallback on)" if ranges else
+                                         "; without its feature ranges (every step runs the model)"), m
+    m = model.init_model(7)
+    return m.pack(), "seeded Kaiming-uniform init (untrained), no feature ranges", m
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def _rel_rmse(f, fo):
+    import numpy as np
+    return float(np.sqrt(((f - fo) ** 2).mean()) / max(np.sqrt((fo ** 2).mean()), 1e-300))
+
+
+def cpu_oracle_suite():
+    """The FP64 oracle as it stands, timed on the host cores single-threaded and with its threaded
+    loops on all cores, on a bounded sample of each workload (stated per entry)."""
+    from oracle import oracle as O
+    from paper_2412_18271_b300 import model, synth
+    nproc = os.cpu_count() or 1
+    s0 = synth.workload("mol64")
+    v0 = synth.velocities(s0.mass, s0.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED["mol64"])
+    s1 = synth.workload("cluster2048")
+    v1 = synth.velocities(s1.mass, s1.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED["cluster2048"])
+    s2 = synth.workload("mol256")
+    m2 = model.init_model(7)
+    s4 = synth.workload("cluster16384")
+    _, _, m4 = learned_model(ranges=False)
+    e1, f1, _ = O.Plain(s1).energy_forces(s1.pos)          # reference data of one frame (not timed)
+    frame = [(s1.element, s1.pos, e1, f1)]
+    cases = [
+        ("mol64_plain_md", 1000, UNIT, lambda: O.Plain(s0).vv(s0.pos, v0, DT_FS, 1000),
+         "1000 velocity-Verlet steps of the 64-atom molecule"),
+        ("cluster2048_plain_md", 20, UNIT, lambda: O.Plain(s1).vv(s1.pos, v1, DT_FS, 20),
+         "20 velocity-Verlet steps of the 2048-atom cluster (21 force evaluations)"),
+        ("mol256_learned_evaluation", 1, "evaluations/s", lambda: O.Learned(m2).energy_forces(s2.element, s2.pos),
+         "one learned energy + force evaluation of the 256-atom molecule"),
+        ("training_iteration_64x2048", 1.0 / 64, "iterations/s", lambda: O.train_loss_grad(m4, frame),
+         "one 2048-atom frame of the 64-frame iteration (energy, forces, feature JVP, parameter gradient); "
+         "iterations/s = 1 / (64 x the frame time)"),
+        ("cluster16384_learned_md", 1, UNIT, lambda: O.Learned(m4).energy_forces(s4.element, s4.pos),
+         "one learned force evaluation of the 16384-atom cluster (the cost of one velocity-Verlet step)"),
+    ]
+    out = {"kind": "oracle", "nproc": nproc, "cpu_model": cpu_model(), "workloads": {}}
+    for name, units, unit, fn, sample in cases:
+        entry = {"unit": unit, "sample": sample}
+        for label, threads in (("single_thread", 1), ("all_cores", nproc)):
+            O.set_threads(threads)
+            t0 = time.perf_counter()
+            fn()
+            dt = time.perf_counter() - t0
+            entry[label] = {"value": units / dt, "seconds": dt, "threads": threads}
+        out["workloads"][name] = entry
+    O.set_threads(1)
+    return out
+
+
+def _timed_on(stream, fn):
+    """CUDA-event milliseconds of fn() enqueued on stream (synchronised on both sides)."""
+    import torch
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b)
 
 
 def learned_leg(args, dev, stream, flush):
+    """The 16,384-atom cluster on the learned path.  Headline: the trained model with its feature ranges
+    (out-of-range steps fall back to the plain force field and are counted), 10,000 NVE steps in one timed
+    region with the energy of every step, the drift with switch steps apart.  Secondary: the model without
+    its ranges, timed in bench steps from the start state, with per-stage times and the roofline."""
     import numpy as np
     import torch
-    from paper_2412_18271_b300 import mdpf, model, synth
+    from oracle import oracle as O
+    from paper_2412_18271_b300 import mdpf, synth
+    from paper_2412_18271_b300.energy_drift import nve_drift
     s = synth.workload(LEARNED_WORKLOAD)
     v0 = synth.velocities(s.mass, s.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED[LEARNED_WORKLOAD])
     n = s.n_atoms
+    md4 = args.learned_run_steps
+    blob_r, desc_r, m_r = learned_model(ranges=True)
+    blob_n, desc_n, m_n = learned_model(ranges=False)
+
+    # errors at the start geometry: the model's BF16 forces against the FP64 oracle of the same model, and
+    # the learned forces against the plain force field (what the learned path stands in for)
+    nctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob_n, dt_fs=DT_FS)
+    e_l, f_l, _ = nctx.compute(s.pos)
+    nctx.close()
+    O.set_threads(os.cpu_count() or 1)
+    e_o, f_o, _ = O.Learned(m_n).energy_forces(s.element, s.pos)
+    O.set_threads(1)
+    pctx = mdpf.Context(s, dt_fs=DT_FS)
+    _, f_p, _ = pctx.compute(s.pos)
+    pctx.close()
+
+    # ---- the workload as stated: ranges on, fallback on, 10,000 steps in one region
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob_r, dt_fs=DT_FS, energy_every=1,
+                       trace_capacity=md4)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            stream.synchronize()
+            ctx.set_state(s.pos, v0)
+            ctx.step_async(200, stream.cuda_stream)
+        stream.synchronize()
+        ctx.set_state(s.pos, v0)
+        c0 = ctx.counters()
+        torch.cuda.synchronize()
+        flush.zero_()
+        with ClockSampler(dev.index) as clk:
+            ms = _timed_on(stream, lambda: ctx.step_async(md4, stream.cuda_stream))
+    c1 = ctx.counters()
+    status_w = c1["status"]
+    U, K = ctx.trace()
+    fb = ctx.trace_fallbacks()
+    drift = nve_drift(U, K, n, fb, c0["fallbacks"])
+    steps_done = int(c1["steps"])
+    T = K / (1.5 * n * 0.0019872041)
+    # e2e: host buffers through the public API, the copies inside the timed region
+    pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_x[:] = s.pos
+    pin_v[:] = v0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.set_state(pin_x, pin_v)
+    e2e_err = None
+    try:
+        ctx.step(md4)
+    except mdpf.MdpfError as exc:       # reported, not raised: the run's outcome is part of the result
+        e2e_err = str(exc)
+    ctx.get_state(pin_x, pin_v)
+    ctx.counters()
+    e2e_s = time.perf_counter() - t0
+    ctx.close()
+    rate = steps_done / (ms / 1000.0) if steps_done else 0.0
+    as_written = {
+        "what": "trained model with its feature ranges: any atom outside the training range sends the whole step "
+                "to the plain force field (counted); %d NVE steps from the start state in one timed region, "
+                "energies every step" % md4,
+        "model": desc_r, "value": rate, "unit": UNIT, "ms_per_md_step": ms / max(steps_done, 1),
+        "ns_per_day": rate * DT_FS * 1e-6 * 86400, "md_steps": steps_done, "status": status_w,
+        "fallback_steps": int(c1["fallbacks"] - c0["fallbacks"]),
+        "fallback_fraction": (c1["fallbacks"] - c0["fallbacks"]) / max(steps_done, 1),
+        "rebuilds": int(c1["rebuilds"] - c0["rebuilds"]),
+        "drift_kcal_mol_atom": drift["drift"],
+        "drift_excluding_switch_steps_kcal_mol_atom": drift["drift_excluding_switches"],
+        "switch_steps": drift["switch_steps"], "switch_steps_dH_kcal_mol_atom": drift["switch_dH_per_atom"],
+        "temperature_K": {"start": float(T[0]), "end": float(T[-1])} if T.size else None,
+        "e2e": {"value": md4 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
+                "d2h_bytes_per_step": 2 * n * 3 * 8 + 48, "error": e2e_err},
+        "clocks": clk.summary(),
+    }
+
+    # ---- secondary: the same model without its ranges (every step runs the learned kernels)
     md = args.learned_md_steps
-    blob, model_desc = learned_model()
-    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, trace_capacity=md,
-                       energy_every=RECORD_EVERY, record_every=RECORD_EVERY, max_frames=max(1, md // RECORD_EVERY))
-    # learned forces against the plain force field at the starting geometry (both on the GPU)
-    _, f_l, _ = ctx.compute(s.pos)
-    plain = mdpf.Context(s, dt_fs=DT_FS)
-    _, f_p, _ = plain.compute(s.pos)
-    plain.close()
-    rmse_vs_plain = float(np.sqrt(((f_l - f_p) ** 2).mean()))
-    rms_plain = float(np.sqrt((f_p ** 2).mean()))
-    ctx.set_state(s.pos, v0)
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob_n, dt_fs=DT_FS, trace_capacity=md,
+                       energy_every=RECORD_EVERY)
     slots = {"neighbors": mdpf.MDPF_PROF_LEARN_NEIGHBORS, "features": mdpf.MDPF_PROF_LEARN_FEATURES,
              "mlp": mdpf.MDPF_PROF_LEARN_MLP, "adjoint": mdpf.MDPF_PROF_LEARN_ADJOINT,
-             "force_eval": mdpf.MDPF_PROF_NONBONDED, "md_step_calls": mdpf.MDPF_PROF_STEP}
-    # every bench step starts from the same state (reset outside the timed region): the
-    # trained potential keeps this cluster intact for a few thousand steps only
+             "force_eval": mdpf.MDPF_PROF_NONBONDED}
     with torch.cuda.stream(stream):
-        # set_state runs on the context's own stream: the previous steps (on `stream`) must be done
         for _ in range(args.warmup):
             stream.synchronize()
             ctx.set_state(s.pos, v0)
             ctx.step_async(md, stream.cuda_stream)
         stream.synchronize()
-        ctx.counters()
         x_mid, _ = ctx.get_state()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        with ClockSampler(dev.index) as clk:
-            for k in range(args.steps):
-                stream.synchronize()
-                ctx.set_state(s.pos, v0)
-                flush.zero_()
-                evs[k][0].record(stream)
-                ctx.step_async(md, stream.cuda_stream)
-                evs[k][1].record(stream)
-            torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
+        tot = 0.0
+        for _ in range(args.steps):
+            stream.synchronize()
+            ctx.set_state(s.pos, v0)
+            flush.zero_()
+            tot += _timed_on(stream, lambda: ctx.step_async(md, stream.cuda_stream))
         x_end, _ = ctx.get_state()
-        # per-stage durations: the same steps again with CUDA events around every stage on the
-        # launch stream (profiling launches each step kernel by kernel instead of as one graph)
+        # per-stage durations: the same steps again, launched kernel by kernel with CUDA events per stage
         ctx.set_profiling(True)
-        for k in range(args.steps):
+        for _ in range(args.steps):
             stream.synchronize()
             ctx.set_state(s.pos, v0)
             flush.zero_()
@@ -283,45 +428,23 @@ def learned_leg(args, dev, stream, flush):
         torch.cuda.synchronize()
     prof = {k: ctx.profile(v) for k, v in slots.items()}
     ctx.set_profiling(False)
-    c = ctx.counters()
-    lc = ctx.learned_counters()
-    if c["status"] != 0:
-        raise RuntimeError("device status %#x after the learned timed region" % c["status"])
-    rate = args.steps * md / (ms / 1000.0)
-
-    pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    pin_x[:] = s.pos
-    pin_v[:] = v0
-    e2e_steps = max(2, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_state(pin_x, pin_v)
-        ctx.step(md)
-        ctx.get_state(pin_x, pin_v)
-        ctx.counters()
-    e2e_rate = e2e_steps * md / (time.perf_counter() - t0)
+    if ctx.counters()["status"] != 0:
+        raise RuntimeError("device status after the learned run without ranges")
     ctx.close()
-    fused = fused_arm(args, s, v0, blob, stream, flush, x_end)
+    rate_n = args.steps * md / (tot / 1000.0)
+    fused = fused_arm(args, s, v0, blob_n, stream, flush, x_end)
 
-    # the plain force field on the same cluster (all pairs, persistent stepper), for the comparison
+    # the plain force field on the same cluster (all pairs, persistent stepper)
     plain_md = max(10, md // 4)
     pctx = mdpf.Context(s, dt_fs=DT_FS, energy_every=RECORD_EVERY, trace_capacity=plain_md)
     pctx.set_state(s.pos, v0)
     pctx.step(plain_md)
     pms = 0.0
-    for _ in range(args.steps):
-        pctx.set_state(s.pos, v0)
-        torch.cuda.synchronize()
-        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            pctx.set_state(s.pos, v0)
             flush.zero_()
-            e0_.record(stream)
-            pctx.step_async(plain_md, stream.cuda_stream)
-            e1_.record(stream)
-        torch.cuda.synchronize()
-        pms += e0_.elapsed_time(e1_)
+            pms += _timed_on(stream, lambda: pctx.step_async(plain_md, stream.cuda_stream))
     if pctx.counters()["status"] != 0:
         raise RuntimeError("device status after the plain run on the learned workload")
     pctx.close()
@@ -345,39 +468,134 @@ def learned_leg(args, dev, stream, flush):
     achieved = flops / avg_s / 1e12
     fe_ms, fe_n = prof["force_eval"]
     return {
-        "workload": LEARNED_DESC, "n_atoms": n, "md_steps_per_bench_step": md, "value": rate, "unit": UNIT,
-        "ms_per_md_step": ms / args.steps / md, "ns_per_day": rate * DT_FS * 1e-6 * 86400,
+        "workload": LEARNED_DESC, "n_atoms": n,
+        "value": as_written["value"], "unit": UNIT, "ms_per_md_step": as_written["ms_per_md_step"],
+        "ns_per_day": as_written["ns_per_day"],
         "dtype": "bf16 GEMM operands / f32 features and forces / f64 state",
-        "model": model_desc,
-        "force_rmse_vs_plain_kcal_mol_A": rmse_vs_plain, "rms_plain_force_kcal_mol_A": rms_plain,
+        "as_written": as_written,
+        "oracle_error_at_start": {"force_rmse_over_rms": _rel_rmse(f_l, f_o), "energy_abs_per_atom": abs(e_l - e_o) / n,
+                                  "what": "model without ranges on the GPU (BF16 MLP) against the FP64 oracle of the "
+                                          "same model at the start geometry"},
+        "force_rmse_vs_plain_kcal_mol_A": float(np.sqrt(((f_l - f_p) ** 2).mean())),
+        "rms_plain_force_kcal_mol_A": float(np.sqrt((f_p ** 2).mean())),
+        "without_ranges": {
+            "what": "secondary: the same model without its feature ranges, every step on the learned kernels; "
+                    "bench steps of %d MD steps, each from the start state (reset outside the timed region)" % md,
+            "value": rate_n, "unit": UNIT, "ms_per_md_step": tot / args.steps / md,
+            "ns_per_day": rate_n * DT_FS * 1e-6 * 86400, "md_steps_per_bench_step": md,
+            "stage_ms_per_force_eval": {k: prof[k][0] / max(prof[k][1], 1) for k in stage_ms},
+            "force_eval_ms": fe_ms / max(fe_n, 1),
+            "pairs_5p2": pairs, "triplets_3p5": triplets,
+            "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "flops_per_launch": flops,
+                         "avg_launch_us": avg_s * 1e6, "launches": prof[dom][1],
+                         "traffic": LEARNED_TRAFFIC.get(dom)},
+            "profile_note": "stage times come from a second, equally sized run launched kernel by kernel with "
+                            "CUDA events around each stage",
+            "fused": dict(fused, vs_stagewise=fused["value"] / rate_n,
+                          fused_kernel_over_stages=fused["fused_kernel_us"] / 1e3 /
+                          sum(prof[k][0] / max(prof[k][1], 1) for k in ("features", "mlp", "adjoint"))),
+        },
         "plain_same_workload": {"value": plain_rate, "unit": UNIT, "ms_per_md_step": pms / args.steps / plain_md,
                                 "md_steps_per_bench_step": plain_md,
                                 "what": "plain force field (all pairs, no cutoff) on the same cluster, persistent "
                                         "stepper, same start state"},
-        "learned_over_plain": rate / plain_rate,
-        "force_rmse_vs_oracle": "<= 1e-2 x RMS(F) against the FP64 oracle (BF16 parity tests)",
-        "stepper": "one CUDA graph launch per MD step (fused neighbour check/build, features, tensor-core MLP, "
-                   "adjoint, integration); every bench step restarts from the cluster's initial state",
-        "profile_note": "stage times and the roofline come from a second, equally sized run launched kernel by "
-                        "kernel with CUDA events around each stage",
-        "stage_ms_per_force_eval": {k: prof[k][0] / max(prof[k][1], 1) for k in stage_ms},
-        "force_eval_ms": fe_ms / max(fe_n, 1),
-        "rebuilds": lc["rebuilds"], "fallback_steps": lc["fallback_steps"], "max_row": lc["max_row"],
-        "pairs_5p2": pairs, "triplets_3p5": triplets,
-        "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6, "launches": prof[dom][1],
-                     "traffic": LEARNED_TRAFFIC.get(dom)},
-        "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 3 * 8,
-                "d2h_bytes_per_step": 2 * n * 3 * 8 + 48},
-        "clocks": clk.summary(),
-        "fused": dict(fused, vs_stagewise=fused["value"] / rate,
-                      fused_kernel_over_stages=fused["fused_kernel_us"] / 1e3 /
-                      sum(prof[k][0] / max(prof[k][1], 1) for k in ("features", "mlp", "adjoint"))),
+        "learned_without_ranges_over_plain": rate_n / plain_rate,
     }
 
 
+def mol256_leg(args, dev, stream):
+    """One learned energy + force evaluation of the 256-atom molecule (seeded model): device time per
+    evaluation (mdpf_compute_device, CUDA events) and the error against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2412_18271_b300 import mdpf, model, synth
+    s = synth.workload("mol256")
+    m = model.init_model(7)
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=m.pack(), dt_fs=DT_FS)
+    e, f, _ = ctx.compute(s.pos)
+    eo, fo, _ = O.Learned(m).energy_forces(s.element, s.pos)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    F = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device=dev)
+    reps = 200
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            ctx.compute_device(pos.data_ptr(), E.data_ptr(), F.data_ptr(), stream.cuda_stream)
+        ms = _timed_on(stream, lambda: [ctx.compute_device(pos.data_ptr(), E.data_ptr(), F.data_ptr(),
+                                                           stream.cuda_stream) for _ in range(reps)])
+    if ctx.counters()["status"] != 0:
+        raise RuntimeError("device status in the 256-atom learned evaluation")
+    ctx.close()
+    return {"workload": "256-atom seeded molecule, learned potential (seeded Kaiming-uniform model with the "
+                        "repulsive core), one energy + force evaluation",
+            "us_per_evaluation": 1000.0 * ms / reps, "evaluations_per_s": reps / (ms / 1000.0),
+            "timing": "mdpf_compute_device back to back on one stream (fresh neighbour build each call), "
+                      "CUDA events over %d calls" % reps,
+            "oracle_error": {"force_rmse_over_rms": _rel_rmse(f, fo), "energy_abs_per_atom": abs(e - eo) / s.n_atoms}}
+
+
+def training_leg(args, dev, stream):
+    """One force-matching iteration (loss, gradient by the device trainer, AdamW) on a batch of 64 frames
+    x 2,048 atoms of the cluster, frames recorded by the plain path; CUDA events on the launch stream."""
+    import torch
+    from oracle import oracle as O
+    from paper_2412_18271_b300 import autograd as AG
+    from paper_2412_18271_b300 import mdpf, model, synth
+    s = synth.workload("cluster2048")
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED["cluster2048"])
+    B = 64
+    ctx = mdpf.Context(s, dt_fs=DT_FS, record_every=10, max_frames=B, energy_every=10)
+    ctx.set_state(s.pos, v0)
+    ctx.step(10 * B)
+    P, En, Fr, _ = ctx.frames(B)
+    ctx.close()
+    _, _, m = learned_model(ranges=False)
+    pos = torch.tensor(P.reshape(-1, 3), dtype=torch.float64, device=dev).contiguous()
+    el = torch.tensor(s.element.astype("int32"), device=dev).repeat(B).contiguous()
+    E = torch.tensor(En, dtype=torch.float64, device=dev)
+    F = torch.tensor(Fr.reshape(-1, 3), dtype=torch.float32, device=dev).contiguous()
+    trainer = mdpf.Trainer(B, s.n_atoms, m.e0, core_a=m.core_a, core_rc=m.core_rc)
+    params = torch.tensor(model.to_flat(m), device=dev, requires_grad=True)
+    opt = AG.CosineAdamW([params], lr=1e-3, total_steps=20000)
+
+    def it():
+        opt.zero_grad(set_to_none=True)
+        L, _ = AG.ForceMatchingLoss.apply(params, trainer, pos, el, E, F)
+        L.backward()
+        opt.step()
+        return L
+
+    iters = 20
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            it()
+        ms = _timed_on(stream, lambda: [it() for _ in range(iters)])
+    if trainer.status() != 0:
+        raise RuntimeError("trainer status after the timed iterations")
+    # the gradient of the first frame against the FP64 oracle (one frame; the oracle takes seconds per frame)
+    f0 = [(s.element, P[0], float(En[0]), Fr[0].astype("float64"))]
+    t1 = mdpf.Trainer(1, s.n_atoms, m.e0, core_a=m.core_a, core_rc=m.core_rc)
+    p1 = torch.tensor(model.to_flat(m), device=dev, requires_grad=True)
+    L1, _ = AG.ForceMatchingLoss.apply(p1, t1, pos[:s.n_atoms].contiguous(), el[:s.n_atoms].contiguous(),
+                                       E[:1].contiguous(), F[:s.n_atoms].contiguous())
+    L1.backward()
+    O.set_threads(os.cpu_count() or 1)
+    Lo, go, _ = O.train_loss_grad(m, f0)
+    O.set_threads(1)
+    g = model.from_flat(p1.grad.detach().cpu().numpy(), m.e0)
+    import numpy as np
+    rel = {k: _rel_rmse(np.asarray(getattr(g, k), dtype=np.float64), go[k]) for k in ("W1", "W2", "b1", "W3")}
+    return {"workload": "force-matching iteration, batch of 64 frames x 2048 atoms (the plain path's cluster "
+                        "trajectory), trained model, forward + double-backward + AdamW",
+            "ms_per_iteration": ms / iters, "iterations_per_s": iters / (ms / 1000.0),
+            "oracle_error_one_frame": {"loss_rel": abs(float(L1.detach()) - Lo) / abs(Lo),
+                                       "gradient_rel_rmse": rel}}
+
+
 def fused_arm(args, s, v0, blob, stream, flush, x_ref):
+
     """The same learned MD, timed the same way, with the fused features -> MLP -> adjoint kernel
     (MDPF_MLP_FUSED: one kernel per force evaluation, features and dE/dG kept on chip)."""
     import numpy as np
@@ -468,9 +686,24 @@ def provider_leg(args, dev, stream):
     plain.close()
     out["provider_overhead_us_per_md_step"] = (out["python_provider"]["us_per_md_step"] -
                                                out["kernel_sequence"]["us_per_md_step"])
+    # the latency floor of the persistent step loop: a 2-atom molecule (one bond, no pair work), the same
+    # resident kernel, barriers and integration as the 64-atom run
+    t2 = tiny_molecule(2)
+    ctx = mdpf.Context(t2, dt_fs=DT_FS, energy_every=10, trace_capacity=1000)
+    ctx.set_state(t2.pos, synth.velocities(t2.mass, t2.pos, 300.0, seed=2))
+    with torch.cuda.stream(stream):
+        ctx.step_async(1000, stream.cuda_stream)
+        ms = _timed_on(stream, lambda: ctx.step_async(10000, stream.cuda_stream))
+    if ctx.counters()["status"] != 0:
+        raise RuntimeError("device status in the empty-loop run")
+    ctx.close()
+    out["empty_loop_floor"] = {"value": 10000 / (ms / 1000.0), "unit": UNIT, "us_per_md_step": ms / 10.0,
+                               "what": "persistent stepper on a 2-atom molecule: the step loop's own latency "
+                                       "(grid barriers, integration, energy steps) with no pair work"}
+    out["persistent_over_floor"] = out["persistent"]["us_per_md_step"] / out["empty_loop_floor"]["us_per_md_step"]
     # an ethanol-sized molecule (9 atoms) on the learned path: the per-step latency floor of the
     # graph-launched learned step
-    blob, _ = learned_model()
+    blob, _, _ = learned_model(ranges=False)
     t9 = synth.molecule(9, seed=9)
     ctx = mdpf.Context(t9, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, energy_every=10,
                        trace_capacity=1000)
@@ -489,6 +722,12 @@ def provider_leg(args, dev, stream):
     ctx.close()
     out["workload"] = "64-atom molecule, plain force field (the provider wraps the library's own force field)"
     return out
+
+
+def tiny_molecule(n: int):
+    """An n-atom molecule of the workloads' generator (seeded), for latency floors."""
+    from paper_2412_18271_b300 import synth
+    return synth.molecule(n, seed=1000 + n)
 
 
 def run_learned_only(args):
@@ -599,12 +838,20 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    # the plain path's error against the FP64 oracle at the timed start state
+    from oracle import oracle as O
+    e_g, f_g, _ = ctx.compute(s.pos)
+    e_o, f_o, _ = O.Plain(s).energy_forces(s.pos)
+    line["oracle_error"] = {"force_rmse_over_rms": _rel_rmse(f_g, f_o), "energy_abs_per_atom": abs(e_g - e_o) / n,
+                            "what": "FP32 forces / FP64 energy on the GPU against the FP64 oracle at the start state"}
     if not args.no_learned:
         line["learned"] = learned_leg(args, dev, stream, flush)
-    if not args.no_learned:
+        line["mol256"] = mol256_leg(args, dev, stream)
+        line["training"] = training_leg(args, dev, stream)
         line["provider"] = provider_leg(args, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+        line["cpu_oracle"] = cpu_oracle_suite()
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -623,6 +870,7 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-md-steps", type=int, default=200)
+    ap.add_argument("--learned-run-steps", type=int, default=LEARNED_MD_STEPS)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--only-learned", action="store_true",
                     help="run and print the learned leg alone (profiling runs; not a bench line)")
