@@ -358,9 +358,12 @@ def learned_leg(args, dev, stream, flush):
     status_w = c1["status"]
     U, K = ctx.trace()
     fb = ctx.trace_fallbacks()
-    drift = nve_drift(U, K, n, fb, c0["fallbacks"])
     steps_done = int(c1["steps"])
-    T = K / (1.5 * n * 0.0019872041)
+    bad = np.nonzero(~(np.isfinite(U) & np.isfinite(K)) | (np.abs(U) > 1e9) | (np.abs(K) > 1e9))[0]
+    first_bad = int(bad[0]) + 1 if bad.size else None       # step number of the first non-finite energy
+    ok_n = (first_bad - 1) if first_bad else U.size
+    drift = nve_drift(U[:ok_n], K[:ok_n], n, fb[:ok_n], c0["fallbacks"])
+    T = K[:max(ok_n, 1)] / (1.5 * n * 0.0019872041)
     # e2e: host buffers through the public API, the copies inside the timed region
     pin_x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     pin_v = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -385,8 +388,10 @@ def learned_leg(args, dev, stream, flush):
                 "energies every step" % md4,
         "model": desc_r, "value": rate, "unit": UNIT, "ms_per_md_step": ms / max(steps_done, 1),
         "ns_per_day": rate * DT_FS * 1e-6 * 86400, "md_steps": steps_done, "status": status_w,
-        "fallback_steps": int(c1["fallbacks"] - c0["fallbacks"]),
-        "fallback_fraction": (c1["fallbacks"] - c0["fallbacks"]) / max(steps_done, 1),
+        "completed": status_w == 0, "first_nonfinite_step": first_bad,
+        "steps_analysed": int(ok_n),
+        "fallback_steps": int(drift["plain_steps"]),
+        "fallback_fraction": drift["plain_steps"] / max(ok_n, 1),
         "rebuilds": int(c1["rebuilds"] - c0["rebuilds"]),
         "drift_kcal_mol_atom": drift["drift"],
         "drift_excluding_switch_steps_kcal_mol_atom": drift["drift_excluding_switches"],
@@ -432,6 +437,24 @@ def learned_leg(args, dev, stream, flush):
         raise RuntimeError("device status after the learned run without ranges")
     ctx.close()
     rate_n = args.steps * md / (tot / 1000.0)
+    # the model without ranges over the full NVE run: completed or not, its drift
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=blob_n, dt_fs=DT_FS, energy_every=1, trace_capacity=md4)
+    ctx.set_state(s.pos, v0)
+    with torch.cuda.stream(stream):
+        ms_n = _timed_on(stream, lambda: ctx.step_async(md4, stream.cuda_stream))
+    cn = ctx.counters()
+    Un, Kn = ctx.trace()
+    badn = np.nonzero(~(np.isfinite(Un) & np.isfinite(Kn)) | (np.abs(Un) > 1e9) | (np.abs(Kn) > 1e9))[0]
+    okn = int(badn[0]) if badn.size else Un.size
+    dn = nve_drift(Un[:okn], Kn[:okn], n)
+    Tn = Kn[:max(okn, 1)] / (1.5 * n * 0.0019872041)
+    run_n = {"md_steps": int(cn["steps"]), "status": cn["status"], "completed": cn["status"] == 0,
+             "first_nonfinite_step": int(badn[0]) + 1 if badn.size else None,
+             "value": cn["steps"] / (ms_n / 1000.0), "unit": UNIT,
+             "drift_kcal_mol_atom": dn["drift"], "steps_analysed": okn,
+             "temperature_K": {"start": float(Tn[0]), "end": float(Tn[-1])} if Tn.size else None,
+             "max_row": ctx.learned_counters()["max_row"]}
+    ctx.close()
     fused = fused_arm(args, s, v0, blob_n, stream, flush, x_end)
 
     # the plain force field on the same cluster (all pairs, persistent stepper)
@@ -483,6 +506,7 @@ def learned_leg(args, dev, stream, flush):
                     "bench steps of %d MD steps, each from the start state (reset outside the timed region)" % md,
             "value": rate_n, "unit": UNIT, "ms_per_md_step": tot / args.steps / md,
             "ns_per_day": rate_n * DT_FS * 1e-6 * 86400, "md_steps_per_bench_step": md,
+            "nve_run": run_n,
             "stage_ms_per_force_eval": {k: prof[k][0] / max(prof[k][1], 1) for k in stage_ms},
             "force_eval_ms": fe_ms / max(fe_n, 1),
             "pairs_5p2": pairs, "triplets_3p5": triplets,

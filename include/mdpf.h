@@ -194,8 +194,10 @@ typedef struct mdpf_params {
  * E = sum_i W3 . celu(W2 celu(W1 G_i + b1) + b2) + b3 + e0, plus an optional
  * repulsive pair core E_core = sum_{i<j, r_ij < rc} A (1 - r/rc)^3 (rc/r)
  * (the features vanish as r -> 0, so the network alone cannot keep two atoms
- * from merging).  Forces are the analytic adjoint -dE/dx.  The GEMM operands run in BF16 (features, CELU
- * outputs and back-propagated deltas rounded to BF16), accumulations in FP32,
+ * from merging).  Forces are the analytic adjoint -dE/dx.  The GEMM operands
+ * run in BF16 (features and back-propagated deltas rounded to BF16; layer 1's
+ * CELU output enters the second GEMM as a pair hi + lo of BF16 values, which
+ * removes the energy bias one rounding would cause), accumulations in FP32,
  * energies and the state in FP64.  The plain topology (bonds, charges, LJ) is
  * still required: it is the fallback force field.
  *

@@ -9,9 +9,10 @@
 //            each row goes to the GEMM operand in shared memory as BF16, in
 //            the 128-byte-swizzled K-major layout TMA would have produced; rows
 //            past the tile's atoms are zero
-//   phase B  the four GEMMs and their epilogues of the tensor-core MLP (as in
-//            mlp_tc.cu, GEMM1's A operand now resident): energy per atom into
-//            E_row and the energy slot, dE/dG into TMEM columns 0..383
+//   phase B  the GEMMs and their epilogues of the tensor-core MLP (as in
+//            mlp_tc.cu, GEMM1's A operand now resident; layer 1's CELU output
+//            enters GEMM2 as a BF16 pair hi + lo): energy per atom into E_row
+//            and the energy slot, dE/dG into TMEM columns 0..383
 //   phase C  per half tile: the 64 rows of dE/dG from TMEM into shared memory
 //            (FP32, the adjoint's padded row layout), then the compute warps
 //            take those atoms one at a time: neighbours again, chain rule to
@@ -160,11 +161,12 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
     // ---------------- phase B: the MLP
     if (warp == kFuProducer) {
         if (lane == 0) {
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < 20; ++c) {
                 const int s = c & 1;
                 if (c >= 2 && !mbar_wait(bar(F_EMPTY + s), ((c >> 1) - 1) & 1, s_abort)) break;
-                const int g = c < 6 ? 0 : (c < 10 ? 1 : (c < 12 ? 2 : 3));
-                const int kc = c - (g == 0 ? 0 : (g == 1 ? 6 : (g == 2 ? 10 : 12)));
+                // phases: 0 GEMM1, 1 GEMM2 (hi), 2 GEMM2 (lo), 3 GEMM3, 4 GEMM4
+                const int g = c < 6 ? 0 : (c < 10 ? 1 : (c < 14 ? 2 : (c < 16 ? 3 : 4)));
+                const int kc = c - (g == 0 ? 0 : (g == 1 ? 6 : (g == 2 ? 10 : (g == 3 ? 14 : 16))));
                 const uint32_t B = sbase + kFuOffScr + s * kFuStage;
                 const int x = kc * 64;
                 const uint32_t fb = bar(F_FULL + s);
@@ -172,10 +174,10 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                     mbar_expect_tx(fb, 32 * 1024);
                     tma_2d(B, &maps.w1, x, e * kH1, fb);
                     tma_2d(B + 16384, &maps.w1, x, e * kH1 + 128, fb);
-                } else if (g == 1) {
+                } else if (g == 1 || g == 2) {
                     mbar_expect_tx(fb, 16 * 1024);
                     tma_2d(B, &maps.w2, x, e * kH2, fb);
-                } else if (g == 2) {
+                } else if (g == 3) {
                     mbar_expect_tx(fb, 32 * 1024);
                     tma_2d(B, &maps.w2t, x, e * kH1, fb);
                     tma_2d(B + 16384, &maps.w2t, x, e * kH1 + 128, fb);
@@ -194,12 +196,12 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
             const uint32_t ra = sbase;
             int c = 0;
             bool ok = true;
-            for (int g = 0; g < 4 && ok; ++g) {
+            for (int g = 0; g < 5 && ok; ++g) {
                 if (g > 0) {
                     if (!mbar_wait(bar(F_EPI), (g - 1) & 1, s_abort)) break;
                     tc_fence_after();
                 }
-                const int nk = g == 0 ? 6 : (g == 2 ? 2 : 4);
+                const int nk = g == 0 ? 6 : (g == 3 ? 2 : 4);
                 for (int kc = 0; kc < nk; ++kc, ++c) {
                     const int s = c & 1;
                     if (!mbar_wait(bar(F_FULL + s), (c >> 1) & 1, s_abort)) {
@@ -211,14 +213,14 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                     const uint32_t B = sbase + kFuOffScr + s * kFuStage;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const uint32_t acc = (kc | k) != 0;
+                        const uint32_t acc = g == 2 || (kc | k) != 0;   // GEMM2 (lo) adds onto GEMM2 (hi)
                         const uint32_t ko = 32u * k;
                         const uint64_t a = sdesc(ra + kc * 16384 + ko);
                         if (g == 0) {
                             mma_bf16(tmem, a, sdesc(B + ko), i256, acc);
-                        } else if (g == 1) {
+                        } else if (g == 1 || g == 2) {
                             mma_bf16(tmem + 256, a, sdesc(B + ko), i128, acc);
-                        } else if (g == 2) {
+                        } else if (g == 3) {
                             mma_bf16(tmem + 256, a, sdesc(B + ko), i256, acc);
                         } else {
                             mma_bf16(tmem, a, sdesc(B + ko), i256, acc);
@@ -237,7 +239,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
         const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
         float v[32], h[32];
         bool ok = true;
-        // epi1: a1 = bf16(celu(H1 + b1)) over the (consumed) G operand
+        // epi1: a1 = celu(H1 + b1): its BF16 value over the (consumed) G operand, a1 (FP32) over H1 in TMEM
         if ((ok = warp_wait(bar(F_ACC), 0, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
@@ -245,19 +247,32 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float x = v[j] + sb1[cc * 32 + j], ex = exp10x_neg(x);
-                    v[j] = celu_e(x, ex);
-                    h[j] = dcelu_e(x, ex);
+                    const float x = v[j] + sb1[cc * 32 + j];
+                    v[j] = celu_e(x, exp10x_neg(x));
                 }
                 st_operand32(res, r, cc * 32, v);
-                tmem_st32(tl + cc * 32, h);   // celu'(H1 + b1) replaces H1 (read again by epi3)
+                tmem_st32(tl + cc * 32, v);
+            }
+            proxy_fence();
+            tc_fence_before();
+            mbar_arrive(bar(F_EPI));
+        }
+        // epi1b: once GEMM2 has read the operand, the BF16 residuals a1 - bf16(a1) replace it
+        if (ok && (ok = warp_wait(bar(F_ACC), 1, s_abort))) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
+                tmem_ld32(tl + cc * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = bf16_residual(v[j]);
+                st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();
             tc_fence_before();
             mbar_arrive(bar(F_EPI));
         }
         // epi2: energy partial and d2 = bf16(W3 * celu'(H2 + b2))
-        if (ok && (ok = warp_wait(bar(F_ACC), 1, s_abort))) {
+        if (ok && (ok = warp_wait(bar(F_ACC), 0, s_abort))) {
             tc_fence_after();
             float E = 0.f;
             tmem_ld32(tl + 256 + cg * 32, v);
@@ -282,14 +297,14 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
             if (efx != nullptr) fx_warp_add_d(&efx[E_LEARN], Er);
         }
         // epi3: d1 = bf16(P1 * celu'(H1 + b1))
-        if (ok && (ok = warp_wait(bar(F_ACC), 0, s_abort))) {
+        if (ok && (ok = warp_wait(bar(F_ACC), 1, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + 256 + cc * 32, v);
-                tmem_ld32(tl + cc * 32, h);   // celu'(H1 + b1), stored by epi1
+                tmem_ld32(tl + cc * 32, h);   // a1, stored by epi1
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = v[j] * h[j];
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * dcelu_from_a(h[j]);
                 st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();
@@ -297,7 +312,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
             mbar_arrive(bar(F_EPI));
         }
         // GEMM4 done: g = dE/dG in TMEM columns 0..383; the operand region and the ring are free
-        if (ok && (ok = warp_wait(bar(F_ACC), 1, s_abort))) tc_fence_after();
+        if (ok && (ok = warp_wait(bar(F_ACC), 0, s_abort))) tc_fence_after();
 
         // ---------------- phase C
         unsigned char *scr = sm + kFuOffScr + warp * kFuWarpScr;

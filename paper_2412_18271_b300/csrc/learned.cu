@@ -340,8 +340,12 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated, unsig
         }
 #pragma unroll
         for (int r = 0; r < kMlpRows; ++r) {
-            sA1[r][t] = BF16 ? bf16r(celu(acc[r])) : celu(acc[r]);
-            sH1d[r][t] = dcelu(acc[r]);
+            // BF16: the tensor-core kernels' operand pair hi + lo (both BF16) of celu(h1), and celu'
+            // recovered from celu(h1) as they do (1, or 10 a + 1 below zero)
+            const float a = celu(acc[r]);
+            const float hi = bf16r(a);
+            sA1[r][t] = BF16 ? hi + bf16r(a - hi) : a;
+            sH1d[r][t] = BF16 ? (a >= 0.f ? 1.f : fmaf(10.f, a, 1.f)) : dcelu(acc[r]);
         }
     }
     __syncthreads();

@@ -2,13 +2,19 @@
 // input gradient dE/dG for one 128-row tile of same-element atoms per CTA.
 //
 //   GEMM1  H1 = G  W1^T      [128 x 256], K = 384   (TMEM columns   0..255)
-//   epi1   a1 = bf16(celu(H1 + b1))                  -> shared A operand; celu'(H1 + b1) -> TMEM 0..255
-//   GEMM2  H2 = a1 W2^T      [128 x 128], K = 256   (TMEM columns 256..383)
+//   epi1   a1 = celu(H1 + b1); hi = bf16(a1)          -> shared A operand; a1 (FP32) -> TMEM 0..255
+//   GEMM2  H2 = hi W2^T      [128 x 128], K = 256   (TMEM columns 256..383)
+//   epi1b  lo = bf16(a1 - hi)                         -> shared A operand (a1 read back from TMEM)
+//   GEMM2' H2 += lo W2^T     (the same W2 chunks again)
 //   epi2   E  = W3 . celu(H2 + b2) + b3 + e0;  d2 = bf16(W3 * celu'(H2 + b2))
 //   GEMM3  P1 = d2 W2        [128 x 256], K = 128   (TMEM columns 256..511)
-//   epi3   d1 = bf16(P1 * celu'(H1 + b1))           (celu' read back from TMEM, no exponential)
+//   epi3   d1 = bf16(P1 * celu'(H1 + b1))           (celu' = 1 or 10 a1 + 1 from a1 in TMEM)
 //   GEMM4  g  = d1 W1        [128 x 384], K = 256   (TMEM columns 0..255, 256..383)
 //   epi4   g -> global FP32
+// a1 enters GEMM2 as the pair hi + lo of BF16 values (16 significant bits):
+// rounding a1 to one BF16 value biases the energy through the curvature of
+// the second CELU (~2e-3 kcal/mol/atom on a trained model, all atoms the same
+// sign), the pair removes that bias; every other GEMM input is one BF16 value.
 //
 // Operands are BF16 in shared memory in the 128-byte-swizzled K-major layout
 // (8-row x 128-byte atoms, the 16-byte unit index XOR-ed with the row index
@@ -44,7 +50,8 @@ constexpr int kGStride = 36;                   // padded row of a 32 x 32 FP32 s
 constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
 static_assert(kSmemBytes <= 232448, "shared memory");
 static_assert(kEpiWarps * 32 * kGStride * 4 <= kStages * kStageBytes, "g staging fits in the ring");
-constexpr int kChunks = 16;                    // 6 + 4 + 2 + 4 K-chunks of 64
+constexpr int kChunks = 20;                    // 6 + 4 + 4 + 2 + 4 K-chunks of 64 (GEMM1, GEMM2, GEMM2', 3, 4)
+constexpr int kPhases = 5;
 
 // barrier block: full[kStages] empty[kStages] acc epi drain, then (from byte 96) tmem address, abort
 // flag, issued, consumed
@@ -53,12 +60,16 @@ static_assert(8 * (B_DRAIN + 1) <= 96, "barrier block");
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory"); }
 
+// K-chunk c of the operand stream: phase g (0 GEMM1, 1 GEMM2 with hi, 2 GEMM2 with lo, 3 GEMM3, 4 GEMM4)
+// and its chunk index kc within the phase.
 __device__ __forceinline__ void chunk_of(int c, int &g, int &kc) {
     if (c < 6) { g = 0; kc = c; }
     else if (c < 10) { g = 1; kc = c - 6; }
-    else if (c < 12) { g = 2; kc = c - 10; }
-    else { g = 3; kc = c - 12; }
+    else if (c < 14) { g = 2; kc = c - 10; }
+    else if (c < 16) { g = 3; kc = c - 14; }
+    else { g = 4; kc = c - 16; }
 }
+__device__ __forceinline__ int phase_chunks(int g) { return g == 0 ? 6 : (g == 3 ? 2 : 4); }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, int gated, unsigned long long *efx) {
@@ -127,10 +138,10 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
                     tma_2d(A, &maps.g, x, row0, fb);
                     tma_2d(B, &maps.w1, x, e * kH1, fb);
                     tma_2d(B + 16384, &maps.w1, x, e * kH1 + 128, fb);
-                } else if (g == 1) {
+                } else if (g == 1 || g == 2) {
                     mbar_expect_tx(fb, 16 * 1024);
                     tma_2d(B, &maps.w2, x, e * kH2, fb);
-                } else if (g == 2) {
+                } else if (g == 3) {
                     mbar_expect_tx(fb, 32 * 1024);
                     tma_2d(B, &maps.w2t, x, e * kH1, fb);
                     tma_2d(B + 16384, &maps.w2t, x, e * kH1 + 128, fb);
@@ -150,12 +161,12 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             const uint32_t res = sbase + kOffRes;
             int c = 0;
             bool ok = true;
-            for (int g = 0; g < 4 && ok; ++g) {
+            for (int g = 0; g < kPhases && ok; ++g) {
                 if (g > 0) {
                     if (!mbar_wait(bar(B_EPI), (g - 1) & 1, s_abort)) break;
                     tc_fence_after();
                 }
-                const int nk = g == 0 ? 6 : (g == 2 ? 2 : 4);
+                const int nk = phase_chunks(g);
                 for (int kc = 0; kc < nk; ++kc, ++c) {
                     const int s = c % kStages;
                     if (!mbar_wait(bar(B_FULL + s), (c / kStages) & 1, s_abort)) {
@@ -167,13 +178,13 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
                     const uint32_t A = sbase + s * kStageBytes, B = g == 0 ? A + 16384 : A;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const uint32_t acc = (kc | k) != 0;
+                        const uint32_t acc = g == 2 || (kc | k) != 0;   // GEMM2' adds onto GEMM2
                         const uint32_t ko = 32u * k;
                         if (g == 0) {
                             mma_bf16(tmem, sdesc(A + ko), sdesc(B + ko), i256, acc);
-                        } else if (g == 1) {
+                        } else if (g == 1 || g == 2) {
                             mma_bf16(tmem + 256, sdesc(res + kc * 16384 + ko), sdesc(B + ko), i128, acc);
-                        } else if (g == 2) {
+                        } else if (g == 3) {
                             mma_bf16(tmem + 256, sdesc(res + kc * 16384 + ko), sdesc(B + ko), i256, acc);
                         } else {
                             const uint64_t a = sdesc(res + kc * 16384 + ko);
@@ -195,7 +206,8 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         unsigned char *res = sm + kOffRes;
         float v[32], h[32];
         bool ok = true;
-        // epi1: a1 = bf16(celu(H1 + b1)), columns 64 cg .. 64 cg + 63
+        // epi1: a1 = celu(H1 + b1), columns 64 cg .. 64 cg + 63: its BF16 value to the operand, a1 itself
+        // (FP32) over H1 in TMEM (read again by epi1b and epi3)
         if ((ok = warp_wait(bar(B_ACC), 0, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
@@ -203,19 +215,32 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float x = v[j] + sb1[cc * 32 + j], ex = exp10x_neg(x);
-                    v[j] = celu_e(x, ex);
-                    h[j] = dcelu_e(x, ex);
+                    const float x = v[j] + sb1[cc * 32 + j];
+                    v[j] = celu_e(x, exp10x_neg(x));
                 }
                 st_operand32(res, r, cc * 32, v);
-                tmem_st32(tl + cc * 32, h);   // celu'(H1 + b1) replaces H1 (read again by epi3)
+                tmem_st32(tl + cc * 32, v);
+            }
+            proxy_fence();
+            tc_fence_before();
+            mbar_arrive(bar(B_EPI));
+        }
+        // epi1b: once GEMM2 has read the operand, the BF16 residuals a1 - bf16(a1) replace it
+        if (ok && (ok = warp_wait(bar(B_ACC), 1, s_abort))) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
+                tmem_ld32(tl + cc * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = bf16_residual(v[j]);
+                st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();
             tc_fence_before();
             mbar_arrive(bar(B_EPI));
         }
         // epi2: energy partial and d2 = bf16(W3 * celu'(H2 + b2)), columns 32 cg .. 32 cg + 31
-        if (ok && (ok = warp_wait(bar(B_ACC), 1, s_abort))) {
+        if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {
             tc_fence_after();
             float E = 0.f;
             tmem_ld32(tl + 256 + cg * 32, v);
@@ -240,14 +265,14 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
             if (efx != nullptr) fx_warp_add_d(&efx[E_LEARN], Er);
         }
         // epi3: d1 = bf16(P1 * celu'(H1 + b1)), columns 64 cg .. 64 cg + 63
-        if (ok && (ok = warp_wait(bar(B_ACC), 0, s_abort))) {
+        if (ok && (ok = warp_wait(bar(B_ACC), 1, s_abort))) {
             tc_fence_after();
 #pragma unroll 1
             for (int cc = 2 * cg; cc < 2 * cg + 2; ++cc) {
                 tmem_ld32(tl + 256 + cc * 32, v);
-                tmem_ld32(tl + cc * 32, h);   // celu'(H1 + b1), stored by epi1
+                tmem_ld32(tl + cc * 32, h);   // a1, stored by epi1
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = v[j] * h[j];
+                for (int j = 0; j < 32; ++j) v[j] = v[j] * dcelu_from_a(h[j]);
                 st_operand32(res, r, cc * 32, v);
             }
             proxy_fence();
@@ -256,7 +281,7 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         }
         // epi4: g = dE/dG, columns 96 cg .. 96 cg + 95, through a per-warp 32 x 32 staging
         // block (in the operand ring, idle once the last GEMM completed) for coalesced stores
-        if (ok && warp_wait(bar(B_ACC), 1, s_abort)) {
+        if (ok && warp_wait(bar(B_ACC), 0, s_abort)) {
             tc_fence_after();
             float *stg = (float *)sm + warp * 32 * kGStride;
             float *gtile = L.g + (size_t)(row0 + 32 * q4) * kNFeat;

@@ -128,6 +128,10 @@ __device__ __forceinline__ float exp10x_neg(float x) {
 // CELU(0.1) and its derivative from one exponential: e = exp(10 min(x, 0)).
 __device__ __forceinline__ float celu_e(float x, float e) { return x > 0.f ? x : kCeluAlphaTc * (e - 1.f); }
 __device__ __forceinline__ float dcelu_e(float x, float e) { return x >= 0.f ? 1.f : e; }
+// CELU(0.1)'s derivative from its value a = celu(x): 1 for a >= 0, exp(10 x) = 10 a + 1 below.
+__device__ __forceinline__ float dcelu_from_a(float a) { return a >= 0.f ? 1.f : fmaf(10.f, a, 1.f); }
+// The BF16 residual of x: x - bf16(x), itself a BF16 value after the operand store rounds it.
+__device__ __forceinline__ float bf16_residual(float x) { return x - __bfloat162float(__float2bfloat16_rn(x)); }
 
 // 32 consecutive FP32 columns into this thread's TMEM lane (store and wait in one statement).
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {

@@ -145,8 +145,8 @@ def _bf(x):
 
 
 def _mlp_emulated(m, element, G):
-    """The kernel's rounding points: BF16 GEMM inputs (features, CELU outputs,
-    deltas), everything else FP64."""
+    """The kernel's rounding points: BF16 GEMM inputs (features, deltas; layer 1's
+    CELU output as the pair hi + lo of BF16 values), everything else FP64."""
     def celu(x):
         return np.where(x > 0, x, 0.1 * np.expm1(x / 0.1))
 
@@ -162,7 +162,8 @@ def _mlp_emulated(m, element, G):
             continue
         W1, W2 = m.W1[e].astype(np.float64), m.W2[e].astype(np.float64)
         h1 = _bf(G[idx]) @ W1.T + m.b1[e]
-        a1 = _bf(celu(h1))
+        a1f = celu(h1).astype(np.float32).astype(np.float64)
+        a1 = _bf(a1f) + _bf(a1f - _bf(a1f))
         h2 = a1 @ W2.T + m.b2[e]
         E[idx] = celu(h2) @ m.W3[e].astype(np.float64) + float(m.b3[e]) + m.e0[e]
         d2 = _bf(m.W3[e] * dcelu(h2))
