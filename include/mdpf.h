@@ -240,15 +240,19 @@ typedef struct mdpf_counters {
  * persistent stepper; a model blob whose celu_alpha is not 0.1).  The blob
  * is checked on the host before any device work.  On error *out is NULL.
  */
+/* Paper: the force object built around the force callable (Methods, Fig. 1). */
 MDPF_API int mdpf_create(const mdpf_topology *topology, const mdpf_params *params, mdpf_ctx **out);
 
 /* Free every device buffer and the context.  NULL is ignored. */
+/* Paper: no counterpart (lifetime of the context). */
 MDPF_API void mdpf_destroy(mdpf_ctx *ctx);
 
 /* Message for the last failure on ctx (or of the last failed mdpf_create when ctx is NULL). */
+/* Paper: no counterpart (error reporting). */
 MDPF_API const char *mdpf_last_error(const mdpf_ctx *ctx);
 
 /* Number of atoms, and the number of angles derived from the bond graph. */
+/* Paper: no counterpart (sizes of the derived topology). */
 MDPF_API int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles);
 
 /*
@@ -262,6 +266,7 @@ MDPF_API int mdpf_sizes(const mdpf_ctx *ctx, int32_t *n_atoms, int32_t *n_angles
  * capacity (128), and OUT_OF_RANGE when the features left the model's range
  * with the fallback off (the outputs then hold the model's values).
  */
+/* Paper: the callable that returns the energy and the forces for given positions (Methods). */
 MDPF_API int mdpf_compute(mdpf_ctx *ctx, const double *pos, double *energy, double *forces, double *terms);
 
 /*
@@ -272,6 +277,7 @@ MDPF_API int mdpf_compute(mdpf_ctx *ctx, const double *pos, double *energy, doub
  * learned mode it shares the neighbour list and feature buffers with
  * mdpf_step: do not run the two concurrently on different streams.
  */
+/* Paper: the callable that returns the energy and the forces for given positions (Methods). */
 MDPF_API int mdpf_compute_device(mdpf_ctx *ctx, const double *d_pos, double *d_energy, float *d_forces,
                                  void *cuda_stream);
 
@@ -280,9 +286,11 @@ MDPF_API int mdpf_compute_device(mdpf_ctx *ctx, const double *d_pos, double *d_e
  * (A/fs), FP64.  Evaluates forces at pos, resets the step counter, the energy
  * trace and the status word, and records h_initial.
  */
+/* Paper: the engine state the NVE runs start from (Results, "Example: Ethanol"). */
 MDPF_API int mdpf_set_state(mdpf_ctx *ctx, const double *pos, const double *vel);
 
 /* Copy the current state to host buffers (any may be NULL): pos, vel [N,3] FP64. */
+/* Paper: the coordinates compared between runs (Results, "Example: Ethanol", Fig. 3). */
 MDPF_API int mdpf_get_state(mdpf_ctx *ctx, double *pos, double *vel);
 
 /*
@@ -294,6 +302,7 @@ MDPF_API int mdpf_get_state(mdpf_ctx *ctx, double *pos, double *vel);
  * non-finite, TIMEOUT if a device-side grid barrier gave up (the state is then
  * undefined; call mdpf_set_state).  Synchronous.
  */
+/* Paper: the NVE velocity-Verlet runs (Results, "Example: Ethanol", Fig. 2); the whole loop on the device answers the per-step overhead of Table 2. */
 MDPF_API int mdpf_step(mdpf_ctx *ctx, int64_t n_steps);
 
 /*
@@ -303,9 +312,11 @@ MDPF_API int mdpf_step(mdpf_ctx *ctx, int64_t n_steps);
  * streams) before calling mdpf_set_state, mdpf_get_state or mdpf_compute on
  * the same context.
  */
+/* Paper: the NVE runs (Results, "Example: Ethanol"), enqueued without a host wait (Table 2's overhead). */
 MDPF_API int mdpf_step_async(mdpf_ctx *ctx, int64_t n_steps, void *cuda_stream);
 
 /* Counters, energies of the current state and the device status word. */
+/* Paper: the energies and their conservation in the NVE runs (Results, "Example: Ethanol", Fig. 2). */
 MDPF_API int mdpf_get_counters(mdpf_ctx *ctx, mdpf_counters *out);
 
 /*
@@ -321,6 +332,7 @@ MDPF_API int mdpf_get_counters(mdpf_ctx *ctx, mdpf_counters *out);
  * integrates (Results, "Example: Ethanol").  Errors: INVALID_ARG (bad
  * temperature, no state set), CUDA.  Synchronous.
  */
+/* Paper: the starting velocities of the NVE runs (Results, "Example: Ethanol"). */
 MDPF_API int mdpf_init_velocities(mdpf_ctx *ctx, double temperature_K, uint64_t seed);
 
 /*
@@ -329,6 +341,7 @@ MDPF_API int mdpf_init_velocities(mdpf_ctx *ctx, double temperature_K, uint64_t 
  * kcal/mol after step step[k] (any output may be NULL).  *n_out receives the
  * count written (at most max_n).
  */
+/* Paper: the potential, kinetic and total energy traces (Results, "Example: Ethanol", Figs. 2 and 4). */
 MDPF_API int mdpf_get_trace(mdpf_ctx *ctx, double *U, double *K, int64_t *step, int64_t max_n, int64_t *n_out);
 
 /*
@@ -340,6 +353,7 @@ MDPF_API int mdpf_get_trace(mdpf_ctx *ctx, double *U, double *K, int64_t *step, 
  * its predecessor's is a switch step, across which H is not conserved (the
  * two potentials differ), so drift is judged on the steps between switches.
  */
+/* Paper: the NVE energy-conservation criterion (Results, "Example: Ethanol", Fig. 2). */
 MDPF_API int mdpf_get_trace_fallbacks(mdpf_ctx *ctx, int64_t *fallbacks, int64_t max_n, int64_t *n_out);
 
 /*
@@ -347,6 +361,7 @@ MDPF_API int mdpf_get_trace_fallbacks(mdpf_ctx *ctx, int64_t *fallbacks, int64_t
  * FP64, energy [n] FP64, forces [n,N,3] FP32, step [n] int64 (any may be
  * NULL).  A frame is taken after every record_every-th step.
  */
+/* Paper: the recorded trajectory frames (Results, "Example: Ethanol", Fig. 3). */
 MDPF_API int mdpf_get_frames(mdpf_ctx *ctx, int64_t max_n, double *pos, double *energy, float *forces,
                              int64_t *step, int64_t *n_out);
 
@@ -355,9 +370,11 @@ MDPF_API int mdpf_get_frames(mdpf_ctx *ctx, int64_t max_n, double *pos, double *
  * offset [N+1] int32 and idx [capacity] int32, each row ascending.  *total
  * receives the number of entries (idx may be NULL to query it).
  */
+/* Paper: no counterpart (topology of the analytic force field). */
 MDPF_API int mdpf_get_exclusions(mdpf_ctx *ctx, int32_t *offset, int32_t *idx, int64_t capacity, int64_t *total);
 
 /* Angles (a, vertex, b) derived on the device, [n_angles,3] int32, vertex-major order. */
+/* Paper: no counterpart (topology of the analytic force field). */
 MDPF_API int mdpf_get_angles(mdpf_ctx *ctx, int32_t *angles, int64_t capacity, int64_t *n_out);
 
 /*
@@ -365,6 +382,7 @@ MDPF_API int mdpf_get_angles(mdpf_ctx *ctx, int32_t *angles, int64_t capacity, i
  * MDPF_STATUS_* bits are OR-ed into the device status word and reported by
  * the next mdpf_step / mdpf_get_counters; bits == 0 clears the word.
  */
+/* Paper: no counterpart (failure detection). */
 MDPF_API int mdpf_debug_set_status(mdpf_ctx *ctx, uint32_t bits);
 
 /*
@@ -373,6 +391,7 @@ MDPF_API int mdpf_debug_set_status(mdpf_ctx *ctx, uint32_t bits);
  * returns MDPF_ERR_TIMEOUT.  Exercises the timeout path of the grid barrier
  * without hanging the GPU.
  */
+/* Paper: no counterpart (failure detection). */
 MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
 
 /*
@@ -386,9 +405,12 @@ MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
  *               GEMM input): atomic energies E_i [N] FP64 and dE/dG [N][384] FP32.
  * MDPF_ERR_UNSUPPORTED unless the context is in learned mode.
  */
+/* Paper: the ML force module the plugin wraps (Methods), stage by stage. */
 MDPF_API int mdpf_learned_neighbors(mdpf_ctx *ctx, const double *pos, int32_t max_per_atom, int32_t *count,
                                     int32_t *idx);
+/* Paper: the ML force module the plugin wraps (Methods), stage by stage. */
 MDPF_API int mdpf_learned_features(mdpf_ctx *ctx, const double *pos, float *G);
+/* Paper: the ML force module the plugin wraps (Methods), stage by stage. */
 MDPF_API int mdpf_learned_mlp(mdpf_ctx *ctx, const float *G, double *E_atom, float *dEdG);
 
 /*
@@ -397,6 +419,7 @@ MDPF_API int mdpf_learned_mlp(mdpf_ctx *ctx, const float *G, double *E_atom, flo
  * plain force field when the fallback is on), and the largest neighbour row
  * seen.
  */
+/* Paper: the ML force module the plugin wraps (Methods); fallback counting has no counterpart. */
 MDPF_API int mdpf_learned_counters(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fallback_steps, int32_t *max_row);
 
 /*
@@ -431,14 +454,21 @@ typedef struct mdpf_train_params {
                                   trained parameters; its energy and forces are part of E_f and F. */
 } mdpf_train_params;
 #define MDPF_TRAIN_PARAMS_PER_ELEMENT 131585
+/* Paper: forces of an energy model by automatic differentiation (Methods); training has no counterpart. */
 MDPF_API int mdpf_trainer_create(const mdpf_train_params *params, mdpf_trainer **out);
+/* Paper: no counterpart (lifetime of the trainer). */
 MDPF_API void mdpf_trainer_destroy(mdpf_trainer *trainer);
+/* Paper: no counterpart (error reporting). */
 MDPF_API const char *mdpf_trainer_last_error(const mdpf_trainer *trainer);
+/* Paper: forces of an energy model by automatic differentiation (Methods); the force-matching gradient has no counterpart. */
 MDPF_API int mdpf_trainer_loss_grad(mdpf_trainer *trainer, const float *d_params, float *d_grad, int32_t n_frames,
                                     const double *d_pos, const int32_t *d_element, const double *d_E_ref,
                                     const float *d_F_ref, double *d_loss3, void *cuda_stream);
+/* Paper: no counterpart (error reporting). */
 MDPF_API int mdpf_trainer_status(mdpf_trainer *trainer, uint32_t *status);
+/* Paper: no counterpart (the range behind the plain fallback). */
 MDPF_API int mdpf_trainer_feature_range(mdpf_trainer *trainer, float *lo, float *hi);
+/* Paper: no counterpart (the optimiser of the training). */
 MDPF_API int mdpf_adamw_step(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t n, int64_t step,
                              double lr, double beta1, double beta2, double eps, double weight_decay,
                              void *cuda_stream);
@@ -448,6 +478,7 @@ MDPF_API int mdpf_adamw_step(float *d_params, const float *d_grad, float *d_m, f
  * U [N][384] FP32 = sum_a dG/dx_a . v_a (the tangent the training gradient
  * uses; for parity checks).  Learned mode only.
  */
+/* Paper: no counterpart (the tangent the training gradient uses). */
 MDPF_API int mdpf_learned_jvp(mdpf_ctx *ctx, const double *pos, const float *v, float *U);
 
 /*
@@ -471,7 +502,9 @@ MDPF_API int mdpf_learned_jvp(mdpf_ctx *ctx, const double *pos, const float *v, 
 #define MDPF_PROF_LEARN_ADJOINT 6
 #define MDPF_PROF_LEARN_FUSED 7
 #define MDPF_PROF_SLOTS 8
+/* Paper: the per-step timings of Table 2. */
 MDPF_API int mdpf_set_profiling(mdpf_ctx *ctx, int32_t enable);
+/* Paper: the per-step timings of Table 2. */
 MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int64_t *launches);
 
 /*
@@ -499,7 +532,10 @@ MDPF_API int mdpf_get_profile(mdpf_ctx *ctx, int32_t slot, double *total_ms, int
  * the library until the process exits; it limits n_atoms to 2048 (larger
  * values return MDPF_ERR_INVALID_ARG).  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  All calls share
+ * current) and keeps it with the device's current context; a call that finds
+ * another context current (the old one was destroyed, e.g. by
+ * cudaDeviceReset) looks it up again.  Make the first call on a device, and
+ * the first after a reset, before any stream capture.  All calls share
  * the array and each call clears what it accumulates, so calls that overlap
  * on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  Errors are reported by the return code and

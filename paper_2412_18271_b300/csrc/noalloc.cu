@@ -13,6 +13,9 @@
 // The arithmetic is the library's all-pairs routine (forcefield.cuh), so for
 // a system without bonds the results equal those of mdpf_compute_device.
 // The paper has no counterpart of this entry point.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -134,6 +137,25 @@ __global__ void k_na_out(const unsigned long long *fx, const unsigned long long 
 
 std::mutex g_na_mutex;
 unsigned char *g_na_ptr[64] = {nullptr};
+CUcontext g_na_ctx[64] = {nullptr};      // the context each cached address belongs to
+
+// The calling thread's current context (the driver call reached through the runtime, so the library
+// needs no link-time dependency on the driver library), or null when it cannot be determined.
+CUcontext current_context() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 }  // namespace
 }  // namespace mdpf
@@ -158,13 +180,16 @@ extern "C" int mdpf_pairs_noalloc(int32_t n, const double *d_pos, const int32_t 
     if (dev < 0 || dev >= 64) return fail(nullptr, MDPF_ERR_UNSUPPORTED, "mdpf_pairs_noalloc: device index >= 64");
     unsigned char *base = nullptr;
     {
-        // once per device, with that device current: the device address of the scratch array
+        // once per device (and again if the device's context was replaced, e.g. after cudaDeviceReset),
+        // with that device current: the device address of the scratch array
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (g_na_ptr[dev] == nullptr) {
+        const CUcontext cur = current_context();   // null before the runtime made a context current: look up
+        if (g_na_ptr[dev] == nullptr || cur == nullptr || cur != g_na_ctx[dev]) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
             if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
             g_na_ptr[dev] = static_cast<unsigned char *>(ptr);
+            g_na_ctx[dev] = cur;
         }
         base = g_na_ptr[dev];
     }

@@ -448,6 +448,8 @@ def pairs_noalloc(n_atoms: int, d_pos: int, d_element: int, d_charge: int, lj_si
                   d_energy: int, d_forces: int, stream: int = 0) -> None:
     """All-pairs LJ + Coulomb through the entry point that allocates no device memory
     (device addresses as ints; see mdpf_pairs_noalloc in include/mdpf.h)."""
+    if len(lj_sigma) != 4 or len(lj_eps) != 4:
+        raise ValueError("lj_sigma and lj_eps need one value per element (4 each)")
     sig = (_f64 * 4)(*[float(v) for v in lj_sigma])
     eps = (_f64 * 4)(*[float(v) for v in lj_eps])
     rc = lib().mdpf_pairs_noalloc(int(n_atoms), _vp(d_pos), _vp(d_element), _vp(d_charge), sig, eps,

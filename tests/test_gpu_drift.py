@@ -51,6 +51,31 @@ def test_learned_bf16_nve_drift_10k_steps(kernel):
     ctx.close()
 
 
+def test_trained_model_nve_drift_on_its_training_cluster():
+    # the trained model on the 2048-atom cluster it was trained on (in distribution; no ranges): the
+    # cluster heats to ~850 K as its start strain relaxes, where the fitted potential is stiffer than the
+    # plain force field.  At dt = 0.5 fs velocity Verlet drifts 0.025 kcal/mol/atom over 10k steps with
+    # either MLP precision (integration error); halving the step cuts that by 8x (BF16) and 27x (FP32).
+    # So the energy conservation of the learned BF16 path is checked with the step resolved: 10,000
+    # steps of 0.25 fs, A16's bound.
+    import os
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(here, "paper_2412_18271_b300", "data", "learned_c3.mdpfmlp"), "rb") as fh:
+        m = model.Model.unpack(fh.read())
+    m.lo = m.hi = None
+    s = synth.workload("cluster2048")
+    v0 = synth.velocities(s.mass, s.pos, 300.0, seed=synth.WORKLOAD_VELOCITY_SEED["cluster2048"])
+    ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=m.pack(), dt_fs=0.25, energy_every=1,
+                       trace_capacity=10000)
+    ctx.set_state(s.pos, v0)
+    ctx.step(10000)
+    U, K = ctx.trace()
+    r = nve_drift(U, K, s.n_atoms)
+    assert r["drift"] <= LEARNED_DRIFT_BOUND, r
+    assert ctx.counters()["status"] == 0
+    ctx.close()
+
+
 def _ranged(m, s, widen):
     G = O.features(s.element, s.pos)
     lo = np.zeros((4, 384), dtype=np.float32)

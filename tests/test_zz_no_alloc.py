@@ -86,3 +86,39 @@ def test_noalloc_largest_size_and_rejects_larger():
         mdpf.pairs_noalloc(n + 1, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, 0.0,
                            de.data_ptr(), df.data_ptr(), 0)
     assert ei.value.name == "INVALID_ARG" and "2048" in str(ei.value)
+
+
+@pytest.mark.parametrize("n", [1, 33, 100, 2047])
+def test_noalloc_ragged_sizes_match_the_oracle(n):
+    # sizes that are not multiples of the 64-atom padding, so the padding atoms the kernel adds take part;
+    # an explicit Coulomb constant; against the FP64 oracle of the same unbonded system
+    import torch
+    from oracle import oracle as O
+    from tests import tiny
+    src = _unbonded(64, 32, 60.0, seed=100)
+    s = tiny.system(src.pos[:n], src.element[:n], charge=src.charge[:n], sigma=src.lj_sigma, eps=src.lj_eps)
+    ke = 300.0
+    eo, fo, _ = O.Plain(s, coulomb_k=ke).energy_forces(s.pos)
+    dpos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+    del_ = torch.tensor(s.element, dtype=torch.int32, device="cuda")
+    dq = torch.tensor(s.charge, dtype=torch.float64, device="cuda")
+    de = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    df = torch.full((n, 3), 7.0, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    mdpf.pairs_noalloc(n, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, ke,
+                       de.data_ptr(), df.data_ptr(), stream)
+    torch.cuda.synchronize()
+    f = df.cpu().numpy().astype(np.float64)
+    rms = np.sqrt((fo ** 2).mean())
+    assert np.sqrt(((f - fo) ** 2).mean()) <= F_RTOL * rms + (1e-12 if n == 1 else 0.0)
+    assert abs(de.item() - eo) / n <= E_TOL_PER_ATOM
+    # either output may be omitted: each alone equals the full call's
+    df2 = torch.full((n, 3), 7.0, dtype=torch.float32, device="cuda")
+    mdpf.pairs_noalloc(n, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, ke,
+                       0, df2.data_ptr(), stream)
+    de2 = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    mdpf.pairs_noalloc(n, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, ke,
+                       de2.data_ptr(), 0, stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(df2.cpu().numpy(), df.cpu().numpy())
+    assert de2.item() == de.item()
