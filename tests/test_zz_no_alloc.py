@@ -96,7 +96,12 @@ def test_noalloc_ragged_sizes_match_the_oracle(n):
     from oracle import oracle as O
     from tests import tiny
     src = _unbonded(64, 32, 60.0, seed=100)
-    s = tiny.system(src.pos[:n], src.element[:n], charge=src.charge[:n], sigma=src.lj_sigma, eps=src.lj_eps)
+    # n atoms on a jittered 3.5 A grid (a dense gas: every pair interacts, no two atoms overlap)
+    rng = np.random.default_rng(n)
+    g = np.arange(13) * 3.5
+    grid = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:n]
+    pos = grid + rng.normal(scale=0.2, size=grid.shape)
+    s = tiny.system(pos, src.element[:n], charge=src.charge[:n], sigma=src.lj_sigma, eps=src.lj_eps)
     ke = 300.0
     eo, fo, _ = O.Plain(s, coulomb_k=ke).energy_forces(s.pos)
     dpos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
