@@ -328,8 +328,9 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                 for (int cc = 3 * cg; cc < 3 * cg + 3; ++cc) {
                     tmem_ld32(tl + cc * 32, v);
                     float *d = dst + (cc < 2 ? 32 * cc : 64 + kAngStride * (cc - 2));
+                    // rounded to BF16 as the per-stage path stores dE/dG, so both give the same forces
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) d[j] = v[j];
+                    for (int j = 0; j < 32; ++j) d[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
                 }
             }
             fu_sync();

@@ -410,7 +410,11 @@ __global__ void __launch_bounds__(256) k_mlp_simt(LearnedDev L, int gated, unsig
                 for (int r = 0; r < kMlpRows; ++r) acc[r] = fmaf(sD1[r][a], wv, acc[r]);
             }
 #pragma unroll
-            for (int r = 0; r < kMlpRows; ++r) L.g[(size_t)(r0 + r) * kNFeat + f] = acc[r];
+            for (int r = 0; r < kMlpRows; ++r) {
+                const size_t q = (size_t)(r0 + r) * kNFeat + f;
+                if (BF16) static_cast<__nv_bfloat16 *>(L.g)[q] = __float2bfloat16_rn(acc[r]);
+                else static_cast<float *>(L.g)[q] = acc[r];
+            }
         }
     }
 }
@@ -436,7 +440,14 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const
     fetch_neighbours(L, pos4, i, lane, nf);
     float gv[kNFeat / 32];
 #pragma unroll
-    for (int b = 0; b < kNFeat / 32; ++b) gv[b] = L.g[(size_t)row * kNFeat + 32 * b + lane];
+    if (L.g_f32) {
+#pragma unroll
+        for (int b = 0; b < kNFeat / 32; ++b) gv[b] = static_cast<const float *>(L.g)[(size_t)row * kNFeat + 32 * b + lane];
+    } else {
+#pragma unroll
+        for (int b = 0; b < kNFeat / 32; ++b)
+            gv[b] = __bfloat162float(static_cast<const __nv_bfloat16 *>(L.g)[(size_t)row * kNFeat + 32 * b + lane]);
+    }
 #pragma unroll
     for (int b = 0; b < kNFeat / 32; ++b) sg[w][g_col(32 * b + lane)] = gv[b];
     int cnt, nr, na;

@@ -47,7 +47,8 @@ struct LearnedDev {
     // features and MLP
     __nv_bfloat16 *G16;          // [n_rows][384] GEMM input
     float *G32;                  // [n_rows][384] FP32 features (parity output) or null
-    float *g;                    // [n_rows][384] dE/dG
+    void *g;                     // [n_rows][384] dE/dG (the adjoint's input): BF16, or FP32 when g_f32
+    int g_f32;                   // 1: the FP32-operand MLP variant, whose forces are the exact FP32 gradient
     double *E_row;               // [n_rows]
     const __nv_bfloat16 *W1, *W1T, *W2, *W2T;  // [4][256][384], [4][384][256], [4][128][256], [4][256][128]
     const float *b1, *b2, *W3, *b3;            // [4][256], [4][128], [4][128], [4]

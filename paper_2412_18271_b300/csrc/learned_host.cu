@@ -257,7 +257,12 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LA(L.nb_bar, 2);
     LA(L.G16, (size_t)n_rows * kNFeat);
     LA(L.G32, (size_t)n_rows * kNFeat);
-    LA(L.g, (size_t)n_rows * kNFeat);
+    {   // dE/dG: room for FP32 (the FP32-operand variant), BF16 otherwise
+        float *gbuf = nullptr;
+        LA(gbuf, (size_t)n_rows * kNFeat);
+        L.g = gbuf;
+        L.g_f32 = h->mlp_kernel == MDPF_MLP_SIMT_FP32 ? 1 : 0;
+    }
     LA(L.E_row, n_rows);
     LA(dW1, W1.size());
     LA(dW1T, W1T.size());
@@ -528,7 +533,15 @@ int mdpf_learned_mlp(mdpf_ctx *c, const float *G, double *E_atom, float *dEdG) {
     std::vector<float> g((size_t)h->n_rows * kNFeat);
     if (h->n_rows > 0) {
         LCK(c, cudaMemcpyAsync(E.data(), h->dev.E_row, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, c->stream));
-        LCK(c, cudaMemcpyAsync(g.data(), h->dev.g, sizeof(float) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+        if (h->dev.g_f32) {
+            LCK(c, cudaMemcpyAsync(g.data(), h->dev.g, sizeof(float) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            std::vector<__nv_bfloat16> gb(g.size());
+            LCK(c, cudaMemcpyAsync(gb.data(), h->dev.g, sizeof(__nv_bfloat16) * gb.size(), cudaMemcpyDeviceToHost,
+                                   c->stream));
+            LCK(c, cudaStreamSynchronize(c->stream));
+            for (size_t q = 0; q < g.size(); ++q) g[q] = __bfloat162float(gb[q]);
+        }
     }
     uint32_t st = 0;
     LCK(c, cudaMemcpyAsync(&st, c->d_status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));

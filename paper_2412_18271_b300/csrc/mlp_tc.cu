@@ -10,7 +10,7 @@
 //   GEMM3  P1 = d2 W2        [128 x 256], K = 128   (TMEM columns 256..511)
 //   epi3   d1 = bf16(P1 * celu'(H1 + b1))           (celu' = 1 or 10 a1 + 1 from a1 in TMEM)
 //   GEMM4  g  = d1 W1        [128 x 384], K = 256   (TMEM columns 0..255, 256..383)
-//   epi4   g -> global FP32
+//   epi4   g -> global, rounded to BF16 (the adjoint's input; half the bytes of FP32)
 // a1 enters GEMM2 as the pair hi + lo of BF16 values (16 significant bits):
 // rounding a1 to one BF16 value biases the energy through the curvature of
 // the second CELU (~2e-3 kcal/mol/atom on a trained model, all atoms the same
@@ -46,10 +46,10 @@ constexpr int kResBytes = 64 * 1024;       // resident A operand: a1 / d2 / d1
 constexpr int kOffRes = kStages * kStageBytes;
 constexpr int kOffPar = kOffRes + kResBytes;   // b1[256] b2[128] w3[128] E partials[4][128], FP32
 constexpr int kOffBar = kOffPar + 4096;
-constexpr int kGStride = 36;                   // padded row of a 32 x 32 FP32 staging block of g
+constexpr int kGStrideW = 20;                  // padded row (32-bit words) of a 32 x 32 BF16 staging block of g
 constexpr int kSmemBytes = kOffBar + 128 + 1024;   // barriers/flags + 1024-byte alignment slack
 static_assert(kSmemBytes <= 232448, "shared memory");
-static_assert(kEpiWarps * 32 * kGStride * 4 <= kStages * kStageBytes, "g staging fits in the ring");
+static_assert(kEpiWarps * 32 * kGStrideW * 4 <= kStages * kStageBytes, "g staging fits in the ring");
 constexpr int kChunks = 20;                    // 6 + 4 + 4 + 2 + 4 K-chunks of 64 (GEMM1, GEMM2, GEMM2', 3, 4)
 constexpr int kPhases = 5;
 
@@ -283,21 +283,23 @@ k_mlp_tc(LearnedDev L, const __grid_constant__ MlpMaps maps, uint32_t *status, i
         // block (in the operand ring, idle once the last GEMM completed) for coalesced stores
         if (ok && warp_wait(bar(B_ACC), 0, s_abort)) {
             tc_fence_after();
-            float *stg = (float *)sm + warp * 32 * kGStride;
-            float *gtile = L.g + (size_t)(row0 + 32 * q4) * kNFeat;
+            uint32_t *stg = reinterpret_cast<uint32_t *>(sm) + warp * 32 * kGStrideW;
+            __nv_bfloat16 *gtile = static_cast<__nv_bfloat16 *>(L.g) + (size_t)(row0 + 32 * q4) * kNFeat;
 #pragma unroll 1
             for (int cc = 3 * cg; cc < 3 * cg + 3; ++cc) {
                 tmem_ld32(tl + cc * 32, v);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    *reinterpret_cast<float4 *>(stg + lane * kGStride + 4 * q) =
-                        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(stg + lane * kGStrideW + 4 * q) =
+                        make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                                   pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
                 __syncwarp();
+                // 32 rows x 64 bytes: lane takes 16 bytes (8 columns) of row (it * 32 + lane) / 4
 #pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int f = it * 32 + lane, rr = f >> 3, c4 = f & 7;
-                    *reinterpret_cast<float4 *>(gtile + (size_t)rr * kNFeat + cc * 32 + 4 * c4) =
-                        *reinterpret_cast<const float4 *>(stg + rr * kGStride + 4 * c4);
+                for (int it = 0; it < 4; ++it) {
+                    const int f = it * 32 + lane, rr = f >> 2, c4 = f & 3;
+                    *reinterpret_cast<uint4 *>(gtile + (size_t)rr * kNFeat + cc * 32 + 8 * c4) =
+                        *reinterpret_cast<const uint4 *>(stg + rr * kGStrideW + 4 * c4);
                 }
                 __syncwarp();
             }

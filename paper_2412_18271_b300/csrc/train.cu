@@ -551,7 +551,12 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     TA(L.bbox, 8);
     TA(L.G16, R * kNFeat);
     TA(L.G32, R * kNFeat);
-    TA(L.g, R * kNFeat);
+    {
+        __nv_bfloat16 *gbuf = nullptr;   // dE/dG in BF16, as the tensor-core MLP writes it
+        TA(gbuf, R * kNFeat);
+        L.g = gbuf;
+        L.g_f32 = 0;
+    }
     TA(L.E_row, R);
     TA(W1, 4 * (size_t)kH1 * kNFeat);
     TA(W1T, 4 * (size_t)kH1 * kNFeat);

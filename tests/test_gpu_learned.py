@@ -9,7 +9,8 @@ Tolerances:
                    |E - E_oracle| / N <= 1e-3 kcal/mol/atom, against the oracle's
                    FP64 evaluation of the same (BF16-valued) weights
   MLP vs emulation a numpy model of the kernel's rounding points (BF16 inputs to
-                   every GEMM, FP64 products) agrees to FP32 accumulation error
+                   every GEMM, FP64 products, dE/dG rounded to BF16) agrees to FP32
+                   accumulation error (plus the odd BF16 rounding flip of dE/dG)
 """
 import numpy as np
 import pytest
@@ -168,7 +169,7 @@ def _mlp_emulated(m, element, G):
         E[idx] = celu(h2) @ m.W3[e].astype(np.float64) + float(m.b3[e]) + m.e0[e]
         d2 = _bf(m.W3[e] * dcelu(h2))
         d1 = _bf((d2 @ W2) * dcelu(h1))
-        g[idx] = d1 @ W1
+        g[idx] = _bf(d1 @ W1)   # dE/dG is stored in BF16 for the adjoint
     return E, g
 
 
