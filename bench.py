@@ -72,7 +72,7 @@ ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 # DRAM bytes (read + write) per launch of each learned kernel on this workload, from an ncu capture of
 # the kernels (valid for the kernels as captured)
-LEARNED_TRAFFIC = {"adjoint": 34463232, "features": 8897024, "mlp": 14992384, "fused": 11452672}
+LEARNED_TRAFFIC = {"adjoint": 21889536, "features": 8896768, "mlp": 14996992, "fused": 11460864}
 LEARNED_MD_STEPS = 10000         # the learned workload's NVE run, timed as one region
 
 
