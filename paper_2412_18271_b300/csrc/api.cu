@@ -1,4 +1,5 @@
 // C ABI entry points of libmdpf (declared in include/mdpf.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -96,10 +97,9 @@ static void free_ctx(mdpf_ctx *c) {
     for (auto e : c->prof_free) cudaEventDestroy(e);
     void *ptrs[] = {c->d_element, c->d_mass, c->d_hdt_m, c->d_pos4, c->d_pos4_b, c->d_pos4_c, c->d_lj,
                     c->d_charge_s, c->d_bonds, c->d_bond_par, c->d_angles, c->d_excl_off, c->d_excl_idx,
-                    c->d_tile_mask, c->d_tile_flag, c->d_items, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
+                    c->d_row_mask, c->d_grp_off, c->d_grp_ent, c->d_grp_aoff, c->d_x, c->d_v, c->d_fx_base, c->d_fx_c,
                     c->d_efx, c->d_efx_c, c->d_trace_u, c->d_trace_k, c->d_trace_step, c->d_trace_fb, c->d_step, c->d_status,
-                    c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_tile_e,
-                    c->d_own_off, c->d_own, c->d_lang_c2, c->frames.pos,
+                    c->d_xc, c->d_fc, c->d_scalar, c->d_barrier, c->d_part, c->d_lang_c2, c->frames.pos,
                     c->frames.energy, c->frames.forces,
                     c->frames.step};
     for (void *p : ptrs)
@@ -226,7 +226,7 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
 
     CKC(cudaGetDevice(&c->device));
     CKC(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    const int np = c->n_pad, T = c->n_tiles;
+    const int np = c->n_pad;
     // host-side preparation of per-atom constants
     std::vector<float> qs(np, 0.f);
     std::vector<float2> lj(np, make_float2(0.f, 0.f));
@@ -244,21 +244,6 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
         bonds[b] = make_int2(t->bonds[2 * b], t->bonds[2 * b + 1]);
         bpar[b] = make_float2((float)t->bond_r0[b], (float)t->bond_k[b]);
     }
-    // work items of the all-pairs sum: 64x32 blocks first, then the 64x64 diagonal blocks
-    std::vector<int4> items;
-    items.reserve((size_t)T * T / 4 + 3 * T);
-    for (int p = 0; p < T / 2; ++p)
-        for (int J = 2 * p + 2; J < T; ++J) items.push_back(make_int4(ITEM_OFF64, p, J, 0));
-    for (int p = 0; p < T / 2; ++p) {
-        items.push_back(make_int4(ITEM_OFF32, 2 * p, 2 * p + 1, 0));
-        items.push_back(make_int4(ITEM_SELF, 2 * p, 0, 0));
-        items.push_back(make_int4(ITEM_SELF, 2 * p + 1, 0, 0));
-    }
-    // the persistent stepper spreads each tile's bonded terms over its diagonal items and one more item
-    if (c->stepper == MDPF_STEPPER_PERSISTENT)
-        for (int tt = 0; tt < T; ++tt) items.push_back(make_int4(ITEM_BONDED, tt, 0, 0));
-    c->n_items = (int)items.size();
-
     CKC(dalloc(&c->d_element, n));
     CKC(dalloc(&c->d_mass, n));
     CKC(dalloc(&c->d_hdt_m, n));
@@ -278,7 +263,6 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     CKC(dalloc(&c->d_charge_s, np));
     CKC(dalloc(&c->d_bonds, t->n_bonds));
     CKC(dalloc(&c->d_bond_par, t->n_bonds));
-    CKC(dalloc(&c->d_items, items.size()));
     CKC(dalloc(&c->d_x, 3 * (size_t)n));
     CKC(dalloc(&c->d_v, 3 * (size_t)n));
     CKC(dalloc(&c->d_xc, 3 * (size_t)n));
@@ -315,7 +299,6 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
         CKC(cudaMemcpyAsync(c->d_bonds, bonds.data(), sizeof(int2) * t->n_bonds, cudaMemcpyHostToDevice, s));
         CKC(cudaMemcpyAsync(c->d_bond_par, bpar.data(), sizeof(float2) * t->n_bonds, cudaMemcpyHostToDevice, s));
     }
-    CKC(cudaMemcpyAsync(c->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
     CKC(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t) * 4, s));
     CKC(cudaMemsetAsync(c->d_step, 0, sizeof(int64_t), s));
     CKC(cudaMemsetAsync(c->d_barrier, 0, sizeof(unsigned int) * 8, s));
@@ -335,27 +318,46 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
             fail(c, MDPF_ERR_UNSUPPORTED, "cooperative launch of the persistent stepper is not available");
             return bail(MDPF_ERR_UNSUPPORTED);
         }
-        // bonded terms by owning tile (bond: first atom; angle: vertex); the angle list comes from the device
+        // bonded entries of each row group: every term once per atom it moves (bond: 2, angle: 3), so that
+        // a group's owner computes every bonded force on its atoms; the angle list comes from the device
         std::vector<int4> angles(c->n_angles);
         if (c->n_angles > 0)
             CKC(cudaMemcpy(angles.data(), c->d_angles, sizeof(int4) * c->n_angles, cudaMemcpyDeviceToHost));
-        std::vector<std::vector<int>> own(T);
-        for (int b = 0; b < t->n_bonds; ++b) own[t->bonds[2 * b] / kTile].push_back(b);
-        for (int k = 0; k < c->n_angles; ++k) own[angles[k].y / kTile].push_back(t->n_bonds + k);
-        std::vector<int> own_off(T + 1, 0), own_flat;
-        for (int tt = 0; tt < T; ++tt) {
-            own_flat.insert(own_flat.end(), own[tt].begin(), own[tt].end());
-            own_off[tt + 1] = (int)own_flat.size();
+        const int NG = c->n_groups;
+        std::vector<std::vector<int2>> ent(NG);
+        auto add = [&](int atom, int term, int role) {
+            ent[atom / 16].push_back(make_int2(term, ((atom % 16) << 2) | role));
+        };
+        for (int b = 0; b < t->n_bonds; ++b) {
+            add(t->bonds[2 * b], b, 0);
+            add(t->bonds[2 * b + 1], b, 1);
         }
-        own_flat.push_back(0);
-        CKC(dalloc(&c->d_part, 2 * (size_t)c->step_grid * 4));
-        CKC(dalloc(&c->d_tile_e, 2 * (size_t)T * 4));
-        CKC(dalloc(&c->d_own_off, T + 1));
-        CKC(dalloc(&c->d_own, own_flat.size()));
+        for (int k = 0; k < c->n_angles; ++k) {
+            add(angles[k].x, t->n_bonds + k, 0);
+            add(angles[k].y, t->n_bonds + k, 1);
+            add(angles[k].z, t->n_bonds + k, 2);
+        }
+        std::vector<int> grp_off(NG + 1, 0), grp_aoff((size_t)NG * 17, 0);
+        std::vector<int2> grp_flat;
+        for (int g = 0; g < NG; ++g) {
+            // by local atom (stable: term order within an atom), with each atom's range recorded
+            std::stable_sort(ent[g].begin(), ent[g].end(),
+                             [](const int2 &u, const int2 &v) { return (u.y >> 2) < (v.y >> 2); });
+            for (size_t e = 0; e < ent[g].size(); ++e) grp_aoff[(size_t)g * 17 + (ent[g][e].y >> 2) + 1]++;
+            for (int a = 0; a < 16; ++a) grp_aoff[(size_t)g * 17 + a + 1] += grp_aoff[(size_t)g * 17 + a];
+            grp_flat.insert(grp_flat.end(), ent[g].begin(), ent[g].end());
+            grp_off[g + 1] = (int)grp_flat.size();
+        }
+        grp_flat.push_back(make_int2(0, 0));
+        CKC(dalloc(&c->d_part, 2 * (size_t)c->step_grid * 8));
+        CKC(dalloc(&c->d_grp_off, NG + 1));
+        CKC(dalloc(&c->d_grp_ent, grp_flat.size()));
+        CKC(dalloc(&c->d_grp_aoff, grp_aoff.size()));
+        CKC(cudaMemcpy(c->d_grp_aoff, grp_aoff.data(), sizeof(int) * grp_aoff.size(), cudaMemcpyHostToDevice));
         CKC(dalloc(&c->d_pos4_b, np));
-        CKC(cudaMemcpy(c->d_own_off, own_off.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(c->d_own, own_flat.data(), sizeof(int) * own_flat.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemset(c->d_tile_e, 0, sizeof(double) * 2 * T * 4));
+        CKC(cudaMemset(c->d_pos4_b, 0, sizeof(float4) * np));   // padding atoms stay at finite positions
+        CKC(cudaMemcpy(c->d_grp_off, grp_off.data(), sizeof(int) * (NG + 1), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(c->d_grp_ent, grp_flat.data(), sizeof(int2) * grp_flat.size(), cudaMemcpyHostToDevice));
     }
 #undef CKC
     *out = c;

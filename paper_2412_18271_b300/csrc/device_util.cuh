@@ -30,7 +30,39 @@ __device__ __forceinline__ void fx_add(unsigned long long *p, float v) {
 __device__ __forceinline__ void fx_add_d(unsigned long long *p, double v) {
     atomicAdd(p, (unsigned long long)__double2ll_rn(v * 4294967296.0));
 }
-__device__ __forceinline__ double fx_val(unsigned long long u) { return (double)(long long)u * kFxInv; }
+// An int64 as the exact double.  For |i| < 2^51 by the exponent-bias
+// method: adding i to the bit pattern of 1.5 * 2^52 places it in the mantissa
+// of a double in [2^52, 2^53), and one exact subtraction removes the bias
+// (one FP64 addition instead of the 64-bit integer-to-float conversion; FP64
+// work is scarce on this GPU).  Larger values take the conversion instruction.
+__device__ __forceinline__ double fx_exact(long long i) {
+    if (i > -(1ll << 51) && i < (1ll << 51))
+        return __longlong_as_double(i + 0x4338000000000000ll) - 6755399441055744.0;
+    return (double)i;
+}
+
+// x * 2^32 rounded to the nearest int64 by the same exponent-bias method
+// (|x| < 2^19), else the conversion instruction.
+__device__ __forceinline__ long long fx_from_double(double x) {
+    const double y = x * kFxScale;
+    if (y > -2251799813685248.0 && y < 2251799813685248.0)
+        return __double_as_longlong(y + 6755399441055744.0) - 0x4338000000000000ll;
+    return __double2ll_rn(y);
+}
+
+// Finite test of a double on its bits (integer instructions only).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+__device__ __forceinline__ double fx_val(unsigned long long u) {
+    return fx_exact((long long)u) * kFxInv;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Per-lane values of a warp, each rounded to fixed point and then summed as
 // integers (exact, so the total does not depend on how values are grouped

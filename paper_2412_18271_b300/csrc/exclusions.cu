@@ -1,5 +1,5 @@
-// Exclusion set (1-2 and 1-3 partners), derived angles and the per-tile
-// exclusion bitmasks of the all-pairs kernels, built on the device.
+// Exclusion set (1-2 and 1-3 partners), derived angles and the skip masks of
+// the all-pairs kernels' row decomposition, built on the device.
 //
 // A pair (i, j) is left out of the nonbonded sum when the atoms are bonded or
 // share a bonded neighbour; every pair of bonds that meets at an atom carries
@@ -126,49 +126,40 @@ __global__ void k_angle_fill(const int *adj_off, const int *adj, const int *ang_
         for (int q = p + 1; q < adj_off[v + 1]; ++q) angles[w++] = make_int4(adj[p], v, adj[q], 0);
 }
 
-// Set the skip bit of every excluded pair in its 32x32 tile.  Word i of a tile
-// pair (I, J) holds bit j for pair (32I+i, 32J+j).  Diagonal tiles get both
-// orientations.
-__global__ void k_tile_masks(const int *excl_off, const int *excl_idx, int n, int T, uint32_t *mask,
-                             uint32_t *flag) {
+// Skip masks of the row decomposition: word (g, c, a) holds bit l for the
+// pair (16 g + a, 32 c + l).  Thread i sets the bits of its own words only:
+// the atom itself and its excluded partners.
+__global__ void k_row_masks(const int *excl_off, const int *excl_idx, int n, int C, uint32_t *mask) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    uint32_t *row = mask + (size_t)(i / 16) * C * 16 + (i % 16);
+    row[(size_t)(i / kTile) * 16] |= 1u << (i % kTile);
     for (int p = excl_off[i]; p < excl_off[i + 1]; ++p) {
         int j = excl_idx[p];
-        if (j <= i) continue;
-        int I = i / kTile, J = j / kTile;
-        int64_t tp = tile_pair_index(I, J, T);
-        atomicOr(&mask[tp * kTile + (i % kTile)], 1u << (j % kTile));
-        if (I == J) atomicOr(&mask[tp * kTile + (j % kTile)], 1u << (i % kTile));
-        flag[tp] = 1u;
+        row[(size_t)(j / kTile) * 16] |= 1u << (j % kTile);
     }
 }
 
-// Padding atoms (index >= n) never interact: mark every pair that touches one
-// in all tile pairs (I, J) with J >= the first tile holding padding.
-__global__ void k_tile_pad(int n, int T, uint32_t *mask, uint32_t *flag) {
-    const int t0 = n / kTile;  // first tile that holds padding (n < 32 T)
-    const int nj = T - t0;
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nj <= 0 || q >= T * nj) return;
-    const int I = q / nj, J = t0 + q % nj;
-    if (J < I) return;
-    const int64_t tp = tile_pair_index(I, J, T);
-    const int vj = n - J * kTile;  // valid j lanes in tile J (may be <= 0)
-    uint32_t jbits = vj >= kTile ? 0u : (vj <= 0 ? 0xffffffffu : ~((1u << vj) - 1u));
-    const int vi = n - I * kTile;
-    for (int l = 0; l < kTile; ++l) {
-        uint32_t w = jbits;
-        if (l >= vi) w = 0xffffffffu;
-        if (w) mask[tp * kTile + l] |= w;
+// Padding atoms (index >= n) never interact: all bits of a padding row, and
+// the bits of padding j-atoms in every row.
+__global__ void k_row_pad(int n, int n_groups, int C, uint32_t *mask) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= (int64_t)n_groups * C * 16) return;
+    const int a = (int)(w % 16), c = (int)((w / 16) % C), g = (int)(w / (16 * (int64_t)C));
+    const int i = 16 * g + a;
+    if (i >= n) {
+        mask[w] = 0xffffffffu;
+        return;
     }
-    flag[tp] = 1u;
+    const int vj = n - kTile * c;   // real j-atoms in chunk c
+    if (vj >= kTile) return;
+    mask[w] |= vj <= 0 ? 0xffffffffu : (0xffffffffu << vj);
 }
 
 }  // namespace
 
 int build_exclusions(mdpf_ctx *ctx) {
-    const int n = ctx->n, nb = ctx->n_bonds, T = ctx->n_tiles;
+    const int n = ctx->n, nb = ctx->n_bonds;
     cudaStream_t s = ctx->stream;
     int *d_deg = nullptr, *d_adj_off = nullptr, *d_adj = nullptr, *d_cursor = nullptr, *d_cnt = nullptr,
         *d_ang_off = nullptr;
@@ -226,20 +217,17 @@ int build_exclusions(mdpf_ctx *ctx) {
                                                ctx->d_status);
     TRY(cudaMalloc(&ctx->d_angles, sizeof(int4) * ((size_t)totals[1] + 1)));
     k_angle_fill<<<(n + B - 1) / B, B, 0, s>>>(d_adj_off, d_adj, d_ang_off, n, ctx->d_angles);
-    // tile masks
-    const int64_t ntp = (int64_t)T * (T + 1) / 2;
-    ctx->n_tile_pairs = ntp;
-    TRY(cudaMalloc(&ctx->d_tile_mask, sizeof(uint32_t) * ntp * kTile));
-    TRY(cudaMalloc(&ctx->d_tile_flag, sizeof(uint32_t) * ntp));
-    TRY(cudaMemsetAsync(ctx->d_tile_mask, 0, sizeof(uint32_t) * ntp * kTile, s));
-    TRY(cudaMemsetAsync(ctx->d_tile_flag, 0, sizeof(uint32_t) * ntp, s));
-    k_tile_masks<<<(n + B - 1) / B, B, 0, s>>>(ctx->d_excl_off, ctx->d_excl_idx, n, T, ctx->d_tile_mask,
-                                                ctx->d_tile_flag);
-    {
-        const int npad_pairs = T * (T - n / kTile);
-        if (npad_pairs > 0)
-            k_tile_pad<<<(npad_pairs + B - 1) / B, B, 0, s>>>(n, T, ctx->d_tile_mask, ctx->d_tile_flag);
-    }
+    // skip masks of the row decomposition
+    // only groups and chunks that hold real atoms take part (padding rows and padding j-atoms inside them are
+    // masked)
+    const int C = (n + kTile - 1) / kTile, NG = (n + 15) / 16;
+    ctx->n_groups = NG;
+    ctx->n_chunks = C;
+    const size_t nwords = (size_t)NG * C * 16;
+    TRY(cudaMalloc(&ctx->d_row_mask, sizeof(uint32_t) * nwords));
+    TRY(cudaMemsetAsync(ctx->d_row_mask, 0, sizeof(uint32_t) * nwords, s));
+    k_row_masks<<<(n + B - 1) / B, B, 0, s>>>(ctx->d_excl_off, ctx->d_excl_idx, n, C, ctx->d_row_mask);
+    k_row_pad<<<(unsigned)((nwords + B - 1) / B), B, 0, s>>>(n, NG, C, ctx->d_row_mask);
     TRY(cudaGetLastError());
     TRY(cudaStreamSynchronize(s));
     cleanup();

@@ -439,7 +439,6 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const
     NbrFetch nf;
     fetch_neighbours(L, pos4, i, lane, nf);
     float gv[kNFeat / 32];
-#pragma unroll
     if (L.g_f32) {
 #pragma unroll
         for (int b = 0; b < kNFeat / 32; ++b) gv[b] = static_cast<const float *>(L.g)[(size_t)row * kNFeat + 32 * b + lane];

@@ -46,8 +46,15 @@ struct PlainDev {
     float angle_k, angle_theta0;
     const uint32_t *tile_mask;  // [n_tile_pairs][32]: bit j of word i set = pair skipped
     const uint32_t *tile_flag;  // [n_tile_pairs]: 1 if any bit set in the tile
-    const int4 *items;          // [n_items] work items of the all-pairs sum (forcefield.cuh)
+    const int4 *items;          // [n_items] work items of the Newton-pair tile sum (forcefield.cuh)
     int n_items;
+    // row decomposition of the all-pairs sum (forcefield.cuh): groups of 16 i-atoms, chunks of 32 j-atoms
+    int n_groups, n_chunks;
+    const uint32_t *row_mask;   // [n_groups][n_chunks][16]: bit l of word a set = pair (16g+a, 32c+l) skipped
+    const int *grp_off;         // [n_groups + 1] bonded entries of each group (CSR)
+    const int2 *grp_ent;        // (term, (local atom << 2) | role): role 0, 1, 2 = the term's atom r.x, r.y, r.z;
+                                // sorted by local atom within a group
+    const int *grp_aoff;        // [n_groups][17]: entries of local atom a are [grp_aoff[a], grp_aoff[a+1]) of the group
     uint32_t *status;           // device status word
     const unsigned int *gate;   // if set, the kernels run only when *gate != 0 (learned-mode fallback)
 };
@@ -83,7 +90,6 @@ struct mdpf_ctx {
     int device = 0;
     int mode = MDPF_MODE_PLAIN;
     int n = 0, n_pad = 0, n_tiles = 0, n_bonds = 0, n_angles = 0;
-    int64_t n_tile_pairs = 0;
     double dt = 0.5, coulomb_k = mdpf::kCoulombDefault;
     int trace_cap = 4096;
     int record_every = 0, max_frames = 0, energy_every = 1;
@@ -104,10 +110,11 @@ struct mdpf_ctx {
     int4 *d_angles = nullptr;
     int32_t *d_excl_off = nullptr;
     int32_t *d_excl_idx = nullptr;
-    uint32_t *d_tile_mask = nullptr;
-    uint32_t *d_tile_flag = nullptr;
-    int4 *d_items = nullptr;
-    int n_items = 0;
+    uint32_t *d_row_mask = nullptr;        // [n_groups][n_chunks][16] skip masks of the row decomposition
+    int *d_grp_off = nullptr;              // [n_groups + 1] bonded entries per row group
+    int2 *d_grp_ent = nullptr;
+    int *d_grp_aoff = nullptr;             // [n_groups][17] per-atom entry ranges within a group
+    int n_groups = 0, n_chunks = 0;        // row groups (16 atoms) and j-chunks (32 atoms) holding real atoms
     float angle_k = 0, angle_theta0 = 0;
 
     // integrator state
@@ -130,9 +137,7 @@ struct mdpf_ctx {
     mdpf::Frames frames{};
 
     // persistent stepper
-    double *d_part = nullptr;              // [2][step_grid][4] per-block energies
-    double *d_tile_e = nullptr;            // [2][n_tiles][4] per-tile kinetic energies
-    int *d_own_off = nullptr, *d_own = nullptr;      // bonded terms owned by each tile
+    long long *d_part = nullptr;           // [2][step_grid][8] per-block energies (fixed point)
     int step_grid = 0;                     // blocks of the persistent stepper
 
     // Langevin (BAOAB) integrator: per-atom noise amplitude, damping factor, seed

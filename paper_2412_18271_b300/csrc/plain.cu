@@ -85,22 +85,38 @@ __global__ void k_bonded(PlainDev p, unsigned long long *fx, unsigned long long 
 
 constexpr int kNbThreads = 256;
 
+// One warp per (row group, slice) task of the row decomposition
+// (forcefield.cuh); the lanes add their fixed-point (atom, slice) sums.
 template <bool ENERGY>
-__global__ void __launch_bounds__(kNbThreads, 2) k_nonbonded(PlainDev p, unsigned long long *fx,
-                                                             unsigned long long *efx, uint32_t *status) {
+__global__ void __launch_bounds__(kNbThreads) k_nonbonded(PlainDev p, unsigned long long *fx,
+                                                          unsigned long long *efx, uint32_t *status) {
     if (p.gate != nullptr && *p.gate == 0u) return;
-    __shared__ JTile jt[kNbThreads / 32];
+    __shared__ RowStage st[kNbThreads / 32];
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    float elj = 0.f, ec = 0.f;
+    const int slices = p.n_chunks < kSlices ? p.n_chunks : kSlices;
+    const int tasks = p.n_groups * slices;
+    double elj = 0.0, ec = 0.0;   // per-task FP32 sums (the same in both steppers) added in FP64
     bool bad = false;
-    for (int it = warp; it < p.n_items; it += nwarps)
-        nonbonded_item<ENERGY>(p, it, lane, jt[threadIdx.x >> 5], fx, elj, ec, bad);
+    for (int task = warp; task < tasks; task += nwarps) {
+        const int g = task / slices, sl = task - g * slices;
+        RowQuad r;
+        float tl = 0.f, tc = 0.f;
+        row_task<ENERGY>(p, p.pos4, g, sl, lane, st[threadIdx.x >> 5], r, tl, tc, [] {});
+        elj += tl;
+        ec += tc;
+        bad |= !quad_finite(r);
+        const RowEmit e = row_emit(lane, r);
+        const int base = 3 * g * kRowGroup;
+        if (base + e.slot_a < 3 * p.n) atomicAdd(&fx[base + e.slot_a], (unsigned long long)e.va);
+        if (e.slot_b >= 0 && base + e.slot_b < 3 * p.n) atomicAdd(&fx[base + e.slot_b], (unsigned long long)e.vb);
+    }
     if (bad) atomicOr(status, MDPF_STATUS_NONFINITE);
     if (ENERGY) {
-        double e_lj = warp_sum_d((double)elj * (1.0 / 6.0));
-        double e_c = warp_sum_d((double)ec);
+        // every pair was met from both of its atoms
+        double e_lj = warp_sum_d(elj * (0.5 / 6.0));
+        double e_c = warp_sum_d(ec * 0.5);
         if (lane == 0) {
             fx_add_d(&efx[E_LJ], e_lj);
             fx_add_d(&efx[E_COUL], e_c);
@@ -441,10 +457,16 @@ PlainDev plain_dev(const mdpf_ctx *ctx, const float4 *pos4) {
     p.angles = ctx->d_angles;
     p.angle_k = ctx->angle_k;
     p.angle_theta0 = ctx->angle_theta0;
-    p.tile_mask = ctx->d_tile_mask;
-    p.tile_flag = ctx->d_tile_flag;
-    p.items = ctx->d_items;
-    p.n_items = ctx->n_items;
+    p.tile_mask = nullptr;
+    p.tile_flag = nullptr;
+    p.items = nullptr;
+    p.n_items = 0;
+    p.n_groups = ctx->n_groups;
+    p.n_chunks = ctx->n_chunks;
+    p.row_mask = ctx->d_row_mask;
+    p.grp_off = ctx->d_grp_off;
+    p.grp_ent = ctx->d_grp_ent;
+    p.grp_aoff = ctx->d_grp_aoff;
     p.status = ctx->d_status;
     p.gate = nullptr;
     return p;
@@ -466,8 +488,8 @@ void launch_bonded(const PlainDev &p, unsigned long long *fx, unsigned long long
 
 void launch_nonbonded(const PlainDev &p, unsigned long long *fx, unsigned long long *efx, bool energy,
                       cudaStream_t s) {
-    int blocks = (p.n_items * 32 + kNbThreads - 1) / kNbThreads;
-    if (blocks > 148 * 8) blocks = 148 * 8;
+    const int slices = p.n_chunks < kSlices ? p.n_chunks : kSlices;
+    int blocks = (p.n_groups * slices * 32 + kNbThreads - 1) / kNbThreads;
     if (blocks < 1) blocks = 1;
     if (energy)
         k_nonbonded<true><<<blocks, kNbThreads, 0, s>>>(p, fx, efx, p.status);

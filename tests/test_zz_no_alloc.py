@@ -18,6 +18,13 @@ pytestmark = pytest.mark.gpu
 
 F_RTOL = 1e-4          # the FP32 force tolerance of the other GPU tests (relative to RMS force)
 E_TOL_PER_ATOM = 1e-5  # kcal/mol/atom
+# The two paths add the FP32 pair energies in different groupings (Newton-pair tiles here, per-row tasks in the
+# context's kernels), so the difference also scales with the size of the sum: one FP32 ulp of the total on top.
+E_RTOL = 1e-7
+
+
+def _e_ok(e, e_ref, n):
+    return abs(e - e_ref) <= E_TOL_PER_ATOM * n + E_RTOL * abs(e_ref)
 
 
 def _unbonded(n_mol, per_mol, radius, seed):
@@ -61,7 +68,7 @@ def test_noalloc_matches_compute_on_two_calls_in_a_row():
         e, f = de.item(), df.cpu().numpy()
         rms = np.sqrt((f_ref.astype(np.float64) ** 2).mean())
         assert np.sqrt(((f - f_ref) ** 2).mean()) <= F_RTOL * rms, call
-        assert abs(e - e_ref) / n <= E_TOL_PER_ATOM, (call, e, e_ref)
+        assert _e_ok(e, e_ref, n), (call, e, e_ref)
 
 
 def test_noalloc_largest_size_and_rejects_larger():
@@ -81,7 +88,7 @@ def test_noalloc_largest_size_and_rejects_larger():
     f = df.cpu().numpy()
     rms = np.sqrt((f_ref.astype(np.float64) ** 2).mean())
     assert np.sqrt(((f - f_ref) ** 2).mean()) <= F_RTOL * rms
-    assert abs(de.item() - e_ref) / n <= E_TOL_PER_ATOM
+    assert _e_ok(de.item(), e_ref, n)
     with pytest.raises(mdpf.MdpfError) as ei:
         mdpf.pairs_noalloc(n + 1, dpos.data_ptr(), del_.data_ptr(), dq.data_ptr(), s.lj_sigma, s.lj_eps, 0.0,
                            de.data_ptr(), df.data_ptr(), 0)
