@@ -7,7 +7,8 @@
 //
 // Block b owns the row groups b, b + G, ... (16 atoms each, G blocks): it
 // computes every force on its atoms and integrates them itself, so an MD step
-// costs one grid barrier:
+// costs one grid barrier.  While SMs are left over, one more block owns no
+// group and sums the energies of each energy step after its barrier.
 //   forces       warp w evaluates slice w of the group's all-pairs row sum
 //                (forcefield.cuh, row decomposition) at x_{s+1} (FP32 copy
 //                P[s & 1]) and the group's bonded entries dealt to it (each
@@ -313,8 +314,9 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_plain_persistent(StepArgs a
             }
         }
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &s_fail)) return;
-        // ---- energies of step `done` (block 0, warp 0), read after the barrier
-        if (energy && blockIdx.x == 0 && w == 0) {
+        // ---- energies of step `done`, read after the barrier by the last block: a block with no group when
+        // the grid has one to spare, so the sum does not delay any group's next step
+        if (energy && blockIdx.x == G - 1 && w == 0) {
             const long long *pp = a.part + (size_t)(s & 1) * G * kPart;
             long long ib = 0, ia = 0, il = 0, ic = 0, ik = 0;
             for (int b = lane; b < G; b += 32) {
@@ -364,8 +366,10 @@ int stepper_grid(const mdpf_ctx *ctx) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_plain_persistent, kStepThreads, 0) != cudaSuccess)
         return 0;
     if (occ < 1) return 0;
-    const int want = ctx->n_groups > 0 ? ctx->n_groups : 1;
-    return want < sms ? want : sms;  // one block per SM: one barrier arrival per SM
+    // one block per group, one block per SM; with more than one group (a grid barrier anyway) one more block
+    // for the per-step energy sums while SMs are left
+    const int want = ctx->n_groups > 1 ? ctx->n_groups + 1 : 1;
+    return want < sms ? want : sms;
 }
 
 cudaError_t launch_plain_persistent(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t s) {
