@@ -109,8 +109,14 @@ typedef struct mdpf_topology {
  *   stepper       MDPF_STEPPER_PERSISTENT (0): mdpf_step runs as one resident
  *                 cooperative kernel with bounded grid barriers;
  *                 MDPF_STEPPER_KERNELS (1): one kernel sequence per step.
- *                 Both give the same trajectory bit for bit.  Learned mode
- *                 always runs the kernel sequence (the field is ignored).
+ *                 Both give the same trajectory bit for bit (plain mode).
+ *                 Learned mode with velocity Verlet: PERSISTENT runs
+ *                 molecules of up to 32 atoms as one resident cooperative
+ *                 kernel (8 blocks, each holding a slice of the network's
+ *                 weights; the same model and rounding points as the
+ *                 tensor-core path, not the same bits), larger systems as
+ *                 one CUDA graph of the stage kernels per step; KERNELS
+ *                 always uses the stage kernels.
  *   energy_every  evaluate U and K every this many steps (0 selects 1); the
  *                 trace holds one entry per such step; record_every must be a
  *                 multiple of it.  Forces are evaluated every step regardless.

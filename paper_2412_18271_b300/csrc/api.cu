@@ -89,6 +89,7 @@ void prof_end(mdpf_ctx *c, int slot, cudaEvent_t a, cudaStream_t s) {
 
 static void free_ctx(mdpf_ctx *c) {
     if (!c) return;
+    small_free(c);
     learned_free(c);
     for (auto &r : c->prof_pending) {
         cudaEventDestroy(r.a);
@@ -311,6 +312,10 @@ int mdpf_create(const mdpf_topology *t, const mdpf_params *prm, mdpf_ctx **out) 
     if (c->mode == MDPF_MODE_LEARNED) {
         rc = learned_create(c, t, prm);
         if (rc != MDPF_OK) return bail(rc);
+        // molecules of up to 32 atoms step in one persistent launch when the device allows it; otherwise the
+        // per-step graph of the stage kernels stays in use
+        if (prm->integrator == MDPF_INTEGRATOR_VERLET && prm->stepper == MDPF_STEPPER_PERSISTENT)
+            small_create(c, t->element);
     }
     if (c->stepper == MDPF_STEPPER_PERSISTENT) {
         c->step_grid = stepper_grid(c);
@@ -539,6 +544,14 @@ static cudaGraphExec_t learned_step_graph(mdpf_ctx *c, bool energy) {
 
 static int enqueue_steps(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     if (n_steps == 0) return MDPF_OK;
+    if (c->small != nullptr) {
+        cudaEvent_t ps = prof_begin(c, s);
+        CK(c, launch_learned_small(c, n_steps, s));
+        prof_end(c, MDPF_PROF_STEPPER, ps, s);
+        c->steps += n_steps;
+        c->force_evals += n_steps;
+        return MDPF_OK;
+    }
     if (c->stepper == MDPF_STEPPER_PERSISTENT) {
         cudaEvent_t ps = prof_begin(c, s);
         CK(c, launch_plain_persistent(c, n_steps, s));

@@ -72,6 +72,10 @@ struct FusedTiles {
     int n;
 };
 
+// the context's learned-path data and whether out-of-range steps fall back (learned_host.cu)
+const LearnedDev &learned_dev(const mdpf_ctx *c);
+int learned_fallback_on(const mdpf_ctx *c);
+
 // launchers (learned.cu)
 // neighbour list (cooperative launch; learned_nb_grid() gives its grid size, 0 if unavailable)
 int learned_nb_grid();

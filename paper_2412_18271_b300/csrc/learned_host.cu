@@ -96,6 +96,9 @@ static void enqueue_mlp(LearnedHost *h, uint32_t *status, bool gated, unsigned l
 
 static LearnedHost *lh(const mdpf_ctx *c) { return static_cast<LearnedHost *>(c->learned); }
 
+const LearnedDev &learned_dev(const mdpf_ctx *c) { return lh(c)->dev; }
+int learned_fallback_on(const mdpf_ctx *c) { return lh(c)->fallback; }
+
 template <typename T>
 static cudaError_t lalloc(LearnedHost *h, T **p, size_t count) {
     cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));

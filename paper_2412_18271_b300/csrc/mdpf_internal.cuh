@@ -153,6 +153,7 @@ struct mdpf_ctx {
 
     // learned mode (learned_host.cu)
     void *learned = nullptr;               // mdpf::LearnedHost
+    void *small = nullptr;                 // mdpf::SmallBuf: the persistent small-molecule stepper (small.cu), or null
     cudaGraphExec_t lgraph[2] = {nullptr, nullptr};   // learned step as a graph: [0] plain step, [1] energy step
     bool lgraph_failed = false;
 
@@ -218,6 +219,11 @@ DispCheck learned_disp_check(const mdpf_ctx *ctx);
 int learned_counter_values(mdpf_ctx *ctx, int64_t *rebuilds, int64_t *fallbacks, double *max_disp);
 // device counter of evaluations that fell back to the plain force field (learned mode), else null
 const long long *learned_fallback_counter(const mdpf_ctx *ctx);
+
+// small.cu: the persistent learned stepper for molecules of up to 32 atoms
+int small_create(mdpf_ctx *ctx, const int32_t *element);   // MDPF_OK, or MDPF_ERR_UNSUPPORTED (not used then)
+void small_free(mdpf_ctx *ctx);
+cudaError_t launch_learned_small(mdpf_ctx *ctx, int64_t n_steps, cudaStream_t s);
 
 // stepper.cu
 int stepper_grid(const mdpf_ctx *ctx);
