@@ -725,25 +725,32 @@ def provider_leg(args, dev, stream):
                                "what": "persistent stepper on a 2-atom molecule: the step loop's own latency "
                                        "(grid barriers, integration, energy steps) with no pair work"}
     out["persistent_over_floor"] = out["persistent"]["us_per_md_step"] / out["empty_loop_floor"]["us_per_md_step"]
-    # an ethanol-sized molecule (9 atoms) on the learned path: the per-step latency floor of the
-    # graph-launched learned step
+    # an ethanol-sized molecule (9 atoms) on the learned path: the persistent small-molecule stepper (the
+    # default for up to 32 atoms) and, beside it, the per-step CUDA graph of the stage kernels
     blob, _, _ = learned_model(ranges=False)
     t9 = synth.molecule(9, seed=9)
-    ctx = mdpf.Context(t9, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, energy_every=10,
-                       trace_capacity=1000)
-    ctx.set_state(t9.pos, synth.velocities(t9.mass, t9.pos, 300.0, seed=9))
-    with torch.cuda.stream(stream):
-        ctx.step_async(100, stream.cuda_stream)
-        stream.synchronize()
-        e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0_.record(stream)
-        ctx.step_async(1000, stream.cuda_stream)
-        e1_.record(stream)
-        stream.synchronize()
-    ms = e0_.elapsed_time(e1_)
-    out["learned_9_atoms"] = {"value": 1000 / (ms / 1000.0), "unit": UNIT, "us_per_md_step": ms,
-                              "what": "9-atom seeded molecule, learned potential, one graph launch per MD step"}
-    ctx.close()
+    for key, stepper, what in (
+            ("learned_9_atoms", mdpf.MDPF_STEPPER_PERSISTENT,
+             "9-atom seeded molecule, learned potential, persistent small-molecule stepper (one launch, 8 blocks "
+             "with the weights resident in shared memory)"),
+            ("learned_9_atoms_graph", mdpf.MDPF_STEPPER_KERNELS,
+             "the same molecule, one CUDA graph of the stage kernels per MD step")):
+        ctx = mdpf.Context(t9, mode=mdpf.MDPF_MODE_LEARNED, model=blob, dt_fs=DT_FS, energy_every=10,
+                           trace_capacity=1000, stepper=stepper)
+        ctx.set_state(t9.pos, synth.velocities(t9.mass, t9.pos, 300.0, seed=9))
+        with torch.cuda.stream(stream):
+            ctx.step_async(100, stream.cuda_stream)
+            stream.synchronize()
+            e0_, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0_.record(stream)
+            ctx.step_async(1000, stream.cuda_stream)
+            e1_.record(stream)
+            stream.synchronize()
+        ms = e0_.elapsed_time(e1_)
+        if ctx.counters()["status"] != 0:
+            raise RuntimeError("device status in the 9-atom learned run")
+        out[key] = {"value": 1000 / (ms / 1000.0), "unit": UNIT, "us_per_md_step": ms, "what": what}
+        ctx.close()
     out["workload"] = "64-atom molecule, plain force field (the provider wraps the library's own force field)"
     return out
 
