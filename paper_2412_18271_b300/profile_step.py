@@ -3,6 +3,10 @@
 
     python -m paper_2412_18271_b300.profile_step cluster16384 --mode learned --steps 8
     python -m paper_2412_18271_b300.profile_step cluster2048 --mode plain --steps 20
+    python -m paper_2412_18271_b300.profile_step molecule9 --steps 20
+
+A workload is a named one of synth.workload, or moleculeN: one seeded N-atom
+molecule (seed 9 for N = 9, else N), as the bench's small-molecule legs use.
 
 Learned mode runs the shipped trained model without its feature ranges (every
 step runs the model: no step is diverted to the plain force field), so each
@@ -31,6 +35,7 @@ def main(argv=None) -> int:
     ap.add_argument("workload", nargs="?", default="cluster16384")
     ap.add_argument("--mode", choices=["learned", "plain"], default="learned")
     ap.add_argument("--mlp", choices=sorted(MLP_KERNELS), default="tensor")
+    ap.add_argument("--stepper", choices=["persistent", "kernels"], default="persistent")
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--setup-steps", type=int, default=2)
     ap.add_argument("--dt-fs", type=float, default=0.5)
@@ -39,8 +44,13 @@ def main(argv=None) -> int:
 
     import torch
     build.build()
+    stepper = mdpf.MDPF_STEPPER_PERSISTENT if a.stepper == "persistent" else mdpf.MDPF_STEPPER_KERNELS
     torch.cuda.set_device(0)
-    s = synth.workload(a.workload)
+    if a.workload.startswith("molecule"):
+        na = int(a.workload[len("molecule"):])
+        s = synth.molecule(na, seed=9 if na == 9 else na)
+    else:
+        s = synth.workload(a.workload)
     seed = a.seed if a.seed is not None else synth.WORKLOAD_VELOCITY_SEED.get(a.workload, 0)
     v0 = synth.velocities(s.mass, s.pos, 300.0, seed=seed)
     if a.mode == "learned":
@@ -48,9 +58,9 @@ def main(argv=None) -> int:
             m = model.Model.unpack(fh.read())
         m.lo = m.hi = None
         ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_LEARNED, model=m.pack(), dt_fs=a.dt_fs,
-                           mlp_kernel=MLP_KERNELS[a.mlp])
+                           mlp_kernel=MLP_KERNELS[a.mlp], stepper=stepper)
     else:
-        ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_PLAIN, dt_fs=a.dt_fs)
+        ctx = mdpf.Context(s, mode=mdpf.MDPF_MODE_PLAIN, dt_fs=a.dt_fs, stepper=stepper)
     ctx.set_state(s.pos, v0)
     if a.setup_steps > 0:
         ctx.step(a.setup_steps)
