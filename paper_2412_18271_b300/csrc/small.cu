@@ -14,15 +14,17 @@
 //              list orders them), the features of learned_terms.cuh, the
 //              range check; the FP32 rows to the exchange buffer.    barrier 0
 //   layer 1    every block: all rows as BF16; z1 = W1 G + b1 for its 32 units
-//              (warp MMA m16n8k16, FP32 accumulation), a1 = CELU(z1) to the
-//              exchange buffer, CELU'(z1) kept.                       barrier 1
+//              (warp MMA m16n8k16, K = 384, FP32 accumulation), a1 =
+//              CELU(z1) to the exchange buffer, CELU'(z1) kept.       barrier 1
 //   layer 2    every block: a1 (all 256 units) as the BF16 pair hi + lo;
 //              z2 = W2 a1 + b2 for its 16 units, the energy terms
 //              w3 CELU(z2), delta2 = w3 CELU'(z2) (BF16); the partial
-//              W2^T delta2 of its 16 units for all 256 hidden units.  barrier 2
+//              W2^T delta2 of its 16 units for all 256 hidden units
+//              (CUDA cores: K = 16, one thread per hidden unit, so the
+//              partial rows leave in coalesced stores).              barrier 2
 //   layer 1'   every block: delta1 = CELU'(z1) (sum of the partials) for its
 //              32 units (BF16); the partial dE/dG = W1^T delta1 of its units
-//              for all 384 features.                                  barrier 3
+//              for all 384 features (warp MMA, K = 32).               barrier 3
 //   adjoint    block b, one warp per atom: dE/dG (sum of the partials in block
 //              order), the chain rule of learned_terms.cuh into fixed-point
 //              forces (and the repulsive core).                      barrier 4
@@ -299,10 +301,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
         }
         if (!plain) {
             // ---- layer 1: z1 = W1 G + b1 for the block's 32 units
-            for (int q = t; q < n * (kNFeat / 2); q += kSThreads) {
-                const int at = q / (kNFeat / 2), c = 2 * (q % (kNFeat / 2));
-                *reinterpret_cast<uint32_t *>(&S.u.g[at][c]) =
-                    pack_bf16(__ldcg(&a.xG[at * kNFeat + c]), __ldcg(&a.xG[at * kNFeat + c + 1]));
+            for (int q = t; q < n * (kNFeat / 4); q += kSThreads) {
+                const int at = q / (kNFeat / 4), c = 4 * (q % (kNFeat / 4));
+                const float4 gv = __ldcg(reinterpret_cast<const float4 *>(&a.xG[at * kNFeat + c]));
+                *reinterpret_cast<uint2 *>(&S.u.g[at][c]) = make_uint2(pack_bf16(gv.x, gv.y), pack_bf16(gv.z, gv.w));
             }
             __syncthreads();
             int e, nt, mt;
@@ -333,12 +335,16 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
             }
             if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B1
             // ---- layer 2: z2 = W2 (hi + lo) + b2 for the block's 16 units; energy terms and delta2
-            for (int q = t; q < n * kH1; q += kSThreads) {
-                const int at = q / kH1, c = q % kH1;
-                const float av = __ldcg(&a.xA1[q]);
-                const __nv_bfloat16 hi = __float2bfloat16_rn(av);
-                S.u.a1.hi[at][c] = hi;
-                S.u.a1.lo[at][c] = __float2bfloat16_rn(av - __bfloat162float(hi));
+            for (int q = t; q < n * (kH1 / 4); q += kSThreads) {
+                const int at = q / (kH1 / 4), c = 4 * (q % (kH1 / 4));
+                const float4 av = __ldcg(reinterpret_cast<const float4 *>(&a.xA1[at * kH1 + c]));
+                const float v4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v4[k]);
+                    S.u.a1.hi[at][c + k] = hi;
+                    S.u.a1.lo[at][c + k] = __float2bfloat16_rn(v4[k] - __bfloat162float(hi));
+                }
             }
             __syncthreads();
             for (int id = w; task_of(S, id, 1, e, nt, mt); id += 8) {
@@ -374,29 +380,36 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 for (int v = 0; v < kU2; ++v) E += S.ev[t][v];
                 a.xE[b * kSmallMax + t] = E;
             }
-            // partial W2^T delta2 over the block's 16 units, for all 256 hidden units
-            for (int id = w; task_of(S, id, kH1 / 16, e, nt, mt); id += 8) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                uint32_t A[4], B[2];
-                frag_at(&S.w2[e][0][0], kW2Stride, 16 * mt, 0, lane, A);
-                frag_b(&S.d2[slot_atom(S, e, 8 * nt + (lane & 7))][0], 0, lane, B);
-                mma16816(acc, A, B);
+            // partial W2^T delta2 over the block's 16 units, for all 256 hidden units (thread u, units in order)
+            for (int at = 0; at < n; ++at) {
+                const int z = S.el[at];
+                float p1 = 0.f;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int u = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
-                    if (idx < S.el_cnt[e]) a.xP1[((size_t)b * kSmallMax + S.el_list[e][idx]) * kH1 + u] = acc[h];
-                }
+                for (int vl = 0; vl < kU2; ++vl)
+                    p1 = fmaf(__bfloat162float(S.w2[z][vl][t]), __bfloat162float(S.d2[at][vl]), p1);
+                a.xP1[((size_t)b * kSmallMax + at) * kH1 + t] = p1;
             }
             if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B2
             // ---- layer 1': delta1 = CELU'(z1) sum_b P1_b for the block's units; partial dE/dG = W1^T delta1
-            for (int q = t; q < n * kU1; q += kSThreads) {
-                const int at = q / kU1, ul = q % kU1;
-                float p1 = 0.f;
+            for (int q = t; q < n * (kU1 / 4); q += kSThreads) {
+                const int at = q / (kU1 / 4), u4 = 4 * (q % (kU1 / 4));
+                float4 p1 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int bb = 0; bb < kSB; ++bb) p1 += __ldcg(&a.xP1[((size_t)bb * kSmallMax + at) * kH1 + kU1 * b + ul]);
-                S.d1[at][ul] = __float2bfloat16_rn(p1 * S.dc1[at][ul]);
+                for (int bb = 0; bb < kSB; ++bb) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(
+                        &a.xP1[((size_t)bb * kSmallMax + at) * kH1 + kU1 * b + u4]));
+                    p1.x += v.x;
+                    p1.y += v.y;
+                    p1.z += v.z;
+                    p1.w += v.w;
+                }
+                S.d1[at][u4 + 0] = __float2bfloat16_rn(p1.x * S.dc1[at][u4 + 0]);
+                S.d1[at][u4 + 1] = __float2bfloat16_rn(p1.y * S.dc1[at][u4 + 1]);
+                S.d1[at][u4 + 2] = __float2bfloat16_rn(p1.z * S.dc1[at][u4 + 2]);
+                S.d1[at][u4 + 3] = __float2bfloat16_rn(p1.w * S.dc1[at][u4 + 3]);
             }
             __syncthreads();
+            // partial dE/dG = W1^T delta1 over the block's 32 units for all 384 features (warp MMA, K = 32)
             for (int id = w; task_of(S, id, kNFeat / 16, e, nt, mt); id += 8) {
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 const __nv_bfloat16 *brow = &S.d1[slot_atom(S, e, 8 * nt + (lane & 7))][0];
@@ -419,12 +432,22 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 const int at = b + kSB * w;
                 if (w < 4 && at < n) {
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) {
-                        const int fi = 32 * k + lane;
-                        float gs = 0.f;
+                    for (int k = 0; k < 3; ++k) {
+                        const int f4 = 128 * k + 4 * lane;
+                        float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                        for (int bb = 0; bb < kSB; ++bb) gs += __ldcg(&a.xPG[((size_t)bb * kSmallMax + at) * kNFeat + fi]);
-                        S.u.adj.sg[w][g_col(fi)] = __bfloat162float(__float2bfloat16_rn(gs));
+                        for (int bb = 0; bb < kSB; ++bb) {
+                            const float4 v = __ldcg(reinterpret_cast<const float4 *>(
+                                &a.xPG[((size_t)bb * kSmallMax + at) * kNFeat + f4]));
+                            gs.x += v.x;
+                            gs.y += v.y;
+                            gs.z += v.z;
+                            gs.w += v.w;
+                        }
+                        S.u.adj.sg[w][g_col(f4 + 0)] = __bfloat162float(__float2bfloat16_rn(gs.x));
+                        S.u.adj.sg[w][g_col(f4 + 1)] = __bfloat162float(__float2bfloat16_rn(gs.y));
+                        S.u.adj.sg[w][g_col(f4 + 2)] = __bfloat162float(__float2bfloat16_rn(gs.z));
+                        S.u.adj.sg[w][g_col(f4 + 3)] = __bfloat162float(__float2bfloat16_rn(gs.w));
                     }
                     NbrFetch f;
                     small_fetch(S, n, at, lane, f);
