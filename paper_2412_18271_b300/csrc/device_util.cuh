@@ -73,6 +73,12 @@ __device__ __forceinline__ void fx_warp_add_d(unsigned long long *p, double v) {
     if ((threadIdx.x & 31) == 0 && q != 0) atomicAdd(p, (unsigned long long)q);
 }
 
+// Butterfly sum over a warp: every lane ends with the same value (IEEE addition commutes), in a fixed order.
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

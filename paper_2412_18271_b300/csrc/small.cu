@@ -6,28 +6,31 @@
 // One cooperative launch of kSB blocks runs all n steps.  Each block keeps a
 // slice of the network's weights in shared memory for the whole launch, so no
 // weight is read from memory inside the step loop:
-//   block b: W1 rows (hidden units) 32 b .. 32 b + 31 and W2 rows 16 b .. 16 b + 15
-//   of every element, BF16, as the tensor-core kernels use them.
+//   block b: W1 rows (hidden units) 32 b .. 32 b + 31 and the W2 columns of the
+//   same units (all 128 rows), of every element, BF16, as the tensor-core
+//   kernels use them.
+// So a block's layer-1 activations are exactly the inputs of its W2 columns:
+// layer 2 leaves the block as partial sums of z2, and layer 2' (W2^T delta2
+// for the block's own units) needs no exchange.
 // An MD step (positions x_{s+1} identical in every block):
 //   features   block b, one warp per atom a = b + 8 w: the neighbours by brute
 //              force over the molecule (ascending index, as the neighbour
 //              list orders them), the features of learned_terms.cuh, the
 //              range check; the FP32 rows to the exchange buffer.    barrier 0
 //   layer 1    every block: all rows as BF16; z1 = W1 G + b1 for its 32 units
-//              (warp MMA m16n8k16, K = 384, FP32 accumulation), a1 =
-//              CELU(z1) to the exchange buffer, CELU'(z1) kept.       barrier 1
-//   layer 2    every block: a1 (all 256 units) as the BF16 pair hi + lo;
-//              z2 = W2 a1 + b2 for its 16 units, the energy terms
-//              w3 CELU(z2), delta2 = w3 CELU'(z2) (BF16); the partial
-//              W2^T delta2 of its 16 units for all 256 hidden units
-//              (CUDA cores: K = 16, one thread per hidden unit, so the
-//              partial rows leave in coalesced stores).              barrier 2
-//   layer 1'   every block: delta1 = CELU'(z1) (sum of the partials) for its
-//              32 units (BF16); the partial dE/dG = W1^T delta1 of its units
-//              for all 384 features (warp MMA, K = 32).               barrier 3
+//              (warp MMA m16n8k16, K = 384, FP32 accumulation); a1 =
+//              CELU(z1) kept as the BF16 pair hi + lo, CELU'(z1) kept;
+//              the partial W2 a1 over its 32 units for all 128 units of
+//              layer 2 (warp MMA, K = 32, hi and lo products apart).  barrier 1
+//   layer 2    every block: z2 = b2 + the partials summed in block order for
+//              all 128 units; delta2 = w3 CELU'(z2) (BF16); block 0 keeps
+//              the energy terms w3 CELU(z2).  Layer 2': delta1 = CELU'(z1)
+//              W2^T delta2 for its 32 units (warp MMA, K = 128; BF16).
+//              Layer 1': the partial dE/dG = W1^T delta1 over its units for
+//              all 384 features (warp MMA, K = 32).                  barrier 2
 //   adjoint    block b, one warp per atom: dE/dG (sum of the partials in block
 //              order), the chain rule of learned_terms.cuh into fixed-point
-//              forces (and the repulsive core).                      barrier 4
+//              forces (and the repulsive core).                      barrier 3
 //   integration every block, the same FP64 arithmetic on the same sums (so
 //              every block holds the same state): v += dt/2 a; (energy and
 //              frames by block 0); v += dt/2 a; x += dt v.
@@ -38,7 +41,7 @@
 //
 // Numerics follow the tensor-core MLP's rounding points: BF16 features, the
 // BF16 pair hi + lo of a1, BF16 delta2 and delta1, BF16 weights, FP32
-// accumulation.  Every sum is taken in a fixed order, so runs repeat bit for
+// accumulation (z2's sum over units taken per block, then over blocks).  Every sum is taken in a fixed order, so runs repeat bit for
 // bit.  Every wait is a bounded grid barrier (1 s, MDPF_STATUS_TIMEOUT).
 #include "forcefield.cuh"
 #include "grid_sync.cuh"
@@ -52,11 +55,9 @@ constexpr int kSB = 8;                 // blocks
 constexpr int kSThreads = 256;         // threads per block (8 warps)
 constexpr int kSmallMax = 32;          // atoms
 constexpr int kU1 = kH1 / kSB;         // 32 hidden units of layer 1 per block
-constexpr int kU2 = kH2 / kSB;         // 16 hidden units of layer 2 per block
 constexpr int kW1Stride = kNFeat + 8;  // BF16 row strides padded by 16 bytes (conflict-free ldmatrix rows)
-constexpr int kW2Stride = kH1 + 8;
-constexpr int kD1Stride = kU1 + 8;
-constexpr int kD2Stride = kU2 + 8;
+constexpr int kU1Stride = kU1 + 8;     // rows over the block's 32 units (W2 columns, a1, delta1)
+constexpr int kD2Stride = kH2 + 8;
 constexpr int kAdjChunkS = 128;
 
 struct SmallArgs {
@@ -70,10 +71,8 @@ struct SmallArgs {
     unsigned long long *fxs;           // state forces F(x) (fixed point) on entry and on exit
     // exchange buffers (global)
     float *xG;                         // [32][384] features
-    float *xA1;                        // [32][256] CELU(z1)
-    float *xP1;                        // [kSB][32][256] partial W2^T delta2
+    float *xZ2;                        // [kSB][32][128] partial W2 a1
     float *xPG;                        // [kSB][32][384] partial dE/dG
-    float *xE;                         // [kSB][32] partial w3 . CELU(z2)
     unsigned long long *fac;           // [2][32][3] forces of a step (fixed point), by step parity
     unsigned long long *eacc;          // [2][4] energies of a step (fixed point): core, bond, angle, LJ + Coulomb
     unsigned int *flag;                // [2] range flag of a step
@@ -96,8 +95,8 @@ struct SmallArgs {
 // Shared memory of a block.  The phases use disjoint parts of one union.
 struct SmallSmem {
     __nv_bfloat16 w1[4][kU1][kW1Stride];     // W1 rows of the block's units
-    __nv_bfloat16 w2[4][kU2][kW2Stride];     // W2 rows of the block's units
-    float b1[4][kU1], b2[4][kU2], w3[4][kU2];
+    __nv_bfloat16 w2[4][kH2][kU1Stride];     // W2 columns of the block's units (all 128 rows)
+    float b1[4][kU1], b2[4][kH2], w3[4][kH2];
     union {
         struct {
             NbrSmem nb[4];
@@ -105,26 +104,26 @@ struct SmallSmem {
         } feat;
         __nv_bfloat16 g[kSmallMax][kW1Stride];                 // features, BF16
         struct {
-            __nv_bfloat16 hi[kSmallMax][kW2Stride], lo[kSmallMax][kW2Stride];   // CELU(z1) as hi + lo
-        } a1;
-        struct {
             NbrSmem nb[4];
             AdjScratch<kAdjChunkS> as[4];
             float sg[4][kGRow];
         } adj;
     } u;
+    __nv_bfloat16 a1hi[kSmallMax][kU1Stride], a1lo[kSmallMax][kU1Stride];   // CELU(z1) of the block's units, hi + lo
     float dc1[kSmallMax][kU1];               // CELU'(z1) of the block's units
-    float ev[kSmallMax][kU2];                // w3 CELU(z2) of the block's units
-    __nv_bfloat16 d2[kSmallMax][kD2Stride];  // delta2 of the block's units
-    __nv_bfloat16 d1[kSmallMax][kD1Stride];  // delta1 of the block's units
+    __nv_bfloat16 d2[kSmallMax][kD2Stride];  // delta2, all 128 units
+    __nv_bfloat16 d1[kSmallMax][kU1Stride];  // delta1 of the block's units
+    float eat[kSmallMax];                    // block 0: w3 . CELU(z2) per atom
     double x[kSmallMax][3], vel[kSmallMax][3], h[kSmallMax], km[kSmallMax];
     float4 pos[kSmallMax];
     int el[kSmallMax];
     int el_list[4][kSmallMax], el_cnt[4];
     double red[8];
-    unsigned int pending;                    // status bits found after barrier 4, raised after the next barrier 0
+    unsigned int pending;                    // status bits found after barrier 3, raised after the next barrier 0
     int s_fail;
 };
+
+static_assert(sizeof(SmallSmem) <= 227 * 1024, "a block's shared memory");
 
 // ---- warp-level MMA (m16n8k16, BF16 in, FP32 accumulate) from shared memory
 __device__ __forceinline__ void ldsm_x4(const void *p, uint32_t (&r)[4]) {
@@ -219,15 +218,15 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
         *reinterpret_cast<uint4 *>(&S.w1[e][u][8 * c]) =
             *reinterpret_cast<const uint4 *>(L.W1 + ((size_t)e * kH1 + kU1 * b + u) * kNFeat + 8 * c);
     }
-    for (int q = t; q < 4 * kU2 * (kH1 / 8); q += kSThreads) {
-        const int e = q / (kU2 * (kH1 / 8)), r = q % (kU2 * (kH1 / 8)), u = r / (kH1 / 8), c = r % (kH1 / 8);
-        *reinterpret_cast<uint4 *>(&S.w2[e][u][8 * c]) =
-            *reinterpret_cast<const uint4 *>(L.W2 + ((size_t)e * kH2 + kU2 * b + u) * kH1 + 8 * c);
+    for (int q = t; q < 4 * kH2 * (kU1 / 8); q += kSThreads) {
+        const int e = q / (kH2 * (kU1 / 8)), r = q % (kH2 * (kU1 / 8)), v = r / (kU1 / 8), c = r % (kU1 / 8);
+        *reinterpret_cast<uint4 *>(&S.w2[e][v][8 * c]) =
+            *reinterpret_cast<const uint4 *>(L.W2 + ((size_t)e * kH2 + v) * kH1 + kU1 * b + 8 * c);
     }
     for (int q = t; q < 4 * kU1; q += kSThreads) S.b1[q / kU1][q % kU1] = L.b1[(q / kU1) * kH1 + kU1 * b + q % kU1];
-    for (int q = t; q < 4 * kU2; q += kSThreads) {
-        S.b2[q / kU2][q % kU2] = L.b2[(q / kU2) * kH2 + kU2 * b + q % kU2];
-        S.w3[q / kU2][q % kU2] = L.W3[(q / kU2) * kH2 + kU2 * b + q % kU2];
+    for (int q = t; q < 4 * kH2; q += kSThreads) {
+        S.b2[q / kH2][q % kH2] = L.b2[q];
+        S.w3[q / kH2][q % kH2] = L.W3[q];
     }
     for (int q = t; q < 4 * kSmallMax; q += kSThreads) S.el_list[q / kSmallMax][q % kSmallMax] = a.el_list[q];
     if (t < 4) S.el_cnt[t] = a.el_cnt[t];
@@ -287,7 +286,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
         if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B0
         const bool out = *(volatile unsigned int *)&a.flag[par] != 0u;
         const bool plain = out && a.fallback;
-        // Status bits are raised only before barrier 4 (here, or by the feature warps), so every block reads
+        // Status bits are raised only before barrier 3 (here, or by the feature warps), so every block reads
         // the same status after it and all stop together.
         if (t == 0 && S.pending != 0u) {
             atomicOr(a.status, S.pending);
@@ -328,88 +327,81 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                         const int at = S.el_list[e][idx];
                         const float z = acc[h] + S.b1[e][ul];
                         const float av = celu_e(z, exp10x_neg(z));
-                        a.xA1[at * kH1 + kU1 * b + ul] = av;
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(av);
+                        S.a1hi[at][ul] = hi;
+                        S.a1lo[at][ul] = __float2bfloat16_rn(av - __bfloat162float(hi));
                         S.dc1[at][ul] = dcelu_from_a(av);
                     }
                 }
             }
-            if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B1
-            // ---- layer 2: z2 = W2 (hi + lo) + b2 for the block's 16 units; energy terms and delta2
-            for (int q = t; q < n * (kH1 / 4); q += kSThreads) {
-                const int at = q / (kH1 / 4), c = 4 * (q % (kH1 / 4));
-                const float4 av = __ldcg(reinterpret_cast<const float4 *>(&a.xA1[at * kH1 + c]));
-                const float v4[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v4[k]);
-                    S.u.a1.hi[at][c + k] = hi;
-                    S.u.a1.lo[at][c + k] = __float2bfloat16_rn(v4[k] - __bfloat162float(hi));
-                }
-            }
             __syncthreads();
-            for (int id = w; task_of(S, id, 1, e, nt, mt); id += 8) {
+            // partial z2 = W2 (hi + lo) over the block's 32 units, for all 128 units of layer 2
+            for (int id = w; task_of(S, id, kH2 / 16, e, nt, mt); id += 8) {
                 float acc2[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // hi and lo products apart
                 const int ra = slot_atom(S, e, 8 * nt + (lane & 7));
-#pragma unroll 4
-                for (int kk = 0; kk < kH1 / 16; ++kk) {
+#pragma unroll
+                for (int kk = 0; kk < kU1 / 16; ++kk) {
                     uint32_t A[4], B[2];
-                    frag_a(&S.w2[e][0][0], kW2Stride, 0, 16 * kk, lane, A);
-                    frag_b(&S.u.a1.hi[ra][0], 16 * kk, lane, B);
+                    frag_a(&S.w2[e][0][0], kU1Stride, 16 * mt, 16 * kk, lane, A);
+                    frag_b(&S.a1hi[ra][0], 16 * kk, lane, B);
                     mma16816(acc2[0], A, B);
-                    frag_b(&S.u.a1.lo[ra][0], 16 * kk, lane, B);
+                    frag_b(&S.a1lo[ra][0], 16 * kk, lane, B);
                     mma16816(acc2[1], A, B);
                 }
-                float acc[4];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) acc[h] = acc2[0][h] + acc2[1][h];
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const int vl = g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
+                    const int v = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
+                    if (idx < S.el_cnt[e])
+                        a.xZ2[((size_t)b * kSmallMax + S.el_list[e][idx]) * kH2 + v] = acc2[0][h] + acc2[1][h];
+                }
+            }
+            if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B1
+            // ---- layer 2: z2 = b2 + the partials in block order, all 128 units (warp: one atom, lane: 4 units)
+            for (int q = t; q < n * (kH2 / 4); q += kSThreads) {
+                const int at = q / (kH2 / 4), v4 = 4 * (q % (kH2 / 4)), z = S.el[at];
+                float4 zs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int bb = 0; bb < kSB; ++bb) {
+                    const float4 pv = __ldcg(reinterpret_cast<const float4 *>(&a.xZ2[((size_t)bb * kSmallMax + at) * kH2 + v4]));
+                    zs.x += pv.x;
+                    zs.y += pv.y;
+                    zs.z += pv.z;
+                    zs.w += pv.w;
+                }
+                const float zv[4] = {zs.x, zs.y, zs.z, zs.w};
+                float ev = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float z2 = S.b2[z][v4 + k] + zv[k], ex = exp10x_neg(z2);
+                    ev += S.w3[z][v4 + k] * celu_e(z2, ex);
+                    S.d2[at][v4 + k] = __float2bfloat16_rn(S.w3[z][v4 + k] * dcelu_e(z2, ex));
+                }
+                ev = warp_sum_f(ev);   // the 32 lanes of this atom, a fixed butterfly
+                if (b == 0 && lane == 0) S.eat[at] = ev;
+            }
+            __syncthreads();
+            // ---- layer 2': delta1 = CELU'(z1) W2^T delta2 for the block's 32 units (K = 128, BF16)
+            for (int id = w; task_of(S, id, kU1 / 16, e, nt, mt); id += 8) {
+                float acc2[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // two K halves in flight
+                const __nv_bfloat16 *brow = &S.d2[slot_atom(S, e, 8 * nt + (lane & 7))][0];
+#pragma unroll
+                for (int kk = 0; kk < kH2 / 16; ++kk) {
+                    uint32_t A[4], B[2];
+                    frag_at(&S.w2[e][0][0], kU1Stride, 16 * mt, 16 * kk, lane, A);
+                    frag_b(brow, 16 * kk, lane, B);
+                    mma16816(acc2[kk & 1], A, B);
+                }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int ul = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
                     if (idx < S.el_cnt[e]) {
                         const int at = S.el_list[e][idx];
-                        const float z = acc[h] + S.b2[e][vl], ex = exp10x_neg(z);
-                        S.ev[at][vl] = S.w3[e][vl] * celu_e(z, ex);
-                        S.d2[at][vl] = __float2bfloat16_rn(S.w3[e][vl] * dcelu_e(z, ex));
+                        S.d1[at][ul] = __float2bfloat16_rn((acc2[0][h] + acc2[1][h]) * S.dc1[at][ul]);
                     }
                 }
             }
             __syncthreads();
-            if (t < n) {   // the block's energy terms of atom t, in unit order
-                float E = 0.f;
-#pragma unroll
-                for (int v = 0; v < kU2; ++v) E += S.ev[t][v];
-                a.xE[b * kSmallMax + t] = E;
-            }
-            // partial W2^T delta2 over the block's 16 units, for all 256 hidden units (thread u, units in order)
-            for (int at = 0; at < n; ++at) {
-                const int z = S.el[at];
-                float p1 = 0.f;
-#pragma unroll
-                for (int vl = 0; vl < kU2; ++vl)
-                    p1 = fmaf(__bfloat162float(S.w2[z][vl][t]), __bfloat162float(S.d2[at][vl]), p1);
-                a.xP1[((size_t)b * kSmallMax + at) * kH1 + t] = p1;
-            }
-            if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B2
-            // ---- layer 1': delta1 = CELU'(z1) sum_b P1_b for the block's units; partial dE/dG = W1^T delta1
-            for (int q = t; q < n * (kU1 / 4); q += kSThreads) {
-                const int at = q / (kU1 / 4), u4 = 4 * (q % (kU1 / 4));
-                float4 p1 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int bb = 0; bb < kSB; ++bb) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(
-                        &a.xP1[((size_t)bb * kSmallMax + at) * kH1 + kU1 * b + u4]));
-                    p1.x += v.x;
-                    p1.y += v.y;
-                    p1.z += v.z;
-                    p1.w += v.w;
-                }
-                S.d1[at][u4 + 0] = __float2bfloat16_rn(p1.x * S.dc1[at][u4 + 0]);
-                S.d1[at][u4 + 1] = __float2bfloat16_rn(p1.y * S.dc1[at][u4 + 1]);
-                S.d1[at][u4 + 2] = __float2bfloat16_rn(p1.z * S.dc1[at][u4 + 2]);
-                S.d1[at][u4 + 3] = __float2bfloat16_rn(p1.w * S.dc1[at][u4 + 3]);
-            }
-            __syncthreads();
-            // partial dE/dG = W1^T delta1 over the block's 32 units for all 384 features (warp MMA, K = 32)
+            // ---- layer 1': partial dE/dG = W1^T delta1 over the block's 32 units for all 384 features (warp MMA, K = 32)
             for (int id = w; task_of(S, id, kNFeat / 16, e, nt, mt); id += 8) {
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
                 const __nv_bfloat16 *brow = &S.d1[slot_atom(S, e, 8 * nt + (lane & 7))][0];
@@ -426,7 +418,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                     if (idx < S.el_cnt[e]) a.xPG[((size_t)b * kSmallMax + S.el_list[e][idx]) * kNFeat + f] = acc[h];
                 }
             }
-            if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B3
+            if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B2
             // ---- adjoint of atoms b + 8 w: dE/dG summed in block order, rounded to BF16 as on the per-stage path
             {
                 const int at = b + kSB * w;
@@ -512,7 +504,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 if (i3) atomicAdd(&eacc[3], (unsigned long long)i3);
             }
         }
-        if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B4
+        if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B3
         // every block reads the status after the same barrier, so all stop together
         const bool stop = energy && *(volatile uint32_t *)a.status != 0u;
         // ---- integration (every block, the same arithmetic on the same integers)
@@ -549,11 +541,8 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
             const double ks = warp_sum_d(kin);   // 3 n <= 96 slots: warps 0..2
             double eu = 0.0;                     // learned: atom t's energy (its terms summed in block order)
             if (!plain && t < n) {
-                float E = 0.f;
-#pragma unroll
-                for (int bb = 0; bb < kSB; ++bb) E += __ldcg(&a.xE[bb * kSmallMax + t]);
                 const int z = S.el[t];
-                eu = (double)E + (double)L.b3[z] + L.e0[z];
+                eu = (double)S.eat[t] + (double)L.b3[z] + L.e0[z];
             }
             eu = warp_sum_d(eu);   // n <= 32: warp 0
             if (lane == 0 && w < 4) S.red[w] = ks;
@@ -597,14 +586,14 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
 namespace mdpf {
 
 struct SmallBuf {
-    float *xG = nullptr, *xA1 = nullptr, *xP1 = nullptr, *xPG = nullptr, *xE = nullptr;
+    float *xG = nullptr, *xZ2 = nullptr, *xPG = nullptr;
     unsigned long long *fac = nullptr, *eacc = nullptr;
     unsigned int *flag = nullptr;
     int *el_list = nullptr, *el_cnt = nullptr;
 };
 
 static void small_release(SmallBuf *b) {
-    void *ptrs[] = {b->xG, b->xA1, b->xP1, b->xPG, b->xE, b->fac, b->eacc, b->flag, b->el_list, b->el_cnt};
+    void *ptrs[] = {b->xG, b->xZ2, b->xPG, b->fac, b->eacc, b->flag, b->el_list, b->el_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -638,10 +627,8 @@ int small_create(mdpf_ctx *c, const int32_t *element) {
         el_list[e * kSmallMax + el_cnt[e]++] = i;
     }
     bool ok = cudaMalloc(&b->xG, sizeof(float) * kSmallMax * kNFeat) == cudaSuccess &&
-              cudaMalloc(&b->xA1, sizeof(float) * kSmallMax * kH1) == cudaSuccess &&
-              cudaMalloc(&b->xP1, sizeof(float) * kSB * kSmallMax * kH1) == cudaSuccess &&
+              cudaMalloc(&b->xZ2, sizeof(float) * kSB * kSmallMax * kH2) == cudaSuccess &&
               cudaMalloc(&b->xPG, sizeof(float) * kSB * kSmallMax * kNFeat) == cudaSuccess &&
-              cudaMalloc(&b->xE, sizeof(float) * kSB * kSmallMax) == cudaSuccess &&
               cudaMalloc(&b->fac, sizeof(unsigned long long) * 2 * 3 * kSmallMax) == cudaSuccess &&
               cudaMalloc(&b->eacc, sizeof(unsigned long long) * 2 * 4) == cudaSuccess &&
               cudaMalloc(&b->flag, sizeof(unsigned int) * 2) == cudaSuccess &&
@@ -678,10 +665,8 @@ cudaError_t launch_learned_small(mdpf_ctx *c, int64_t n_steps, cudaStream_t s) {
     a.v = c->d_v;
     a.fxs = c->d_fx;
     a.xG = buf->xG;
-    a.xA1 = buf->xA1;
-    a.xP1 = buf->xP1;
+    a.xZ2 = buf->xZ2;
     a.xPG = buf->xPG;
-    a.xE = buf->xE;
     a.fac = buf->fac;
     a.eacc = buf->eacc;
     a.flag = buf->flag;
