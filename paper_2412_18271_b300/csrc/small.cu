@@ -111,7 +111,10 @@ struct SmallSmem {
     } u;
     __nv_bfloat16 a1hi[kSmallMax][kU1Stride], a1lo[kSmallMax][kU1Stride];   // CELU(z1) of the block's units, hi + lo
     float dc1[kSmallMax][kU1];               // CELU'(z1) of the block's units
-    __nv_bfloat16 d2[kSmallMax][kD2Stride];  // delta2, all 128 units
+    union {
+        __nv_bfloat16 d2[kSmallMax][kD2Stride];   // delta2, all 128 units
+        float zp[2][kSmallMax][kU1];               // layer 1: z1 over each half of K
+    };
     __nv_bfloat16 d1[kSmallMax][kU1Stride];  // delta1 of the block's units
     float eat[kSmallMax];                    // block 0: w3 . CELU(z2) per atom
     double x[kSmallMax][3], vel[kSmallMax][3], h[kSmallMax], km[kSmallMax];
@@ -185,6 +188,23 @@ __device__ __forceinline__ void small_fetch(const SmallSmem &S, int n, int at, i
 // their output columns are discarded).
 __device__ __forceinline__ int slot_atom(const SmallSmem &S, int e, int idx) {
     return idx < S.el_cnt[e] ? S.el_list[e][idx] : S.el_list[e][0];
+}
+
+// The two output columns of an MMA fragment lane (atom slots 8 nt + 2 t4 and the next): their atoms and
+// whether they are real.  Read once, before any store, so that the stores of an epilogue (through pointers
+// the compiler cannot tell from shared memory) do not force these shared reads to repeat after each.
+struct EpiRows {
+    int at[2];
+    bool ok[2];
+};
+__device__ __forceinline__ EpiRows epi_rows(const SmallSmem &S, int e, int nt, int t4) {
+    const int i0 = 8 * nt + 2 * t4, c = S.el_cnt[e];
+    EpiRows r;
+    r.at[0] = S.el_list[e][i0];       // i0 + 1 <= 31: within the element's list (unused slots hold 0)
+    r.at[1] = S.el_list[e][i0 + 1];
+    r.ok[0] = i0 < c;
+    r.ok[1] = i0 + 1 < c;
+    return r;
 }
 
 // Tasks (element e, n-tile of 8 atoms, m-tile) of one GEMM phase, enumerated in a fixed order: element,
@@ -271,12 +291,15 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 feature_row(S.u.feat.nb[w], nr, na, S.u.feat.ts[w], lane, v);
                 const int z = S.el[at];
                 bool out = false;
+                if (L.lo != nullptr) {   // every range load issued before the first store
 #pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    const int fi = 32 * k + lane;
-                    if (L.lo != nullptr) out |= (v[k] < L.lo[z * kNFeat + fi]) || (v[k] > L.hi[z * kNFeat + fi]);
-                    a.xG[at * kNFeat + fi] = v[k];
+                    for (int k = 0; k < 12; ++k) {
+                        const int fi = 32 * k + lane;
+                        out |= (v[k] < L.lo[z * kNFeat + fi]) || (v[k] > L.hi[z * kNFeat + fi]);
+                    }
                 }
+#pragma unroll
+                for (int k = 0; k < 12; ++k) a.xG[at * kNFeat + 32 * k + lane] = v[k];
                 if (__any_sync(0xffffffffu, out) && lane == 0) {
                     atomicOr(&a.flag[par], 1u);
                     if (!a.fallback) atomicOr(a.status, MDPF_STATUS_OUT_OF_RANGE);
@@ -306,53 +329,71 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 *reinterpret_cast<uint2 *>(&S.u.g[at][c]) = make_uint2(pack_bf16(gv.x, gv.y), pack_bf16(gv.z, gv.w));
             }
             __syncthreads();
+            // a task: (element, n-tile, half of K), both m-tiles of the block's 32 units, four chains in flight
             int e, nt, mt;
             for (int id = w; task_of(S, id, 2, e, nt, mt); id += 8) {
-                float acc2[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // two K halves in flight
+                float acc[2][2][4] = {};   // [m-tile][k parity]
                 const __nv_bfloat16 *brow = &S.u.g[slot_atom(S, e, 8 * nt + (lane & 7))][0];
-#pragma unroll 4
-                for (int kk = 0; kk < kNFeat / 16; ++kk) {
-                    uint32_t A[4], B[2];
-                    frag_a(&S.w1[e][0][0], kW1Stride, 16 * mt, 16 * kk, lane, A);
-                    frag_b(brow, 16 * kk, lane, B);
-                    mma16816(acc2[kk & 1], A, B);
-                }
-                float acc[4];
+                const int k0 = mt * (kNFeat / 32);   // mt is the K half here
+#pragma unroll 2
+                for (int k2 = 0; k2 < kNFeat / 32; k2 += 2) {
 #pragma unroll
-                for (int h = 0; h < 4; ++h) acc[h] = acc2[0][h] + acc2[1][h];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int ul = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
-                    if (idx < S.el_cnt[e]) {
-                        const int at = S.el_list[e][idx];
-                        const float z = acc[h] + S.b1[e][ul];
-                        const float av = celu_e(z, exp10x_neg(z));
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(av);
-                        S.a1hi[at][ul] = hi;
-                        S.a1lo[at][ul] = __float2bfloat16_rn(av - __bfloat162float(hi));
-                        S.dc1[at][ul] = dcelu_from_a(av);
+                    for (int par = 0; par < 2; ++par) {
+                        const int kk = k0 + k2 + par;
+                        uint32_t A0[4], A1[4], B[2];
+                        frag_b(brow, 16 * kk, lane, B);
+                        frag_a(&S.w1[e][0][0], kW1Stride, 0, 16 * kk, lane, A0);
+                        frag_a(&S.w1[e][0][0], kW1Stride, 16, 16 * kk, lane, A1);
+                        mma16816(acc[0][par], A0, B);
+                        mma16816(acc[1][par], A1, B);
                     }
+                }
+                const EpiRows er = epi_rows(S, e, nt, t4);
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const int m = h >> 2, hh = h & 3;
+                    const int ul = 16 * m + g4 + 8 * (hh >> 1);
+                    if (er.ok[hh & 1]) S.zp[mt][er.at[hh & 1]][ul] = acc[m][0][hh] + acc[m][1][hh];
                 }
             }
             __syncthreads();
-            // partial z2 = W2 (hi + lo) over the block's 32 units, for all 128 units of layer 2
-            for (int id = w; task_of(S, id, kH2 / 16, e, nt, mt); id += 8) {
-                float acc2[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};   // hi and lo products apart
+            for (int q = t; q < n * kU1; q += kSThreads) {
+                const int at = q / kU1, ul = q % kU1;
+                const float z = (S.zp[0][at][ul] + S.zp[1][at][ul]) + S.b1[S.el[at]][ul];
+                const float av = celu_e(z, exp10x_neg(z));
+                const __nv_bfloat16 hi = __float2bfloat16_rn(av);
+                S.a1hi[at][ul] = hi;
+                S.a1lo[at][ul] = __float2bfloat16_rn(av - __bfloat162float(hi));
+                S.dc1[at][ul] = dcelu_from_a(av);
+            }
+            __syncthreads();
+            // partial z2 = W2 (hi + lo) over the block's 32 units, for all 128 units of layer 2; a task is
+            // (element, n-tile, group of 4 m-tiles), its B fragments shared
+            for (int id = w; task_of(S, id, kH2 / 64, e, nt, mt); id += 8) {
                 const int ra = slot_atom(S, e, 8 * nt + (lane & 7));
+                uint32_t Bh[2][2], Bl[2][2];
 #pragma unroll
                 for (int kk = 0; kk < kU1 / 16; ++kk) {
-                    uint32_t A[4], B[2];
-                    frag_a(&S.w2[e][0][0], kU1Stride, 16 * mt, 16 * kk, lane, A);
-                    frag_b(&S.a1hi[ra][0], 16 * kk, lane, B);
-                    mma16816(acc2[0], A, B);
-                    frag_b(&S.a1lo[ra][0], 16 * kk, lane, B);
-                    mma16816(acc2[1], A, B);
+                    frag_b(&S.a1hi[ra][0], 16 * kk, lane, Bh[kk]);
+                    frag_b(&S.a1lo[ra][0], 16 * kk, lane, Bl[kk]);
                 }
+                float acc[4][2][4] = {};   // [m-tile][hi, lo]: the hi and lo products apart
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int v = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
-                    if (idx < S.el_cnt[e])
-                        a.xZ2[((size_t)b * kSmallMax + S.el_list[e][idx]) * kH2 + v] = acc2[0][h] + acc2[1][h];
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int kk = 0; kk < kU1 / 16; ++kk) {
+                        uint32_t A[4];
+                        frag_a(&S.w2[e][0][0], kU1Stride, 16 * (4 * mt + j), 16 * kk, lane, A);
+                        mma16816(acc[j][0], A, Bh[kk]);
+                        mma16816(acc[j][1], A, Bl[kk]);
+                    }
+                const EpiRows er = epi_rows(S, e, nt, t4);
+                float *zr[2] = {a.xZ2 + ((size_t)b * kSmallMax + er.at[0]) * kH2, a.xZ2 + ((size_t)b * kSmallMax + er.at[1]) * kH2};
+#pragma unroll
+                for (int h = 0; h < 16; ++h) {
+                    const int j = h >> 2, hh = h & 3;
+                    const int v = 16 * (4 * mt + j) + g4 + 8 * (hh >> 1);
+                    if (er.ok[hh & 1]) zr[hh & 1][v] = acc[j][0][hh] + acc[j][1][hh];
                 }
             }
             if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B1
@@ -391,31 +432,38 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                     frag_b(brow, 16 * kk, lane, B);
                     mma16816(acc2[kk & 1], A, B);
                 }
+                const EpiRows er = epi_rows(S, e, nt, t4);
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const int ul = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
-                    if (idx < S.el_cnt[e]) {
-                        const int at = S.el_list[e][idx];
-                        S.d1[at][ul] = __float2bfloat16_rn((acc2[0][h] + acc2[1][h]) * S.dc1[at][ul]);
-                    }
+                    const int ul = 16 * mt + g4 + 8 * (h >> 1), at = er.at[h & 1];
+                    if (er.ok[h & 1]) S.d1[at][ul] = __float2bfloat16_rn((acc2[0][h] + acc2[1][h]) * S.dc1[at][ul]);
                 }
             }
             __syncthreads();
-            // ---- layer 1': partial dE/dG = W1^T delta1 over the block's 32 units for all 384 features (warp MMA, K = 32)
-            for (int id = w; task_of(S, id, kNFeat / 16, e, nt, mt); id += 8) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            // ---- layer 1': partial dE/dG = W1^T delta1 over the block's 32 units for all 384 features (warp MMA,
+            // K = 32); a task is (element, n-tile, group of 6 m-tiles), its B fragments shared
+            for (int id = w; task_of(S, id, kNFeat / 96, e, nt, mt); id += 8) {
                 const __nv_bfloat16 *brow = &S.d1[slot_atom(S, e, 8 * nt + (lane & 7))][0];
+                uint32_t B[2][2];
 #pragma unroll
-                for (int kk = 0; kk < kU1 / 16; ++kk) {
-                    uint32_t A[4], B[2];
-                    frag_at(&S.w1[e][0][0], kW1Stride, 16 * mt, 16 * kk, lane, A);
-                    frag_b(brow, 16 * kk, lane, B);
-                    mma16816(acc, A, B);
-                }
+                for (int kk = 0; kk < kU1 / 16; ++kk) frag_b(brow, 16 * kk, lane, B[kk]);
+                float acc[6][4] = {};
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int f = 16 * mt + g4 + 8 * (h >> 1), idx = 8 * nt + 2 * t4 + (h & 1);
-                    if (idx < S.el_cnt[e]) a.xPG[((size_t)b * kSmallMax + S.el_list[e][idx]) * kNFeat + f] = acc[h];
+                for (int j = 0; j < 6; ++j)
+#pragma unroll
+                    for (int kk = 0; kk < kU1 / 16; ++kk) {
+                        uint32_t A[4];
+                        frag_at(&S.w1[e][0][0], kW1Stride, 16 * (6 * mt + j), 16 * kk, lane, A);
+                        mma16816(acc[j], A, B[kk]);
+                    }
+                const EpiRows er = epi_rows(S, e, nt, t4);
+                float *gr[2] = {a.xPG + ((size_t)b * kSmallMax + er.at[0]) * kNFeat,
+                                a.xPG + ((size_t)b * kSmallMax + er.at[1]) * kNFeat};
+#pragma unroll
+                for (int h = 0; h < 24; ++h) {
+                    const int j = h >> 2, hh = h & 3;
+                    const int f = 16 * (6 * mt + j) + g4 + 8 * (hh >> 1);
+                    if (er.ok[hh & 1]) gr[hh & 1][f] = acc[j][hh];
                 }
             }
             if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B2
