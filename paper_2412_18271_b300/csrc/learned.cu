@@ -285,11 +285,19 @@ __global__ void __launch_bounds__(32 * kFeatWarps) k_features(LearnedDev L, cons
     feature_row(sn[w], nr, na, st[w], lane, v);
     const int row = L.row_of[i];
     const int z = L.el[i];
+    // every range load before the first store: a load that follows a store through a pointer that may alias
+    // it is issued only after that store, so interleaving them costs an L2 round trip per column block
     bool out = false;
+    if (L.lo != nullptr) {
+#pragma unroll
+        for (int b = 0; b < 12; ++b) {
+            const int f = 32 * b + lane;
+            out |= (v[b] < L.lo[z * kNFeat + f]) || (v[b] > L.hi[z * kNFeat + f]);
+        }
+    }
 #pragma unroll
     for (int b = 0; b < 12; ++b) {
         const int f = 32 * b + lane;
-        if (L.lo != nullptr) out |= (v[b] < L.lo[z * kNFeat + f]) || (v[b] > L.hi[z * kNFeat + f]);
         L.G16[(size_t)row * kNFeat + f] = __float2bfloat16_rn(v[b]);
         if (write_f32) L.G32[(size_t)row * kNFeat + f] = v[b];
     }
@@ -548,7 +556,14 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_jvp(LearnedDev L, const flo
     }
     __syncwarp();
     float *out = U + (size_t)L.row_of[i] * kNFeat;
-    for (int f = lane; f < kNFeat; f += 32) out[f] = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
+    float ov[kNFeat / 32];   // every shared read before the first (possibly aliasing) store
+#pragma unroll
+    for (int k = 0; k < kNFeat / 32; ++k) {
+        const int f = 32 * k + lane;
+        ov[k] = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
+    }
+#pragma unroll
+    for (int k = 0; k < kNFeat / 32; ++k) out[32 * k + lane] = ov[k];
 }
 
 __global__ void k_learn_begin(LearnedDev L) {
