@@ -43,7 +43,7 @@ constexpr int kFuWarps = 16;
 constexpr int kFuThreads = 32 * kFuWarps + 64;
 constexpr int kFuProducer = kFuWarps, kFuMma = kFuWarps + 1;
 constexpr int kFuStage = 48 * 1024;
-constexpr int kFuRes = 99 * 1024;
+constexpr int kFuRes = 106 * 1024;   // 64 g rows of the adjoint layout (the GEMM operands need 96 KB)
 constexpr int kFuChunk = 32;    // triplets staged per adjoint pass (no effect on the result)
 using FuAdj = AdjScratch<kFuChunk>;
 constexpr int kFuWarpScr = ((int)sizeof(NbrSmem) + (sizeof(FuAdj) > sizeof(TripStage) ? (int)sizeof(FuAdj)

@@ -1,5 +1,8 @@
 // Grid-wide barrier of the persistent (cooperative) kernels: a 64-bit
-// arrival counter with a release add and an acquire poll, every wait bounded.
+// arrival counter with an acq_rel add and an acquire poll, every wait bounded.
+// The add returns the count before it, so the last block to arrive knows the
+// barrier is complete (its acq_rel add has synchronised with every earlier
+// release) and does not poll.
 #pragma once
 
 #include "mdpf_internal.cuh"
@@ -12,9 +15,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long *p, unsigned long long v) {
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p, unsigned long long v) {
     unsigned long long old;
-    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
 
@@ -33,10 +36,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned l
         int fail = 0;
         if (gridDim.x > 1) {
             const unsigned long long target = epoch * gridDim.x;
-            atom_add_release(bar, 1ull);
+            const unsigned long long old = atom_add_acq_rel(bar, 1ull);
             const unsigned long long t0 = globaltimer();
             unsigned int spins = 0;
-            while (ld_acquire(bar) < target) {
+            while (old + 1 < target && ld_acquire(bar) < target) {
                 if ((++spins & 31u) == 0u && (long long)(globaltimer() - t0) > limit_ns) {
                     atomicOr(status, MDPF_STATUS_TIMEOUT);
                     fail = 1;

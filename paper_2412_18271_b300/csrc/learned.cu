@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const
     if (gated && L.lflags[1]) return;
     __shared__ NbrSmem sn[kAtomWarps];
     __shared__ AdjScratch<kAdjChunk> sa[kAtomWarps];
-    __shared__ float sg[kAtomWarps][kGRow];
+    __shared__ __align__(16) float sg[kAtomWarps][kGRow];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kAtomWarps + w;
     if (i >= L.n) return;

@@ -363,9 +363,11 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
 
 // ------------------------------------------------------------------ adjoint
 
-// Angular blocks of a g row are stored kAngStride floats apart, so that lanes
-// working on different element pairs read different banks.
-constexpr int kAngStride = 33;
+// Angular blocks of a g row are stored kAngStride floats apart: a multiple of
+// four, so that every 8-float run of a block is two 16-byte loads, and 4 mod
+// 32 banks apart, so that lanes working on different element pairs mostly
+// read different banks.  Rows are 16-byte aligned.
+constexpr int kAngStride = 36;
 constexpr int kGRow = 64 + 10 * kAngStride;   // floats of one g row in that layout
 
 // Per-warp scratch of the adjoint: Chunk triplets are staged per pass (a
@@ -410,13 +412,19 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
         const float4 d = s.d[q];
         const float r = d.w;
         const float fc = s.fc[q].x, dfc = s.fc[q].y;
-        const float *gz = g + 16 * s.el[q];
+        const float4 *gz = reinterpret_cast<const float4 *>(g + 16 * s.el[q]);
         float dEdr = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            const float x = r - (0.9f + (float)k * (4.3f / 16.f));
-            const float ex = exp_neg(-kEtaR * x * x);
-            dEdr = fmaf(gz[k], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+            const float4 g4 = gz[k4];
+            const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k = 4 * k4 + kk;
+                const float x = r - (0.9f + (float)k * (4.3f / 16.f));
+                const float ex = exp_neg(-kEtaR * x * x);
+                dEdr = fmaf(gk[kk], ex * (-2.f * kEtaR * x * fc + dfc), dEdr);
+            }
         }
         if (r < core.y) {
             float ec, dc;
@@ -458,16 +466,18 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
             const float dfj = s.fc[qa].w, dfk = s.fc[qb].w;
             const float C = fj * fk;
             const float ravg = 0.5f * (rj + rk);
-            const float *gp = g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]);
-            // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta)
+            const float4 *gp = reinterpret_cast<const float4 *>(g + 64 + kAngStride * pair_index(s.el[qa], s.el[qb]));
+            // angular factors A_p = 2^-31 (1 + cos(theta - theta_p))^32 and their derivatives in cos(theta),
+            // 2^-31 * 32 (1 + cos(theta - theta_p))^31 (cos theta_p - cot sin theta_p), both without their
+            // power-of-two factors, which scale the three sums below exactly and are applied to them at the end
             float Ap[8], dAp[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
                 const float base = 1.f + cs * cpv[p] + sn2 * spv[p];
                 const float b2 = base * base, b4 = b2 * b2, b8 = b4 * b4, b16 = b8 * b8;
                 const float b31 = b16 * b8 * b4 * b2 * base;
-                Ap[p] = kTwoPowM31 * b31 * base;
-                dAp[p] = kTwoPowM31 * 32.f * b31 * (cpv[p] - cot * spv[p]);
+                Ap[p] = b31 * base;
+                dAp[p] = b31 * (cpv[p] - cot * spv[p]);
             }
             float Sc = 0.f, Sr = 0.f, SC = 0.f;
 #pragma unroll
@@ -475,17 +485,21 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
                 const float x = ravg - (0.9f + (float)m * 0.65f);
                 const float B = exp_neg(-kEtaA * x * x);
                 const float dB = -2.f * kEtaA * x * B;
+                const float4 ga = gp[2 * m], gb = gp[2 * m + 1];
+                const float gv[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
                 float sa_ = 0.f, sdA = 0.f;
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
-                    const float gv = gp[8 * m + p];
-                    sa_ = fmaf(gv, Ap[p], sa_);
-                    sdA = fmaf(gv, dAp[p], sdA);
+                    sa_ = fmaf(gv[p], Ap[p], sa_);
+                    sdA = fmaf(gv[p], dAp[p], sdA);
                 }
                 Sc = fmaf(sdA, B * C, Sc);
                 Sr = fmaf(sa_, dB * C, Sr);
                 SC = fmaf(sa_, B, SC);
             }
+            Sc *= kTwoPowM31 * 32.f;
+            Sr *= kTwoPowM31;
+            SC *= kTwoPowM31;
             const float dEdrj = 0.5f * Sr + SC * dfj * fk, dEdrk = 0.5f * Sr + SC * fj * dfk;
             const float gc = Sc * kAngScale;
             const float gjx = gc * (ukx - ct * ujx) * irj + dEdrj * ujx;

@@ -106,7 +106,7 @@ struct SmallSmem {
         struct {
             NbrSmem nb[4];
             AdjScratch<kAdjChunkS> as[4];
-            float sg[4][kGRow];
+            alignas(16) float sg[4][kGRow];
         } adj;
     } u;
     __nv_bfloat16 a1hi[kSmallMax][kU1Stride], a1lo[kSmallMax][kU1Stride];   // CELU(z1) of the block's units, hi + lo
