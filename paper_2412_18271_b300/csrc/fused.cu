@@ -13,7 +13,7 @@
 //            mlp_tc.cu, GEMM1's A operand now resident; layer 1's CELU output
 //            enters GEMM2 as a BF16 pair hi + lo): energy per atom into E_row
 //            and the energy slot, dE/dG into TMEM columns 0..383
-//   phase C  per half tile: the 64 rows of dE/dG from TMEM into shared memory
+//   phase C  per quarter tile: the 32 rows of dE/dG from TMEM into shared memory
 //            (FP32, the adjoint's padded row layout), then the compute warps
 //            take those atoms one at a time: neighbours again, chain rule to
 //            fixed-point forces (learned_terms.cuh)
@@ -21,8 +21,8 @@
 // same bit for bit as features + k_mlp_tc + k_adjoint.
 //
 // Shared memory (dynamic, 1024-byte aligned):
-//   [0, 99 KB)          G operand (6 x 16 KB) -> a1 / d2 / d1 -> half-tile g (64 x 394 FP32)
-//   [99 KB, +120 KB)    per-warp scratch (phases A and C) or the weight ring (2 x 48 KB, phase B)
+//   [0, 96 KB)          G operand (6 x 16 KB) -> a1 / d2 / d1 -> quarter-tile g (32 x 424 FP32)
+//   [96 KB, +118 KB)    per-warp scratch (phases A and C) or the weight ring (2 x 48 KB, phase B)
 //   then b1, b2, W3, energy partials (4 KB), barriers and flags
 // Warps 0-15: compute and epilogue (warp w reads TMEM lanes 32 (w mod 4) ..
 // +31 and column group w / 4); warp 16: TMA producer; warp 17: TMEM
@@ -43,7 +43,7 @@ constexpr int kFuWarps = 16;
 constexpr int kFuThreads = 32 * kFuWarps + 64;
 constexpr int kFuProducer = kFuWarps, kFuMma = kFuWarps + 1;
 constexpr int kFuStage = 48 * 1024;
-constexpr int kFuRes = 106 * 1024;   // 64 g rows of the adjoint layout (the GEMM operands need 96 KB)
+constexpr int kFuRes = 96 * 1024;
 constexpr int kFuChunk = 32;    // triplets staged per adjoint pass (no effect on the result)
 using FuAdj = AdjScratch<kFuChunk>;
 constexpr int kFuWarpScr = ((int)sizeof(NbrSmem) + (sizeof(FuAdj) > sizeof(TripStage) ? (int)sizeof(FuAdj)
@@ -54,7 +54,7 @@ constexpr int kFuOffScr = kFuRes;
 constexpr int kFuOffPar = kFuOffScr + kFuScr;
 constexpr int kFuOffBar = kFuOffPar + 4096;
 constexpr int kFuSmem = kFuOffBar + 128 + 1024;
-static_assert(6 * 16384 <= kFuRes && 64 * kGRow * 4 <= kFuRes, "resident region");
+static_assert(6 * 16384 <= kFuRes && 32 * kGRow * 4 <= kFuRes, "resident region");
 static_assert(kFuSmem <= 232448, "shared memory");
 static_assert(sizeof(NbrSmem) % 16 == 0, "scratch alignment");
 
@@ -85,7 +85,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
     volatile int *s_abort = (volatile int *)(sm + kFuOffBar + 68);
     volatile int *s_issued = (volatile int *)(sm + kFuOffBar + 72);
     volatile int *s_consumed = (volatile int *)(sm + kFuOffBar + 76);
-    int *s_next = (int *)(sm + kFuOffBar + 80);   // atom counters: phase A, phase C halves 0 and 1
+    int *s_next = (int *)(sm + kFuOffBar + 80);   // atom counters: phase A, phase C quarters 0-3
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x;
@@ -102,7 +102,7 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
         *s_abort = 0;
         *s_issued = 0;
         *s_consumed = 0;
-        s_next[0] = s_next[1] = s_next[2] = 0;
+        s_next[0] = s_next[1] = s_next[2] = s_next[3] = s_next[4] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kFuMma) {
@@ -320,10 +320,10 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
         FuAdj &A = *reinterpret_cast<FuAdj *>(scr + sizeof(NbrSmem));
         float *gst = reinterpret_cast<float *>(res);
 #pragma unroll 1
-        for (int hh = 0; hh < 2; ++hh) {
-            if (64 * hh >= cnt) break;   // the same in every warp
-            if (ok && (q4 >> 1) == hh) {
-                float *dst = gst + (32 * (q4 & 1) + lane) * kGRow;
+        for (int hh = 0; hh < 4; ++hh) {
+            if (32 * hh >= cnt) break;   // the same in every warp
+            if (ok && q4 == hh) {
+                float *dst = gst + lane * kGRow;
 #pragma unroll 1
                 for (int cc = 3 * cg; cc < 3 * cg + 3; ++cc) {
                     tmem_ld32(tl + cc * 32, v);
@@ -338,15 +338,15 @@ k_fused(LearnedDev L, FusedTiles T, const __grid_constant__ MlpMaps maps, const 
                 int k = 0;
                 if (lane == 0) k = atomicAdd(&s_next[1 + hh], 1);
                 k = __shfl_sync(0xffffffffu, k, 0);
-                const int rr = 64 * hh + k;
-                if (k >= 64 || rr >= cnt || *s_abort) break;
+                const int rr = 32 * hh + k;
+                if (k >= 32 || rr >= cnt || *s_abort) break;
                 const int i = L.atom_of[row0 + rr];
                 int nc, nr, na;
                 load_neighbours<false>(L, pos4, i, sn, lane, nc, nr, na);
                 adjoint_atom(i, sn, nc, nr, na, gst + k * kGRow, A, fx, lane, make_float2(L.core_a, L.core_rc),
                              efx != nullptr ? efx + E_LEARN : nullptr);
             }
-            fu_sync();   // the half's g rows are no longer read
+            fu_sync();   // the quarter's g rows are no longer read
         }
         tc_fence_before();
     }

@@ -58,12 +58,14 @@ struct NbrSmem {
     int nae[4];                   // angular neighbours of each element (features)
 };
 
-// Cosine cutoff and its derivative at both cutoffs from one sincospi each:
+// Cosine cutoff and its derivative at both cutoffs from one approximate
+// sine/cosine pair each (the single-instruction forms, absolute error ~1e-6
+// on [0, pi], the range used; larger arguments give values that are dropped):
 // fc(r; rc) = (1 + cos(pi r / rc)) / 2, fc' = -pi / (2 rc) sin(pi r / rc), zero from rc on.
 __device__ __forceinline__ float4 cutoffs(float r) {
     float sr, cr, sa, ca;
-    sincospif(r * (1.f / kRcRad), &sr, &cr);
-    sincospif(r * (1.f / kRcAng), &sa, &ca);
+    __sincosf(r * (kPi / kRcRad), &sr, &cr);
+    __sincosf(r * (kPi / kRcAng), &sa, &ca);
     const bool inr = r < kRcRad, ina = r < kRcAng;
     return make_float4(inr ? 0.5f * cr + 0.5f : 0.f, inr ? (-0.5f * kPi / kRcRad) * sr : 0.f,
                        ina ? 0.5f * ca + 0.5f : 0.f, ina ? (-0.5f * kPi / kRcAng) * sa : 0.f);
@@ -200,14 +202,15 @@ __device__ __forceinline__ int triplet_index(int a, int b, int na) { return a * 
 
 // ------------------------------------------------------------------ features
 
-// Per-warp staging of one batch of 32 triplet slots, and the atom's pair-type
-// table (1,232 bytes).
+// Per-warp staging of one batch of 32 triplet slots, the atom's pair-type
+// table and its angular sums (2,512 bytes).
 struct TripStage {
     float4 q[32];    // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k), pair type
     float4 b[32];    // radial-shell factors of the 4 shells
     int4 type[10];   // per pair type: first slot, triplets, first angular index of e1 | of e2 << 8 | count of
                      // e2 << 16, e1 == e2
     float rcp[12];   // 1 / (count of e2)
+    float acc[10][32];   // angular block of each pair type: column 8 m + p of the block in lane 8 m + p
 };
 
 // Features of one atom whose neighbours are in s.  On return lane l holds
@@ -222,9 +225,11 @@ struct TripStage {
 //     slot's geometry; then lane 8 t4 + p takes slot t4 of every group of 4
 //     (all of one type), computes its angular factor for section p once and
 //     adds it, times the 4 shell factors, to its 4 column sums (m = 0..3).
-//     When the type changes the 4 slots are combined in a fixed shuffle order
-//     and lane 8 m + p adds sum m to its register for that pair, column
-//     64 + 32 P + 8 m + p.
+//     When the type changes, the four slot groups' sums are combined by a
+//     reduce-scatter in a fixed order (lanes t4 and t4 ^ 2 first, then t4 and
+//     t4 ^ 1), after which lane 8 m + p holds sum m of its section and adds it
+//     to the shared sum of column 64 + 32 P + 8 m + p (each type is flushed
+//     once: its slots are contiguous).
 // Every sum is taken in a fixed order, so the result does not depend on the
 // caller.
 __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, TripStage &ts, int lane, float (&v)[12]) {
@@ -274,26 +279,25 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
             off[P] = total;
             total += (n + 3) & ~3;
         }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) ts.acc[k][lane] = 0.f;
         __syncwarp();
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        float areg[10];
-#pragma unroll
-        for (int k = 0; k < 10; ++k) areg[k] = 0.f;
         int curP = -1;
+        const bool hi = (t4 & 2) != 0, lo = (t4 & 1) != 0;
         auto flush = [&]() {
-            float red[4];
+            // lanes t4 and t4 ^ 2 exchange the two sums the other keeps (m with bit 1 = its t4's bit 1) ...
+            const float a0 = acc[0], a1 = acc[1], a2 = acc[2], a3 = acc[3];
+            float k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+            const float s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
+            k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+            k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+            // ... then lanes t4 and t4 ^ 1 the one with bit 0 = the other's t4's bit 0: lane 8 m + p has sum m
+            float mine = lo ? k1 : k0;
+            mine += __shfl_xor_sync(0xffffffffu, lo ? k0 : k1, 8);
+            ts.acc[curP][lane] += mine;
 #pragma unroll
-            for (int mm = 0; mm < 4; ++mm) {
-                float x = acc[mm];
-                x += __shfl_xor_sync(0xffffffffu, x, 8);
-                x += __shfl_xor_sync(0xffffffffu, x, 16);
-                red[mm] = x;
-                acc[mm] = 0.f;
-            }
-            const float mine = t4 == 0 ? red[0] : (t4 == 1 ? red[1] : (t4 == 2 ? red[2] : red[3]));
-#pragma unroll
-            for (int k = 0; k < 10; ++k)
-                if (k == curP) areg[k] += mine;
+            for (int mm = 0; mm < 4; ++mm) acc[mm] = 0.f;
         };
         for (int base = 0; base < total; base += 32) {
             const int slot = base + lane;
@@ -356,8 +360,9 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
             __syncwarp();
         }
         if (curP >= 0) flush();
+        __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 10; ++k) v[2 + k] = areg[k];
+        for (int k = 0; k < 10; ++k) v[2 + k] = ts.acc[k][lane];
     }
 }
 
