@@ -401,6 +401,23 @@ MDPF_API int mdpf_debug_set_status(mdpf_ctx *ctx, uint32_t bits);
 MDPF_API int mdpf_debug_wait_timeout(mdpf_ctx *ctx, int32_t limit_us);
 
 /*
+ * Check of the tensor-core operand path the MLP kernels share (tests only; no
+ * context).  One CTA stores A [128 x 64] and B [n x 64] (BF16, row-major,
+ * device pointers d_a and d_b, caller-owned) into its shared memory at byte
+ * offsets a_off and b_off with the swizzled K-major store the MLP epilogues
+ * use for their operands, issues the four tcgen05 MMAs of one 64-wide K chunk
+ * with the MLP kernels' descriptors, and writes D = A B^T [128 x n] (FP32,
+ * row-major) to d_d.  n: 128 or 256; offsets: multiples of 1024, the operands
+ * disjoint and inside 225 KB; otherwise MDPF_ERR_INVALID_ARG.  Asynchronous
+ * on cuda_stream (NULL: the default stream); if the bounded completion wait
+ * expires the kernel ORs MDPF_STATUS_TIMEOUT into *d_status (a device word
+ * the caller clears) and writes no D.
+ */
+/* Paper: no counterpart (test of the tensor-core helpers). */
+MDPF_API int mdpf_debug_tc_probe(const void *d_a, const void *d_b, float *d_d, int32_t n, int32_t a_off,
+                                 int32_t b_off, uint32_t *d_status, void *cuda_stream);
+
+/*
  * Learned-path stages at host positions pos [N,3] (for parity checks; any
  * output may be NULL):
  *   neighbours  rows of the cell-list neighbour list (radius 5.2 + skin, FP32

@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         "mdpf_get_angles": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
         "mdpf_debug_set_status": (ctypes.c_int, [_vp, ctypes.c_uint32]),
         "mdpf_debug_wait_timeout": (ctypes.c_int, [_vp, _i32]),
+        "mdpf_debug_tc_probe": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
         "mdpf_set_profiling": (ctypes.c_int, [_vp, _i32]),
         "mdpf_get_profile": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
         "mdpf_learned_neighbors": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -454,6 +455,16 @@ def pairs_noalloc(n_atoms: int, d_pos: int, d_element: int, d_charge: int, lj_si
     eps = (_f64 * 4)(*[float(v) for v in lj_eps])
     rc = lib().mdpf_pairs_noalloc(int(n_atoms), _vp(d_pos), _vp(d_element), _vp(d_charge), sig, eps,
                                   float(coulomb_k), _vp(d_energy), _vp(d_forces), _vp(stream))
+    if rc != MDPF_OK:
+        raise MdpfError(rc, lib().mdpf_last_error(None).decode())
+
+
+def debug_tc_probe(d_a: int, d_b: int, d_d: int, n: int, a_off: int, b_off: int, d_status: int,
+                   stream: int = 0) -> None:
+    """D = A B^T through the MLP kernels' tensor-core operand path with the operands at chosen
+    shared-memory offsets (device addresses as ints; see mdpf_debug_tc_probe in include/mdpf.h)."""
+    rc = lib().mdpf_debug_tc_probe(_vp(d_a), _vp(d_b), _vp(d_d), int(n), int(a_off), int(b_off), _vp(d_status),
+                                   _vp(stream))
     if rc != MDPF_OK:
         raise MdpfError(rc, lib().mdpf_last_error(None).decode())
 

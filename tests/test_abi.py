@@ -126,3 +126,24 @@ def test_null_context_is_rejected(lib):
     assert lib.mdpf_step(None, 1) == -1
     assert lib.mdpf_compute(None, None, None, None, None) == -1
     lib.mdpf_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["null", "n", "misaligned", "outside", "overlap"])
+def test_tc_probe_rejects_bad_arguments(lib, case):
+    # checked on the host before any CUDA call, so no device is needed
+    fake = ctypes.c_void_p(256)
+    n, a_off, b_off = 128, 0, 16384
+    ptrs = [fake, fake, fake, fake]
+    if case == "null":
+        ptrs[2] = None
+    elif case == "n":
+        n = 96
+    elif case == "misaligned":
+        b_off = 16384 + 512
+    elif case == "outside":
+        b_off = 224 * 1024
+    elif case == "overlap":
+        b_off = 8192
+    rc = lib.mdpf_debug_tc_probe(ptrs[0], ptrs[1], ptrs[2], n, a_off, b_off, ptrs[3], None)
+    assert rc == -1   # MDPF_ERR_INVALID_ARG
+    assert b"tc_probe" in lib.mdpf_last_error(None)
