@@ -55,7 +55,7 @@ RECORD_EVERY = 10            # frames and energies every 10 steps (the workload'
 # DRAM bytes (read + write) per launch of k_plain_persistent, from an ncu capture of this workload:
 # the L2-resident working set read once from a cold L2 (the bench flushes L2 between launches),
 # independent of the MD steps per launch
-PLAIN_TRAFFIC = 1014272
+PLAIN_TRAFFIC = 1018880
 FP32_LANES_PER_SM = 128
 N_SM = 148
 
@@ -72,7 +72,7 @@ ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 # DRAM bytes (read + write) per launch of each learned kernel on this workload, from an ncu capture of
 # the kernels (valid for the kernels as captured)
-LEARNED_TRAFFIC = {"adjoint": 21889536, "features": 8896768, "mlp": 14996992, "fused": 11460864}
+LEARNED_TRAFFIC = {"adjoint": 21890560, "features": 8888576, "mlp": 14997760, "fused": None}
 LEARNED_MD_STEPS = 10000         # the learned workload's NVE run, timed as one region
 
 
