@@ -33,8 +33,12 @@ __device__ __forceinline__ float unord_f(unsigned int u) {
 //
 // One cooperative kernel: it returns at once unless a rebuild is requested
 // (or forced); otherwise four phases separated by grid barriers:
-//   A  bounding box (block min/max, then global ordered-int atomics)
-//   B  cell grid from the box (computed identically by every block), cells cleared
+//   A  bounding box (block min/max, then global ordered-int atomics) and the
+//      first two moments of the positions per axis (fixed-point sums)
+//   B  cell grid (computed identically by every block), cells cleared: the
+//      bounding box cut to mean +- 4 standard deviations per axis, so that a
+//      few atoms far from the rest (a gas-phase cluster evaporates) do not
+//      stretch the cells; atoms outside the grid fall in its edge cells
 //   C  cell fill (atomic slot per atom; overflow flagged, never written)
 //   D  rows: every j != i in the 27 surrounding cells with
 //      fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < fl32(rc^2), sorted ascending.
@@ -82,11 +86,32 @@ __device__ __forceinline__ bool nb_barrier(unsigned long long *bar, unsigned lon
     return *s_fail == 0;
 }
 
-__device__ __forceinline__ CellGrid make_grid(const unsigned int *bb, float rc_list) {
+// Fixed-point scales of the position moments (sums over atoms of u = x - x0 and u^2, u clamped to
+// +-1e4 A so that both products fit 32-bit integers: the conversions are the 32-bit ones), and the number
+// of copies of the six sums that the blocks' adds are spread over.
+constexpr float kMom1 = 64.f, kMom2 = 4.f, kMomClamp = 1.0e4f;
+constexpr int kMomCopies = 8;
+
+// The grid: per axis the bounding box [lo, hi], cut to mu +- 4 sigma of the
+// positions (mom: the fixed-point sums, n atoms, x0 the reference position).
+// Clamping a cell index to the grid never moves two indices further apart,
+// so two atoms within the list radius stay in neighbouring cells wherever
+// they are; the cut only decides how wide the cells are.
+__device__ __forceinline__ CellGrid make_grid(const unsigned int *bb, const long long *mom, int n, float4 x0,
+                                              float rc_list) {
     float lo[3], ext = 0.f, e3[3];
+    const float ref[3] = {x0.x, x0.y, x0.z};
     for (int d = 0; d < 3; ++d) {
         lo[d] = unord_f(bb[d]);
-        e3[d] = unord_f(bb[3 + d]) - lo[d];
+        float hi = unord_f(bb[3 + d]);
+        const double m1 = (double)mom[d] / ((double)kMom1 * n), m2 = (double)mom[3 + d] / ((double)kMom2 * n);
+        const double sd = sqrt(fmax(m2 - m1 * m1, 0.0));
+        const float cl = (float)(ref[d] + m1 - 4.0 * sd), ch = (float)(ref[d] + m1 + 4.0 * sd);
+        if (cl < ch) {   // false for non-finite moments: the plain bounding box
+            lo[d] = fmaxf(lo[d], cl);
+            hi = fminf(hi, ch);
+        }
+        e3[d] = fmaxf(hi - lo[d], 0.f);
         ext = fmaxf(ext, e3[d]);
     }
     // cells a little wider than the list radius, so that rounding in the cell
@@ -201,13 +226,20 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
     __shared__ unsigned long long s_base;
     __shared__ int s_fail;
     __shared__ unsigned int s_bb[6];
+    __shared__ unsigned long long s_mom[6];
     const int nb = gridDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     if (threadIdx.x == 0) s_base = *(volatile unsigned long long *)&L.nb_bar[1];
-    if (threadIdx.x < 6) s_bb[threadIdx.x] = threadIdx.x < 3 ? 0xFFFFFFFFu : 0u;
+    if (threadIdx.x < 6) {
+        s_bb[threadIdx.x] = threadIdx.x < 3 ? 0xFFFFFFFFu : 0u;
+        s_mom[threadIdx.x] = 0ull;
+    }
     __syncthreads();
     const unsigned long long base = s_base;
-    // A: bounding box (the global box was reset to empty by the previous build)
+    const float4 x0 = pos4[0];
+    // A: bounding box and moments (the global box and sums were reset by the previous build); the moments
+    // are integer sums, so they do not depend on the order of the adds
+    long long m[6] = {0, 0, 0, 0, 0, 0};
     for (int a = tid; a < L.n; a += stride) {
         const float4 p = pos4[a];
         atomicMin(&s_bb[0], ord_f(p.x));
@@ -216,19 +248,46 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
         atomicMax(&s_bb[3], ord_f(p.x));
         atomicMax(&s_bb[4], ord_f(p.y));
         atomicMax(&s_bb[5], ord_f(p.z));
+        const float q[3] = {p.x - x0.x, p.y - x0.y, p.z - x0.z};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float u = fminf(fmaxf(q[d], -kMomClamp), kMomClamp);   // non-finite positions stay bounded
+            m[d] += __float2int_rn(u * kMom1);
+            m[3 + d] += __float2int_rn(u * u * kMom2);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        long long v = m[d];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(&s_mom[d], (unsigned long long)v);
     }
     __syncthreads();
     if (threadIdx.x < 3) atomicMin(&L.bbox[threadIdx.x], s_bb[threadIdx.x]);
     else if (threadIdx.x < 6) atomicMax(&L.bbox[threadIdx.x], s_bb[threadIdx.x]);
+    else if (threadIdx.x < 12 && s_mom[threadIdx.x - 6] != 0ull)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&L.bmom[6 * (blockIdx.x % kMomCopies) + threadIdx.x - 6]),
+                  s_mom[threadIdx.x - 6]);
     if (!nb_barrier(L.nb_bar, base + nb, status, limit_ns, &s_fail)) return;
     // B: the grid (identical in every block), cells cleared
-    unsigned int bb[6];
-    for (int d = 0; d < 6; ++d) bb[d] = *(volatile unsigned int *)&L.bbox[d];
-    const CellGrid g = make_grid(bb, L.rc_list);
+    // one thread per block reads the box and the sums (every thread reading the same few words made them a
+    // hot spot) and forms the grid for the block
+    __shared__ CellGrid s_grid;
+    if (threadIdx.x == 0) {
+        unsigned int bb[6];
+        long long mom[6] = {0, 0, 0, 0, 0, 0};
+        for (int d = 0; d < 6; ++d) bb[d] = *(volatile unsigned int *)&L.bbox[d];
+        for (int k = 0; k < kMomCopies; ++k)
+            for (int d = 0; d < 6; ++d) mom[d] += *(volatile long long *)&L.bmom[6 * k + d];
+        s_grid = make_grid(bb, mom, L.n, x0, L.rc_list);
+    }
+    __syncthreads();
+    const CellGrid g = s_grid;
     for (int c = tid; c < g.ncell; c += stride) L.cell_cnt[c] = 0;
     if (!nb_barrier(L.nb_bar, base + 2ull * nb, status, limit_ns, &s_fail)) return;
-    // every block has read the box: reset it for the next build
+    // every block has read the box and the moments: reset them for the next build
     if (blockIdx.x == 0 && threadIdx.x < 6) L.bbox[threadIdx.x] = threadIdx.x < 3 ? 0xFFFFFFFFu : 0u;
+    if (blockIdx.x == 0 && threadIdx.x < 6 * kMomCopies) L.bmom[threadIdx.x] = 0;
     // C: cell fill
     for (int a = tid; a < L.n; a += stride) {
         int cx, cy, cz;

@@ -65,6 +65,23 @@ def test_neighbors_bit_exact(name, mdl):
     assert ctx.learned_counters()["max_row"] == int(cnt.max())
 
 
+def test_neighbors_with_far_outliers(mdl):
+    # a cluster with a few atoms 1000 A away (a gas-phase cluster evaporates): the cell grid must not grow
+    # with the bounding box until its cells overflow; rows (incl. the pairs among the far atoms) stay exact
+    s = synth.workload("cluster2048")
+    pos = np.array(s.pos, dtype=np.float64)
+    far = {3: (1000.0, 0.0, 0.0), 700: (-1000.0, 0.0, 0.0), 1400: (0.0, 1000.0, 0.0), 1900: (0.0, -1000.0, 0.0),
+           40: (0.0, 0.0, 1000.0), 1041: (0.0, 0.0, -1000.0), 77: (1000.0, 3.0, 0.0), 1777: (1000.0, 0.0, 4.0)}
+    for a, p in far.items():
+        pos[a] = p
+    ctx = _ctx(s, mdl)
+    cnt, rows = ctx.learned_neighbors(pos)
+    orows = O.neighbors(np.float32(pos), O.RC_LIST)
+    _rows_equal(rows, orows)
+    assert sorted(rows[3]) == [77, 1777]
+    assert ctx.counters()["status"] == 0
+
+
 def test_neighbors_skin_sets_the_radius(mdl):
     s = synth.workload("mol256")
     ctx = _ctx(s, mdl, skin=0.25)
