@@ -72,7 +72,7 @@ ADJ_FLOPS_PER_PAIR = 150        # radial chain rule incl. 16 exp
 ADJ_FLOPS_PER_TRIPLET = 900     # angular chain rule: 32 columns x (value + derivative) + geometry
 # DRAM bytes (read + write) per launch of each learned kernel on this workload, from an ncu capture of
 # the kernels (valid for the kernels as captured)
-LEARNED_TRAFFIC = {"adjoint": 21890560, "features": 8888576, "mlp": 14997760, "fused": None}
+LEARNED_TRAFFIC = {"adjoint": 21890560, "features": 8888576, "mlp": 14997760, "fused": 11460864}
 LEARNED_MD_STEPS = 10000         # the learned workload's NVE run, timed as one region
 
 
