@@ -231,9 +231,11 @@ struct TripStage {
 //     to the shared sum of column 64 + 32 P + 8 m + p (each type is flushed
 //     once: its slots are contiguous).
 // Every sum is taken in a fixed order, so the result does not depend on the
-// caller.
+// caller.  Part: 1 the radial columns only (v[0..1]), 2 the angular ones only
+// (v[2..11]), 3 both; a part's values are the same bits in every case.
+template <int Part = 3>
 __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, TripStage &ts, int lane, float (&v)[12]) {
-    {
+    if (Part & 1) {
         const int h = lane >> 4, k = lane & 15;
         const float Rk = 0.9f + (float)k * (4.3f / 16.f);
         float racc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -253,7 +255,7 @@ __device__ __forceinline__ void feature_row(const NbrSmem &s, int nr, int na, Tr
         v[0] = h ? tot[1] : tot[0];   // column l      = 16 h + k:       element h
         v[1] = h ? tot[3] : tot[2];   // column 32 + l = 16 (2 + h) + k: element 2 + h
     }
-    {
+    if (Part & 2) {
         const int t4 = lane >> 3, p = lane & 7;
         const float thp = (float)(2 * p + 1) * (kPi / 16.f);
         const float cp = cosf(thp), sp = sinf(thp);
@@ -401,8 +403,10 @@ __device__ __forceinline__ int g_col(int f) { return f < 64 ? f : 64 + kAngStrid
 // core = (A, rc) of the repulsive core (rc == 0: none).  Every pair sits in
 // both atoms' rows, so each side adds half of the pair's core energy and
 // force; the half energies of atom i go to *ecore (fixed point) when ecore is
-// set.
-template <int Chunk>
+// set.  Part: 1 the radial pairs (and the core) only, 2 the angular triplets
+// only, 3 both (two warps may share an atom that way: their fixed-point adds
+// commute, though the split rounds each part to fixed point apart).
+template <int Chunk, int Part = 3>
 __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, int nr, int na, const float *g,
                                              AdjScratch<Chunk> &A, unsigned long long *fx, int lane,
                                              float2 core = make_float2(0.f, 0.f),
@@ -412,7 +416,7 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
     float fix = 0.f, fiy = 0.f, fiz = 0.f;
     float ecore_i = 0.f;
     // radial pairs: dE/dr = sum_k g[16 Zj + k] dT_k/dr;  F_j = -dE/dr u,  F_i += dE/dr u
-    for (int u = lane; u < nr; u += 32) {
+    for (int u = lane; (Part & 1) && u < nr; u += 32) {
         const int q = s.rad[u];
         const float4 d = s.d[q];
         const float r = d.w;
@@ -449,7 +453,7 @@ __device__ __forceinline__ void adjoint_atom(int i, const NbrSmem &s, int cnt, i
     // angular triplets; cos and sin of theta_p = (2 p + 1) pi / 16 as literals (immediate operands)
     constexpr float cpv[8] = {9.807852804e-01f, 8.314696123e-01f, 5.555702330e-01f, 1.950903220e-01f, -1.950903220e-01f, -5.555702330e-01f, -8.314696123e-01f, -9.807852804e-01f};
     constexpr float spv[8] = {1.950903220e-01f, 5.555702330e-01f, 8.314696123e-01f, 9.807852804e-01f, 9.807852804e-01f, 8.314696123e-01f, 5.555702330e-01f, 1.950903220e-01f};
-    const int ntrip = na * (na - 1) / 2;
+    const int ntrip = (Part & 2) ? na * (na - 1) / 2 : 0;
     int kcur[kKmax / 32] = {0, 0, 0, 0};
     for (int t0 = 0; t0 < ntrip; t0 += Chunk) {
         const int t1 = min(t0 + Chunk, ntrip);

@@ -13,10 +13,13 @@
 // layer 2 leaves the block as partial sums of z2, and layer 2' (W2^T delta2
 // for the block's own units) needs no exchange.
 // An MD step (positions x_{s+1} identical in every block):
-//   features   block b, one warp per atom a = b + 8 w: the neighbours by brute
-//              force over the molecule (ascending index, as the neighbour
-//              list orders them), the features of learned_terms.cuh, the
-//              range check; the FP32 rows to the exchange buffer.    barrier 0
+//   features   block b, two warps per atom a = b + 8 p (warps p and p + 4):
+//              warp p lists the neighbours by brute force over the molecule
+//              (ascending index, as the neighbour list orders them) into
+//              shared memory for both; then warp p computes the radial and
+//              warp p + 4 the angular columns of learned_terms.cuh (the same
+//              bits as one warp doing both), with their range checks; the
+//              FP32 rows to the exchange buffer.                     barrier 0
 //   layer 1    every block: all rows as BF16; z1 = W1 G + b1 for its 32 units
 //              (warp MMA m16n8k16, K = 384, FP32 accumulation); a1 =
 //              CELU(z1) kept as the BF16 pair hi + lo, CELU'(z1) kept;
@@ -28,9 +31,11 @@
 //              W2^T delta2 for its 32 units (warp MMA, K = 128; BF16).
 //              Layer 1': the partial dE/dG = W1^T delta1 over its units for
 //              all 384 features (warp MMA, K = 32).                  barrier 2
-//   adjoint    block b, one warp per atom: dE/dG (sum of the partials in block
-//              order), the chain rule of learned_terms.cuh into fixed-point
-//              forces (and the repulsive core).                      barrier 3
+//   adjoint    block b, the same two warps per atom: dE/dG (sum of the
+//              partials in block order; each warp its own columns), the chain
+//              rule of learned_terms.cuh into fixed-point forces, warp p the
+//              radial pairs (and the repulsive core), warp p + 4 the triplets,
+//              each adding its own fixed-point sums.                 barrier 3
 //   integration every block, the same FP64 arithmetic on the same sums (so
 //              every block holds the same state): v += dt/2 a; (energy and
 //              frames by block 0); v += dt/2 a; x += dt v.
@@ -41,8 +46,12 @@
 //
 // Numerics follow the tensor-core MLP's rounding points: BF16 features, the
 // BF16 pair hi + lo of a1, BF16 delta2 and delta1, BF16 weights, FP32
-// accumulation (z2's sum over units taken per block, then over blocks).  Every sum is taken in a fixed order, so runs repeat bit for
-// bit.  Every wait is a bounded grid barrier (1 s, MDPF_STATUS_TIMEOUT).
+// accumulation (z2's sum over units taken per block, then over blocks).
+// Every sum is taken in a fixed order or in integers, so runs repeat bit for
+// bit; the forces differ from the stage kernels' only in rounding each atom's
+// radial and angular parts to fixed point apart.  Every wait is a bounded grid
+// barrier (1 s, MDPF_STATUS_TIMEOUT); the warp pairs' named barriers wait for
+// a partner that runs the same code path.
 #include "forcefield.cuh"
 #include "grid_sync.cuh"
 #include "learned_terms.cuh"
@@ -58,7 +67,7 @@ constexpr int kU1 = kH1 / kSB;         // 32 hidden units of layer 1 per block
 constexpr int kW1Stride = kNFeat + 8;  // BF16 row strides padded by 16 bytes (conflict-free ldmatrix rows)
 constexpr int kU1Stride = kU1 + 8;     // rows over the block's 32 units (W2 columns, a1, delta1)
 constexpr int kD2Stride = kH2 + 8;
-constexpr int kAdjChunkS = 128;
+constexpr int kAdjChunkS = 128;  // triplets staged per adjoint pass of the angular warps (no effect on the result)
 
 struct SmallArgs {
     LearnedDev L;
@@ -99,14 +108,15 @@ struct SmallSmem {
     float b1[4][kU1], b2[4][kH2], w3[4][kH2];
     union {
         struct {
-            NbrSmem nb[4];
-            TripStage ts[4];
+            NbrSmem nb[4];        // atom b + 8 p's neighbours, shared by warps p and p + 4
+            TripStage ts[4];      // the angular warp's staging
         } feat;
         __nv_bfloat16 g[kSmallMax][kW1Stride];                 // features, BF16
         struct {
-            NbrSmem nb[4];
-            AdjScratch<kAdjChunkS> as[4];
-            alignas(16) float sg[4][kGRow];
+            NbrSmem nb[4];                  // as in feat
+            AdjScratch<32> asr[4];          // the radial warps' (they stage no triplets)
+            AdjScratch<kAdjChunkS> asa[4];  // the angular warps'
+            alignas(16) float sg[4][kGRow]; // dE/dG of atom b + 8 p: radial columns by warp p, angular by p + 4
         } adj;
     } u;
     __nv_bfloat16 a1hi[kSmallMax][kU1Stride], a1lo[kSmallMax][kU1Stride];   // CELU(z1) of the block's units, hi + lo
@@ -122,6 +132,7 @@ struct SmallSmem {
     int el[kSmallMax];
     int el_list[4][kSmallMax], el_cnt[4];
     double red[8];
+    int nbc[4][3];                           // neighbour row length, radial and angular counts of atom b + 8 p
     unsigned int pending;                    // status bits found after barrier 3, raised after the next barrier 0
     int s_fail;
 };
@@ -222,6 +233,31 @@ __device__ __forceinline__ bool task_of(const SmallSmem &S, int id, int mtiles, 
     return false;
 }
 
+// Warps p and p + 4 of a block share atom b + 8 p in the feature and adjoint phases: warp p lists the
+// neighbours into shared memory and both wait here (named barrier 1 + p, 64 threads) before reading them.
+__device__ __forceinline__ void pair_sync(int p) { asm volatile("bar.sync %0, 64;" ::"r"(1 + p) : "memory"); }
+
+// The neighbours of atom `at` into S.u.<phase>.nb[p] by warp p (ang false); the counts in every lane of both
+// warps after the pair barrier.
+template <bool ByElement>
+__device__ __forceinline__ void pair_neighbours(SmallSmem &S, NbrSmem &nb, int n, int at, int p, bool ang, int lane,
+                                                int &cnt, int &nr, int &na) {
+    if (!ang) {
+        NbrFetch f;
+        small_fetch(S, n, at, lane, f);
+        store_neighbours<ByElement>(f, nb, lane, cnt, nr, na);
+        if (lane == 0) {
+            S.nbc[p][0] = cnt;
+            S.nbc[p][1] = nr;
+            S.nbc[p][2] = na;
+        }
+    }
+    pair_sync(p);
+    cnt = S.nbc[p][0];
+    nr = S.nbc[p][1];
+    na = S.nbc[p][2];
+}
+
 __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem &S = *reinterpret_cast<SmallSmem *>(smem_raw);
@@ -279,27 +315,30 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
         unsigned long long *fac = a.fac + par * 3 * kSmallMax;
         unsigned long long *eacc = a.eacc + par * 4;
         bool bad = false;
-        // ---- features of atoms b + 8 w
+        // ---- features of atoms b + 8 (w mod 4): warp w < 4 the radial columns, warp w + 4 the angular ones
         {
-            const int at = b + kSB * w;
-            if (w < 4 && at < n) {
-                NbrFetch f;
-                small_fetch(S, n, at, lane, f);
+            const int pr = w & 3, at = b + kSB * pr;
+            const bool ang = w >= 4;
+            if (at < n) {
                 int cnt, nr, na;
-                store_neighbours<true>(f, S.u.feat.nb[w], lane, cnt, nr, na);
+                pair_neighbours<true>(S, S.u.feat.nb[pr], n, at, pr, ang, lane, cnt, nr, na);
                 float v[12];
-                feature_row(S.u.feat.nb[w], nr, na, S.u.feat.ts[w], lane, v);
+                if (ang) feature_row<2>(S.u.feat.nb[pr], nr, na, S.u.feat.ts[pr], lane, v);
+                else feature_row<1>(S.u.feat.nb[pr], nr, na, S.u.feat.ts[pr], lane, v);
+                const int k0 = ang ? 2 : 0, k1 = ang ? 12 : 2;
                 const int z = S.el[at];
                 bool out = false;
                 if (L.lo != nullptr) {   // every range load issued before the first store
 #pragma unroll
                     for (int k = 0; k < 12; ++k) {
                         const int fi = 32 * k + lane;
-                        out |= (v[k] < L.lo[z * kNFeat + fi]) || (v[k] > L.hi[z * kNFeat + fi]);
+                        if (k >= k0 && k < k1)
+                            out |= (v[k] < L.lo[z * kNFeat + fi]) || (v[k] > L.hi[z * kNFeat + fi]);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 12; ++k) a.xG[at * kNFeat + 32 * k + lane] = v[k];
+                for (int k = 0; k < 12; ++k)
+                    if (k >= k0 && k < k1) a.xG[at * kNFeat + 32 * k + lane] = v[k];
                 if (__any_sync(0xffffffffu, out) && lane == 0) {
                     atomicOr(&a.flag[par], 1u);
                     if (!a.fallback) atomicOr(a.status, MDPF_STATUS_OUT_OF_RANGE);
@@ -467,13 +506,16 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                 }
             }
             if (!grid_barrier(a.bar, ++epoch, a.status, a.limit_ns, &S.s_fail)) return;   // B2
-            // ---- adjoint of atoms b + 8 w: dE/dG summed in block order, rounded to BF16 as on the per-stage path
+            // ---- adjoint of atoms b + 8 (w mod 4), warp w < 4 its radial pairs, warp w + 4 its triplets: dE/dG
+            // (the warp's columns) summed in block order, rounded to BF16 as on the per-stage path
             {
-                const int at = b + kSB * w;
-                if (w < 4 && at < n) {
+                const int pr = w & 3, at = b + kSB * pr;
+                const bool ang = w >= 4;
+                if (at < n) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const int f4 = 128 * k + 4 * lane;
+                        if ((f4 >= 64) != ang) continue;
                         float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                         for (int bb = 0; bb < kSB; ++bb) {
@@ -484,17 +526,20 @@ __global__ void __launch_bounds__(kSThreads, 1) k_learned_small(SmallArgs a) {
                             gs.z += v.z;
                             gs.w += v.w;
                         }
-                        S.u.adj.sg[w][g_col(f4 + 0)] = __bfloat162float(__float2bfloat16_rn(gs.x));
-                        S.u.adj.sg[w][g_col(f4 + 1)] = __bfloat162float(__float2bfloat16_rn(gs.y));
-                        S.u.adj.sg[w][g_col(f4 + 2)] = __bfloat162float(__float2bfloat16_rn(gs.z));
-                        S.u.adj.sg[w][g_col(f4 + 3)] = __bfloat162float(__float2bfloat16_rn(gs.w));
+                        S.u.adj.sg[pr][g_col(f4 + 0)] = __bfloat162float(__float2bfloat16_rn(gs.x));
+                        S.u.adj.sg[pr][g_col(f4 + 1)] = __bfloat162float(__float2bfloat16_rn(gs.y));
+                        S.u.adj.sg[pr][g_col(f4 + 2)] = __bfloat162float(__float2bfloat16_rn(gs.z));
+                        S.u.adj.sg[pr][g_col(f4 + 3)] = __bfloat162float(__float2bfloat16_rn(gs.w));
                     }
-                    NbrFetch f;
-                    small_fetch(S, n, at, lane, f);
                     int cnt, nr, na;
-                    store_neighbours<false>(f, S.u.adj.nb[w], lane, cnt, nr, na);
-                    adjoint_atom(at, S.u.adj.nb[w], cnt, nr, na, S.u.adj.sg[w], S.u.adj.as[w], fac, lane,
-                                 make_float2(L.core_a, L.core_rc), L.core_rc > 0.f ? &eacc[0] : nullptr);
+                    pair_neighbours<false>(S, S.u.adj.nb[pr], n, at, pr, ang, lane, cnt, nr, na);
+                    if (ang)
+                        adjoint_atom<kAdjChunkS, 2>(at, S.u.adj.nb[pr], cnt, nr, na, S.u.adj.sg[pr], S.u.adj.asa[pr],
+                                                    fac, lane);
+                    else
+                        adjoint_atom<32, 1>(at, S.u.adj.nb[pr], cnt, nr, na, S.u.adj.sg[pr], S.u.adj.asr[pr], fac, lane,
+                                            make_float2(L.core_a, L.core_rc),
+                                                    L.core_rc > 0.f ? &eacc[0] : nullptr);
                 }
             }
         } else if (b == 0) {
