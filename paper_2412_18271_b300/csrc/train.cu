@@ -33,8 +33,10 @@ constexpr int kOW1 = 0, kOb1 = kH1 * kNFeat, kOW2 = kOb1 + kH1, kOb2 = kOW2 + kH
               kOb3 = kOW3 + kH2, kPPE = kOb3 + 1;
 constexpr int kSplits = 8;     // row-range splits of the weight-matrix gradients
 constexpr int kVSplits = 64;   // row-range splits of the bias / output-weight gradients
-constexpr int kTrRows = 16;    // rows per block of the training MLP kernel
-constexpr int kTrSmem = (2 * kTrRows * kNFeat + 2 * kTrRows * kH1) * 4;
+constexpr int kTrRows = 32;    // rows per block of the training MLP kernel (4 MMA n-tiles)
+// its BF16 row planes: G and U (hi, lo), then a1 and ta1 (hi, lo); bt2 and bh2 (hi, lo) and the FP32
+// s'(h1), s''(h1) t1 of the rows reuse the first
+constexpr int kTrSmem = (4 * kTrRows * (kNFeat + 8) + 4 * kTrRows * (kH1 + 8)) * 2;
 
 // ------------------------------------------------------------ batch layout
 
@@ -267,22 +269,115 @@ struct RowOut {
     float *bh2, *bt2, *w3g;        // [rows][128]
 };
 
-// kTrRows rows of one element per block, thread t = hidden unit.  FP32
-// arithmetic on the BF16-valued weights; FP32 features G and tangents U.
-// Each weight loaded from global memory feeds 2 x kTrRows FMAs; the row
-// operands come from shared memory four at a time.
-__global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U, const float *c_row, RowOut o) {
+// kTrRows rows of one element per block, 8 warps, on the tensor cores through
+// warp-level MMA (m16n8k16, BF16 operands, FP32 accumulation).  The weights are
+// BF16 values already; every FP32 row operand X (features G, tangents U and
+// the layer outputs that feed the next GEMM) enters as the pair
+// hi = bf16(X), lo = bf16(X - hi), and W X is accumulated as W hi + W lo, so
+// the products keep about 16 bits of X (the FP32 CUDA-core sums they replace
+// kept 24; the rows' own features are FP32 values of a BF16 model).
+//   layer 1   h1 = W1 G + b1, t1 = W1 U       (M = 256 units, N = 32 rows, K = 384)
+//             a1 = s(h1), ta1 = s'(h1) t1
+//   layer 2   h2 = W2 a1 + b2, t2 = W2 ta1    (M = 128, K = 256)
+//             bt2 = -w3 s'(h2), bh2 = -w3 s''(h2) t2 + c w3 s'(h2), w3g = c s(h2) - s'(h2) t2
+//   layer 1'  bta1 = W2^T bt2, ba1 = W2^T bh2 (M = 256, K = 128)
+//             bt1 = s'(h1) bta1, bh1 = s''(h1) t1 bta1 + s'(h1) ba1
+// The rows sit in shared memory as BF16 [row][k] planes (the MMA's B operand,
+// read with ldmatrix); the A fragments (weight rows, K contiguous) come from
+// global memory, two k-steps ahead of their MMAs.  Warp w owns units
+// 32 w .. 32 w + 31 in layers 1 and 1' and units 16 w .. 16 w + 15 in layer
+// 2; s'(h1) and s''(h1) t1 of its layer-1 fragments wait in shared memory
+// for layer 1'.
+constexpr int kXs = kNFeat + 8;   // BF16 row strides padded by 16 bytes (conflict-free ldmatrix rows)
+constexpr int kAs = kH1 + 8;
+constexpr int kBs = kH2 + 8;
+constexpr int kPlaneX = kTrRows * kXs, kPlaneA = kTrRows * kAs, kPlaneB = kTrRows * kBs;
+static_assert(4 * kPlaneB * 2 + 2 * kTrRows * kH1 * 4 <= 4 * kPlaneX * 2, "bt2 / bh2 planes and s', s'' t1 fit");
+static_assert(kTrSmem == (4 * kPlaneX + 4 * kPlaneA) * 2, "shared-memory size of the training MLP kernel");
+static_assert(kRowTile % kTrRows == 0, "a block's rows lie in one row tile (one element)");
+
+__device__ __forceinline__ uint32_t tr_smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Fragments of two n-tiles (rows 8 j .. 8 j + 15) of a [row][k] plane at k-step k0: b[0..1] for n-tile j,
+// b[2..3] for n-tile j + 1.
+__device__ __forceinline__ void tr_frag_b2(const __nv_bfloat16 *plane, int ld, int j, int k0, int lane,
+                                           uint32_t (&b)[4]) {
+    const __nv_bfloat16 *p = plane + (size_t)(8 * j + ((lane >> 4) << 3) + (lane & 7)) * ld + k0 + ((lane >> 3) & 1) * 8;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+                 : "r"(tr_smem_u32(p)));
+}
+
+// The A fragment of rows m0 .. m0 + 15, columns k0 .. k0 + 15 of a row-major BF16 matrix in global memory.
+__device__ __forceinline__ void tr_frag_a(const __nv_bfloat16 *W, int ld, int m0, int k0, int lane, uint32_t (&a)[4]) {
+    const int g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 *p = W + (size_t)(m0 + g) * ld + k0 + 2 * t;
+    a[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
+    a[1] = __ldg(reinterpret_cast<const unsigned int *>(p + 8 * ld));
+    a[2] = __ldg(reinterpret_cast<const unsigned int *>(p + 8));
+    a[3] = __ldg(reinterpret_cast<const unsigned int *>(p + 8 * ld + 8));
+}
+
+__device__ __forceinline__ void tr_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// D_h += W (P0 + P1), D_t += W (P2 + P3) over K = 16 KS for MT m-tiles of W (rows m0 + 16 i) and the four
+// n-tiles of the block's rows; P0..P3 are consecutive [row][k] planes `plane` elements apart.
+template <int MT, int KS>
+__device__ __forceinline__ void tr_gemm(const __nv_bfloat16 *W, int ldw, int m0, const __nv_bfloat16 *P, int ld,
+                                        int plane, int lane, float (&dh)[MT][4][4], float (&dt)[MT][4][4]) {
+    uint32_t a[3][MT][4];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < MT; ++i) tr_frag_a(W, ldw, m0 + 16 * i, 16 * s, lane, a[s][i]);
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        if (ks + 2 < KS) {
+#pragma unroll
+            for (int i = 0; i < MT; ++i) tr_frag_a(W, ldw, m0 + 16 * i, 16 * (ks + 2), lane, a[(ks + 2) % 3][i]);
+        }
+#pragma unroll
+        for (int op = 0; op < 4; ++op) {
+            uint32_t b[2][4];
+            tr_frag_b2(P + op * plane, ld, 0, 16 * ks, lane, b[0]);
+            tr_frag_b2(P + op * plane, ld, 2, 16 * ks, lane, b[1]);
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float(&d)[4] = op < 2 ? dh[i][j] : dt[i][j];
+                    tr_mma(d, a[ks % 3][i], b[j >> 1][2 * (j & 1)], b[j >> 1][2 * (j & 1) + 1]);
+                }
+        }
+    }
+}
+
+// x as the BF16 pair (hi, lo) at [r][c] of two planes.
+__device__ __forceinline__ void tr_put_pair(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int idx, float x) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float *U, const float *c_row, RowOut o) {
     const int r0 = blockIdx.x * kTrRows;
     if (r0 >= *L.n_tiles_live * kRowTile) return;
-    extern __shared__ float4 tr_smem4[];
-    float *sm = reinterpret_cast<float *>(tr_smem4);
-    float (*sG)[kNFeat] = reinterpret_cast<float (*)[kNFeat]>(sm);
-    float (*sU)[kNFeat] = reinterpret_cast<float (*)[kNFeat]>(sm + kTrRows * kNFeat);
-    float (*sA1)[kH1] = reinterpret_cast<float (*)[kH1]>(sm + 2 * kTrRows * kNFeat);
-    float (*sTA1)[kH1] = reinterpret_cast<float (*)[kH1]>(sm + 2 * kTrRows * kNFeat + kTrRows * kH1);
+    extern __shared__ __align__(16) unsigned char tr_smem[];
+    __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(tr_smem);              // G hi, G lo, U hi, U lo
+    __nv_bfloat16 *sA = sX + 4 * kPlaneX;                                        // a1 hi, lo, ta1 hi, lo
+    __nv_bfloat16 *sB = sX;                                                      // bt2 hi, lo, bh2 hi, lo
     __shared__ float sc[kTrRows];
     __shared__ int sreal[kTrRows];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
     const int e = L.tile_el[r0 / kRowTile];
     if (t < kTrRows) {
         sreal[t] = L.atom_of[r0 + t] >= 0;
@@ -290,108 +385,112 @@ __global__ void __launch_bounds__(256) k_mlp_train(LearnedDev L, const float *U,
     }
     __syncthreads();
     for (int q = t; q < kTrRows * kNFeat / 4; q += 256) {
-        const int r = q / (kNFeat / 4), f4 = q % (kNFeat / 4);
+        const int r = q / (kNFeat / 4), f = 4 * (q % (kNFeat / 4));
         const bool re = sreal[r];
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        reinterpret_cast<float4 *>(sG[r])[f4] = re ? reinterpret_cast<const float4 *>(L.G32 + (size_t)(r0 + r) * kNFeat)[f4] : z;
-        reinterpret_cast<float4 *>(sU[r])[f4] = re ? reinterpret_cast<const float4 *>(U + (size_t)(r0 + r) * kNFeat)[f4] : z;
+        const float4 gv = re ? *reinterpret_cast<const float4 *>(L.G32 + (size_t)(r0 + r) * kNFeat + f) : z;
+        const float4 uv = re ? *reinterpret_cast<const float4 *>(U + (size_t)(r0 + r) * kNFeat + f) : z;
+        const float gs[4] = {gv.x, gv.y, gv.z, gv.w}, us[4] = {uv.x, uv.y, uv.z, uv.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            tr_put_pair(sX, sX + kPlaneX, r * kXs + f + c, gs[c]);
+            tr_put_pair(sX + 2 * kPlaneX, sX + 3 * kPlaneX, r * kXs + f + c, us[c]);
+        }
     }
     __syncthreads();
-    // layer 1 (thread = unit a): h1 = W1 G + b1, t1 = W1 U
-    float h1[kTrRows], t1[kTrRows];
+    // ---- layer 1: units 32 w + 16 i + g (+ 8), rows 8 j + 2 t4 (+ 1)
+    float h1[2][4][4], t1[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h1[i][j][q] = t1[i][j][q] = 0.f;
+    tr_gemm<2, kNFeat / 16>(L.W1 + (size_t)e * kH1 * kNFeat, kNFeat, 32 * w, sX, kXs, kPlaneX, lane, h1, t1);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = 32 * w + 16 * i + g + 8 * (q >> 1);
+            const float b = L.b1[e * kH1 + u];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = 8 * j + 2 * t4 + (q & 1);
+                const float h = h1[i][j][q] + b, a1 = tr_s(h), ta1 = tr_ds(h) * t1[i][j][q];
+                h1[i][j][q] = h;
+                o.a1[(size_t)(r0 + r) * kH1 + u] = a1;
+                o.ta1[(size_t)(r0 + r) * kH1 + u] = ta1;
+                tr_put_pair(sA, sA + kPlaneA, r * kAs + u, a1);
+                tr_put_pair(sA + 2 * kPlaneA, sA + 3 * kPlaneA, r * kAs + u, ta1);
+            }
+        }
+    __syncthreads();
+    // s'(h1) and s''(h1) t1 of the warp's fragments go to the free tail of the G / U planes (FP32, columns
+    // swizzled by the row so that a fragment's lanes hit 32 banks); layer 1' reads them back
+    float *sD = reinterpret_cast<float *>(sX + 4 * kPlaneB);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = 32 * w + 16 * i + g + 8 * (q >> 1), r = 8 * j + 2 * t4 + (q & 1);
+                const int idx = r * kH1 + (u ^ ((r & 7) << 2));
+                sD[idx] = tr_ds(h1[i][j][q]);
+                sD[kTrRows * kH1 + idx] = tr_dds(h1[i][j][q]) * t1[i][j][q];
+            }
+    // ---- layer 2: units 16 w + g (+ 8); the bt2 / bh2 planes replace the G / U planes
     {
-        const __nv_bfloat16 *W = L.W1T + (size_t)e * kNFeat * kH1;
-        const float b = L.b1[e * kH1 + t];
+        float h2[1][4][4], t2[1][4][4];
 #pragma unroll
-        for (int r = 0; r < kTrRows; ++r) {
-            h1[r] = b;
-            t1[r] = 0.f;
-        }
-        for (int f = 0; f < kNFeat; f += 4) {
-            float wv[4];
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(f + u) * kH1 + t]);
+            for (int q = 0; q < 4; ++q) h2[0][j][q] = t2[0][j][q] = 0.f;
+        tr_gemm<1, kH1 / 16>(L.W2 + (size_t)e * kH2 * kH1, kH1, 16 * w, sA, kAs, kPlaneA, lane, h2, t2);
 #pragma unroll
-            for (int r = 0; r < kTrRows; ++r) {
-                const float4 g = *reinterpret_cast<const float4 *>(&sG[r][f]);
-                const float4 x = *reinterpret_cast<const float4 *>(&sU[r][f]);
-                h1[r] = fmaf(g.x, wv[0], fmaf(g.y, wv[1], fmaf(g.z, wv[2], fmaf(g.w, wv[3], h1[r]))));
-                t1[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], t1[r]))));
+        for (int q = 0; q < 4; ++q) {
+            const int v = 16 * w + g + 8 * (q >> 1);
+            const float b = L.b2[e * kH2 + v], w3 = L.W3[e * kH2 + v];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = 8 * j + 2 * t4 + (q & 1);
+                const float cr = sc[r];
+                const float h = h2[0][j][q] + b, tt = t2[0][j][q];
+                const float d1 = tr_ds(h);
+                const float bt2 = -w3 * d1;
+                const float bh2 = -w3 * tr_dds(h) * tt + cr * w3 * d1;
+                o.bt2[(size_t)(r0 + r) * kH2 + v] = bt2;
+                o.bh2[(size_t)(r0 + r) * kH2 + v] = bh2;
+                o.w3g[(size_t)(r0 + r) * kH2 + v] = cr * tr_s(h) - d1 * tt;
+                tr_put_pair(sB, sB + kPlaneB, r * kBs + v, bt2);
+                tr_put_pair(sB + 2 * kPlaneB, sB + 3 * kPlaneB, r * kBs + v, bh2);
             }
-        }
-#pragma unroll
-        for (int r = 0; r < kTrRows; ++r) {
-            const float a1 = tr_s(h1[r]), ta1 = tr_ds(h1[r]) * t1[r];
-            sA1[r][t] = a1;
-            sTA1[r][t] = ta1;
-            o.a1[(size_t)(r0 + r) * kH1 + t] = a1;
-            o.ta1[(size_t)(r0 + r) * kH1 + t] = ta1;
         }
     }
     __syncthreads();
-    float (*sBT2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sG[0][0]);
-    float (*sBH2)[kH2] = reinterpret_cast<float (*)[kH2]>(&sU[0][0]);
-    // layer 2 and its reverse (thread = unit b < 128): J = c E - W3 . ta2
-    if (t < kH2) {
-        const __nv_bfloat16 *W = L.W2T + (size_t)e * kH1 * kH2;
-        const float b = L.b2[e * kH2 + t], w3 = L.W3[e * kH2 + t];
-        float h2[kTrRows], t2[kTrRows];
+    // ---- layer 1' (the same units as layer 1)
+    float bta1[2][4][4], ba1[2][4][4];
 #pragma unroll
-        for (int r = 0; r < kTrRows; ++r) {
-            h2[r] = b;
-            t2[r] = 0.f;
-        }
-        for (int a = 0; a < kH1; a += 4) {
-            float wv[4];
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(a + u) * kH2 + t]);
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int r = 0; r < kTrRows; ++r) {
-                const float4 x = *reinterpret_cast<const float4 *>(&sA1[r][a]);
-                const float4 y = *reinterpret_cast<const float4 *>(&sTA1[r][a]);
-                h2[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], h2[r]))));
-                t2[r] = fmaf(y.x, wv[0], fmaf(y.y, wv[1], fmaf(y.z, wv[2], fmaf(y.w, wv[3], t2[r]))));
+            for (int q = 0; q < 4; ++q) bta1[i][j][q] = ba1[i][j][q] = 0.f;
+    tr_gemm<2, kH2 / 16>(L.W2T + (size_t)e * kH1 * kH2, kH2, 32 * w, sB, kBs, kPlaneB, lane, bta1, ba1);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int u = 32 * w + 16 * i + g + 8 * (q >> 1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = 8 * j + 2 * t4 + (q & 1);
+                const int idx = r * kH1 + (u ^ ((r & 7) << 2));
+                const float d1 = sD[idx], dd = sD[kTrRows * kH1 + idx];
+                o.bt1[(size_t)(r0 + r) * kH1 + u] = d1 * bta1[i][j][q];
+                o.bh1[(size_t)(r0 + r) * kH1 + u] = dd * bta1[i][j][q] + d1 * ba1[i][j][q];
             }
         }
-#pragma unroll
-        for (int r = 0; r < kTrRows; ++r) {
-            const float cr = sc[r];
-            const float d1 = tr_ds(h2[r]);
-            const float bt2 = -w3 * d1;
-            const float bh2 = -w3 * tr_dds(h2[r]) * t2[r] + cr * w3 * d1;
-            sBT2[r][t] = bt2;
-            sBH2[r][t] = bh2;
-            o.bt2[(size_t)(r0 + r) * kH2 + t] = bt2;
-            o.bh2[(size_t)(r0 + r) * kH2 + t] = bh2;
-            o.w3g[(size_t)(r0 + r) * kH2 + t] = cr * tr_s(h2[r]) - d1 * t2[r];
-        }
-    }
-    __syncthreads();
-    // reverse through layer 2 into layer 1 (thread = unit a)
-    {
-        const __nv_bfloat16 *W = L.W2 + (size_t)e * kH2 * kH1;
-        float bta1[kTrRows], ba1[kTrRows];
-#pragma unroll
-        for (int r = 0; r < kTrRows; ++r) bta1[r] = ba1[r] = 0.f;
-        for (int b = 0; b < kH2; b += 4) {
-            float wv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) wv[u] = __bfloat162float(W[(size_t)(b + u) * kH1 + t]);
-#pragma unroll
-            for (int r = 0; r < kTrRows; ++r) {
-                const float4 x = *reinterpret_cast<const float4 *>(&sBT2[r][b]);
-                const float4 y = *reinterpret_cast<const float4 *>(&sBH2[r][b]);
-                bta1[r] = fmaf(x.x, wv[0], fmaf(x.y, wv[1], fmaf(x.z, wv[2], fmaf(x.w, wv[3], bta1[r]))));
-                ba1[r] = fmaf(y.x, wv[0], fmaf(y.y, wv[1], fmaf(y.z, wv[2], fmaf(y.w, wv[3], ba1[r]))));
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kTrRows; ++r) {
-            const float d1 = tr_ds(h1[r]);
-            o.bt1[(size_t)(r0 + r) * kH1 + t] = d1 * bta1[r];
-            o.bh1[(size_t)(r0 + r) * kH1 + t] = tr_dds(h1[r]) * t1[r] * bta1[r] + d1 * ba1[r];
-        }
-    }
 }
 
 // ------------------------------------------------------------ weight gradients
