@@ -32,7 +32,7 @@ namespace {
 constexpr int kOW1 = 0, kOb1 = kH1 * kNFeat, kOW2 = kOb1 + kH1, kOb2 = kOW2 + kH2 * kH1, kOW3 = kOb2 + kH2,
               kOb3 = kOW3 + kH2, kPPE = kOb3 + 1;
 constexpr int kSplits = 8;     // row-range splits of the weight-matrix gradients
-constexpr int kVSplits = 64;   // row-range splits of the bias / output-weight gradients
+constexpr int kVSplits = 64;   // block-range splits of the bias / output-weight gradients
 constexpr int kTrRows = 32;    // rows per block of the training MLP kernel (4 MMA n-tiles)
 // its BF16 row planes: G and U (hi, lo), then a1 and ta1 (hi, lo); bt2 and bh2 (hi, lo) and the FP32
 // s'(h1), s''(h1) t1 of the rows reuse the first
@@ -264,9 +264,14 @@ __device__ __forceinline__ float tr_s(float z) { return z > 0.f ? z : 0.1f * (__
 __device__ __forceinline__ float tr_ds(float z) { return z >= 0.f ? 1.f : __expf(10.f * z); }
 __device__ __forceinline__ float tr_dds(float z) { return z >= 0.f ? 0.f : 10.f * __expf(10.f * z); }
 
+// Columns of a block's vector-gradient partials: sum over its real rows of bh1 (b1), bh2 (b2),
+// c s(h2) - s'(h2) t2 (W3) and c (b3).
+constexpr int kVb1 = 0, kVb2 = kH1, kVW3 = kH1 + kH2, kVb3 = kH1 + 2 * kH2, kVLen = kVb3 + 1;
+
 struct RowOut {
     float *bh1, *bt1, *a1, *ta1;   // [rows][256]
-    float *bh2, *bt2, *w3g;        // [rows][128]
+    float *bh2, *bt2;              // [rows][128]
+    float *vpart;                  // [rows / kTrRows][kVLen]
 };
 
 // kTrRows rows of one element per block, 8 warps, on the tensor cores through
@@ -367,6 +372,24 @@ __device__ __forceinline__ void tr_put_pair(__nv_bfloat16 *hi, __nv_bfloat16 *lo
     lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
+// Two per-lane column sums (units g and g + 8 of a fragment) summed over the four lanes of the quad
+// (t4 = 0..3, xor 1 then xor 2: a fixed order) and stored by lane t4 = 0 at columns ca and cb.
+__device__ __forceinline__ void tr_quad_sums(const float (&x)[2], const float (&y)[2], float *out, int ca, int cb,
+                                             int t4) {
+    float v[4] = {x[0], x[1], y[0], y[1]};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
+    }
+    if (t4 == 0) {
+        out[ca] = v[0];
+        out[ca + 8] = v[1];
+        out[cb] = v[2];
+        out[cb + 8] = v[3];
+    }
+}
+
 __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float *U, const float *c_row, RowOut o) {
     const int r0 = blockIdx.x * kTrRows;
     if (r0 >= *L.n_tiles_live * kRowTile) return;
@@ -447,6 +470,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
 #pragma unroll
             for (int q = 0; q < 4; ++q) h2[0][j][q] = t2[0][j][q] = 0.f;
         tr_gemm<1, kH1 / 16>(L.W2 + (size_t)e * kH2 * kH1, kH1, 16 * w, sA, kAs, kPlaneA, lane, h2, t2);
+        float vb2[2] = {0.f, 0.f}, vw3[2] = {0.f, 0.f};   // unit g and g + 8: the lane's rows, then the quad's
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int v = 16 * w + g + 8 * (q >> 1);
@@ -461,11 +485,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
                 const float bh2 = -w3 * tr_dds(h) * tt + cr * w3 * d1;
                 o.bt2[(size_t)(r0 + r) * kH2 + v] = bt2;
                 o.bh2[(size_t)(r0 + r) * kH2 + v] = bh2;
-                o.w3g[(size_t)(r0 + r) * kH2 + v] = cr * tr_s(h) - d1 * tt;
+                if (sreal[r]) {
+                    vb2[q >> 1] += bh2;
+                    vw3[q >> 1] += cr * tr_s(h) - d1 * tt;
+                }
                 tr_put_pair(sB, sB + kPlaneB, r * kBs + v, bt2);
                 tr_put_pair(sB + 2 * kPlaneB, sB + 3 * kPlaneB, r * kBs + v, bh2);
             }
         }
+        tr_quad_sums(vb2, vw3, o.vpart + (size_t)blockIdx.x * kVLen, kVb2 + 16 * w + g, kVW3 + 16 * w + g, t4);
     }
     __syncthreads();
     // ---- layer 1' (the same units as layer 1)
@@ -477,6 +505,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
 #pragma unroll
             for (int q = 0; q < 4; ++q) bta1[i][j][q] = ba1[i][j][q] = 0.f;
     tr_gemm<2, kH2 / 16>(L.W2T + (size_t)e * kH1 * kH2, kH2, 32 * w, sB, kBs, kPlaneB, lane, bta1, ba1);
+    float vb1[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // [i][unit g, g + 8]
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -487,39 +516,47 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
                 const int r = 8 * j + 2 * t4 + (q & 1);
                 const int idx = r * kH1 + (u ^ ((r & 7) << 2));
                 const float d1 = sD[idx], dd = sD[kTrRows * kH1 + idx];
+                const float bh1 = dd * bta1[i][j][q] + d1 * ba1[i][j][q];
                 o.bt1[(size_t)(r0 + r) * kH1 + u] = d1 * bta1[i][j][q];
-                o.bh1[(size_t)(r0 + r) * kH1 + u] = dd * bta1[i][j][q] + d1 * ba1[i][j][q];
+                o.bh1[(size_t)(r0 + r) * kH1 + u] = bh1;
+                if (sreal[r]) vb1[i][q >> 1] += bh1;
             }
         }
+    float *vp = o.vpart + (size_t)blockIdx.x * kVLen;
+    tr_quad_sums(vb1[0], vb1[1], vp, kVb1 + 32 * w + g, kVb1 + 32 * w + 16 + g, t4);
+    if (t == 0) {
+        float c = 0.f;
+        for (int r = 0; r < kTrRows; ++r)
+            if (sreal[r]) c += sc[r];
+        vp[kVb3] = c;
+    }
+}
+
+// Per (element, split, column): the block partials of the split's blocks of that element, in block order.
+__global__ void k_vsum(LearnedDev L, const float *vpart, float *part) {
+    const int e = blockIdx.y, sp = blockIdx.z;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kVLen) return;
+    const int nb = *L.n_tiles_live * (kRowTile / kTrRows);
+    const int b0 = (int)((long long)nb * sp / kVSplits), b1 = (int)((long long)nb * (sp + 1) / kVSplits);
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b)
+        if (L.tile_el[b / (kRowTile / kTrRows)] == e) s += vpart[(size_t)b * kVLen + j];
+    part[((size_t)sp * 4 + e) * kVLen + j] = s;
+}
+
+// The vector gradients of element e: the split sums in split order.
+__global__ void k_vfinal(const float *part, float *grad) {
+    const int e = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kVLen) return;
+    float s = 0.f;
+    for (int sp = 0; sp < kVSplits; ++sp) s += part[((size_t)sp * 4 + e) * kVLen + j];
+    const int col = j < kVb2 ? kOb1 + j : j < kVW3 ? kOb2 + (j - kVb2) : j < kVb3 ? kOW3 + (j - kVW3) : kOb3;
+    grad[(size_t)e * kPPE + col] = s;
 }
 
 // ------------------------------------------------------------ weight gradients
-
-// out[split][e][j] = sum over the split's rows of element e of X[r][j] (X = null: c_row), fixed order.
-__global__ void k_vgrad(LearnedDev L, const float *X, const float *c_row, int len, int tiles_max, float *out) {
-    const int e = blockIdx.y / kVSplits, sp = blockIdx.y % kVSplits;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= len) return;
-    const int live = *L.n_tiles_live;
-    const int t0 = (int)((long long)tiles_max * sp / kVSplits), t1 = (int)((long long)tiles_max * (sp + 1) / kVSplits);
-    float s = 0.f;
-    for (int tile = t0; tile < t1 && tile < live; ++tile) {
-        if (L.tile_el[tile] != e) continue;
-        for (int r = tile * kRowTile; r < (tile + 1) * kRowTile; ++r)
-            if (L.atom_of[r] >= 0) s += X ? X[(size_t)r * len + j] : c_row[r];
-    }
-    out[((size_t)sp * 4 + e) * len + j] = s;
-}
-
-// grad[e][off + j] = sum_s part[s][e][j] (in split order)
-__global__ void k_reduce_splits(const float *part, int len, int off, int splits, float *grad) {
-    const int e = blockIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= len) return;
-    float s = 0.f;
-    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * 4 + e) * len + j];
-    grad[(size_t)e * kPPE + off + j] = s;
-}
 
 // ------------------------------------------------------------ AdamW
 
@@ -681,10 +718,11 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     TA(t->ro.ta1, R * kH1);
     TA(t->ro.bh2, R * kH2);
     TA(t->ro.bt2, R * kH2);
-    TA(t->ro.w3g, R * kH2);
+    TA(t->ro.vpart, (R / kTrRows) * kVLen);
     TA(t->d_part, (size_t)kSplits * 4 * kH1 * kNFeat);
     static_assert((size_t)kWgSplits * (kH1 * kNFeat + kH2 * kH1) <= (size_t)kSplits * 4 * kH1 * kNFeat,
                   "partial buffer");
+    static_assert((size_t)kVSplits * 4 * kVLen <= (size_t)kSplits * 4 * kH1 * kNFeat, "vector partial buffer");
     TA(t->d_etiles, 4 * (size_t)t->tiles_max);
     TA(t->d_wsplit, kWgSplits);
     TA(t->d_lparts, 2 * (size_t)t->max_frames);
@@ -810,20 +848,15 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     // 5. per-row reverse over the tangent pass
     k_mlp_train<<<t->rows_max / kTrRows, 256, kTrSmem, s>>>(L, t->d_U, t->d_c, t->ro);
     // 6. weight-matrix gradients on the tensor cores (K splits over each element's row tiles, summed in
-    //    order); bias and output-weight gradients as split row sums
+    //    order); the bias and output-weight gradients from the row kernel's per-block column sums, summed by
+    //    split in block order, then over the splits in order
     WgradIn wg{t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1,
                L.atom_of, L.tile_el, L.n_tiles_live, t->tiles_max, t->d_etiles, t->d_wsplit, t->d_part,
                d_grad, kPPE, kOW1, kOW2, t->d_status};
     ce = learned_wgrad_tc(wg, s);
     if (ce != cudaSuccess) return tr_cuda(t, ce, "learned_wgrad_tc");
-    k_vgrad<<<dim3(1, 4 * kVSplits), 256, 0, s>>>(L, t->ro.bh1, nullptr, kH1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 256, 0, s>>>(t->d_part, kH1, kOb1, kVSplits, d_grad);
-    k_vgrad<<<dim3(1, 4 * kVSplits), 128, 0, s>>>(L, t->ro.bh2, nullptr, kH2, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOb2, kVSplits, d_grad);
-    k_vgrad<<<dim3(1, 4 * kVSplits), 128, 0, s>>>(L, t->ro.w3g, nullptr, kH2, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 128, 0, s>>>(t->d_part, kH2, kOW3, kVSplits, d_grad);
-    k_vgrad<<<dim3(1, 4 * kVSplits), 32, 0, s>>>(L, nullptr, t->d_c, 1, t->tiles_max, t->d_part);
-    k_reduce_splits<<<dim3(1, 4), 32, 0, s>>>(t->d_part, 1, kOb3, kVSplits, d_grad);
+    k_vsum<<<dim3((kVLen + 127) / 128, 4, kVSplits), 128, 0, s>>>(L, t->ro.vpart, t->d_part);
+    k_vfinal<<<dim3((kVLen + 127) / 128, 4), 128, 0, s>>>(t->d_part, d_grad);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return tr_cuda(t, ce, "training launches");
     return MDPF_OK;
