@@ -62,15 +62,35 @@ struct WgArgs {
 
 // The live row tiles of each element, and the K splits: kWgSplits handed out
 // in proportion to the elements' tile counts (at least one per element that
-// has tiles, at most one per tile).  One thread.
-__global__ void k_wg_table(const int *tile_el, const int *n_live, int tiles_max, int *etiles, int4 *split) {
-    if (threadIdx.x != 0) return;
-    int cnt[4] = {0, 0, 0, 0};
+// has tiles, at most one per tile).  The block stages the tile elements in
+// shared memory 1024 at a time and warp 0 lists each element's tiles in
+// ascending order by ballots; thread 0 then deals the splits.
+constexpr int kWgTableThreads = 256, kWgTableChunk = 1024;
+
+__global__ void __launch_bounds__(kWgTableThreads) k_wg_table(const int *tile_el, const int *n_live, int tiles_max,
+                                                             int *etiles, int4 *split) {
+    __shared__ int s_el[kWgTableChunk];
+    const int t = threadIdx.x, lane = t & 31;
     const int live = *n_live;
-    for (int t = 0; t < live; ++t) {
-        const int e = tile_el[t];
-        etiles[e * tiles_max + cnt[e]++] = t;
+    int cnt[4] = {0, 0, 0, 0};   // warp 0: tiles of each element listed so far (the same in every lane)
+    for (int base = 0; base < live; base += kWgTableChunk) {
+        const int m = min(kWgTableChunk, live - base);
+        for (int k = t; k < m; k += kWgTableThreads) s_el[k] = tile_el[base + k];
+        __syncthreads();
+        if (t < 32) {
+            for (int k0 = 0; k0 < m; k0 += 32) {
+                const int e = k0 + lane < m ? s_el[k0 + lane] : -1;
+#pragma unroll
+                for (int ee = 0; ee < 4; ++ee) {
+                    const unsigned int mask = __ballot_sync(0xffffffffu, e == ee);
+                    if (e == ee) etiles[ee * tiles_max + cnt[ee] + __popc(mask & ((1u << lane) - 1u))] = base + k0 + lane;
+                    cnt[ee] += __popc(mask);
+                }
+            }
+        }
+        __syncthreads();
     }
+    if (t != 0) return;   // thread 0 is in warp 0, whose lanes all hold the counts
     const int total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     int se[4], used = 0;
     for (int e = 0; e < 4; ++e) {
@@ -264,7 +284,7 @@ cudaError_t learned_wgrad_tc_prepare() {
 }
 
 cudaError_t learned_wgrad_tc(const WgradIn &w, cudaStream_t s) {
-    k_wg_table<<<1, 32, 0, s>>>(w.tile_el, w.n_live, w.tiles_max, w.etiles, w.split);
+    k_wg_table<<<1, kWgTableThreads, 0, s>>>(w.tile_el, w.n_live, w.tiles_max, w.etiles, w.split);
     WgArgs a{};
     a.p[0] = WgProblem{{w.bh1, w.bt1}, {w.G, w.U}, kH1, kNFeat, w.off_w1};
     a.p[1] = WgProblem{{w.bh2, w.bt2}, {w.a1, w.ta1}, kH2, kH1, w.off_w2};
