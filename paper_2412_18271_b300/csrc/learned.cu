@@ -524,105 +524,204 @@ __global__ void __launch_bounds__(32 * kAtomWarps) k_adjoint(LearnedDev L, const
 
 // ------------------------------------------------------------------ feature JVP
 
+// Per-warp staging of the JVP: one batch of 32 triplet slots (value and
+// tangent factors), the pair-type table and the angular column sums, plus
+// w_j = v_j - v_i and the tangent of r_ij for every neighbour.
+struct JvpStage {
+    float4 q[32];    // cos, sin of the scaled angle, 2^-31 fc(r_j) fc(r_k) = C, pair type
+    float4 qd[32];   // cot, 32 x tangent of the scaled cosine, 2^-31 tangent of C, 0
+    float4 b[32];    // radial-shell factors B_m of the 4 shells
+    float4 bd[32];   // their tangents
+    int4 type[10];   // as in the feature stage: first slot, triplets, first angular indices and count, e1 == e2
+    float rcp[12];
+    float acc[10][32];
+    float4 w[kKmax];   // v_j - v_i (x, y, z), tangent of r_ij
+};
+
 // Tangent of the features along per-atom vectors v: U_i = sum_a dG_i/dx_a . v_a.
-// Same lane layout and summation order as k_features; per pair the tangent of
-// r_ij is u_ij . (v_j - v_i), per triplet that of cos(theta) is
+// The lane layout of the features: radial lane 16 h + k sums every second
+// in-cutoff neighbour into four per-element registers; angular triplets laid
+// out pair type by pair type in padded runs, lane 8 t4 + p taking slot t4 of
+// each group of 4 for section p and its four shells, the four slot groups'
+// sums combined by a reduce-scatter at each type change.  Per pair the
+// tangent of r_ij is u_ij . (v_j - v_i); per triplet that of cos(theta) is
 // ((u_k - c u_j)/r_j) . (v_j - v_i) + ((u_j - c u_k)/r_k) . (v_k - v_i).
 __global__ void __launch_bounds__(32 * kAtomWarps) k_jvp(LearnedDev L, const float4 *pos4, const float *v, float *U) {
     __shared__ NbrSmem sn[kAtomWarps];
-    __shared__ float accR[kAtomWarps][2][64];
-    __shared__ float accA[kAtomWarps][320];
-    __shared__ float tcs[kAtomWarps][32], tsn[kAtomWarps][32], tcot[kAtomWarps][32], tcsd[kAtomWarps][32];
-    __shared__ float tC[kAtomWarps][32], tCd[kAtomWarps][32], tB[kAtomWarps][32][4], tBd[kAtomWarps][32][4];
-    __shared__ int tP[kAtomWarps][32];
+    __shared__ JvpStage st[kAtomWarps];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kAtomWarps + w;
     if (i >= L.n) return;
     NbrSmem &s = sn[w];
-    for (int f = lane; f < 128; f += 32) (&accR[w][0][0])[f] = 0.f;
-    for (int f = lane; f < 320; f += 32) accA[w][f] = 0.f;
+    JvpStage &ts = st[w];
     int cnt, nr, na;
-    load_neighbours<false>(L, pos4, i, s, lane, cnt, nr, na);
-    const float vix = v[3 * i], viy = v[3 * i + 1], viz = v[3 * i + 2];
     {
+        NbrFetch f;
+        fetch_neighbours(L, pos4, i, lane, f);
+        float3 vj[kKmax / 32];
+        const float vix = v[3 * i], viy = v[3 * i + 1], viz = v[3 * i + 2];
+#pragma unroll
+        for (int k = 0; k < kKmax / 32; ++k)
+            if (lane + 32 * k < f.cnt) vj[k] = make_float3(v[3 * f.j[k]], v[3 * f.j[k] + 1], v[3 * f.j[k] + 2]);
+        store_neighbours<true>(f, s, lane, cnt, nr, na);
+#pragma unroll
+        for (int k = 0; k < kKmax / 32; ++k) {
+            const int q = lane + 32 * k;
+            if (q < cnt) {
+                const float4 d = s.d[q];
+                const float wx = vj[k].x - vix, wy = vj[k].y - viy, wz = vj[k].z - viz;
+                ts.w[q] = make_float4(wx, wy, wz, d.x * wx + d.y * wy + d.z * wz);
+            }
+        }
+        __syncwarp();
+    }
+    float out[12];
+    {   // radial: d/de of sum_j exp(-eta (r - R_k)^2) fc(r) = (-2 eta (r - R_k) fc + fc') exp(.) rdot
         const int h = lane >> 4, k = lane & 15;
         const float Rk = 0.9f + (float)k * (4.3f / 16.f);
+        float racc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int u = h; u < nr; u += 2) {
             const int q = s.rad[u];
-            const float4 d = s.d[q];
-            const int j = s.j[q];
-            const float r = d.w;
-            const float rdot = d.x * (v[3 * j] - vix) + d.y * (v[3 * j + 1] - viy) + d.z * (v[3 * j + 2] - viz);
-            const float x = r - Rk;
-            const float ex = __expf(-kEtaR * x * x);
-            accR[w][h][16 * s.el[q] + k] += ex * (-2.f * kEtaR * x * s.fc[q].x + s.fc[q].y) * rdot;
+            const float x = s.d[q].w - Rk;
+            const float ex = exp_neg(-kEtaR * x * x);
+            const float t = ex * (-2.f * kEtaR * x * s.fc[q].x + s.fc[q].y) * ts.w[q].w;
+            const int e = s.el[q];
+#pragma unroll
+            for (int ee = 0; ee < 4; ++ee)
+                if (ee == e) racc[ee] += t;
         }
+        float tot[4];
+#pragma unroll
+        for (int ee = 0; ee < 4; ++ee) tot[ee] = racc[ee] + __shfl_xor_sync(0xffffffffu, racc[ee], 16);
+        out[0] = h ? tot[1] : tot[0];
+        out[1] = h ? tot[3] : tot[2];
     }
-    {
-        const int m = lane >> 3, p = lane & 7;
+    {   // angular
+        const int t4 = lane >> 3, p = lane & 7;
         const float thp = (float)(2 * p + 1) * (kPi / 16.f);
         const float cp = cosf(thp), sp = sinf(thp);
-        const int ntrip = na * (na - 1) / 2;
-        for (int base = 0; base < ntrip; base += 32) {
-            const int t = base + lane;
-            if (t < ntrip) {
-                int a, b;
-                triplet_ab(t, na, a, b);
-                const int qa = s.ang[a], qb = s.ang[b];
-                const float4 dj = s.d[qa], dk = s.d[qb];
-                const int ja = s.j[qa], jb = s.j[qb];
-                const float rj = dj.w, rk = dk.w;
-                const float ujx = dj.x, ujy = dj.y, ujz = dj.z;
-                const float ukx = dk.x, uky = dk.y, ukz = dk.z;
-                const float wjx = v[3 * ja] - vix, wjy = v[3 * ja + 1] - viy, wjz = v[3 * ja + 2] - viz;
-                const float wkx = v[3 * jb] - vix, wky = v[3 * jb + 1] - viy, wkz = v[3 * jb + 2] - viz;
-                const float ct = ujx * ukx + ujy * uky + ujz * ukz;
-                const float rjd = ujx * wjx + ujy * wjy + ujz * wjz, rkd = ukx * wkx + uky * wky + ukz * wkz;
-                const float ctd = ((ukx - ct * ujx) * wjx + (uky - ct * ujy) * wjy + (ukz - ct * ujz) * wjz) / rj +
-                                  ((ujx - ct * ukx) * wkx + (ujy - ct * uky) * wky + (ujz - ct * ukz) * wkz) / rk;
-                const float cs = kAngScale * ct;
-                const float sn2 = sqrtf(1.f - cs * cs);
-                tcs[w][lane] = cs;
-                tsn[w][lane] = sn2;
-                tcot[w][lane] = cs / sn2;
-                tcsd[w][lane] = kAngScale * ctd;
-                const float fj = s.fc[qa].z, fk = s.fc[qb].z;
-                tC[w][lane] = fj * fk;
-                tCd[w][lane] = s.fc[qa].w * fk * rjd + fj * s.fc[qb].w * rkd;
-                const float ravg = 0.5f * (rj + rk), ravgd = 0.5f * (rjd + rkd);
+        int ne[4], stt[4], off[10];
 #pragma unroll
-                for (int mm = 0; mm < 4; ++mm) {
-                    const float x = ravg - (0.9f + (float)mm * 0.65f);
-                    const float B = __expf(-kEtaA * x * x);
-                    tB[w][lane][mm] = B;
-                    tBd[w][lane][mm] = -2.f * kEtaA * x * B * ravgd;
-                }
-                tP[w][lane] = pair_index(s.el[qa], s.el[qb]);
+        for (int e = 0; e < 4; ++e) ne[e] = s.nae[e];
+        stt[0] = 0;
+        stt[1] = ne[0];
+        stt[2] = stt[1] + ne[1];
+        stt[3] = stt[2] + ne[2];
+        int total = 0;
+#pragma unroll
+        for (int P = 0; P < 10; ++P) {
+            constexpr int e1s[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3}, e2s[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+            const int e1 = e1s[P], e2 = e2s[P];
+            const int n = e1 == e2 ? ne[e1] * (ne[e1] - 1) / 2 : ne[e1] * ne[e2];
+            if (lane == P) {
+                ts.type[P] = make_int4(total, n, stt[e1] | (stt[e2] << 8) | (ne[e2] << 16), e1 == e2 ? 1 : 0);
+                ts.rcp[P] = ne[e2] > 0 ? 1.f / (float)ne[e2] : 0.f;
             }
+            off[P] = total;
+            total += (n + 3) & ~3;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) ts.acc[k][lane] = 0.f;
+        __syncwarp();
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        int curP = -1;
+        const bool hi = (t4 & 2) != 0, lo = (t4 & 1) != 0;
+        auto flush = [&]() {
+            const float a0 = acc[0], a1 = acc[1], a2 = acc[2], a3 = acc[3];
+            float k0 = hi ? a2 : a0, k1 = hi ? a3 : a1;
+            const float s0 = hi ? a0 : a2, s1 = hi ? a1 : a3;
+            k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+            k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+            float mine = lo ? k1 : k0;
+            mine += __shfl_xor_sync(0xffffffffu, lo ? k0 : k1, 8);
+            ts.acc[curP][lane] += mine;
+#pragma unroll
+            for (int mm = 0; mm < 4; ++mm) acc[mm] = 0.f;
+        };
+        for (int base = 0; base < total; base += 32) {
+            const int slot = base + lane;
+            int P = 0;
+#pragma unroll
+            for (int k = 1; k < 10; ++k) P += slot >= off[k] ? 1 : 0;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f), qd = q, bq = q, bdq = q;
+            if (slot < total) {
+                const int4 ty = ts.type[P];
+                const int l = slot - ty.x;
+                if (l < ty.y) {
+                    const int a0 = ty.z & 255, b0 = (ty.z >> 8) & 255, c2 = ty.z >> 16;
+                    int a, b;
+                    if (ty.w) {
+                        triplet_ab(l, c2, a, b);
+                        a += a0;
+                        b += a0;
+                    } else {
+                        a = (int)(((float)l + 0.5f) * ts.rcp[P]);
+                        b = b0 + (l - a * c2);
+                        a += a0;
+                    }
+                    const int qa = s.ang[a], qb = s.ang[b];
+                    const float4 dj = s.d[qa], dk = s.d[qb], wj = ts.w[qa], wk = ts.w[qb];
+                    const float rj = dj.w, rk = dk.w;
+                    const float ct = dj.x * dk.x + dj.y * dk.y + dj.z * dk.z;
+                    const float ctd = ((dk.x - ct * dj.x) * wj.x + (dk.y - ct * dj.y) * wj.y + (dk.z - ct * dj.z) * wj.z) /
+                                          rj +
+                                      ((dj.x - ct * dk.x) * wk.x + (dj.y - ct * dk.y) * wk.y + (dj.z - ct * dk.z) * wk.z) /
+                                          rk;
+                    const float cs = kAngScale * ct;
+                    const float sn2 = sqrtf(1.f - cs * cs);
+                    const float fj = s.fc[qa].z, fk = s.fc[qb].z;
+                    q = make_float4(cs, sn2, kTwoPowM31 * fj * fk, 0.f);
+                    qd = make_float4(cs / sn2, 32.f * kAngScale * ctd,
+                                     kTwoPowM31 * (s.fc[qa].w * fk * wj.w + fj * s.fc[qb].w * wk.w), 0.f);
+                    const float ravg = 0.5f * (rj + rk), ravgd = 0.5f * (wj.w + wk.w);
+                    float bm[4], bdm[4];
+#pragma unroll
+                    for (int mm = 0; mm < 4; ++mm) {
+                        const float x = ravg - (0.9f + (float)mm * 0.65f);
+                        bm[mm] = __expf(-kEtaA * x * x);
+                        bdm[mm] = -2.f * kEtaA * x * bm[mm] * ravgd;
+                    }
+                    bq = make_float4(bm[0], bm[1], bm[2], bm[3]);
+                    bdq = make_float4(bdm[0], bdm[1], bdm[2], bdm[3]);
+                }
+            }
+            q.w = __int_as_float(P);   // empty slots of a run carry its type and contribute zero
+            ts.q[lane] = q;
+            ts.qd[lane] = qd;
+            ts.b[lane] = bq;
+            ts.bd[lane] = bdq;
             __syncwarp();
-            const int nt = min(32, ntrip - base);
-            for (int u = 0; u < nt; ++u) {
-                const float x = 1.f + tcs[w][u] * cp + tsn[w][u] * sp;
+            const int ng = min(32, total - base);   // a multiple of 4
+            for (int u = 0; u < ng; u += 4) {
+                const float4 qq = ts.q[u + t4], dd = ts.qd[u + t4];
+                const int Pu = __float_as_int(ts.q[u].w);
+                if (Pu != curP) {
+                    if (curP >= 0) flush();
+                    curP = Pu;
+                }
+                // A = 2^-31 x^32 and dA/dcos = 2^-31 32 x^31 (cos theta_p - cot sin theta_p), x = 1 + cos(theta - theta_p)
+                const float x = 1.f + qq.x * cp + qq.y * sp;
                 const float x2 = x * x, x4 = x2 * x2, x8 = x4 * x4, x16 = x8 * x8;
                 const float x31 = x16 * x8 * x4 * x2 * x;
-                const float A = kTwoPowM31 * x31 * x;
-                const float dA = kTwoPowM31 * 32.f * x31 * (cp - tcot[w][u] * sp);
-                const float B = tB[w][u][m], C = tC[w][u];
-                accA[w][32 * tP[w][u] + lane] += dA * tcsd[w][u] * B * C + A * (tBd[w][u][m] * C + B * tCd[w][u]);
+                const float A = x31 * x, dA = x31 * (cp - dd.x * sp);
+                const float cB = dA * dd.y * qq.z + A * dd.z;   // multiplies B_m
+                const float cBd = A * qq.z;                      // multiplies the tangent of B_m
+                const float4 bb = ts.b[u + t4], bd = ts.bd[u + t4];
+                acc[0] = fmaf(cB, bb.x, fmaf(cBd, bd.x, acc[0]));
+                acc[1] = fmaf(cB, bb.y, fmaf(cBd, bd.y, acc[1]));
+                acc[2] = fmaf(cB, bb.z, fmaf(cBd, bd.z, acc[2]));
+                acc[3] = fmaf(cB, bb.w, fmaf(cBd, bd.w, acc[3]));
             }
             __syncwarp();
         }
-    }
-    __syncwarp();
-    float *out = U + (size_t)L.row_of[i] * kNFeat;
-    float ov[kNFeat / 32];   // every shared read before the first (possibly aliasing) store
+        if (curP >= 0) flush();
+        __syncwarp();
 #pragma unroll
-    for (int k = 0; k < kNFeat / 32; ++k) {
-        const int f = 32 * k + lane;
-        ov[k] = f < 64 ? accR[w][0][f] + accR[w][1][f] : accA[w][f - 64];
+        for (int k = 0; k < 10; ++k) out[2 + k] = ts.acc[k][lane];
     }
+    float *row = U + (size_t)L.row_of[i] * kNFeat;
 #pragma unroll
-    for (int k = 0; k < kNFeat / 32; ++k) out[32 * k + lane] = ov[k];
+    for (int k = 0; k < kNFeat / 32; ++k) row[32 * k + lane] = out[k];
 }
 
 __global__ void k_learn_begin(LearnedDev L) {
