@@ -35,8 +35,9 @@ constexpr int kSplits = 8;     // row-range splits of the weight-matrix gradient
 constexpr int kVSplits = 64;   // block-range splits of the bias / output-weight gradients
 constexpr int kTrRows = 32;    // rows per block of the training MLP kernel (4 MMA n-tiles)
 // its BF16 row planes: G and U (hi, lo), then a1 and ta1 (hi, lo); bt2 and bh2 (hi, lo) and the FP32
-// s'(h1), s''(h1) t1 of the rows reuse the first
-constexpr int kTrSmem = (4 * kTrRows * (kNFeat + 8) + 4 * kTrRows * (kH1 + 8)) * 2;
+// s'(h1), s''(h1) t1 of the rows reuse the first; then each warp's ring of weight fragments (4 stages of
+// two 16 x 16 BF16 tiles)
+constexpr int kTrSmem = (4 * kTrRows * (kNFeat + 8) + 4 * kTrRows * (kH1 + 8) + 8 * 4 * 2 * 16 * 16) * 2;
 
 // ------------------------------------------------------------ batch layout
 
@@ -329,8 +330,8 @@ struct RowOut {
 //   layer 1'  bta1 = W2^T bt2, ba1 = W2^T bh2 (M = 256, K = 128)
 //             bt1 = s'(h1) bta1, bh1 = s''(h1) t1 bta1 + s'(h1) ba1
 // The rows sit in shared memory as BF16 [row][k] planes (the MMA's B operand,
-// read with ldmatrix); the A fragments (weight rows, K contiguous) come from
-// global memory, two k-steps ahead of their MMAs.  Warp w owns units
+// read with ldmatrix); the A fragments (weight rows, K contiguous) reach a
+// per-warp shared ring by cp.async three k-steps ahead of their MMAs.  Warp w owns units
 // 32 w .. 32 w + 31 in layers 1 and 1' and units 16 w .. 16 w + 15 in layer
 // 2; s'(h1) and s''(h1) t1 of its layer-1 fragments wait in shared memory
 // for layer 1'.
@@ -339,7 +340,6 @@ constexpr int kAs = kH1 + 8;
 constexpr int kBs = kH2 + 8;
 constexpr int kPlaneX = kTrRows * kXs, kPlaneA = kTrRows * kAs, kPlaneB = kTrRows * kBs;
 static_assert(4 * kPlaneB * 2 + 2 * kTrRows * kH1 * 4 <= 4 * kPlaneX * 2, "bt2 / bh2 planes and s', s'' t1 fit");
-static_assert(kTrSmem == (4 * kPlaneX + 4 * kPlaneA) * 2, "shared-memory size of the training MLP kernel");
 static_assert(kRowTile % kTrRows == 0, "a block's rows lie in one row tile (one element)");
 
 __device__ __forceinline__ uint32_t tr_smem_u32(const void *p) {
@@ -356,16 +356,6 @@ __device__ __forceinline__ void tr_frag_b2(const __nv_bfloat16 *plane, int ld, i
                  : "r"(tr_smem_u32(p)));
 }
 
-// The A fragment of rows m0 .. m0 + 15, columns k0 .. k0 + 15 of a row-major BF16 matrix in global memory.
-__device__ __forceinline__ void tr_frag_a(const __nv_bfloat16 *W, int ld, int m0, int k0, int lane, uint32_t (&a)[4]) {
-    const int g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16 *p = W + (size_t)(m0 + g) * ld + k0 + 2 * t;
-    a[0] = __ldg(reinterpret_cast<const unsigned int *>(p));
-    a[1] = __ldg(reinterpret_cast<const unsigned int *>(p + 8 * ld));
-    a[2] = __ldg(reinterpret_cast<const unsigned int *>(p + 8));
-    a[3] = __ldg(reinterpret_cast<const unsigned int *>(p + 8 * ld + 8));
-}
-
 __device__ __forceinline__ void tr_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
@@ -374,22 +364,64 @@ __device__ __forceinline__ void tr_mma(float (&d)[4], const uint32_t (&a)[4], ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// The weight (A) fragments travel through a per-warp ring of kTrRing k-steps in shared memory, filled by
+// 16-byte cp.async copies kTrRing - 1 k-steps ahead of their MMAs.  A stage holds MT m-tiles of 16 rows x 16
+// columns (32 bytes a row); the two 16-byte halves of rows 4..7 and 12..15 are swapped, so that the eight rows
+// an ldmatrix reads lie in eight different bank groups.
+constexpr int kTrRing = 4;
+constexpr int kTrStage = 2 * 16 * 16;   // BF16 elements of a stage (two m-tiles)
+
+static_assert(kTrSmem == (4 * kPlaneX + 4 * kPlaneA + 8 * kTrRing * kTrStage) * 2,
+              "shared-memory size of the training MLP kernel");
+
+__device__ __forceinline__ void tr_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tr_smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <int MT>
+__device__ __forceinline__ void tr_ring_fill(const __nv_bfloat16 *W, int ldw, int m0, int k0, __nv_bfloat16 *stage,
+                                             int lane) {
+#pragma unroll
+    for (int x = 0; x < MT; ++x) {
+        const int c = lane + 32 * x, i = c >> 5, row = (c & 31) >> 1, half = c & 1;
+        tr_cp16(stage + i * 256 + row * 16 + ((half ^ ((row >> 2) & 1)) << 3),
+                W + (size_t)(m0 + 16 * i + row) * ldw + k0 + 8 * half);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The A fragment of m-tile i of a stage (ldmatrix x4: rows 0-7 / 8-15, columns 0-7 / 8-15).
+__device__ __forceinline__ void tr_frag_a_ring(const __nv_bfloat16 *stage, int i, int lane, uint32_t (&a)[4]) {
+    const int mi = lane >> 3, r = (mi & 1) * 8 + (lane & 7), half = mi >> 1;
+    const __nv_bfloat16 *p = stage + i * 256 + r * 16 + ((half ^ ((r >> 2) & 1)) << 3);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(tr_smem_u32(p)));
+}
+
 // D_h += W (P0 + P1), D_t += W (P2 + P3) over K = 16 KS for MT m-tiles of W (rows m0 + 16 i) and the four
-// n-tiles of the block's rows; P0..P3 are consecutive [row][k] planes `plane` elements apart.
+// n-tiles of the block's rows; P0..P3 are consecutive [row][k] planes `plane` elements apart.  ring: the
+// warp's kTrRing stages.
 template <int MT, int KS>
 __device__ __forceinline__ void tr_gemm(const __nv_bfloat16 *W, int ldw, int m0, const __nv_bfloat16 *P, int ld,
-                                        int plane, int lane, float (&dh)[MT][4][4], float (&dt)[MT][4][4]) {
-    uint32_t a[3][MT][4];
+                                        int plane, __nv_bfloat16 *ring, int lane, float (&dh)[MT][4][4],
+                                        float (&dt)[MT][4][4]) {
+    __syncwarp();   // the ring's previous contents have been read by every lane
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < MT; ++i) tr_frag_a(W, ldw, m0 + 16 * i, 16 * s, lane, a[s][i]);
-#pragma unroll
+    for (int s = 0; s < kTrRing - 1; ++s) {
+        if (s < KS) tr_ring_fill<MT>(W, ldw, m0, 16 * s, ring + s * kTrStage, lane);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+#pragma unroll 1
     for (int ks = 0; ks < KS; ++ks) {
-        if (ks + 2 < KS) {
+        const int kn = ks + kTrRing - 1;
+        if (kn < KS) tr_ring_fill<MT>(W, ldw, m0, 16 * kn, ring + (kn % kTrRing) * kTrStage, lane);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kTrRing - 1) : "memory");
+        __syncwarp();
+        uint32_t a[MT][4];
 #pragma unroll
-            for (int i = 0; i < MT; ++i) tr_frag_a(W, ldw, m0 + 16 * i, 16 * (ks + 2), lane, a[(ks + 2) % 3][i]);
-        }
+        for (int i = 0; i < MT; ++i) tr_frag_a_ring(ring + (ks % kTrRing) * kTrStage, i, lane, a[i]);
 #pragma unroll
         for (int op = 0; op < 4; ++op) {
             uint32_t b[2][4];
@@ -400,9 +432,10 @@ __device__ __forceinline__ void tr_gemm(const __nv_bfloat16 *W, int ldw, int m0,
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float(&d)[4] = op < 2 ? dh[i][j] : dt[i][j];
-                    tr_mma(d, a[ks % 3][i], b[j >> 1][2 * (j & 1)], b[j >> 1][2 * (j & 1) + 1]);
+                    tr_mma(d, a[i], b[j >> 1][2 * (j & 1)], b[j >> 1][2 * (j & 1) + 1]);
                 }
         }
+        __syncwarp();   // every lane's ldmatrix of this stage is done before it is refilled
     }
 }
 
@@ -438,6 +471,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
     __nv_bfloat16 *sX = reinterpret_cast<__nv_bfloat16 *>(tr_smem);              // G hi, G lo, U hi, U lo
     __nv_bfloat16 *sA = sX + 4 * kPlaneX;                                        // a1 hi, lo, ta1 hi, lo
     __nv_bfloat16 *sB = sX;                                                      // bt2 hi, lo, bh2 hi, lo
+    __nv_bfloat16 *ring = sA + 4 * kPlaneA + (threadIdx.x >> 5) * kTrRing * kTrStage;   // the warp's weight ring
     __shared__ float sc[kTrRows];
     __shared__ int sreal[kTrRows];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -470,7 +504,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) h1[i][j][q] = t1[i][j][q] = 0.f;
-    tr_gemm<2, kNFeat / 16>(L.W1 + (size_t)e * kH1 * kNFeat, kNFeat, 32 * w, sX, kXs, kPlaneX, lane, h1, t1);
+    tr_gemm<2, kNFeat / 16>(L.W1 + (size_t)e * kH1 * kNFeat, kNFeat, 32 * w, sX, kXs, kPlaneX, ring, lane, h1, t1);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -510,7 +544,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) h2[0][j][q] = t2[0][j][q] = 0.f;
-        tr_gemm<1, kH1 / 16>(L.W2 + (size_t)e * kH2 * kH1, kH1, 16 * w, sA, kAs, kPlaneA, lane, h2, t2);
+        tr_gemm<1, kH1 / 16>(L.W2 + (size_t)e * kH2 * kH1, kH1, 16 * w, sA, kAs, kPlaneA, ring, lane, h2, t2);
         float vb2[2] = {0.f, 0.f}, vw3[2] = {0.f, 0.f};   // unit g and g + 8: the lane's rows, then the quad's
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -545,7 +579,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) bta1[i][j][q] = ba1[i][j][q] = 0.f;
-    tr_gemm<2, kH2 / 16>(L.W2T + (size_t)e * kH1 * kH2, kH2, 32 * w, sB, kBs, kPlaneB, lane, bta1, ba1);
+    tr_gemm<2, kH2 / 16>(L.W2T + (size_t)e * kH1 * kH2, kH2, 32 * w, sB, kBs, kPlaneB, ring, lane, bta1, ba1);
     float vb1[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // [i][unit g, g + 8]
 #pragma unroll
     for (int i = 0; i < 2; ++i)
