@@ -106,8 +106,8 @@ cudaError_t learned_mlp_tc(const LearnedDev &L, const MlpMaps &maps, uint32_t *s
 // over each element's row tiles, the splits summed in order into grad[e * per_element + off + ...]
 constexpr int kWgSplits = 24;
 struct WgradIn {
-    const float *bh1, *bt1, *G, *U;       // [rows][256], [rows][256], [rows][384], [rows][384]
-    const float *bh2, *bt2, *a1, *ta1;    // [rows][128], [rows][128], [rows][256], [rows][256]
+    const __nv_bfloat16 *bh1, *bt1, *G, *U;   // BF16 [rows][256], [rows][256], [rows][384], [rows][384]
+    const __nv_bfloat16 *bh2, *bt2, *a1, *ta1;  // BF16 [rows][128], [rows][128], [rows][256], [rows][256]
     const int *atom_of, *tile_el, *n_live;
     int tiles_max;
     int *etiles;                          // scratch [4][tiles_max]

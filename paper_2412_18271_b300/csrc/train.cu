@@ -310,10 +310,13 @@ __device__ __forceinline__ float tr_dds(float z) { return z >= 0.f ? 0.f : 10.f 
 // c s(h2) - s'(h2) t2 (W3) and c (b3).
 constexpr int kVb1 = 0, kVb2 = kH1, kVW3 = kH1 + kH2, kVb3 = kH1 + 2 * kH2, kVLen = kVb3 + 1;
 
+// The row kernel's outputs for the weight-gradient GEMMs, rounded to BF16 (their operand type), and the
+// per-block vector-gradient partials.
 struct RowOut {
-    float *bh1, *bt1, *a1, *ta1;   // [rows][256]
-    float *bh2, *bt2;              // [rows][128]
-    float *vpart;                  // [rows / kTrRows][kVLen]
+    __nv_bfloat16 *bh1, *bt1, *a1, *ta1;   // [rows][256]
+    __nv_bfloat16 *bh2, *bt2;              // [rows][128]
+    __nv_bfloat16 *u16;                    // [rows][384]: the tangents U
+    float *vpart;                          // [rows / kTrRows][kVLen]
 };
 
 // kTrRows rows of one element per block, 8 warps, on the tensor cores through
@@ -439,11 +442,12 @@ __device__ __forceinline__ void tr_gemm(const __nv_bfloat16 *W, int ldw, int m0,
     }
 }
 
-// x as the BF16 pair (hi, lo) at [r][c] of two planes.
-__device__ __forceinline__ void tr_put_pair(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int idx, float x) {
+// x as the BF16 pair (hi, lo) at [r][c] of two planes; returns hi = bf16(x).
+__device__ __forceinline__ __nv_bfloat16 tr_put_pair(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int idx, float x) {
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     hi[idx] = h;
     lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+    return h;
 }
 
 // Two per-lane column sums (units g and g + 8 of a fragment) summed over the four lanes of the quad
@@ -489,11 +493,13 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
         const float4 gv = re ? *reinterpret_cast<const float4 *>(L.G32 + (size_t)(r0 + r) * kNFeat + f) : z;
         const float4 uv = re ? *reinterpret_cast<const float4 *>(U + (size_t)(r0 + r) * kNFeat + f) : z;
         const float gs[4] = {gv.x, gv.y, gv.z, gv.w}, us[4] = {uv.x, uv.y, uv.z, uv.w};
+        __align__(8) __nv_bfloat16 uh[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             tr_put_pair(sX, sX + kPlaneX, r * kXs + f + c, gs[c]);
-            tr_put_pair(sX + 2 * kPlaneX, sX + 3 * kPlaneX, r * kXs + f + c, us[c]);
+            uh[c] = tr_put_pair(sX + 2 * kPlaneX, sX + 3 * kPlaneX, r * kXs + f + c, us[c]);
         }
+        *reinterpret_cast<uint2 *>(o.u16 + (size_t)(r0 + r) * kNFeat + f) = *reinterpret_cast<const uint2 *>(uh);
     }
     __syncthreads();
     // ---- layer 1: units 32 w + 16 i + g (+ 8), rows 8 j + 2 t4 (+ 1)
@@ -516,10 +522,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
                 const int r = 8 * j + 2 * t4 + (q & 1);
                 const float h = h1[i][j][q] + b, a1 = tr_s(h), ta1 = tr_ds(h) * t1[i][j][q];
                 h1[i][j][q] = h;
-                o.a1[(size_t)(r0 + r) * kH1 + u] = a1;
-                o.ta1[(size_t)(r0 + r) * kH1 + u] = ta1;
-                tr_put_pair(sA, sA + kPlaneA, r * kAs + u, a1);
-                tr_put_pair(sA + 2 * kPlaneA, sA + 3 * kPlaneA, r * kAs + u, ta1);
+                o.a1[(size_t)(r0 + r) * kH1 + u] = tr_put_pair(sA, sA + kPlaneA, r * kAs + u, a1);
+                o.ta1[(size_t)(r0 + r) * kH1 + u] = tr_put_pair(sA + 2 * kPlaneA, sA + 3 * kPlaneA, r * kAs + u, ta1);
             }
         }
     __syncthreads();
@@ -558,14 +562,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
                 const float d1 = tr_ds(h);
                 const float bt2 = -w3 * d1;
                 const float bh2 = -w3 * tr_dds(h) * tt + cr * w3 * d1;
-                o.bt2[(size_t)(r0 + r) * kH2 + v] = bt2;
-                o.bh2[(size_t)(r0 + r) * kH2 + v] = bh2;
                 if (sreal[r]) {
                     vb2[q >> 1] += bh2;
                     vw3[q >> 1] += cr * tr_s(h) - d1 * tt;
                 }
-                tr_put_pair(sB, sB + kPlaneB, r * kBs + v, bt2);
-                tr_put_pair(sB + 2 * kPlaneB, sB + 3 * kPlaneB, r * kBs + v, bh2);
+                o.bt2[(size_t)(r0 + r) * kH2 + v] = tr_put_pair(sB, sB + kPlaneB, r * kBs + v, bt2);
+                o.bh2[(size_t)(r0 + r) * kH2 + v] = tr_put_pair(sB + 2 * kPlaneB, sB + 3 * kPlaneB, r * kBs + v, bh2);
             }
         }
         tr_quad_sums(vb2, vw3, o.vpart + (size_t)blockIdx.x * kVLen, kVb2 + 16 * w + g, kVW3 + 16 * w + g, t4);
@@ -592,8 +594,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train(LearnedDev L, const float 
                 const int idx = r * kH1 + (u ^ ((r & 7) << 2));
                 const float d1 = sD[idx], dd = sD[kTrRows * kH1 + idx];
                 const float bh1 = dd * bta1[i][j][q] + d1 * ba1[i][j][q];
-                o.bt1[(size_t)(r0 + r) * kH1 + u] = d1 * bta1[i][j][q];
-                o.bh1[(size_t)(r0 + r) * kH1 + u] = bh1;
+                o.bt1[(size_t)(r0 + r) * kH1 + u] = __float2bfloat16_rn(d1 * bta1[i][j][q]);
+                o.bh1[(size_t)(r0 + r) * kH1 + u] = __float2bfloat16_rn(bh1);
                 if (sreal[r]) vb1[i][q >> 1] += bh1;
             }
         }
@@ -793,6 +795,7 @@ int mdpf_trainer_create(const mdpf_train_params *p, mdpf_trainer **out) {
     TA(t->ro.ta1, R * kH1);
     TA(t->ro.bh2, R * kH2);
     TA(t->ro.bt2, R * kH2);
+    TA(t->ro.u16, R * kNFeat);
     TA(t->ro.vpart, (R / kTrRows) * kVLen);
     TA(t->d_part, (size_t)kSplits * 4 * kH1 * kNFeat);
     static_assert((size_t)kWgSplits * (kH1 * kNFeat + kH2 * kH1) <= (size_t)kSplits * 4 * kH1 * kNFeat,
@@ -925,7 +928,7 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     // 6. weight-matrix gradients on the tensor cores (K splits over each element's row tiles, summed in
     //    order); the bias and output-weight gradients from the row kernel's per-block column sums, summed by
     //    split in block order, then over the splits in order
-    WgradIn wg{t->ro.bh1, t->ro.bt1, L.G32, t->d_U, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1,
+    WgradIn wg{t->ro.bh1, t->ro.bt1, L.G16, t->ro.u16, t->ro.bh2, t->ro.bt2, t->ro.a1, t->ro.ta1,
                L.atom_of, L.tile_el, L.n_tiles_live, t->tiles_max, t->d_etiles, t->d_wsplit, t->d_part,
                d_grad, kPPE, kOW1, kOW2, t->d_status};
     ce = learned_wgrad_tc(wg, s);

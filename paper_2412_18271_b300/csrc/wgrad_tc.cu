@@ -13,10 +13,10 @@
 // tile count and summed afterwards in split order, so the result is
 // reproducible bit for bit.
 //
-// The row arrays are FP32 [rows][width]: the operands are MN-major.  The
-// eight producer warps read them coalesced (one output row or column per
-// thread, 64 rows per K chunk), round to BF16 and write them transposed into
-// the 128-byte-swizzled K-major layout (8-row x 128-byte atoms, the 16-byte
+// The row arrays are BF16 [rows][width] (rounded where they are produced):
+// the operands are MN-major.  The eight producer warps read them coalesced
+// (one output row or column per thread, 64 rows per K chunk) and write them
+// transposed into the 128-byte-swizzled K-major layout (8-row x 128-byte atoms, the 16-byte
 // unit index XOR-ed with the row index mod 8) through a three-stage ring; rows
 // past a frame's atoms are zero.  One thread of warp 8 issues
 // tcgen05.mma kind::f16 (BF16 x BF16 -> FP32, M = N = 128) into 128 TMEM
@@ -44,8 +44,8 @@ enum { W_FULL = 0, W_EMPTY = kWgStages, W_ACC = 2 * kWgStages, W_DRAIN = 2 * kWg
 static_assert(8 * (W_DRAIN + 1) <= 64, "barrier block");
 
 struct WgProblem {
-    const float *A[2];   // [rows][M]: the two terms
-    const float *B[2];   // [rows][N]
+    const __nv_bfloat16 *A[2];   // [rows][M]: the two terms
+    const __nv_bfloat16 *B[2];   // [rows][N]
     int M, N;
     int off;             // offset of the gradient block within one element's parameters
 };
@@ -184,25 +184,27 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_wgrad_tc(WgArgs a) {
             const int term = (c >> 1) & 1, r0 = tl * kRowTile + (c & 1) * 64;
             const unsigned int mk0 = __ballot_sync(0xffffffffu, a.atom_of[r0 + lane] >= 0);
             const unsigned int mk1 = __ballot_sync(0xffffffffu, a.atom_of[r0 + 32 + lane] >= 0);
-            const float *src = (isA ? P.A[term] + m0 : P.B[term] + n0) + (size_t)r0 * stride + row;
+            const unsigned short *src =
+                reinterpret_cast<const unsigned short *>(isA ? P.A[term] + m0 : P.B[term] + n0) + (size_t)r0 * stride +
+                row;
             unsigned char *dst = sm + s * kWgStage + (isA ? 0 : 16384) + row * 128;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const unsigned int mk = half ? mk1 : mk0;
-                float x[32];
+                uint32_t x[32];   // BF16 bit patterns (zero on padding rows)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) x[j] = src[(size_t)(32 * half + j) * stride];
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    if (!((mk >> j) & 1u)) x[j] = 0.f;
+                    if (!((mk >> j) & 1u)) x[j] = 0u;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int u = 4 * half + q;
                     uint4 w;
-                    w.x = pack_bf16(x[8 * q + 0], x[8 * q + 1]);
-                    w.y = pack_bf16(x[8 * q + 2], x[8 * q + 3]);
-                    w.z = pack_bf16(x[8 * q + 4], x[8 * q + 5]);
-                    w.w = pack_bf16(x[8 * q + 6], x[8 * q + 7]);
+                    w.x = x[8 * q + 0] | (x[8 * q + 1] << 16);
+                    w.y = x[8 * q + 2] | (x[8 * q + 3] << 16);
+                    w.z = x[8 * q + 4] | (x[8 * q + 5] << 16);
+                    w.w = x[8 * q + 6] | (x[8 * q + 7] << 16);
                     *reinterpret_cast<uint4 *>(dst + ((u ^ (row & 7)) << 4)) = w;
                 }
             }
