@@ -127,71 +127,35 @@ __global__ void k_tr_pos(const double *pos, int n, float4 *pos4) {
     if (a < n) pos4[a] = make_float4((float)pos[3 * a], (float)pos[3 * a + 1], (float)pos[3 * a + 2], 0.f);
 }
 
-// Neighbours within the atom's own frame, brute force, ascending.  A warp
-// takes kNbGroup consecutive atoms; when they lie in one frame each j-chunk
-// of the frame is loaded once for all of them (else atom by atom).  Same
-// FP32 predicate and order either way.
-constexpr int kNbGroup = 8;
-
+// Neighbours within the atom's own frame, brute force, ascending: one thread
+// per atom, each walking its frame's atoms in index order and appending the
+// ones within the list radius to its own row (the FP32 predicate evaluated
+// with explicitly rounded operations, so no contraction changes it).  The
+// threads of a warp mostly share a frame, so each j position is one
+// broadcast load.
 __device__ __forceinline__ bool tr_in_list(const float4 &pi, const float4 &pj, float rc2) {
     const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < rc2;
 }
 
-__global__ void k_tr_nb(LearnedDev L, const float4 *pos4, int N, uint32_t *status) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int i0 = w * kNbGroup;
-    if (i0 >= L.n) return;
-    const int i1 = min(i0 + kNbGroup, L.n);
-    const unsigned int below = (1u << lane) - 1u;
-    if (i1 - i0 == kNbGroup && i0 / N == (i1 - 1) / N) {
-        const int f0 = (i0 / N) * N;
-        float4 pi[kNbGroup];
-        int m[kNbGroup];
-#pragma unroll
-        for (int k = 0; k < kNbGroup; ++k) {
-            pi[k] = pos4[i0 + k];
-            m[k] = 0;
-        }
-        for (int j0 = f0; j0 < f0 + N; j0 += 32) {
-            const int j = j0 + lane;
-            const bool ok = j < f0 + N;
-            const float4 pj = ok ? pos4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < kNbGroup; ++k) {
-                const bool in = ok && j != i0 + k && tr_in_list(pi[k], pj, L.rc_list2);
-                const unsigned int bal = __ballot_sync(0xffffffffu, in);
-                const int q = m[k] + __popc(bal & below);
-                if (in && q < kKmax) L.nb_idx[(size_t)(i0 + k) * kKmax + q] = j;
-                m[k] += __popc(bal);
-            }
-        }
-        if (lane < kNbGroup) {
-            int mm = m[0];
-#pragma unroll
-            for (int k = 1; k < kNbGroup; ++k) mm = lane == k ? m[k] : mm;
-            L.nb_count[i0 + lane] = min(mm, kKmax);
-            if (mm > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
-        }
-        return;
-    }
-    for (int i = i0; i < i1; ++i) {
-        const int f0 = (i / N) * N;
-        const float4 pi = pos4[i];
-        int m = 0;
-        for (int j0 = f0; j0 < f0 + N; j0 += 32) {
-            const int j = j0 + lane;
-            const bool in = j < f0 + N && j != i && tr_in_list(pi, pos4[j < f0 + N ? j : f0], L.rc_list2);
-            const unsigned int bal = __ballot_sync(0xffffffffu, in);
-            const int q = m + __popc(bal & below);
-            if (in && q < kKmax) L.nb_idx[(size_t)i * kKmax + q] = j;
-            m += __popc(bal);
-        }
-        if (lane == 0) {
-            L.nb_count[i] = min(m, kKmax);
-            if (m > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+__global__ void __launch_bounds__(256) k_tr_nb(LearnedDev L, const float4 *pos4, int N, uint32_t *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const int f0 = (i / N) * N;
+    const float4 pi = pos4[i];
+    const float rc2 = L.rc_list2;
+    int *row = L.nb_idx + (size_t)i * kKmax;
+    int m = 0;
+#pragma unroll 4
+    for (int j = f0; j < f0 + N; ++j) {
+        const bool in = j != i && tr_in_list(pi, __ldg(&pos4[j]), rc2);
+        if (in) {
+            if (m < kKmax) row[m] = j;
+            ++m;
         }
     }
+    L.nb_count[i] = min(m, kKmax);
+    if (m > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
 }
 
 // BF16 weights (and their transposes) and contiguous FP32 bias / output vectors from the master parameters.
@@ -904,7 +868,7 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     // 2. positions, neighbours, weights
     k_tr_pos<<<(n + 255) / 256, 256, 0, s>>>(d_pos, n, t->d_pos4);
     cudaMemsetAsync(t->d_status, 0, sizeof(uint32_t), s);
-    k_tr_nb<<<((n + kNbGroup - 1) / kNbGroup * 32 + 255) / 256, 256, 0, s>>>(L, t->d_pos4, N, t->d_status);
+    k_tr_nb<<<(n + 255) / 256, 256, 0, s>>>(L, t->d_pos4, N, t->d_status);
     k_tr_weights<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(
         d_params, const_cast<__nv_bfloat16 *>(L.W1), const_cast<__nv_bfloat16 *>(L.W1T),
         const_cast<__nv_bfloat16 *>(L.W2), const_cast<__nv_bfloat16 *>(L.W2T), const_cast<float *>(L.b1),
