@@ -325,6 +325,59 @@ __global__ void __launch_bounds__(kNbThreads) k_nb_all(LearnedDev L, const float
     }
 }
 
+// Rows of small systems (n <= kNbSmallMax) by brute force, one warp per atom:
+// every j != i in index order, 32 at a time, with the row predicate of the
+// cell-list build (so the same rows, ascending by construction).  One plain
+// launch with no grid barrier: below a few hundred atoms the four phases of
+// the cell-list build cost more than the O(n^2) scan.  The last block to
+// finish (an arrival count, no waiting) clears the rebuild request and counts
+// the build.
+constexpr int kNbSmallMax = 512;
+
+__global__ void __launch_bounds__(kNbThreads) k_nb_small(LearnedDev L, const float4 *pos4, uint32_t *status,
+                                                          int forced) {
+    if (!forced && L.lflags[0] == 0u) return;   // the same decision in every block
+    __shared__ int s_max[kNbThreads / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int i = blockIdx.x * (kNbThreads / 32) + wib;
+    int m = 0;
+    if (i < L.n) {
+        const float4 pi = pos4[i];
+        int *out = L.nb_idx + (size_t)i * kKmax;
+        for (int j0 = 0; j0 < L.n; j0 += 32) {
+            const int j = j0 + lane;
+            bool in = false;
+            if (j < L.n && j != i) {
+                const float4 pj = pos4[j];
+                const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+                in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < L.rc_list2;
+            }
+            const unsigned int bal = __ballot_sync(0xffffffffu, in);
+            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+            if (in && pos < kKmax) out[pos] = j;
+            m += __popc(bal);
+        }
+        if (lane == 0) {
+            L.nb_count[i] = min(m, kKmax);
+            L.pos_build[i] = pi;
+        }
+    }
+    if (lane == 0) s_max[wib] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int mx = 0;
+        for (int w = 0; w < kNbThreads / 32; ++w) mx = max(mx, s_max[w]);
+        if (mx > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
+        atomicMax((unsigned long long *)&L.lcount[2], (unsigned long long)min(mx, kKmax + 1));
+        __threadfence();   // this block's read of the request precedes its arrival
+        if (atomicAdd(&L.nb_bar[2], 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            L.nb_bar[2] = 0ull;
+            L.lflags[0] = 0u;
+            L.lcount[0] += 1;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ features
 
 constexpr int kFeatWarps = 2;   // warps (atoms) per block of k_features ...
@@ -787,6 +840,10 @@ int learned_nb_grid() {
 cudaError_t learned_neighbors(const LearnedDev &L, const float4 *pos4, bool forced, uint32_t *status,
                               cudaStream_t s) {
     int f = forced ? 1 : 0;
+    if (L.n <= kNbSmallMax) {
+        k_nb_small<<<(L.n + kNbThreads / 32 - 1) / (kNbThreads / 32), kNbThreads, 0, s>>>(L, pos4, status, f);
+        return cudaGetLastError();
+    }
     long long limit = 1000000000LL;   // 1 s per barrier wait
     const int want = (L.n + kNbThreads / 32 - 1) / (kNbThreads / 32);   // one warp per atom in the row phase
     const int grid = want < L.nb_grid ? want : L.nb_grid;

@@ -44,7 +44,7 @@ struct LearnedDev {
     unsigned int *bbox;          // [6] ordered-int min/max (empty box between builds)
     long long *bmom;             // [8][6] fixed-point sums of u = x - x0 and u^2 per axis, x0 = atom 0, spread
                                  // over 8 copies (zero between builds)
-    unsigned long long *nb_bar;  // [2] grid-barrier arrival counter, base of the next build
+    unsigned long long *nb_bar;  // [3] grid-barrier arrival counter, base of the next build; small-build arrivals
     int nb_grid;                 // blocks of the cooperative neighbour kernel
     // features and MLP
     __nv_bfloat16 *G16;          // [n_rows][384] GEMM input

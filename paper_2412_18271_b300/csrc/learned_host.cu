@@ -258,7 +258,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LA(L.grid, 1);
     LA(L.bbox, 8);
     LA(L.bmom, 48);
-    LA(L.nb_bar, 2);
+    LA(L.nb_bar, 3);
     LA(L.G16, (size_t)n_rows * kNFeat);
     LA(L.G32, (size_t)n_rows * kNFeat);
     {   // dE/dG: room for FP32 (the FP32-operand variant), BF16 otherwise
@@ -321,7 +321,7 @@ int learned_create(mdpf_ctx *c, const mdpf_topology *t, const mdpf_params *prm) 
     LC(cudaMemset(L.lflags, 0, sizeof(unsigned int) * 4));
     LC(cudaMemset(L.lcount, 0, sizeof(long long) * 4));
     LC(cudaMemset(L.nb_count, 0, sizeof(int) * n));
-    LC(cudaMemset(L.nb_bar, 0, sizeof(unsigned long long) * 2));
+    LC(cudaMemset(L.nb_bar, 0, sizeof(unsigned long long) * 3));
     LC(cudaMemset(L.bmom, 0, sizeof(long long) * 48));
     {
         const unsigned int empty_box[8] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u, 0u};
