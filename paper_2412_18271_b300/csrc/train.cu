@@ -130,30 +130,55 @@ __global__ void k_tr_pos(const double *pos, int n, float4 *pos4) {
 // Neighbours within the atom's own frame, brute force, ascending: one thread
 // per atom, each walking its frame's atoms in index order and appending the
 // ones within the list radius to its own row (the FP32 predicate evaluated
-// with explicitly rounded operations, so no contraction changes it).  The
-// threads of a warp mostly share a frame, so each j position is one
-// broadcast load.
+// with explicitly rounded operations, so no contraction changes it).  When a
+// block's atoms share one frame, the frame's positions pass through shared
+// memory 256 at a time; a block that straddles two frames reads them from
+// global memory.
 __device__ __forceinline__ bool tr_in_list(const float4 &pi, const float4 &pj, float rc2) {
     const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < rc2;
 }
 
-__global__ void __launch_bounds__(256) k_tr_nb(LearnedDev L, const float4 *pos4, int N, uint32_t *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L.n) return;
-    const int f0 = (i / N) * N;
-    const float4 pi = pos4[i];
+constexpr int kTrNbThreads = 256;
+
+__global__ void __launch_bounds__(kTrNbThreads) k_tr_nb(LearnedDev L, const float4 *pos4, int N, uint32_t *status) {
+    __shared__ float4 s_pj[kTrNbThreads];
+    const int a0 = blockIdx.x * kTrNbThreads, t = threadIdx.x;
+    const int i = a0 + t;
+    const int alast = min(a0 + kTrNbThreads, L.n) - 1;
+    const bool one_frame = a0 / N == alast / N;   // the same in every thread of the block
+    const bool live = i < L.n;
+    const int f0 = ((live ? i : alast) / N) * N;
+    const float4 pi = pos4[live ? i : alast];
     const float rc2 = L.rc_list2;
-    int *row = L.nb_idx + (size_t)i * kKmax;
+    int *row = L.nb_idx + (size_t)(live ? i : 0) * kKmax;
     int m = 0;
-#pragma unroll 4
-    for (int j = f0; j < f0 + N; ++j) {
-        const bool in = j != i && tr_in_list(pi, __ldg(&pos4[j]), rc2);
-        if (in) {
-            if (m < kKmax) row[m] = j;
-            ++m;
+    if (one_frame) {
+        for (int c0 = 0; c0 < N; c0 += kTrNbThreads) {
+            const int cn = min(kTrNbThreads, N - c0);
+            __syncthreads();
+            if (t < cn) s_pj[t] = pos4[f0 + c0 + t];
+            __syncthreads();
+            if (live) {
+#pragma unroll 8
+                for (int k = 0; k < cn; ++k) {
+                    const int j = f0 + c0 + k;
+                    if (j != i && tr_in_list(pi, s_pj[k], rc2)) {
+                        if (m < kKmax) row[m] = j;
+                        ++m;
+                    }
+                }
+            }
+        }
+    } else if (live) {
+        for (int j = f0; j < f0 + N; ++j) {
+            if (j != i && tr_in_list(pi, pos4[j], rc2)) {
+                if (m < kKmax) row[m] = j;
+                ++m;
+            }
         }
     }
+    if (!live) return;
     L.nb_count[i] = min(m, kKmax);
     if (m > kKmax) atomicOr(status, MDPF_STATUS_NEIGHBOR_OVERFLOW);
 }
@@ -868,7 +893,7 @@ int mdpf_trainer_loss_grad(mdpf_trainer *t, const float *d_params, float *d_grad
     // 2. positions, neighbours, weights
     k_tr_pos<<<(n + 255) / 256, 256, 0, s>>>(d_pos, n, t->d_pos4);
     cudaMemsetAsync(t->d_status, 0, sizeof(uint32_t), s);
-    k_tr_nb<<<(n + 255) / 256, 256, 0, s>>>(L, t->d_pos4, N, t->d_status);
+    k_tr_nb<<<(n + kTrNbThreads - 1) / kTrNbThreads, kTrNbThreads, 0, s>>>(L, t->d_pos4, N, t->d_status);
     k_tr_weights<<<dim3((kH1 * kNFeat + 255) / 256, 4), 256, 0, s>>>(
         d_params, const_cast<__nv_bfloat16 *>(L.W1), const_cast<__nv_bfloat16 *>(L.W1T),
         const_cast<__nv_bfloat16 *>(L.W2), const_cast<__nv_bfloat16 *>(L.W2T), const_cast<float *>(L.b1),
