@@ -169,9 +169,10 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_wgrad_tc(WgArgs a) {
     const uint32_t tmem = *s_tmem;
 
     if (warp < kWgProd) {
-        // ---------------- producers: thread = one row of A (tid < 128) or of B, 64 K values per chunk
+        // ---------------- producers: thread = two adjacent rows of A (tid < 128) or of B and one half (32) of
+        // the chunk's 64 K values; each 4-byte load brings both rows' values of one K index
         const bool isA = tid < 128;
-        const int row = tid & 127;
+        const int pr = tid & 63, kh = (tid >> 6) & 1;
         const int stride = isA ? P.M : P.N;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
@@ -182,29 +183,30 @@ __global__ void __launch_bounds__(kWgThreads, 2) k_wgrad_tc(WgArgs a) {
             }
             const int tl = a.etiles[e * a.tiles_max + spl.y + (c >> 2)];
             const int term = (c >> 1) & 1, r0 = tl * kRowTile + (c & 1) * 64;
-            const unsigned int mk0 = __ballot_sync(0xffffffffu, a.atom_of[r0 + lane] >= 0);
-            const unsigned int mk1 = __ballot_sync(0xffffffffu, a.atom_of[r0 + 32 + lane] >= 0);
-            const unsigned short *src =
-                reinterpret_cast<const unsigned short *>(isA ? P.A[term] + m0 : P.B[term] + n0) + (size_t)r0 * stride +
-                row;
-            unsigned char *dst = sm + s * kWgStage + (isA ? 0 : 16384) + row * 128;
+            const unsigned int mk = __ballot_sync(0xffffffffu, a.atom_of[r0 + 32 * kh + lane] >= 0);
+            const uint32_t *src = reinterpret_cast<const uint32_t *>((isA ? P.A[term] + m0 : P.B[term] + n0) +
+                                                                     (size_t)(r0 + 32 * kh) * stride + 2 * pr);
+            uint32_t x[32];   // BF16 bit patterns of rows 2 pr (low half) and 2 pr + 1 (high half)
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const unsigned int mk = half ? mk1 : mk0;
-                uint32_t x[32];   // BF16 bit patterns (zero on padding rows)
+            for (int j = 0; j < 32; ++j) x[j] = src[(size_t)j * (stride / 2)];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) x[j] = src[(size_t)(32 * half + j) * stride];
+            for (int j = 0; j < 32; ++j)
+                if (!((mk >> j) & 1u)) x[j] = 0u;   // rows past a frame's atoms are zero
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (!((mk >> j) & 1u)) x[j] = 0u;
+            for (int h = 0; h < 2; ++h) {
+                const int row = 2 * pr + h;
+                unsigned char *dst = sm + s * kWgStage + (isA ? 0 : 16384) + row * 128;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int u = 4 * half + q;
+                    const int u = 4 * kh + q;
+                    uint32_t v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = h ? (x[8 * q + k] >> 16) : (x[8 * q + k] & 0xFFFFu);
                     uint4 w;
-                    w.x = x[8 * q + 0] | (x[8 * q + 1] << 16);
-                    w.y = x[8 * q + 2] | (x[8 * q + 3] << 16);
-                    w.z = x[8 * q + 4] | (x[8 * q + 5] << 16);
-                    w.w = x[8 * q + 6] | (x[8 * q + 7] << 16);
+                    w.x = v[0] | (v[1] << 16);
+                    w.y = v[2] | (v[3] << 16);
+                    w.z = v[4] | (v[5] << 16);
+                    w.w = v[6] | (v[7] << 16);
                     *reinterpret_cast<uint4 *>(dst + ((u ^ (row & 7)) << 4)) = w;
                 }
             }
