@@ -399,8 +399,8 @@ static int enqueue_provider(mdpf_ctx *c, const double *x, unsigned long long *fx
 // Force evaluation into (fx, efx) at the FP32 positions pos4 (learned mode:
 // with a fresh neighbour list).
 static int enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *fx, unsigned long long *efx,
-                          uint32_t *status, bool energy, cudaStream_t s) {
-    launch_zero_fx(fx, 3 * c->n_pad, efx, s);
+                          uint32_t *status, bool energy, cudaStream_t s, bool zeroed = false) {
+    if (!zeroed) launch_zero_fx(fx, 3 * c->n_pad, efx, s);
     if (c->mode == MDPF_MODE_LEARNED) return learned_enqueue_forces(c, pos4, fx, efx, status, true, false, s);
     PlainDev p = plain_dev(c, pos4);
     p.status = status;
@@ -413,16 +413,15 @@ int mdpf_compute_device(mdpf_ctx *c, const double *d_pos, double *d_energy, floa
     GUARD(c);
     if (!d_pos) return fail(c, MDPF_ERR_INVALID_ARG, "d_pos is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    launch_pos4_from_x(d_pos, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, s);
+    // positions and cleared sums in one launch; forces, energy terms and the caller's energy in one
+    launch_eval_begin(d_pos, c->d_charge_s, c->d_pos4_c, c->n, c->n_pad, c->d_fx_c, 3 * c->n_pad, c->d_efx_c, s);
     {
         const int rc = c->mode == MDPF_MODE_CALLBACK
-                           ? enqueue_provider(c, d_pos, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s)
-                           : enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s);
+                           ? enqueue_provider(c, d_pos, c->d_fx_c, c->d_efx_c, c->d_status + 1, false, s)
+                           : enqueue_forces(c, c->d_pos4_c, c->d_fx_c, c->d_efx_c, c->d_status + 1, true, s, true);
         if (rc != MDPF_OK) return rc;
     }
-    if (d_forces) launch_fx_to_forces(c->d_fx_c, c->n, nullptr, d_forces, s);
-    launch_energy_out(c->d_efx_c, c->d_scalar + 2, s);
-    if (d_energy) CK(c, cudaMemcpyAsync(d_energy, c->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_eval_end(c->d_fx_c, c->n, d_forces, c->d_efx_c, c->d_scalar + 2, d_energy, s);
     CK(c, cudaGetLastError());
     return MDPF_OK;
 }

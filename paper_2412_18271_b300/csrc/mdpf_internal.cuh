@@ -200,6 +200,11 @@ void launch_nonbonded(const PlainDev &p, unsigned long long *fx, unsigned long l
                       cudaStream_t s);
 void launch_fx_to_forces(const unsigned long long *fx, int n, double *f64, float *f32, cudaStream_t s);
 void launch_energy_out(const unsigned long long *efx, double *out6, cudaStream_t s);
+// a single evaluation's first and last launches: positions and cleared sums; forces, energy terms and total
+void launch_eval_begin(const double *x, const float *qs, float4 *pos4, int n, int n_pad, unsigned long long *fx,
+                       int n3, unsigned long long *efx, cudaStream_t s);
+void launch_eval_end(const unsigned long long *fx, int n, float *f32, const unsigned long long *efx, double *out6,
+                     double *energy, cudaStream_t s);
 void launch_kick_drift(mdpf_ctx *ctx, cudaStream_t s);
 void launch_kick_finish(mdpf_ctx *ctx, bool energy, cudaStream_t s);
 void launch_kinetic(mdpf_ctx *ctx, cudaStream_t s);

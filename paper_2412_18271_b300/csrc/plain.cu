@@ -48,6 +48,36 @@ __global__ void k_energy_out(const unsigned long long *efx, double *out) {
                  fx_val(efx[E_LEARN]);
 }
 
+// The start of a single evaluation in one launch: FP32 positions (and
+// charges) from FP64 x, padding rows zero, and the fixed-point force and
+// energy sums cleared.
+__global__ void k_eval_begin(const double *x, const float *qs, float4 *pos4, int n, int n_pad,
+                             unsigned long long *fx, int n3, unsigned long long *efx) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) pos4[q] = make_float4((float)x[3 * q], (float)x[3 * q + 1], (float)x[3 * q + 2], qs[q]);
+    else if (q < n_pad) pos4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < n3) fx[q] = 0ull;
+    if (q < E_SLOTS) efx[q] = 0ull;
+}
+
+// Its end in one launch: FP32 forces (f32 may be null), the energy terms as
+// k_energy_out writes them, and the total energy to *energy (may be null).
+__global__ void k_eval_end(const unsigned long long *fx, int n3, float *f32, const unsigned long long *efx,
+                           double *out, double *energy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f32 != nullptr && i < n3) f32[i] = (float)fx_val(fx[i]);
+    if (blockIdx.x == 0) {
+        const int t = threadIdx.x;
+        if (t < 5) out[1 + t] = fx_val(efx[t]);
+        if (t == 0) {
+            const double U = fx_val(efx[E_BOND]) + fx_val(efx[E_ANGLE]) + fx_val(efx[E_LJ]) + fx_val(efx[E_COUL]) +
+                             fx_val(efx[E_LEARN]);
+            out[0] = U;
+            if (energy != nullptr) *energy = U;
+        }
+    }
+}
+
 // An external provider's FP32 forces and FP64 energy into the fixed-point sums.
 __global__ void k_provider_to_fx(const float *forces, const double *energy, int n, unsigned long long *fx,
                                  unsigned long long *efx, uint32_t *status) {
@@ -503,6 +533,19 @@ void launch_fx_to_forces(const unsigned long long *fx, int n, double *f64, float
 
 void launch_energy_out(const unsigned long long *efx, double *out6, cudaStream_t s) {
     k_energy_out<<<1, 32, 0, s>>>(efx, out6);
+}
+
+void launch_eval_begin(const double *x, const float *qs, float4 *pos4, int n, int n_pad, unsigned long long *fx,
+                       int n3, unsigned long long *efx, cudaStream_t s) {
+    int m = n_pad > n3 ? n_pad : n3;
+    if (m < E_SLOTS) m = E_SLOTS;
+    k_eval_begin<<<(m + 255) / 256, 256, 0, s>>>(x, qs, pos4, n, n_pad, fx, n3, efx);
+}
+
+void launch_eval_end(const unsigned long long *fx, int n, float *f32, const unsigned long long *efx, double *out6,
+                     double *energy, cudaStream_t s) {
+    const int m = f32 != nullptr ? 3 * n : 1;
+    k_eval_end<<<(m + 255) / 256, 256, 0, s>>>(fx, 3 * n, f32, efx, out6, energy);
 }
 
 // FP64 integrator kernels use small blocks so that the (slow) FP64 work of a
