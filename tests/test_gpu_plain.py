@@ -116,6 +116,28 @@ def test_compute_device_matches_host():
     np.testing.assert_array_equal(df.cpu().numpy(), f_h.astype(np.float32))
 
 
+def test_compute_device_single_outputs():
+    # one output pointer NULL at a time: the other output is the same as with both (plain and learned mode)
+    import torch
+    from paper_2412_18271_b300 import model
+    s = synth.workload("mol64")
+    for kw in ({}, {"mode": mdpf.MDPF_MODE_LEARNED, "model": model.init_model(7).pack()}):
+        ctx = mdpf.Context(s, **kw)
+        dpos = torch.tensor(s.pos, dtype=torch.float64, device="cuda")
+        st = torch.cuda.current_stream()
+        de = torch.zeros(1, dtype=torch.float64, device="cuda")
+        df = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+        ctx.compute_device(dpos.data_ptr(), de.data_ptr(), df.data_ptr(), st.cuda_stream)
+        de1 = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+        ctx.compute_device(dpos.data_ptr(), de1.data_ptr(), 0, st.cuda_stream)
+        df1 = torch.full((s.n_atoms, 3), 7.0, dtype=torch.float32, device="cuda")
+        ctx.compute_device(dpos.data_ptr(), 0, df1.data_ptr(), st.cuda_stream)
+        st.synchronize()
+        assert de1.item() == de.item()
+        assert torch.equal(df1, df)
+        assert ctx.counters()["status"] == 0
+
+
 def test_compute_is_deterministic_and_stateless():
     s = synth.workload("cluster2048")
     ctx = mdpf.Context(s)
