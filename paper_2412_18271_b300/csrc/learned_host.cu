@@ -353,8 +353,9 @@ int learned_enqueue_forces(mdpf_ctx *c, const float4 *pos4, unsigned long long *
                            uint32_t *status, bool forced_build, bool write_f32, cudaStream_t s) {
     LearnedHost *h = lh(c);
     const LearnedDev &L = h->dev;
-    // the range flag is cleared by the end-of-evaluation kernel; single evaluations clear it first
-    if (forced_build) learned_begin(L, s);
+    // the range flag is cleared by the end-of-evaluation kernel; single evaluations clear it first (a model
+    // without ranges never raises it)
+    if (forced_build && L.lo != nullptr) learned_begin(L, s);
     cudaEvent_t ev = prof_begin(c, s);
     cudaError_t ce = learned_neighbors(L, pos4, forced_build, status, s);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "learned_neighbors");
